@@ -1,0 +1,282 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU (``-m "not gpu"``).  Each one checks the oracle
+against something other than itself: a value the paper prints, a closed form,
+an invariant, an independent solver route, or brute-force statistics.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import oracle as O
+from paper_2507_09730_gb300 import workloads as W
+from conftest import GOLDEN
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10: published known-answer values (Salmon et al., SC'11)
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+def test_philox_counter_sensitivity_and_uniformity():
+    # every output word is a bijective function of the counter; distinct counters
+    # give distinct blocks, and the low bits are uniform (chi-square on 256 bins)
+    outs = np.array([O.philox4x32_10([i, 0, 7, 1], [3, 5]) for i in range(4096)])
+    assert len({tuple(o) for o in outs}) == 4096
+    h = np.bincount((outs.reshape(-1) & 255).astype(np.int64), minlength=256)
+    assert stats.chisquare(h).pvalue > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Jump law (Eq. 6) and its 2^24 quantisation
+def test_alpha_table_closed_forms():
+    eps = np.array([2.5, 3.9, 7.0, 25.0])
+    Wt = O.w_table(eps).astype(np.int64)
+    for a in range(4):
+        assert Wt[a, a] == 2 ** 23                      # eps/(eps+eps) = 1/2
+        assert Wt[a, O.BOUNDARY] == 2 ** 24             # boundary neighbour, alpha = 1
+        for b in range(4):
+            assert abs(Wt[a, b] + Wt[b, a] - 2 ** 24) <= 1  # alpha_ab + alpha_ba = 1
+            assert abs(Wt[a, b] - eps[b] / (eps[a] + eps[b]) * 2 ** 24) <= 0.5
+
+
+# ---------------------------------------------------------------------------
+# Homogeneous cube: Proposition 2's 0.3373 N^2, symmetry, N = 2 by hand
+def test_homogeneous_expected_steps_matches_paper():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "homogeneous_expected_steps.txt"))
+            if l.strip() and not l.startswith("#")]
+    for N, coef, tol in rows:
+        N = int(N)
+        Et = O.expected_steps(N, np.ones((N, N, N)))
+        assert abs(Et / N ** 2 - float(coef)) <= float(tol)
+
+
+def test_two_by_two_cube_by_hand():
+    # N = 2: all 8 nodes are central; each has 3 interior neighbours (alpha 1/2)
+    # and 3 boundary panels (alpha 1): absorption probability 2/3 per step, so
+    # E(tau) = 3/2, and by symmetry every one of the 24 panels gets 1/24.
+    P = O.sgf(2, np.ones((2, 2, 2)))
+    np.testing.assert_allclose(P, 1.0 / 24.0, rtol=0, atol=1e-15)
+    assert abs(O.expected_steps(2, np.ones((2, 2, 2))) - 1.5) < 1e-14
+
+
+@pytest.mark.parametrize("N", [4, 8, 16])
+def test_homogeneous_faces_get_one_sixth(N):
+    P = O.sgf(N, np.full((N, N, N), 3.9))
+    np.testing.assert_allclose(P.sum(axis=(1, 2)), 1.0 / 6.0, atol=1e-13)
+    # mirror symmetry inside a face
+    np.testing.assert_allclose(P[0], P[0][::-1, :], atol=1e-14)
+    np.testing.assert_allclose(P[0], P[0].T, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+def _rand_lattice(rng, N, n_mat=4):
+    return rng.integers(0, n_mat, (N, N, N)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("N,seed", [(4, 0), (6, 1), (6, 2)])
+def test_cg_sgf_equals_chain_solve(N, seed):
+    """Theorem 1's two sides computed by unrelated routes: the symmetric FD system
+    (CG, C) and the absorbing chain of Eq. 9 (sparse LU, scipy)."""
+    rng = np.random.default_rng(seed)
+    eps = np.array([2.5, 3.9, 7.0, 25.0])
+    lat = _rand_lattice(rng, N)
+    P = O.sgf(N, eps[lat])
+    Pc, Et = O.absorption_exact(N, lat, eps, quantised=False)
+    np.testing.assert_allclose(P, Pc, rtol=0, atol=1e-13)
+    assert abs(P.sum() - 1.0) < 1e-13
+    assert abs(O.expected_steps(N, eps[lat]) - Et) < 1e-10 * Et
+
+
+def _series_potential(eps_profile):
+    """Exact 1-D potential with unit flux through layers of unit thickness:
+    f(z) = int_0^z 1/eps.  Returns (f at node centres k+1/2, f(0), f(N))."""
+    inv = 1.0 / np.asarray(eps_profile, np.float64)
+    edges = np.concatenate([[0.0], np.cumsum(inv)])
+    nodes = edges[:-1] + 0.5 * inv
+    return nodes, edges[0], edges[-1]
+
+
+def _boundary_values(N, axis, f_nodes, f_lo, f_hi):
+    """Panel values of a potential depending on the coordinate along `axis` only."""
+    V = np.zeros((6, N, N))
+    for a in range(3):
+        o = [b for b in range(3) if b != a]
+        for side in range(2):
+            f = 2 * a + side
+            if a == axis:
+                V[f] = f_hi if side else f_lo
+            elif o[0] == axis:
+                V[f] = f_nodes[:, None]
+            else:
+                V[f] = f_nodes[None, :]
+    return V
+
+
+@pytest.mark.parametrize("N,axis,seed", [(8, 2, 0), (8, 0, 1), (12, 1, 2)])
+def test_stratified_sgf_reproduces_series_capacitor(N, axis, seed):
+    """For a stratified lattice the FD scheme of Eq. 4-5 (interface coupling
+    eps1/(eps1+eps0)) is exact for the piecewise-linear potential of a layered
+    capacitor (normal D continuous), so the SGF must reproduce it at the centre."""
+    rng = np.random.default_rng(seed)
+    prof = rng.choice([2.5, 3.9, 7.0, 25.0], N)
+    shape = [1, 1, 1]
+    shape[axis] = N
+    e = np.broadcast_to(prof.reshape(shape), (N, N, N)).copy()
+    fn, flo, fhi = _series_potential(prof)
+    P = O.sgf(N, e)
+    V = _boundary_values(N, axis, fn, flo, fhi)
+    centre = 0.5 * (fn[N // 2 - 1] + fn[N // 2])
+    assert abs((P * V).sum() - centre) < 1e-12 * max(1.0, abs(centre))
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_flux_kernel_linear_exactness_homogeneous(N):
+    for n in range(3):
+        F = O.flux(N, np.ones((N, N, N)), n)
+        assert abs(F.sum()) < 1e-13                      # flux of a constant
+        x = np.arange(N) + 0.5
+        V = _boundary_values(N, n, x, 0.0, float(N))     # phi = coordinate along n
+        assert abs((F * V).sum() - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("N,seed", [(8, 0), (10, 3)])
+def test_flux_kernel_layered_exactness(N, seed):
+    """Normal along the layering: the discrete flux of the series potential equals
+    the unit flux D exactly.  Normal across the layering: the flux of phi = x_n is
+    the mean permittivity of the two central layers."""
+    rng = np.random.default_rng(seed)
+    prof = rng.choice([2.5, 3.9, 7.0, 25.0], N)
+    a = 2
+    e = np.broadcast_to(prof.reshape(1, 1, N), (N, N, N)).copy()
+    fn, flo, fhi = _series_potential(prof)
+    F = O.flux(N, e, a)
+    assert abs(F.sum()) < 1e-12
+    assert abs((F * _boundary_values(N, a, fn, flo, fhi)).sum() - 1.0) < 1e-12
+    for n in (0, 1):
+        F = O.flux(N, e, n)
+        x = np.arange(N) + 0.5
+        got = (F * _boundary_values(N, n, x, 0.0, float(N))).sum()
+        assert abs(got - 0.5 * (prof[N // 2 - 1] + prof[N // 2])) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Theorem 1 / Eq. 11 by brute-force statistics of the oracle's MicroWalk
+@pytest.mark.parametrize("seed", [0, 1])
+def test_microwalk_hits_exact_sgf(seed):
+    N = 8
+    cubes = W.random_cubes(4, N=N, seed=seed)
+    for c in range(2):
+        lat = O.lattice_from_ranges(N, cubes.bg[c], cubes.ranges[c, :cubes.nblk[c]],
+                                    cubes.mat[c, :cubes.nblk[c]])
+        Pq, Et = O.absorption_exact(N, lat, cubes.eps, quantised=True)
+        n = 200_000
+        nodes, steps = O.microwalk_many(N, lat, cubes.eps, seed=11, request=c, walk0=0, n=n)
+        hist = np.bincount(O.node_to_panel(N, nodes), minlength=6 * N * N)
+        exp = Pq.reshape(-1) * n
+        big = exp >= 5
+        obs_b = np.concatenate([hist[big], [hist[~big].sum()]])
+        exp_b = np.concatenate([exp[big], [exp[~big].sum()]])
+        keep = exp_b > 0
+        chi = ((obs_b[keep] - exp_b[keep]) ** 2 / exp_b[keep]).sum()
+        p = stats.chi2.sf(chi, keep.sum() - 1)
+        assert p > 1e-3, (c, p)
+        m, se = steps.mean(), steps.std() / np.sqrt(n)
+        assert abs(m - Et) < 4 * se, (m, Et, se)
+
+
+def test_microwalk_start_is_a_central_node_and_exit_on_boundary():
+    N = 8
+    lat = np.zeros((N, N, N), np.uint8)
+    nodes, steps = O.microwalk_many(N, lat, np.array([1.0]), 0, 0, 0, 5000)
+    assert (steps >= 4).all()     # 4 steps at least from a central node of an 8-cube
+    on_b = ((nodes == -1) | (nodes == N)).sum(axis=1)
+    assert (on_b == 1).all()
+
+
+# ---------------------------------------------------------------------------
+# Whole estimator (Algorithm 1)
+def test_uniform_permittivity_scaling_is_exact():
+    s = W.tiny_two_plate()
+    r1 = O.frw_run(s, 0, 3000, N=8, seed=5)
+    r2 = O.frw_run(s.scaled_eps(2.0), 0, 3000, N=8, seed=5)
+    np.testing.assert_array_equal(r2.S1, 2.0 * r1.S1)
+    r3 = O.frw_run(s.scaled_eps(3.7), 0, 3000, N=8, seed=5)
+    np.testing.assert_allclose(r3.S1, 3.7 * r1.S1, rtol=1e-9)
+
+
+def test_mirror_symmetry_and_reciprocity():
+    s = W.tiny_two_plate()
+    n = 40_000
+    r0 = O.frw_run(s, 0, n, N=8, seed=1)
+    r1 = O.frw_run(s, 1, n, N=8, seed=2)
+    # C11 = C22 (mirror about y = 2), C12 = C21 (reciprocity)
+    s11 = np.hypot(r0.stderr[0], r1.stderr[1])
+    s12 = np.hypot(r0.stderr[1], r1.stderr[0])
+    assert abs(r0.C[0] - r1.C[1]) < 3.5 * s11
+    assert abs(r0.C[1] - r1.C[0]) < 3.5 * s12
+    assert r0.C[0] > 0 and r0.C[1] < 0 and r0.C[2] < 0
+
+
+def test_row_sum_is_zero():
+    """Gauss: with every electrode at 1 V there is no charge, so sum_k C_ik = 0."""
+    s = W.tiny_two_plate()
+    r = O.frw_run(s, 0, 30_000, N=8, seed=3)
+    om = r.omega[r.k >= 0]
+    assert abs(om.mean()) < 4 * om.std() / np.sqrt(len(om))
+    assert abs(r.S1.sum() - om.sum()) < 1e-9 * np.abs(om).sum()
+
+
+def test_gaussian_offset_independence():
+    s = W.tiny_two_plate()
+    a = O.frw_run(s, 0, 30_000, N=8, seed=4, gauss_frac=0.5)
+    b = O.frw_run(s, 0, 30_000, N=8, seed=9, gauss_frac=0.3)
+    sig = np.hypot(a.stderr, b.stderr)
+    assert (np.abs(a.C - b.C) < 3.5 * sig).all()
+
+
+def test_hybrid_dispatch_does_not_change_the_estimate():
+    """Theorem 1 at the estimator level: stratified cubes via the analytical SGF or
+    via MicroWalk give the same capacitances within statistical error."""
+    s = W.tiny_two_plate()
+    a = O.frw_run(s, 0, 30_000, N=8, seed=6, hybrid=1)
+    b = O.frw_run(s, 0, 30_000, N=8, seed=7, hybrid=0)
+    sig = np.hypot(a.stderr, b.stderr)
+    assert (np.abs(a.C - b.C) < 3.5 * sig).all()
+    assert b.stats[2] == 0 and b.stats[3] == 0    # no analytical hops when hybrid is off
+
+
+def test_stop_rule_stops_on_batch_boundary():
+    s = W.tiny_two_plate()
+    r = O.frw_run(s, 0, 200_000, N=8, seed=0, sigma_target=0.05, batch=1000)
+    assert r.n % 1000 == 0 and r.n < 200_000
+    assert r.stderr[0] <= 0.05 * abs(r.C[0])
+    # one batch earlier the rule did not hold
+    q = O.frw_run(s, 0, r.n - 1000, N=8, seed=0)
+    big = max((j for j in range(2) if j != 0), key=lambda j: abs(q.C[j]))
+    assert (q.stderr[0] > 0.05 * abs(q.C[0])) or (q.stderr[big] > 0.05 * abs(q.C[big]))
+    # and the estimate equals the plain run over the same prefix
+    p = O.frw_run(s, 0, r.n, N=8, seed=0)
+    np.testing.assert_array_equal(p.S1, r.S1)
+
+
+def test_tables_are_valid_cdfs():
+    N = 8
+    eps = np.array([2.5, 3.9, 7.0, 25.0])
+    prof = np.array([0, 0, 1, 3, 3, 2, 1, 1], np.uint8)
+    for kind, ax, nax in ((O.KIND_SGF, 2, 0), (O.KIND_SGF, 0, 0), (O.KIND_FLUX_PAR, 1, 1),
+                          (O.KIND_FLUX_PERP, 2, 0), (O.KIND_SGF_HOM, 2, 0), (O.KIND_FLUX_HOM, 0, 2)):
+        thr, neg, tot = O.table(N, kind, ax, nax, prof, eps)
+        assert (np.diff(thr.astype(np.int64)) >= 0).all()
+        assert tot > 0
+        nodes = np.array([O.panel_node(N, kind, ax, nax, n) for n in range(6 * N * N)])
+        assert len(set(map(tuple, nodes))) == 6 * N * N   # canonical order is a bijection
