@@ -1,0 +1,203 @@
+/*
+ * frw.h -- C ABI of the GB300 floating-random-walk (FRW) capacitance engine with
+ * MicroWalk transitions (Huang & Yu, "Efficient FRW Transitions via Stochastic
+ * Finite Differences for Handling Non-Stratified Dielectrics").
+ *
+ * Plain C types only.  Pointers marked "host" point to host memory, "device" to
+ * memory of the context's CUDA device.  Every entry point returns an int status
+ * (FRW_OK = 0, else one of the FRW_E* codes; frw_strerror gives a message) and
+ * never throws.  A context is used by one host thread at a time.
+ *
+ * Units: lengths in micrometres, permittivities relative, capacitances in fF
+ * (the vacuum permittivity 8.8541878128e-3 fF/um is applied inside).
+ *
+ * Method summary (paper sections):
+ *   - Algorithm 1 (FRW): a walk starts on the master's Gaussian surface, makes a
+ *     first transition that carries the weight omega, then hops from cube centre
+ *     to cube surface until it reaches an electrode k; C_ik accumulates omega.
+ *   - Transition cube (Sec. II-A): the largest conductor-free cube centred at the
+ *     walk's point, voxelised into an N x N x N lattice with one permittivity per
+ *     voxel (Sec. III-A).
+ *   - Algorithm 3 (MicroWalk): for a non-stratified cube, a random walk on the
+ *     lattice with the jump law of Eq. 6, exact by Theorem 1.
+ *   - Sec. III-C (hybrid): stratified cubes take the analytical route (the exact
+ *     FD surface Green's function of the layered lattice, Eq. 8, cached by
+ *     profile); the first cube uses the special treatment (stratified /
+ *     shrink-to-stratified / homogenise).
+ */
+#ifndef FRW_H
+#define FRW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FRW_OK 0
+#define FRW_EINVAL 1      /* bad argument or structure (message via frw_last_error) */
+#define FRW_ENOMEM 2      /* device allocation failed / admission refused */
+#define FRW_ETIMEOUT 3    /* a bounded wait gave up */
+#define FRW_EDEVICE 4     /* CUDA error, or a device-side check failed */
+#define FRW_ENOTCONV 5    /* walk budget exhausted before the sigma target (results valid) */
+#define FRW_ECAPACITY 6   /* a fixed-size table (materials, cache, jobs) is full */
+#define FRW_ENOTFOUND 7   /* unknown structure id / ticket */
+
+/* ---- option values ---- */
+#define FRW_FP64_GEOM 0   /* cube sizing, voxel ranges and points in FP64 */
+#define FRW_FP32_GEOM 1   /* the same in FP32 with a conservative margin on the cube size */
+#define FRW_FIRST_HYBRID 0
+
+/* ---- table kinds of the analytical route (frw_table) ---- */
+#define FRW_TAB_SGF 0        /* surface Green's function, layered along table axis t2 */
+#define FRW_TAB_FLUX_PAR 1   /* first-cube flux kernel, normal = t2 = layering axis */
+#define FRW_TAB_FLUX_PERP 2  /* first-cube flux kernel, normal = t0, layering axis t2 */
+#define FRW_TAB_SGF_HOM 3    /* surface Green's function of a homogeneous cube */
+#define FRW_TAB_FLUX_HOM 4   /* flux kernel of a homogeneous cube with eps = 1 */
+
+#define FRW_MAX_N 32         /* lattice edge N: even, 2 <= N <= 32 */
+#define FRW_MAX_MATERIALS 15 /* distinct permittivities per context */
+#define FRW_MAX_CUBE_BLOCKS 14
+
+typedef struct frw_ctx frw_ctx;
+
+/* Axis-aligned box [lo, hi] (um), lo < hi on every axis. */
+typedef struct {
+    double lo[3], hi[3];
+} frw_box;
+
+/* Dielectric block: box + material index into the structure's eps_r table.
+ * Where blocks overlap, the later block in the array wins (the background is
+ * below every block); a block is sampled at voxel centres with lo <= x < hi. */
+typedef struct {
+    double lo[3], hi[3];
+    int32_t mat;
+    int32_t reserved;
+} frw_block;
+
+typedef struct {
+    int32_t N;                 /* lattice edge per transition cube (paper: 24) */
+    int32_t precision;         /* FRW_FP64_GEOM or FRW_FP32_GEOM */
+    uint64_t seed;             /* Philox key material */
+    int32_t first_cube_mode;   /* FRW_FIRST_HYBRID */
+    int32_t hybrid;            /* 1: stratified cubes take the analytical route; 0: MicroWalk */
+    double gauss_offset_frac;  /* Gaussian surface offset = frac * smallest gap (0 < frac < 1) */
+    int32_t max_hops;          /* hop cap; a capped walk counts with zero contribution */
+    int32_t slots;             /* walks in flight on the device (0: default) */
+    int32_t table_capacity;    /* analytical-table cache entries (0: default) */
+    int32_t mw_warps_per_cta;  /* MicroWalk kernel launch shape (0: default) */
+    int32_t mw_ctas_per_sm;    /* (0: default) */
+    int32_t geom_threads;      /* geometry kernel block size (0: default) */
+    int32_t reserved[6];
+} frw_options;
+
+/* One extraction: a row of the capacitance matrix for one master conductor. */
+typedef struct {
+    uint64_t walk_budget;      /* maximum number of walks */
+    double sigma_target;       /* stop when stderr/|C| <= target on C_ii and on the
+                                  largest |C_ij| (j != i, ground excluded); 0 = budget only */
+    uint64_t request_id;       /* RNG stream of this request (with the context seed) */
+    uint64_t batch;            /* walks per convergence check (0: 16384) */
+    uint64_t walk_begin;       /* first walk id (0 normally; resume / sharding offset) */
+} frw_extract_params;
+
+typedef struct {
+    uint64_t walks;            /* walks counted in the estimate */
+    uint64_t hops;             /* transitions, first one included */
+    uint64_t micro_steps;      /* MicroWalk lattice steps */
+    uint64_t truncated;        /* walks that hit max_hops */
+    uint64_t branch[3];        /* first cube: stratified / shrunk to stratified / homogenised */
+    uint64_t strat_hops;       /* later hops through the analytical route, layered cube */
+    uint64_t hom_hops;         /* ... homogeneous cube */
+    uint64_t mw_hops;          /* later hops through MicroWalk */
+    uint64_t tables_built;     /* analytical tables filled on the device during the call */
+    uint64_t rounds;           /* engine rounds (geometry + fill + MicroWalk launches) */
+    double seconds;            /* wall time of the call */
+} frw_stats;
+
+/* Fill *opt with defaults (N = 24, FP64 geometry, hybrid on, offset 0.5,
+ * max_hops = 100000, seed 0). */
+void frw_default_options(frw_options *opt);
+
+/* Create a context on CUDA device `device`.  Allocates the device working set
+ * (walk slots, queues, table cache) and computes the homogeneous tables on the
+ * device.  *out owns all device memory until frw_destroy. */
+int frw_create(frw_ctx **out, int device, const frw_options *opt);
+void frw_destroy(frw_ctx *ctx);
+
+/* Launch subsequent work on this CUDA stream (cudaStream_t as void*; NULL =
+ * the context's own stream). */
+int frw_set_stream(frw_ctx *ctx, void *cuda_stream);
+
+/* Load a structure (Algorithm 1 input): grounded domain box, n_cond disjoint
+ * conductor boxes inside it, permittivity table eps_r[n_mat] (> 0), background
+ * material, dielectric blocks.  All inputs are host pointers, copied; the caller
+ * keeps ownership.  Returns FRW_EINVAL for overlapping/outside conductors, bad
+ * material ids or non-positive permittivities, FRW_ECAPACITY if the context would
+ * exceed FRW_MAX_MATERIALS distinct permittivities. */
+int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *conductors,
+                       int32_t n_cond, const double *eps_r, int32_t n_mat, int32_t background_mat,
+                       const frw_block *blocks, int32_t n_blocks, int32_t *structure_id);
+int frw_unload_structure(frw_ctx *ctx, int32_t structure_id);
+
+/* Capacitance row of `master` (Algorithm 1 output).  C_row and stderr_row are host
+ * arrays of n_cond + 1 doubles (last entry = grounded walls).  stats may be NULL.
+ * Returns FRW_ENOTCONV (results still filled) when the budget ran out before the
+ * sigma target.  Results are bit-reproducible for a given (seed, request_id). */
+int frw_extract(frw_ctx *ctx, int32_t structure_id, int32_t master,
+                const frw_extract_params *params, double *C_row, double *stderr_row,
+                frw_stats *stats);
+
+/* Several extractions (possibly different structures, masters, budgets and
+ * targets) interleaved in one engine run.  C_rows / stderr_rows are host arrays
+ * holding each job's n_cond + 1 entries back to back in job order; stats (may be
+ * NULL) has n_jobs entries. */
+typedef struct {
+    int32_t structure_id;
+    int32_t master;
+    uint64_t walk_budget;
+    double sigma_target;
+    uint64_t request_id;
+    uint64_t batch;
+} frw_job;
+
+int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs, double *C_rows,
+                      double *stderr_rows, frw_stats *stats);
+
+/* Per-walk records of walks walk_begin .. walk_begin + n_walks - 1 (host arrays of
+ * n_walks entries each; any may be NULL): weight omega, electrode reached
+ * (n_cond = ground, -1 = capped), hop count, MicroWalk steps, first-cube branch. */
+int frw_walk_records(frw_ctx *ctx, int32_t structure_id, int32_t master, uint64_t request_id,
+                     uint64_t walk_begin, uint64_t n_walks, double *omega, int32_t *electrode,
+                     uint32_t *hops, uint64_t *micro_steps, int32_t *branch);
+
+/* MicroWalk alone (Algorithm 3) on n_cubes lattice cubes of edge N given as
+ * integer voxel ranges; samples_per_cube walks from the centre of each.
+ * d_cubes (device): n_cubes records of 64 int32: [0] background material,
+ * [1] block count K <= 6, [2 + 7b .. 8 + 7b] block b = (i0, i1, j0, j1, k0, k1, mat)
+ * with 0 <= lo < hi <= N; later blocks win.  Material ids index eps_r (host).
+ * Sample s of cube c is walk id c * samples_per_cube + s.  Outputs (device):
+ * d_exit[walk] = (x+1) | (y+1) << 8 | (z+1) << 16 of the exit node (one coordinate
+ * is -1 or N), d_steps[walk] = number of steps.  Either output may be NULL. */
+int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t *d_cubes,
+                        const double *eps_r, int32_t n_mat, uint64_t samples_per_cube,
+                        uint64_t request_id, uint32_t *d_exit, uint32_t *d_steps);
+
+/* One analytical table computed on the device (Eq. 8 for SGF kinds; the
+ * first-cube flux kernel for FLUX kinds) for the context's N: profile[N] = material
+ * ids (into eps_r) of the layers along table axis t2 (ignored for HOM kinds).
+ * Host outputs: thr[6N^2] sampling thresholds in canonical panel order,
+ * neg[6N^2] sign flags (flux kinds), *total = sum of |values| (flux) or of P (SGF),
+ * values[6N^2] (may be NULL) the raw panel values. */
+int frw_table(frw_ctx *ctx, int32_t kind, const int32_t *profile, const double *eps_r,
+              int32_t n_mat, uint32_t *thr, uint8_t *neg, double *total, double *values);
+
+/* Message for a status code, and the detail of the context's last error. */
+const char *frw_strerror(int code);
+const char *frw_last_error(frw_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRW_H */

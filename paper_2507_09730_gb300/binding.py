@@ -1,0 +1,310 @@
+"""Thin ctypes binding of the C ABI in ``include/frw.h``.
+
+Functions carry the C names and only marshal arguments; every step of the walk
+runs in ``libfrw.so`` (CUDA kernels for sm_103a).  There is no CPU path: if the
+library cannot be built or loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_uint8, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+FRW_OK, FRW_EINVAL, FRW_ENOMEM, FRW_ETIMEOUT, FRW_EDEVICE, FRW_ENOTCONV, FRW_ECAPACITY, FRW_ENOTFOUND = range(8)
+FRW_FP64_GEOM, FRW_FP32_GEOM = 0, 1
+FRW_TAB_SGF, FRW_TAB_FLUX_PAR, FRW_TAB_FLUX_PERP, FRW_TAB_SGF_HOM, FRW_TAB_FLUX_HOM = range(5)
+
+EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream", "frw_load_structure",
+           "frw_unload_structure", "frw_extract", "frw_extract_batch", "frw_walk_records",
+           "frw_microwalk_cubes", "frw_table", "frw_strerror", "frw_last_error")
+
+
+class frw_box(ctypes.Structure):
+    _fields_ = [("lo", c_double * 3), ("hi", c_double * 3)]
+
+
+class frw_block(ctypes.Structure):
+    _fields_ = [("lo", c_double * 3), ("hi", c_double * 3), ("mat", c_int32), ("reserved", c_int32)]
+
+
+class frw_options(ctypes.Structure):
+    _fields_ = [("N", c_int32), ("precision", c_int32), ("seed", c_uint64), ("first_cube_mode", c_int32),
+                ("hybrid", c_int32), ("gauss_offset_frac", c_double), ("max_hops", c_int32),
+                ("slots", c_int32), ("table_capacity", c_int32), ("mw_warps_per_cta", c_int32),
+                ("mw_ctas_per_sm", c_int32), ("geom_threads", c_int32), ("reserved", c_int32 * 6)]
+
+
+class frw_extract_params(ctypes.Structure):
+    _fields_ = [("walk_budget", c_uint64), ("sigma_target", c_double), ("request_id", c_uint64),
+                ("batch", c_uint64), ("walk_begin", c_uint64)]
+
+
+class frw_job(ctypes.Structure):
+    _fields_ = [("structure_id", c_int32), ("master", c_int32), ("walk_budget", c_uint64),
+                ("sigma_target", c_double), ("request_id", c_uint64), ("batch", c_uint64)]
+
+
+class frw_stats(ctypes.Structure):
+    _fields_ = [("walks", c_uint64), ("hops", c_uint64), ("micro_steps", c_uint64), ("truncated", c_uint64),
+                ("branch", c_uint64 * 3), ("strat_hops", c_uint64), ("hom_hops", c_uint64),
+                ("mw_hops", c_uint64), ("tables_built", c_uint64), ("rounds", c_uint64), ("seconds", c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "branch"}
+        d["branch"] = list(self.branch)
+        return d
+
+
+class FRWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"frw error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load (building in-tree if needed) libfrw.so and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    P = POINTER
+    L.frw_default_options.argtypes = [P(frw_options)]
+    L.frw_default_options.restype = None
+    L.frw_create.argtypes = [P(c_void_p), c_int, P(frw_options)]
+    L.frw_destroy.argtypes = [c_void_p]
+    L.frw_destroy.restype = None
+    L.frw_set_stream.argtypes = [c_void_p, c_void_p]
+    L.frw_load_structure.argtypes = [c_void_p, P(frw_box), P(frw_box), c_int32, P(c_double), c_int32, c_int32,
+                                     P(frw_block), c_int32, P(c_int32)]
+    L.frw_unload_structure.argtypes = [c_void_p, c_int32]
+    L.frw_extract.argtypes = [c_void_p, c_int32, c_int32, P(frw_extract_params), P(c_double), P(c_double),
+                              P(frw_stats)]
+    L.frw_extract_batch.argtypes = [c_void_p, P(frw_job), c_int32, P(c_double), P(c_double), P(frw_stats)]
+    L.frw_walk_records.argtypes = [c_void_p, c_int32, c_int32, c_uint64, c_uint64, c_uint64, P(c_double),
+                                   P(c_int32), P(c_uint32), P(c_uint64), P(c_int32)]
+    L.frw_microwalk_cubes.argtypes = [c_void_p, c_int32, c_int32, c_void_p, P(c_double), c_int32, c_uint64,
+                                      c_uint64, c_void_p, c_void_p]
+    L.frw_table.argtypes = [c_void_p, c_int32, P(c_int32), P(c_double), c_int32, P(c_uint32), P(c_uint8),
+                            P(c_double), P(c_double)]
+    L.frw_strerror.argtypes = [c_int]
+    L.frw_strerror.restype = ctypes.c_char_p
+    L.frw_last_error.argtypes = [c_void_p]
+    L.frw_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("frw_default_options", "frw_destroy", "frw_strerror", "frw_last_error"):
+            getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(POINTER(ct)) if a is not None else None
+
+
+def _check(ctx, rc, allow=(FRW_OK,)):
+    if rc not in allow:
+        msg = lib().frw_last_error(ctx).decode() if ctx else ""
+        raise FRWError(rc, (lib().frw_strerror(rc).decode() + (": " + msg if msg else "")))
+    return rc
+
+
+# ---------------------------------------------------------------------------
+def frw_strerror(code: int) -> str:
+    return lib().frw_strerror(code).decode()
+
+
+def frw_last_error(ctx) -> str:
+    return lib().frw_last_error(ctx).decode()
+
+
+def frw_default_options(**kw) -> frw_options:
+    o = frw_options()
+    lib().frw_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def frw_create(device: int = 0, options: frw_options | None = None):
+    ctx = c_void_p()
+    rc = lib().frw_create(ctypes.byref(ctx), int(device), ctypes.byref(options) if options is not None else None)
+    _check(None, rc)
+    return ctx
+
+
+def frw_destroy(ctx) -> None:
+    lib().frw_destroy(ctx)
+
+
+def frw_set_stream(ctx, stream_handle: int | None) -> None:
+    _check(ctx, lib().frw_set_stream(ctx, c_void_p(stream_handle or 0)))
+
+
+def frw_load_structure(ctx, s) -> int:
+    """Load a :class:`workloads.Structure` (host arrays are copied)."""
+    dom = frw_box((c_double * 3)(*s.domain_lo), (c_double * 3)(*s.domain_hi))
+    cond = (frw_box * s.n_cond)()
+    for k in range(s.n_cond):
+        cond[k].lo = (c_double * 3)(*s.cond_lo[k])
+        cond[k].hi = (c_double * 3)(*s.cond_hi[k])
+    blk = (frw_block * max(1, s.n_blocks))()
+    for b in range(s.n_blocks):
+        blk[b].lo = (c_double * 3)(*s.block_lo[b])
+        blk[b].hi = (c_double * 3)(*s.block_hi[b])
+        blk[b].mat = int(s.block_mat[b])
+    eps = np.ascontiguousarray(s.eps, np.float64)
+    sid = c_int32(-1)
+    rc = lib().frw_load_structure(ctx, ctypes.byref(dom), cond, s.n_cond, _ptr(eps, c_double), len(eps),
+                                  int(s.background), blk, s.n_blocks, ctypes.byref(sid))
+    _check(ctx, rc)
+    return sid.value
+
+
+def frw_unload_structure(ctx, sid: int) -> None:
+    _check(ctx, lib().frw_unload_structure(ctx, int(sid)))
+
+
+def frw_extract(ctx, sid: int, master: int, n_cond: int, walk_budget: int, sigma_target: float = 0.0,
+                request_id: int = 0, batch: int = 0, walk_begin: int = 0):
+    """-> (C row [n_cond+1], stderr row, stats dict, converged flag)."""
+    p = frw_extract_params(int(walk_budget), float(sigma_target), int(request_id), int(batch), int(walk_begin))
+    C = np.zeros(n_cond + 1)
+    se = np.zeros(n_cond + 1)
+    st = frw_stats()
+    rc = lib().frw_extract(ctx, int(sid), int(master), ctypes.byref(p), _ptr(C, c_double), _ptr(se, c_double),
+                           ctypes.byref(st))
+    _check(ctx, rc, (FRW_OK, FRW_ENOTCONV))
+    return C, se, st.as_dict(), rc == FRW_OK
+
+
+def frw_extract_batch(ctx, jobs, n_conds):
+    """jobs: list of dicts (structure_id, master, walk_budget, sigma_target, request_id, batch);
+    n_conds: conductor count of each job's structure.  -> list of (C, stderr, stats) and converged flag."""
+    n = len(jobs)
+    arr = (frw_job * max(1, n))()
+    for i, j in enumerate(jobs):
+        arr[i] = frw_job(int(j["structure_id"]), int(j["master"]), int(j["walk_budget"]),
+                         float(j.get("sigma_target", 0.0)), int(j.get("request_id", 0)), int(j.get("batch", 0)))
+    tot = sum(nc + 1 for nc in n_conds)
+    C = np.zeros(max(1, tot))
+    se = np.zeros(max(1, tot))
+    st = (frw_stats * max(1, n))()
+    rc = lib().frw_extract_batch(ctx, arr, n, _ptr(C, c_double), _ptr(se, c_double), st)
+    _check(ctx, rc, (FRW_OK, FRW_ENOTCONV))
+    out, off = [], 0
+    for i, nc in enumerate(n_conds):
+        out.append((C[off:off + nc + 1].copy(), se[off:off + nc + 1].copy(), st[i].as_dict()))
+        off += nc + 1
+    return out, rc == FRW_OK
+
+
+def frw_walk_records(ctx, sid: int, master: int, request_id: int, walk_begin: int, n_walks: int):
+    n = int(n_walks)
+    om = np.zeros(n)
+    k = np.zeros(n, np.int32)
+    hops = np.zeros(n, np.uint32)
+    steps = np.zeros(n, np.uint64)
+    br = np.zeros(n, np.int32)
+    rc = lib().frw_walk_records(ctx, int(sid), int(master), int(request_id), int(walk_begin), n,
+                                _ptr(om, c_double), _ptr(k, c_int32), _ptr(hops, c_uint32),
+                                _ptr(steps, c_uint64), _ptr(br, c_int32))
+    _check(ctx, rc)
+    return {"omega": om, "k": k, "hops": hops, "steps": steps, "branch": br}
+
+
+def pack_cubes(cubes) -> np.ndarray:
+    """:class:`workloads.CubeSet` -> int32 records of 64 words (see frw_microwalk_cubes)."""
+    rec = np.zeros((cubes.n, 64), np.int32)
+    rec[:, 0] = cubes.bg
+    rec[:, 1] = cubes.nblk
+    for b in range(cubes.ranges.shape[1]):
+        rec[:, 2 + 7 * b:8 + 7 * b] = cubes.ranges[:, b, :]
+        rec[:, 8 + 7 * b] = cubes.mat[:, b]
+    return rec
+
+
+def frw_microwalk_cubes(ctx, N: int, n_cubes: int, d_cubes_ptr: int, eps, samples_per_cube: int,
+                        request_id: int, d_exit_ptr: int, d_steps_ptr: int) -> None:
+    e = np.ascontiguousarray(eps, np.float64)
+    rc = lib().frw_microwalk_cubes(ctx, int(N), int(n_cubes), c_void_p(d_cubes_ptr), _ptr(e, c_double), len(e),
+                                   int(samples_per_cube), int(request_id), c_void_p(d_exit_ptr or 0),
+                                   c_void_p(d_steps_ptr or 0))
+    _check(ctx, rc)
+
+
+def frw_table(ctx, N: int, kind: int, profile=None, eps=None):
+    """-> (thresholds u32[6N^2], negative flags u8[6N^2], total, values f64[6N^2])."""
+    P = 6 * N * N
+    thr = np.zeros(P, np.uint32)
+    neg = np.zeros(P, np.uint8)
+    tot = np.zeros(1)
+    vals = np.zeros(P)
+    prof = np.ascontiguousarray(profile, np.int32) if profile is not None else None
+    e = np.ascontiguousarray(eps, np.float64) if eps is not None else None
+    rc = lib().frw_table(ctx, int(kind), _ptr(prof, c_int32), _ptr(e, c_double), 0 if e is None else len(e),
+                         _ptr(thr, c_uint32), _ptr(neg, c_uint8), _ptr(tot, c_double), _ptr(vals, c_double))
+    _check(ctx, rc)
+    return thr, neg, float(tot[0]), vals
+
+
+def decode_exit(packed: np.ndarray) -> np.ndarray:
+    """Packed exit nodes -> (n, 3) int coordinates (one of them -1 or N)."""
+    p = np.asarray(packed, np.int64)
+    return np.stack([(p & 255) - 1, ((p >> 8) & 255) - 1, ((p >> 16) & 255) - 1], axis=1)
+
+
+class Context:
+    """Convenience owner of a context (destroyed on close / garbage collection)."""
+
+    def __init__(self, device: int = 0, **opts):
+        self.options = frw_default_options(**opts)
+        self.N = self.options.N
+        self.ctx = frw_create(device, self.options)
+        self._n_cond = {}
+
+    def close(self):
+        if self.ctx:
+            frw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load(self, s) -> int:
+        sid = frw_load_structure(self.ctx, s)
+        self._n_cond[sid] = s.n_cond
+        return sid
+
+    def unload(self, sid):
+        frw_unload_structure(self.ctx, sid)
+        self._n_cond.pop(sid, None)
+
+    def extract(self, sid, master, walk_budget, sigma_target=0.0, request_id=0, batch=0, walk_begin=0):
+        return frw_extract(self.ctx, sid, master, self._n_cond.get(sid, 0), walk_budget, sigma_target,
+                           request_id, batch, walk_begin)
+
+    def extract_batch(self, jobs):
+        return frw_extract_batch(self.ctx, jobs, [self._n_cond.get(j["structure_id"], 0) for j in jobs])
+
+    def walk_records(self, sid, master, n_walks, request_id=0, walk_begin=0):
+        return frw_walk_records(self.ctx, sid, master, request_id, walk_begin, n_walks)
+
+    def table(self, kind, profile=None, eps=None):
+        return frw_table(self.ctx, self.N, kind, profile, eps)

@@ -1,0 +1,179 @@
+// frw_internal.h -- device data layout shared by the kernels (frw_kernels.cu) and
+// the host runtime (frw_runtime.cu).  Not part of the public ABI (include/frw.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace frw {
+
+constexpr int MAXN = 32;                 // lattice edge limit (mask rows, byte coords)
+constexpr int KMAX = 14;                 // blocks per transition cube (mask bits 1..14)
+constexpr int BOUNDARY = 15;             // material id of absorbing boundary nodes
+constexpr int NMAT = 16;                 // material slots (15 real + boundary)
+constexpr double EPS0 = 8.8541878128e-3; // fF / um
+
+// analytical table kinds (same numbering as the ABI's FRW_TAB_*)
+enum : uint32_t { TAB_SGF = 0, TAB_FLUX_PAR = 1, TAB_FLUX_PERP = 2, TAB_SGF_HOM = 3, TAB_FLUX_HOM = 4 };
+// table cache entry states
+enum : uint32_t { TE_EMPTY = 0, TE_CLAIMED = 1, TE_REQUESTED = 2, TE_READY = 3 };
+// walk slot states
+enum : uint32_t { ST_IDLE = 0, ST_FRESH = 1, ST_FIRST = 2, ST_HOP = 3, ST_MW = 4, ST_MWDONE = 5 };
+// device error flags (status word 1)
+enum : uint32_t {
+    ERR_MWQ_OVERFLOW = 1u, ERR_CACHE_FULL = 2u, ERR_FILL = 4u, ERR_SHRINK = 8u, ERR_ACC_RANGE = 16u,
+    ERR_MW_STEPS = 32u
+};
+// status words
+enum { STAT_ACTIVE = 0, STAT_ERR = 1, STAT_BUILT = 2, STAT_MWJOBS = 3, STAT_ACTIVE_CTR = 4,
+       STAT_WORDS = 8 };
+
+// cube classes
+enum : int { CUBE_HOM = 0, CUBE_STRAT = 1, CUBE_NONSTRAT = 2, CUBE_OVERFLOW = 3 };
+
+// fixed-point scales of the exact 128-bit accumulators
+constexpr double ACC_S1_SCALE = 18446744073709551616.0;   // 2^64
+constexpr double ACC_S2_SCALE = 1099511627776.0;          // 2^40
+
+// One loaded structure.  Coordinates SoA: x[a * n + i].  Material ids are the
+// context's global ids.
+struct DevStructure {
+    int n_c, n_b, bg;
+    int pad;
+    double dom_lo[3], dom_hi[3];
+    float dom_lo_f[3], dom_hi_f[3];
+    double tau;            // absorption distance, FP64 mode
+    float tau_f;           // absorption distance, FP32 mode
+    float margin_f;        // FP32 cube-size safety margin
+    const double *c_lo, *c_hi;
+    const float *c_lo_f, *c_hi_f;
+    const double *b_lo, *b_hi;
+    const float *b_lo_f, *b_hi_f;
+    const uint8_t *b_mat;
+};
+
+// One extraction job (request x master).
+struct DevJob {
+    int sid;               // index into the structure table
+    int master;
+    int n_c;
+    int record;            // write per-walk records
+    uint32_t key0, key1;   // Philox key
+    double g_lo[3], g_hi[3];
+    double cum[6];         // cumulative face areas of the Gaussian surface
+    double area;
+    uint64_t walk_begin;   // walk ids walk_begin .. walk_begin + walk_count - 1
+    uint64_t walk_count;
+    uint64_t batch;        // walks per accumulator batch
+    uint64_t acc_base;     // u64 offset of batch 0 in the accumulator pool
+    uint32_t acc_stride;   // u64 words per batch
+    uint32_t pad;
+    uint64_t rec_base;     // offset of walk 0 in the record arrays
+};
+
+// per-batch accumulator block (u64 words):
+//   [0, 2(nc+1))            S1 as (lo, hi) int128 pairs, fixed point 2^-64
+//   [2(nc+1), 4(nc+1))      S2 as (lo, hi) pairs, fixed point 2^-40
+//   +0 done, +1 hops, +2 steps, +3 strat, +4 hom, +5 mw, +6..8 branches, +9 truncated
+constexpr int ACC_EXTRA = 10;
+__host__ __device__ inline uint32_t acc_stride_for(int nc) { return 4u * (uint32_t)(nc + 1) + ACC_EXTRA; }
+
+// MicroWalk job: one non-stratified transition cube handed from the geometry
+// kernel to the MicroWalk kernel.  rng[b] = (i0 | i1<<8 | j0<<16 | j1<<24,
+// k0 | k1<<8 | mat<<16) for the cube's blocks in priority order.
+struct alignas(16) MWJob {
+    uint32_t slot, hop, walk_lo, walk_hi;
+    uint32_t start, K, mm_lo, mm_hi;   // start node packed x|y<<8|z<<16; material nibble map
+    uint32_t key0, key1, pad0, pad1;
+    uint2 rng[KMAX];
+};
+
+struct SlotArrays {
+    uint32_t *state, *job, *hop, *exitnode, *cnt_sh, *cnt_mw;
+    int32_t *branch;
+    uint64_t *walk, *steps;
+    double *pos;      // [3][NS]
+    double *cube;     // [4][NS]  c0, c1, c2, R of the cube handed to MicroWalk
+    double *omega;
+};
+
+struct RecArrays {
+    double *omega;
+    int32_t *k;
+    uint32_t *hops;
+    uint64_t *steps;
+    int32_t *branch;
+};
+
+struct TableCache {
+    uint32_t cap;          // power of two
+    uint32_t P;            // panels per table = 6 N^2
+    uint32_t P32;          // sign words per table
+    uint32_t *keys;        // [cap][5]
+    uint32_t *state;       // [cap]
+    uint32_t *thr;         // [cap + 2][P]; entries cap, cap+1 = homogeneous SGF / flux
+    uint32_t *sgn;         // [cap + 2][P32]
+    double *ktot;          // [cap + 2]
+    uint32_t *fillq;       // [cap]
+    uint32_t *fillq_count, *fillq_head;
+};
+
+// Constants of the separable solve (host-computed, see fill kernel):
+// u[(p-1)*N + i] = DST-II basis, lam[p-1], a[p-1], d[p-1].
+struct FillConsts {
+    const double *u, *lam, *a, *d;
+};
+
+struct EngineView {
+    int N;
+    int hybrid;
+    int max_hops;
+    int fp32;
+    uint32_t NS;           // slots
+    int n_jobs;
+    SlotArrays s;
+    const DevStructure *structs;
+    const DevJob *jobs;
+    unsigned long long *job_next;
+    int *job_cancel;
+    unsigned long long *acc;
+    RecArrays rec;
+    MWJob *mwq;
+    uint32_t *mwq_count, *mwq_head;
+    uint32_t mwq_cap;
+    TableCache tc;
+    const uint32_t *W;     // [16][16]
+    const double *eps;     // [16]
+    FillConsts fc;
+    uint32_t *status;      // STAT_WORDS
+    int hop_budget;        // analytical hops per slot per round
+    int walk_budget;       // walks started per slot per round
+};
+
+// ---- launchers (frw_kernels.cu) ----
+struct LaunchShape {
+    int geom_threads;
+    int mw_warps;
+    int mw_ctas_per_sm;
+    int fill_ctas;
+    int sms;
+};
+
+cudaError_t launch_init_slots(const EngineView &E, cudaStream_t st);
+cudaError_t launch_round(const EngineView &E, const LaunchShape &L, cudaStream_t st);
+cudaError_t launch_geom(const EngineView &E, const LaunchShape &L, cudaStream_t st);
+cudaError_t launch_fill(const EngineView &E, const LaunchShape &L, cudaStream_t st);
+cudaError_t launch_mw(const EngineView &E, const LaunchShape &L, cudaStream_t st);
+cudaError_t launch_round_end(const EngineView &E, cudaStream_t st);
+// fill one table with an explicit key into entry `entry` of the cache arrays
+cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4],
+                            uint32_t entry, double *values_out, cudaStream_t st);
+size_t fill_smem_bytes(int N);
+size_t mw_smem_bytes(int N, int warps);
+cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uint64_t spc,
+                            uint32_t key0, uint32_t key1, const uint8_t *matmap_local_to_global,
+                            const uint32_t *W, uint32_t *d_exit, uint32_t *d_steps,
+                            unsigned long long *d_head, uint32_t *d_err, const LaunchShape &L,
+                            cudaStream_t st);
+cudaError_t set_kernel_attributes(int N, int mw_warps);
+
+}  // namespace frw

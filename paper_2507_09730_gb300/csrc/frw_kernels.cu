@@ -1,0 +1,1317 @@
+// frw_kernels.cu -- sm_103a kernels of the FRW + MicroWalk engine.
+//
+// One engine round is four launches on one stream:
+//   k_geom   one lane per walk slot: issues walks, makes the first transition,
+//            sizes transition cubes, classifies them (hybrid dispatch), samples the
+//            analytical route in place and hands non-stratified cubes to MicroWalk;
+//            requests missing analytical tables.
+//   k_fill   one CTA per requested table: the exact FD surface Green's function (or
+//            first-cube flux kernel) of a layered lattice by separation of variables.
+//   k_mw     persistent MicroWalk kernel (Algorithm 3): each lane runs one lattice
+//            walk at a time and refills from the device job queue at 4-step group
+//            boundaries, so walks of uneven length do not idle the warp.
+//   k_round_end  resets the per-round queues and publishes the active-slot count.
+// No kernel waits on another kernel or on the host: ordering comes only from the
+// launch order on the stream.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "frw_internal.h"
+
+namespace frw {
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 Philox bijection,
+// multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// 53-bit uniform in [0, 1) from two words.
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b)
+{
+    return __dmul_rn(__dadd_rn(__dmul_rn((double)(a >> 5), 67108864.0), (double)(b >> 6)),
+                     1.0 / 9007199254740992.0);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry arithmetic with explicit IEEE rounding (no contraction into FMA), so
+// that FP64 decisions reproduce a plain host evaluation of the same expressions.
+template <typename T> struct Ar;
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+
+template <typename T> struct SView {
+    int n_c, n_b, bg;
+    T dlo[3], dhi[3];
+    T tau, margin;
+    const T *clo, *chi, *blo, *bhi;
+    const uint8_t *bmat;
+};
+
+template <typename T> __device__ __forceinline__ SView<T> sview(const DevStructure &S);
+template <> __device__ __forceinline__ SView<double> sview<double>(const DevStructure &S)
+{
+    SView<double> v;
+    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
+    for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo[a]; v.dhi[a] = S.dom_hi[a]; }
+    v.tau = S.tau; v.margin = 0.0;
+    v.clo = S.c_lo; v.chi = S.c_hi; v.blo = S.b_lo; v.bhi = S.b_hi; v.bmat = S.b_mat;
+    return v;
+}
+template <> __device__ __forceinline__ SView<float> sview<float>(const DevStructure &S)
+{
+    SView<float> v;
+    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
+    for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo_f[a]; v.dhi[a] = S.dom_hi_f[a]; }
+    v.tau = S.tau_f; v.margin = S.margin_f;
+    v.clo = S.c_lo_f; v.chi = S.c_hi_f; v.blo = S.b_lo_f; v.bhi = S.b_hi_f; v.bmat = S.b_mat;
+    return v;
+}
+
+// L-infinity distance to the nearest electrode (conductor box or grounded wall);
+// who = conductor index (lowest index on ties) or n_c for the walls.
+template <typename T>
+__device__ T nearest_electrode(const SView<T> &S, const T p[3], int &who)
+{
+    typedef Ar<T> A;
+    T best = A::inf();
+    int kb = -1;
+    const int n = S.n_c;
+    for (int k = 0; k < n; k++) {
+        T d = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const T t1 = A::sub(__ldg(&S.clo[a * n + k]), p[a]);
+            const T t2 = A::sub(p[a], __ldg(&S.chi[a * n + k]));
+            if (t1 > d) d = t1;
+            if (t2 > d) d = t2;
+        }
+        if (d < best) { best = d; kb = k; }
+    }
+    T dw = A::inf();
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        T t = A::sub(p[a], S.dlo[a]);
+        if (t < dw) dw = t;
+        t = A::sub(S.dhi[a], p[a]);
+        if (t < dw) dw = t;
+    }
+    if (best <= dw) { who = kb; return best; }
+    who = n;
+    return dw;
+}
+
+// Voxel centre i of an axis: (c - R) + (i + 0.5) h.
+template <typename T> __device__ __forceinline__ T vcentre(T base, T h, int i)
+{
+    return Ar<T>::add(base, Ar<T>::mul(T(i) + T(0.5), h));
+}
+
+// Smallest i in [0, N] with centre_i >= v (centres are non-decreasing in i).
+template <typename T> __device__ int first_ge(T base, T h, T invh, int N, T v)
+{
+    T e = (v - base) * invh - T(0.5);
+    int i;
+    if (!(e > T(0))) i = 0;
+    else if (e >= T(N)) i = N;
+    else i = (int)ceil(e);
+    while (i > 0 && vcentre(base, h, i - 1) >= v) i--;
+    while (i < N && vcentre(base, h, i) < v) i++;
+    return i;
+}
+
+struct CubeInfo {
+    int kind, axis, bg, K;
+    uint32_t prof[4];         // layer materials along the layering axis (nibbles)
+    uint2 rng[KMAX];          // packed voxel ranges + material of the listed blocks
+};
+
+__device__ __forceinline__ int rng_lo(const uint2 r, int a) { return (a == 2) ? (int)(r.y & 255u) : (int)((r.x >> (16 * a)) & 255u); }
+__device__ __forceinline__ int rng_hi(const uint2 r, int a) { return (a == 2) ? (int)((r.y >> 8) & 255u) : (int)((r.x >> (16 * a + 8)) & 255u); }
+__device__ __forceinline__ int rng_mat(const uint2 r) { return (int)((r.y >> 16) & 255u); }
+
+// Transition cube of half-size R centred at c: which blocks take part (some voxel
+// centre inside), list reset by a block covering every voxel, and the class:
+// homogeneous, layered along one axis, non-stratified, or too many blocks.
+template <typename T>
+__device__ void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeInfo &q)
+{
+    typedef Ar<T> A;
+    const T h = A::div(A::mul(T(2), R), T(N));
+    const T invh = T(1) / h;
+    T base[3], xmax[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        base[a] = A::sub(c[a], R);
+        xmax[a] = vcentre(base[a], h, N - 1);
+    }
+    int count = 0;
+    int bg = S.bg;
+    const int nb = S.n_b;
+    for (int b = 0; b < nb; b++) {
+        T lo[3], hi[3];
+        bool rej = false;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            lo[a] = __ldg(&S.blo[a * nb + b]);
+            hi[a] = __ldg(&S.bhi[a * nb + b]);
+            rej |= !(hi[a] > base[a]) || (lo[a] > xmax[a]);
+        }
+        if (rej) continue;
+        int r0[3], r1[3];
+        bool empty = false, full = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            r0[a] = first_ge(base[a], h, invh, N, lo[a]);
+            r1[a] = first_ge(base[a], h, invh, N, hi[a]);
+            empty |= r0[a] >= r1[a];
+            full &= (r0[a] == 0) && (r1[a] == N);
+        }
+        if (empty) continue;
+        const int m = __ldg(&S.bmat[b]);
+        if (full) { count = 0; bg = m; continue; }
+        if (count < KMAX)
+            q.rng[count] = make_uint2((uint32_t)r0[0] | ((uint32_t)r1[0] << 8) | ((uint32_t)r0[1] << 16) |
+                                          ((uint32_t)r1[1] << 24),
+                                      (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | ((uint32_t)m << 16));
+        count++;
+    }
+    q.bg = bg;
+    q.K = count;
+    q.axis = 2;
+    if (count > KMAX) { q.kind = CUBE_OVERFLOW; return; }
+    if (count == 0) {
+        q.kind = CUBE_HOM;
+        return;
+    }
+    int ax0 = -2;
+    bool same = true;
+    for (int t = 0; t < count; t++) {
+        const uint2 r = q.rng[t];
+        int ax = -1;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+            if (rng_lo(r, o1) == 0 && rng_hi(r, o1) == N && rng_lo(r, o2) == 0 && rng_hi(r, o2) == N) ax = a;
+        }
+        if (t == 0) ax0 = ax;
+        else if (ax != ax0) same = false;
+    }
+    if (!(same && ax0 >= 0)) { q.kind = CUBE_NONSTRAT; return; }
+    q.kind = CUBE_STRAT;
+    q.axis = ax0;
+    // layer profile along ax0 (later blocks win)
+    uint32_t pf[4];
+    const uint32_t bgn = (uint32_t)bg * 0x11111111u;
+    pf[0] = pf[1] = pf[2] = pf[3] = bgn;
+    for (int t = 0; t < count; t++) {
+        const uint2 r = q.rng[t];
+        const uint32_t m = (uint32_t)rng_mat(r);
+        for (int cc = rng_lo(r, ax0); cc < rng_hi(r, ax0); cc++) {
+            const int w = cc >> 3, sh = 4 * (cc & 7);
+            pf[w] = (pf[w] & ~(15u << sh)) | (m << sh);
+        }
+    }
+    // entries beyond N stay 0 so that keys are canonical
+    for (int cc = N; cc < 32; cc++) {
+        const int w = cc >> 3, sh = 4 * (cc & 7);
+        pf[w] &= ~(15u << sh);
+    }
+    q.prof[0] = pf[0]; q.prof[1] = pf[1]; q.prof[2] = pf[2]; q.prof[3] = pf[3];
+}
+
+// Volume-mean permittivity of the cube's lattice: constant-mask runs per axis,
+// material of each run triple by the last listed block containing it.
+__device__ double mean_eps(const CubeInfo &q, int N, const double *eps)
+{
+    int cut[3][2 * KMAX + 2];
+    int ncut[3];
+    for (int a = 0; a < 3; a++) {
+        int n = 0;
+        cut[a][n++] = 0;
+        cut[a][n++] = N;
+        for (int t = 0; t < q.K; t++) {
+            const int l = rng_lo(q.rng[t], a), h = rng_hi(q.rng[t], a);
+            cut[a][n++] = l;
+            cut[a][n++] = h;
+        }
+        // insertion sort + unique
+        for (int i = 1; i < n; i++) {
+            int v = cut[a][i], j = i - 1;
+            while (j >= 0 && cut[a][j] > v) { cut[a][j + 1] = cut[a][j]; j--; }
+            cut[a][j + 1] = v;
+        }
+        int m = 0;
+        for (int i = 0; i < n; i++)
+            if (m == 0 || cut[a][i] != cut[a][m - 1]) cut[a][m++] = cut[a][i];
+        ncut[a] = m;
+    }
+    double count[NMAT];
+    for (int m = 0; m < NMAT; m++) count[m] = 0.0;
+    for (int ix = 0; ix + 1 < ncut[0]; ix++)
+        for (int iy = 0; iy + 1 < ncut[1]; iy++)
+            for (int iz = 0; iz + 1 < ncut[2]; iz++) {
+                const int x = cut[0][ix], y = cut[1][iy], z = cut[2][iz];
+                int mat = q.bg;
+                for (int t = 0; t < q.K; t++) {
+                    const uint2 r = q.rng[t];
+                    if (rng_lo(r, 0) <= x && x < rng_hi(r, 0) && rng_lo(r, 1) <= y && y < rng_hi(r, 1) &&
+                        rng_lo(r, 2) <= z && z < rng_hi(r, 2))
+                        mat = rng_mat(r);
+                }
+                count[mat] += (double)((cut[0][ix + 1] - x) * (cut[1][iy + 1] - y) * (cut[2][iz + 1] - z));
+            }
+    double acc = 0.0;
+    for (int m = 0; m < NMAT; m++) acc += count[m] * eps[m];
+    return acc / (double)(N * N * N);
+}
+
+// ---------------------------------------------------------------------------
+// Analytical-table cache: open addressing on (kind, profile); compute-if-absent
+// by a later fill launch.  Returns the entry when ready, -1 to retry next round,
+// -2 when the probe window is full.
+__device__ __forceinline__ uint32_t hash5(uint32_t k, const uint32_t p[4])
+{
+    uint32_t h = 0x9747b28cu ^ (k * 0x85ebca6bu);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        uint32_t x = p[i] * 0xcc9e2d51u;
+        x = (x << 15) | (x >> 17);
+        h ^= x * 0x1b873593u;
+        h = ((h << 13) | (h >> 19)) * 5u + 0xe6546b64u;
+    }
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ int table_lookup(const TableCache &tc, uint32_t kind, const uint32_t prof[4])
+{
+    const uint32_t h = hash5(kind, prof);
+    for (uint32_t probe = 0; probe < 64; probe++) {
+        const uint32_t e = (h + probe) & (tc.cap - 1);
+        uint32_t st = ((volatile uint32_t *)tc.state)[e];
+        if (st == TE_EMPTY) {
+            const uint32_t old = atomicCAS(&tc.state[e], TE_EMPTY, TE_CLAIMED);
+            if (old == TE_EMPTY) {
+                uint32_t *k = tc.keys + 5 * e;
+                k[0] = kind; k[1] = prof[0]; k[2] = prof[1]; k[3] = prof[2]; k[4] = prof[3];
+                __threadfence();
+                atomicExch(&tc.state[e], TE_REQUESTED);
+                const uint32_t qi = atomicAdd(tc.fillq_count, 1u);
+                if (qi < tc.cap) tc.fillq[qi] = e;
+                return -1;
+            }
+            st = old;
+        }
+        if (st == TE_CLAIMED) return -1;
+        __threadfence();
+        const volatile uint32_t *k = tc.keys + 5 * e;
+        if (k[0] == kind && k[1] == prof[0] && k[2] == prof[1] && k[3] == prof[2] && k[4] == prof[3])
+            return (st == TE_READY) ? (int)e : -1;
+    }
+    return -2;
+}
+
+// smallest n in [0, P-1] with u < thr[n] (thr[P-1] counts as 2^32)
+__device__ __forceinline__ int sample_thr(const uint32_t *__restrict__ thr, int P, uint32_t u)
+{
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (u < __ldg(&thr[mid])) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Table frames: table axes (t0, t1, t2) -> cube axes.
+__device__ __forceinline__ void frame_sgf(int a, int fr[3]) { fr[0] = (a + 1) % 3; fr[1] = (a + 2) % 3; fr[2] = a; }
+__device__ __forceinline__ void frame_perp(int n, int a, int fr[3]) { fr[0] = n; fr[1] = 3 - n - a; fr[2] = a; }
+
+// canonical table panel n -> boundary node in cube coordinates (-1 / N on the face axis)
+__device__ __forceinline__ void panel_node(int N, const int fr[3], int n, int q[3])
+{
+    const int NN = N * N;
+    const int f = n / NN, rem = n - f * NN;
+    const int u = rem / N, w = rem - u * N;
+    const int ta = f >> 1, side = f & 1;
+    const int t1 = ta == 0 ? 1 : 0, t2 = ta == 2 ? 1 : 2;
+    q[fr[ta]] = side ? N : -1;
+    q[fr[t1]] = u;
+    q[fr[t2]] = w;
+}
+
+template <typename T>
+__device__ __forceinline__ void node_point(const T c[3], T R, int N, const int node[3], T p[3])
+{
+    typedef Ar<T> A;
+    const T h = A::div(A::mul(T(2), R), T(N));
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (node[a] < 0) p[a] = A::sub(c[a], R);
+        else if (node[a] >= N) p[a] = A::add(c[a], R);
+        else p[a] = vcentre(A::sub(c[a], R), h, node[a]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exact 128-bit fixed-point accumulation (order-independent, so results are
+// bit-reproducible whatever the completion order of walks).
+__device__ __forceinline__ void acc_i128(unsigned long long *p, double v, double scale)
+{
+    const double s = rint(v * scale);
+    const double a = fabs(s);
+    const double ah = floor(a * 5.421010862427522e-20);   // * 2^-64
+    const double al = a - ah * 18446744073709551616.0;
+    unsigned long long lo = (unsigned long long)al, hi = (unsigned long long)ah;
+    if (s < 0) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const unsigned long long old = atomicAdd(&p[0], lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    atomicAdd(&p[1], hi + carry);
+}
+
+// ---------------------------------------------------------------------------
+// Walk slot bookkeeping
+struct WalkState {
+    uint32_t job, hop, cnt_sh, cnt_mw;
+    int32_t branch;
+    uint64_t walk, steps;
+    double omega;
+};
+
+__device__ void finish_walk(const EngineView &E, const DevJob &J, const WalkState &w, int k)
+{
+    const uint64_t rel = w.walk - J.walk_begin;
+    const uint64_t g = rel / J.batch;
+    unsigned long long *acc = E.acc + J.acc_base + g * J.acc_stride;
+    const int nc1 = J.n_c + 1;
+    if (k >= 0) {
+        acc_i128(acc + 2 * k, w.omega, ACC_S1_SCALE);
+        acc_i128(acc + 2 * nc1 + 2 * k, w.omega * w.omega, ACC_S2_SCALE);
+    }
+    unsigned long long *ex = acc + 4 * nc1;
+    atomicAdd(&ex[0], 1ull);
+    atomicAdd(&ex[1], (unsigned long long)w.hop);
+    atomicAdd(&ex[2], (unsigned long long)w.steps);
+    atomicAdd(&ex[3], (unsigned long long)(w.cnt_sh & 0xffffu));
+    atomicAdd(&ex[4], (unsigned long long)(w.cnt_sh >> 16));
+    atomicAdd(&ex[5], (unsigned long long)w.cnt_mw);
+    if (w.branch >= 0 && w.branch < 3) atomicAdd(&ex[6 + w.branch], 1ull);
+    if (k < 0) atomicAdd(&ex[9], 1ull);
+    if (J.record) {
+        const uint64_t r = J.rec_base + rel;
+        E.rec.omega[r] = w.omega;
+        E.rec.k[r] = k;
+        E.rec.hops[r] = w.hop;
+        E.rec.steps[r] = w.steps;
+        E.rec.branch[r] = w.branch;
+    }
+}
+
+// First transition (hop 0): point on the Gaussian surface, first cube with the
+// special treatment, weight omega (Algorithm 1; flux reading of FirstTransition).
+// Returns false when a table is not ready yet (retry next round, same draws).
+template <typename T>
+__device__ bool first_transition(const EngineView &E, const DevJob &J, const SView<T> &S, WalkState &w,
+                                 T pos[3])
+{
+    typedef Ar<T> A;
+    const int N = E.N;
+    const uint32_t wl = (uint32_t)w.walk, wh = (uint32_t)(w.walk >> 32);
+    const uint4 b0 = philox10(wl, wh, 0u, 0u, J.key0, J.key1);
+    const uint4 b1 = philox10(wl, wh, 0u, 1u, J.key0, J.key1);
+    const double uf = u53(b0.x, b0.y), ua = u53(b0.z, b0.w), ub = u53(b1.x, b1.y);
+    const double tt = __dmul_rn(uf, J.area);
+    int f = 0;
+    while (f < 5 && !(tt < J.cum[f])) f++;
+    const int na = f >> 1, side = f & 1;
+    const int o1 = na == 0 ? 1 : 0, o2 = na == 2 ? 1 : 2;
+    double r[3];
+    r[na] = side ? J.g_hi[na] : J.g_lo[na];
+    r[o1] = __dadd_rn(J.g_lo[o1], __dmul_rn(ua, __dsub_rn(J.g_hi[o1], J.g_lo[o1])));
+    r[o2] = __dadd_rn(J.g_lo[o2], __dmul_rn(ub, __dsub_rn(J.g_hi[o2], J.g_lo[o2])));
+    const double orient = side ? 1.0 : -1.0;
+    T rt[3] = {(T)r[0], (T)r[1], (T)r[2]};
+    int who;
+    T R0 = nearest_electrode(S, rt, who);
+    if (E.fp32) R0 = A::sub(R0, S.margin);
+    CubeInfo q;
+    classify_cube(S, rt, R0, N, q);
+    int guard = 0;
+    while (q.kind == CUBE_OVERFLOW && guard++ < 40) {
+        R0 = A::mul(R0, T(0.5));
+        classify_cube(S, rt, R0, N, q);
+    }
+    if (q.kind == CUBE_OVERFLOW) {          // unreachable in practice: > 14 blocks at 2^-40 R
+        atomicOr(&E.status[STAT_ERR], ERR_SHRINK);
+        return false;
+    }
+    int br = 0;
+    T Rc = R0;
+    CubeInfo qc;
+    bool use_qc = false;
+    if (q.kind != CUBE_HOM && q.kind != CUBE_STRAT) {
+        br = 2;
+        for (int m = 1; m <= N / 4; m++) {
+            const T Rs = A::div(A::mul(R0, T(N - 2 * m)), T(N));
+            classify_cube(S, rt, Rs, N, qc);
+            if (qc.kind == CUBE_HOM || qc.kind == CUBE_STRAT) {
+                Rc = Rs;
+                br = 1;
+                use_qc = true;
+                break;
+            }
+        }
+    }
+    const CubeInfo &qq = use_qc ? qc : q;
+    const uint32_t *thr;
+    const uint32_t *sgn;
+    double keff;
+    int fr[3];
+    const TableCache &tc = E.tc;
+    if (br == 2) {
+        const double em = mean_eps(q, N, E.eps);
+        thr = tc.thr + (size_t)(tc.cap + 1) * tc.P;
+        sgn = tc.sgn + (size_t)(tc.cap + 1) * tc.P32;
+        keff = __dmul_rn(em, tc.ktot[tc.cap + 1]);
+        frame_sgf(na, fr);
+    } else if (qq.kind == CUBE_HOM) {
+        thr = tc.thr + (size_t)(tc.cap + 1) * tc.P;
+        sgn = tc.sgn + (size_t)(tc.cap + 1) * tc.P32;
+        keff = __dmul_rn(E.eps[qq.bg], tc.ktot[tc.cap + 1]);
+        frame_sgf(na, fr);
+    } else {
+        const uint32_t kind = (qq.axis == na) ? TAB_FLUX_PAR : TAB_FLUX_PERP;
+        const int e = table_lookup(tc, kind, qq.prof);
+        if (e < 0) {
+            if (e == -2) atomicOr(&E.status[STAT_ERR], ERR_CACHE_FULL);
+            return false;
+        }
+        thr = tc.thr + (size_t)e * tc.P;
+        sgn = tc.sgn + (size_t)e * tc.P32;
+        keff = tc.ktot[e];
+        if (kind == TAB_FLUX_PAR) frame_sgf(na, fr);
+        else frame_perp(na, qq.axis, fr);
+    }
+    const int m = sample_thr(thr, (int)tc.P, b1.z);
+    const double sg = ((__ldg(&sgn[m >> 5]) >> (m & 31)) & 1u) ? -1.0 : 1.0;
+    int node[3];
+    panel_node(N, fr, m, node);
+    const T h = A::div(A::mul(T(2), Rc), T(N));
+    w.omega = __dmul_rn(__dmul_rn(__ddiv_rn(__dmul_rn(__dmul_rn(-J.area, EPS0), keff), (double)h), sg), orient);
+    w.branch = br;
+    node_point(rt, Rc, N, node, pos);
+    return true;
+}
+
+__device__ __forceinline__ uint32_t nib(uint32_t v, int i) { return (v >> (4 * i)) & 15u; }
+
+template <typename T>
+__device__ void process_slot(const EngineView &E, uint32_t s)
+{
+    typedef Ar<T> A;
+    uint32_t st = E.s.state[s];
+    if (st == ST_IDLE) return;
+    const int N = E.N;
+    const uint32_t NS = E.NS;
+    WalkState w;
+    w.job = E.s.job[s];
+    w.hop = E.s.hop[s];
+    w.walk = E.s.walk[s];
+    w.steps = E.s.steps[s];
+    w.cnt_sh = E.s.cnt_sh[s];
+    w.cnt_mw = E.s.cnt_mw[s];
+    w.branch = E.s.branch[s];
+    w.omega = E.s.omega[s];
+    T pos[3] = {(T)E.s.pos[s], (T)E.s.pos[NS + s], (T)E.s.pos[2 * NS + s]};
+    int hop_budget = E.hop_budget, walk_budget = E.walk_budget;
+    bool dirty_pos = false;
+    for (;;) {
+        if (st != ST_FRESH && st != ST_IDLE && E.job_cancel[w.job]) st = ST_FRESH;
+        if (st == ST_FRESH) {
+            if (walk_budget-- <= 0) break;
+            bool found = false;
+            for (int t = 0; t < E.n_jobs; t++) {
+                const uint32_t jj = (w.job + t) % (uint32_t)E.n_jobs;
+                if (E.job_cancel[jj]) continue;
+                const DevJob &Jc = E.jobs[jj];
+                if (((volatile unsigned long long *)E.job_next)[jj] >= Jc.walk_count) continue;
+                const unsigned long long x = atomicAdd(&E.job_next[jj], 1ull);
+                if (x < Jc.walk_count) {
+                    w.job = jj;
+                    w.walk = Jc.walk_begin + x;
+                    found = true;
+                    break;
+                }
+            }
+            if (!found) { st = ST_IDLE; break; }
+            w.hop = 0; w.steps = 0; w.cnt_sh = 0; w.cnt_mw = 0; w.branch = -1; w.omega = 0.0;
+            st = ST_FIRST;
+        }
+        const DevJob &J = E.jobs[w.job];
+        const SView<T> S = sview<T>(E.structs[J.sid]);
+        if (st == ST_FIRST) {
+            if (!first_transition<T>(E, J, S, w, pos)) break;   // table not ready
+            dirty_pos = true;
+            w.hop = 1;
+            st = ST_HOP;
+        }
+        if (st == ST_MWDONE) {
+            const uint32_t en = E.s.exitnode[s];
+            const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
+            const T c[3] = {(T)E.s.cube[s], (T)E.s.cube[NS + s], (T)E.s.cube[2 * NS + s]};
+            const T R = (T)E.s.cube[3 * NS + s];
+            node_point(c, R, N, node, pos);
+            dirty_pos = true;
+            w.hop++;
+            st = ST_HOP;
+        }
+        if (st == ST_MW) break;
+        // st == ST_HOP
+        if (hop_budget-- <= 0) break;
+        int who;
+        const T d = nearest_electrode(S, pos, who);
+        if (d <= S.tau) {
+            finish_walk(E, J, w, who);
+            st = ST_FRESH;
+            continue;
+        }
+        if ((int)w.hop >= E.max_hops) {
+            finish_walk(E, J, w, -1);
+            st = ST_FRESH;
+            continue;
+        }
+        T R = E.fp32 ? A::sub(d, S.margin) : d;
+        CubeInfo q;
+        classify_cube(S, pos, R, N, q);
+        int guard = 0;
+        while (q.kind == CUBE_OVERFLOW && guard++ < 40) {
+            R = A::mul(R, T(0.5));
+            classify_cube(S, pos, R, N, q);
+        }
+        if (q.kind == CUBE_OVERFLOW) {      // unreachable in practice: count the walk as capped
+            atomicOr(&E.status[STAT_ERR], ERR_SHRINK);
+            finish_walk(E, J, w, -1);
+            st = ST_FRESH;
+            continue;
+        }
+        const uint4 hb = philox10((uint32_t)w.walk, (uint32_t)(w.walk >> 32), w.hop, 0u, J.key0, J.key1);
+        if (E.hybrid && q.kind == CUBE_HOM) {
+            const int m = sample_thr(E.tc.thr + (size_t)E.tc.cap * E.tc.P, (int)E.tc.P, hb.x);
+            int fr[3] = {0, 1, 2}, node[3];
+            panel_node(N, fr, m, node);
+            node_point(pos, R, N, node, pos);
+            dirty_pos = true;
+            w.hop++;
+            w.cnt_sh += 1u << 16;
+            continue;
+        }
+        if (E.hybrid && q.kind == CUBE_STRAT) {
+            const int e = table_lookup(E.tc, TAB_SGF, q.prof);
+            if (e < 0) {
+                if (e == -2) atomicOr(&E.status[STAT_ERR], ERR_CACHE_FULL);
+                break;   // retry this hop next round
+            }
+            const int m = sample_thr(E.tc.thr + (size_t)e * E.tc.P, (int)E.tc.P, hb.x);
+            int fr[3], node[3];
+            frame_sgf(q.axis, fr);
+            panel_node(N, fr, m, node);
+            node_point(pos, R, N, node, pos);
+            dirty_pos = true;
+            w.hop++;
+            w.cnt_sh += 1u;
+            continue;
+        }
+        // MicroWalk job (Algorithm 3) for this cube
+        const uint32_t qi = atomicAdd(E.mwq_count, 1u);
+        if (qi >= E.mwq_cap) {
+            atomicOr(&E.status[STAT_ERR], ERR_MWQ_OVERFLOW);
+            break;
+        }
+        MWJob *jb = E.mwq + qi;
+        const uint32_t s3 = hb.x >> 29;
+        const uint32_t c0 = (uint32_t)(N / 2 - 1);
+        const uint32_t start = (c0 + (s3 & 1u)) | ((c0 + ((s3 >> 1) & 1u)) << 8) | ((c0 + ((s3 >> 2) & 1u)) << 16);
+        // material nibble map: slot 0 boundary, 1 background, 2 + t listed block t
+        uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)q.bg << 4);
+        for (int t = 0; t < q.K; t++) mm |= (uint64_t)rng_mat(q.rng[t]) << (4 * (t + 2));
+        jb->slot = s;
+        jb->hop = w.hop;
+        jb->walk_lo = (uint32_t)w.walk;
+        jb->walk_hi = (uint32_t)(w.walk >> 32);
+        jb->start = start;
+        jb->K = (uint32_t)q.K;
+        jb->mm_lo = (uint32_t)mm;
+        jb->mm_hi = (uint32_t)(mm >> 32);
+        jb->key0 = J.key0;
+        jb->key1 = J.key1;
+        for (int t = 0; t < q.K; t++) jb->rng[t] = q.rng[t];
+        E.s.cube[s] = (double)pos[0];
+        E.s.cube[NS + s] = (double)pos[1];
+        E.s.cube[2 * NS + s] = (double)pos[2];
+        E.s.cube[3 * NS + s] = (double)R;
+        w.cnt_mw++;
+        st = ST_MW;
+        break;
+    }
+    E.s.state[s] = st;
+    E.s.job[s] = w.job;
+    E.s.hop[s] = w.hop;
+    E.s.walk[s] = w.walk;
+    E.s.steps[s] = w.steps;
+    E.s.cnt_sh[s] = w.cnt_sh;
+    E.s.cnt_mw[s] = w.cnt_mw;
+    E.s.branch[s] = w.branch;
+    E.s.omega[s] = w.omega;
+    if (dirty_pos) {
+        E.s.pos[s] = (double)pos[0];
+        E.s.pos[NS + s] = (double)pos[1];
+        E.s.pos[2 * NS + s] = (double)pos[2];
+    }
+    if (st != ST_IDLE) atomicAdd(&E.status[STAT_ACTIVE_CTR], 1u);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_geom(EngineView E)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < E.NS; s += stride) process_slot<T>(E, s);
+}
+
+__global__ void k_init_slots(EngineView E)
+{
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < E.NS; s += stride) {
+        E.s.state[s] = ST_FRESH;
+        E.s.job[s] = E.n_jobs > 0 ? s % (uint32_t)E.n_jobs : 0u;
+        E.s.hop[s] = 0;
+        E.s.steps[s] = 0;
+        E.s.cnt_sh[s] = 0;
+        E.s.cnt_mw[s] = 0;
+        E.s.branch[s] = -1;
+        E.s.omega[s] = 0.0;
+    }
+}
+
+__global__ void k_round_end(EngineView E)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        E.status[STAT_ACTIVE] = E.status[STAT_ACTIVE_CTR];
+        E.status[STAT_ACTIVE_CTR] = 0;
+        E.status[STAT_MWJOBS] += *E.mwq_count;
+        *E.mwq_count = 0;
+        *E.mwq_head = 0;
+        *E.tc.fillq_count = 0;
+        *E.tc.fillq_head = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MicroWalk kernel (Algorithm 3).  Per warp, shared memory holds one column of
+// per-axis block masks per lane: mask(a, c) has bit 0 (background) and bit t+1
+// for every listed block whose range on axis a contains c; rows c = -1 and c = N
+// are 0 (boundary).  The material of node (x, y, z) is given by the highest set
+// bit of mask(0,x) & mask(1,y) & mask(2,z) through a 16-entry nibble map.
+// Layout [row][lane] keeps every lane in its own bank.
+
+__device__ __forceinline__ int mat_of(uint64_t mm, uint32_t mask)
+{
+    const int slot = 32 - __clz((int)mask);
+    return (int)((mm >> (4 * slot)) & 15ull);
+}
+
+// One step of the lattice walk: weights W[mv][m_k] of Eq. 6 (quantised), integer
+// prefix sums, neighbour chosen by (u * S) >> 32.  Returns true on reaching a
+// boundary node.
+__device__ __forceinline__ bool mw_step(const uint32_t *__restrict__ M, const uint32_t *__restrict__ Wsm,
+                                        int NP2, int N, int &x, int &y, int &z, uint64_t mm, uint32_t u)
+{
+    const uint32_t *Mx = M;
+    const uint32_t *My = M + NP2 * 32;
+    const uint32_t *Mz = M + 2 * NP2 * 32;
+    const uint32_t xm = Mx[x * 32], x0 = Mx[(x + 1) * 32], xp = Mx[(x + 2) * 32];
+    const uint32_t ym = My[y * 32], y0 = My[(y + 1) * 32], yp = My[(y + 2) * 32];
+    const uint32_t zm = Mz[z * 32], z0 = Mz[(z + 1) * 32], zp = Mz[(z + 2) * 32];
+    const uint32_t yz = y0 & z0, xz = x0 & z0, xy = x0 & y0;
+    const int mv = mat_of(mm, xy & z0);
+    const uint32_t *Wr = Wsm + mv * 16;
+    const uint32_t w0 = Wr[mat_of(mm, xm & yz)];
+    const uint32_t w1 = Wr[mat_of(mm, xp & yz)];
+    const uint32_t w2 = Wr[mat_of(mm, ym & xz)];
+    const uint32_t w3 = Wr[mat_of(mm, yp & xz)];
+    const uint32_t w4 = Wr[mat_of(mm, zm & xy)];
+    const uint32_t w5 = Wr[mat_of(mm, zp & xy)];
+    const uint32_t p0 = w0, p1 = p0 + w1, p2 = p1 + w2, p3 = p2 + w3, p4 = p3 + w4, p5 = p4 + w5;
+    const uint32_t r = __umulhi(u, p5);
+    const int k = (int)(r >= p0) + (int)(r >= p1) + (int)(r >= p2) + (int)(r >= p3) + (int)(r >= p4);
+    const int d = (k & 1) ? 1 : -1;
+    const int ax = k >> 1;
+    x += (ax == 0) ? d : 0;
+    y += (ax == 1) ? d : 0;
+    z += (ax == 2) ? d : 0;
+    return ((unsigned)x >= (unsigned)N) | ((unsigned)y >= (unsigned)N) | ((unsigned)z >= (unsigned)N);
+}
+
+struct MWLane {
+    uint32_t walk_lo, walk_hi, hop, key0, key1, tag;
+    uint64_t mm;
+};
+
+// Job source: the engine's per-round queue.
+struct QueueSource {
+    const MWJob *q;
+    const uint32_t *cnt;
+    uint32_t *head;
+    uint32_t *err;
+    SlotArrays s;
+    uint32_t NS;
+    __device__ uint64_t grab(uint32_t n) const { return atomicAdd(head, n); }
+    __device__ bool valid(uint64_t j) const { return j < (uint64_t)min(*cnt, NS); }
+    __device__ void overrun() const { atomicOr(err, ERR_MW_STEPS); }
+    __device__ void build(uint64_t j, uint32_t *Mcol, int NP2, int N, int lane) const
+    {
+        const MWJob &b = q[j];
+        const int K = (int)b.K;
+        for (int row = lane; row < 3 * NP2; row += 32) {
+            const int a = row / NP2;
+            const int c = row - a * NP2 - 1;
+            uint32_t m = 0;
+            if (c >= 0 && c < N) {
+                m = 1u;
+                for (int t = 0; t < K; t++) {
+                    const uint2 r = b.rng[t];
+                    if (rng_lo(r, a) <= c && c < rng_hi(r, a)) m |= 2u << t;
+                }
+            }
+            Mcol[row * 32] = m;
+        }
+    }
+    __device__ void load(uint64_t j, MWLane &L, int &x, int &y, int &z) const
+    {
+        const MWJob &b = q[j];
+        L.walk_lo = b.walk_lo; L.walk_hi = b.walk_hi; L.hop = b.hop;
+        L.key0 = b.key0; L.key1 = b.key1; L.tag = b.slot;
+        L.mm = (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32);
+        x = (int)(b.start & 255u); y = (int)((b.start >> 8) & 255u); z = (int)((b.start >> 16) & 255u);
+    }
+    __device__ void finish(const MWLane &L, int x, int y, int z, uint32_t steps) const
+    {
+        const uint32_t sl = L.tag;
+        s.exitnode[sl] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+        s.steps[sl] += steps;
+        s.state[sl] = ST_MWDONE;
+    }
+};
+
+// Job source: stand-alone cubes given as integer voxel ranges (64 int32 per cube).
+struct CubeSource {
+    const int32_t *cubes;
+    uint64_t n_cubes, spc, total;
+    unsigned long long *head;
+    uint32_t key0, key1;
+    uint64_t mmap_lo;        // local material id -> global id nibbles (ids 0..15)
+    uint32_t *d_exit, *d_steps;
+    uint32_t *err;
+    int N;
+    __device__ uint64_t grab(uint32_t n) const { return atomicAdd(head, (unsigned long long)n); }
+    __device__ void overrun() const { atomicOr(err, ERR_MW_STEPS); }
+    __device__ bool valid(uint64_t j) const { return j < total; }
+    __device__ int gmat(int local) const { return (int)((mmap_lo >> (4 * (local & 15))) & 15ull); }
+    __device__ void build(uint64_t j, uint32_t *Mcol, int NP2, int N_, int lane) const
+    {
+        const int32_t *c = cubes + (j / spc) * 64;
+        const int K = min(max(c[1], 0), 8);   // a 64-word record holds at most 8 blocks
+        for (int row = lane; row < 3 * NP2; row += 32) {
+            const int a = row / NP2;
+            const int cc = row - a * NP2 - 1;
+            uint32_t m = 0;
+            if (cc >= 0 && cc < N_) {
+                m = 1u;
+                for (int t = 0; t < K; t++)
+                    if (c[2 + 7 * t + 2 * a] <= cc && cc < c[3 + 7 * t + 2 * a]) m |= 2u << t;
+            }
+            Mcol[row * 32] = m;
+        }
+    }
+    __device__ void load(uint64_t j, MWLane &L, int &x, int &y, int &z) const
+    {
+        const int32_t *c = cubes + (j / spc) * 64;
+        const int K = min(max(c[1], 0), 8);
+        uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)gmat(c[0]) << 4);
+        for (int t = 0; t < K; t++) mm |= (uint64_t)gmat(c[2 + 7 * t + 6]) << (4 * (t + 2));
+        L.mm = mm;
+        L.walk_lo = (uint32_t)j;
+        L.walk_hi = (uint32_t)(j >> 32);
+        L.hop = 0;
+        L.key0 = key0;
+        L.key1 = key1;
+        L.tag = 0;
+        const uint4 b = philox10(L.walk_lo, L.walk_hi, 0u, 0u, key0, key1);
+        const uint32_t s3 = b.x >> 29;
+        const int c0 = N / 2 - 1;
+        x = c0 + (int)(s3 & 1u);
+        y = c0 + (int)((s3 >> 1) & 1u);
+        z = c0 + (int)((s3 >> 2) & 1u);
+    }
+    __device__ void finish(const MWLane &L, int x, int y, int z, uint32_t steps) const
+    {
+        const uint64_t j = (uint64_t)L.walk_lo | ((uint64_t)L.walk_hi << 32);
+        if (d_exit) d_exit[j] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+        if (d_steps) d_steps[j] = steps;
+    }
+};
+
+constexpr uint32_t MW_STEP_CAP = 1u << 26;
+
+template <class Src>
+__global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict__ Wg, int N)
+{
+    extern __shared__ uint32_t smem[];
+    uint32_t *Wsm = smem;
+    const int NP2 = N + 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *Mw = smem + 256 + (size_t)warp * 3 * NP2 * 32;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) Wsm[i] = Wg[i];
+    __syncthreads();
+    const uint32_t *M = Mw + lane;
+    bool active = false, exhausted = false;
+    int x = 0, y = 0, z = 0;
+    uint32_t t = 0;
+    MWLane L;
+    L.walk_lo = L.walk_hi = L.hop = L.key0 = L.key1 = L.tag = 0;
+    L.mm = 0;
+    for (;;) {
+        const bool need = !active && !exhausted;
+        const uint32_t bal = __ballot_sync(FULL_MASK, need);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = src.grab((uint32_t)__popc(bal));
+            base = __shfl_sync(FULL_MASK, base, leader);
+            const uint64_t myj = base + (uint64_t)__popc(bal & ((1u << lane) - 1u));
+            const bool got = need && src.valid(myj);
+            if (need && !got) exhausted = true;
+            uint32_t todo = __ballot_sync(FULL_MASK, got);
+            while (todo) {
+                const int r = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const uint64_t jr = __shfl_sync(FULL_MASK, myj, r);
+                src.build(jr, Mw + r, NP2, N, lane);
+            }
+            __syncwarp();
+            if (got) {
+                src.load(myj, L, x, y, z);
+                t = 0;
+                active = true;
+            }
+        }
+        if (__ballot_sync(FULL_MASK, active) == 0u) break;
+        if (active) {
+            const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
+            const uint32_t words[4] = {blk.x, blk.y, blk.z, blk.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (active) {
+                    if (mw_step(M, Wsm, NP2, N, x, y, z, L.mm, words[k])) {
+                        src.finish(L, x, y, z, t + (uint32_t)k + 1u);
+                        active = false;
+                    }
+                }
+            }
+            t += 4;
+            if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
+                src.overrun();
+                src.finish(L, x, y, z, t);
+                active = false;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Analytical table fill (one CTA per table).
+//
+// A layered lattice (permittivity eps_k along table axis t2) separates: in the
+// two lateral axes the FD operator of Eq. 4-5 is (eps_k / 2) T with T the
+// cell-centred Dirichlet Laplacian (diagonal 3 at both ends), whose eigenvectors
+// are the DST-II vectors u_p(i) = sqrt(2/N) sin(pi p (i + 1/2) / N) (p < N),
+// u_N(i) = (-1)^i / sqrt(N), eigenvalues lam_p = 4 sin^2(pi p / (2N)).  In that
+// basis the symmetric system S y = b (S = diag(eps) times Eq. 6) becomes one
+// tridiagonal system per lateral mode (p, q) along t2, solved by the Thomas
+// algorithm; the panel values eps_v y_v (Eq. 8: P = e_c^T A_II^{-1} A_IB) are
+// assembled face by face with two small contractions each.  Only the modes that
+// the right-hand side excites are kept: odd p and q for the SGF and the
+// layer-normal flux kernel, even p with odd q for the flux kernel across layers.
+struct FillJob {
+    uint32_t kind;
+    uint32_t prof[4];
+    uint32_t *thr;
+    uint32_t *sgn;
+    double *ktot;
+    double *values;        // optional raw panel values (canonical order)
+    uint32_t *err;
+};
+
+__device__ void fill_table(const FillJob &F, int N, const double *__restrict__ eps, const FillConsts &C,
+                           double *sm)
+{
+    const int H = N / 2, M = H * H, P = 6 * N * N;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double *ek = sm;                 // N
+    double *yh = ek + MAXN;          // M * N
+    double *Z = yh + M * N;          // N * N
+    double *V = Z + MAXN * MAXN;     // P
+    double *red = V + P;             // nt
+    const uint32_t kind = F.kind;
+    const bool hom = (kind == TAB_SGF_HOM || kind == TAB_FLUX_HOM);
+    const bool perp = (kind == TAB_FLUX_PERP);
+    const bool flux = (kind == TAB_FLUX_PAR || kind == TAB_FLUX_PERP || kind == TAB_FLUX_HOM);
+    for (int k = tid; k < N; k += nt) ek[k] = hom ? 1.0 : eps[nib(F.prof[k >> 3], k & 7)];
+    __syncthreads();
+    const int c0 = H - 1, c1 = H;
+    // tridiagonal solve per mode
+    for (int m = tid; m < M; m += nt) {
+        const int ip = m / H, iq = m - ip * H;
+        const int p = perp ? 2 * (ip + 1) : 2 * ip + 1;   // 1-based mode numbers
+        const int q = 2 * iq + 1;
+        const double lam = C.lam[p - 1] + C.lam[q - 1];
+        double cp[MAXN], dp[MAXN];
+        double prev_off = 0.0;
+        for (int k = 0; k < N; k++) {
+            const double e = ek[k];
+            const double glo = (k == 0) ? e : e * ek[k - 1] / (e + ek[k - 1]);
+            const double ghi = (k == N - 1) ? e : e * ek[k + 1] / (e + ek[k + 1]);
+            const double diag = 0.5 * e * lam + glo + ghi;
+            const double off = (k == N - 1) ? 0.0 : -ghi;
+            double rhs = 0.0;
+            if (kind == TAB_SGF || kind == TAB_SGF_HOM) {
+                if (k == c0 || k == c1) rhs = 0.5 * C.a[p - 1] * C.a[q - 1];
+            } else if (perp) {
+                if (k == c0 || k == c1) rhs = 0.5 * e * C.d[p - 1] * C.a[q - 1];
+            } else {
+                const double wgt = 2.0 * ek[c0] * ek[c1] / (ek[c0] + ek[c1]);
+                if (k == c1) rhs = wgt * C.a[p - 1] * C.a[q - 1];
+                if (k == c0) rhs = -wgt * C.a[p - 1] * C.a[q - 1];
+            }
+            if (k == 0) {
+                cp[0] = off / diag;
+                dp[0] = rhs / diag;
+            } else {
+                const double den = diag - prev_off * cp[k - 1];
+                cp[k] = off / den;
+                dp[k] = (rhs - prev_off * dp[k - 1]) / den;
+            }
+            prev_off = off;
+        }
+        double yk = dp[N - 1];
+        yh[m * N + N - 1] = yk;
+        for (int k = N - 2; k >= 0; k--) {
+            yk = dp[k] - cp[k] * yk;
+            yh[m * N + k] = yk;
+        }
+    }
+    __syncthreads();
+    const double *U = C.u;   // U[(p-1)*N + i]
+    // faces: f = 2*ta + side; panel (u, w) on the other two table axes in increasing order
+    for (int f = 0; f < 6; f++) {
+        const int ta = f >> 1, side = f & 1;
+        const int fix = side ? N - 1 : 0;
+        // stage 1: contract one lateral index
+        if (ta == 2) {
+            // Z[ip][j] = sum_iq u_q(j) yh[ip,iq][fix]
+            for (int o = tid; o < H * N; o += nt) {
+                const int ip = o / N, j = o - ip * N;
+                double acc = 0.0;
+                for (int iq = 0; iq < H; iq++) acc += U[(2 * iq) * N + j] * yh[(ip * H + iq) * N + fix];
+                Z[o] = acc;
+            }
+        } else if (ta == 0) {
+            // Z[iq][k] = sum_ip u_p(fix) yh[ip,iq][k]
+            for (int o = tid; o < H * N; o += nt) {
+                const int iq = o / N, k = o - iq * N;
+                double acc = 0.0;
+                for (int ip = 0; ip < H; ip++) {
+                    const int p = perp ? 2 * (ip + 1) : 2 * ip + 1;
+                    acc += U[(p - 1) * N + fix] * yh[(ip * H + iq) * N + k];
+                }
+                Z[o] = acc;
+            }
+        } else {
+            // Z[ip][k] = sum_iq u_q(fix) yh[ip,iq][k]
+            for (int o = tid; o < H * N; o += nt) {
+                const int ip = o / N, k = o - ip * N;
+                double acc = 0.0;
+                for (int iq = 0; iq < H; iq++) acc += U[(2 * iq) * N + fix] * yh[(ip * H + iq) * N + k];
+                Z[o] = acc;
+            }
+        }
+        __syncthreads();
+        // stage 2
+        for (int o = tid; o < N * N; o += nt) {
+            const int u = o / N, w = o - u * N;
+            double acc = 0.0, e;
+            if (ta == 2) {           // (u, w) = (i, j); layer fix
+                for (int ip = 0; ip < H; ip++) {
+                    const int p = perp ? 2 * (ip + 1) : 2 * ip + 1;
+                    acc += U[(p - 1) * N + u] * Z[ip * N + w];
+                }
+                e = ek[fix];
+            } else if (ta == 0) {    // (u, w) = (j, k)
+                for (int iq = 0; iq < H; iq++) acc += U[(2 * iq) * N + u] * Z[iq * N + w];
+                e = ek[w];
+            } else {                 // (u, w) = (i, k)
+                for (int ip = 0; ip < H; ip++) {
+                    const int p = perp ? 2 * (ip + 1) : 2 * ip + 1;
+                    acc += U[(p - 1) * N + u] * Z[ip * N + w];
+                }
+                e = ek[w];
+            }
+            V[f * N * N + o] = e * acc;
+        }
+        __syncthreads();
+    }
+    // totals and thresholds in canonical order (chunked sequential scan)
+    const int chunk = (P + nt - 1) / nt;
+    const int b0 = tid * chunk, b1 = min(P, b0 + chunk);
+    double part = 0.0;
+    for (int n = b0; n < b1; n++) part += flux ? fabs(V[n]) : V[n];
+    red[tid] = part;
+    __syncthreads();
+    if (tid == 0) {
+        double run = 0.0;
+        for (int i = 0; i < nt; i++) {
+            const double v = red[i];
+            red[i] = run;
+            run += v;
+        }
+        red[nt] = run;
+    }
+    __syncthreads();
+    const double total = red[nt];
+    double cum = red[tid];
+    for (int n = b0; n < b1; n++) {
+        cum += flux ? fabs(V[n]) : V[n];
+        double tv = floor((cum / total) * 4294967296.0);
+        if (tv > 4294967295.0) tv = 4294967295.0;
+        if (tv < 0.0) tv = 0.0;
+        F.thr[n] = (uint32_t)tv;
+        if (F.values) F.values[n] = V[n];
+    }
+    const int P32 = (P + 31) / 32;
+    for (int wd = tid; wd < P32; wd += nt) {
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; b++) {
+            const int n = wd * 32 + b;
+            if (n < P && flux && V[n] < 0.0) bits |= 1u << b;
+        }
+        F.sgn[wd] = bits;
+    }
+    if (tid == 0) {
+        *F.ktot = total;
+        if (!flux && fabs(total - 1.0) > 1e-9) atomicOr(F.err, ERR_FILL);
+        if (!(total > 0.0)) atomicOr(F.err, ERR_FILL);
+    }
+}
+
+__global__ void k_fill(EngineView E)
+{
+    extern __shared__ double fsm[];
+    __shared__ uint32_t e_sh;
+    const TableCache &tc = E.tc;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t qi = atomicAdd(tc.fillq_head, 1u);
+            const uint32_t cnt = min(*tc.fillq_count, tc.cap);
+            e_sh = (qi < cnt) ? tc.fillq[qi] : 0xffffffffu;
+        }
+        __syncthreads();
+        const uint32_t e = e_sh;
+        if (e == 0xffffffffu) break;
+        FillJob F;
+        const uint32_t *k = tc.keys + 5 * e;
+        F.kind = k[0];
+        F.prof[0] = k[1]; F.prof[1] = k[2]; F.prof[2] = k[3]; F.prof[3] = k[4];
+        F.thr = tc.thr + (size_t)e * tc.P;
+        F.sgn = tc.sgn + (size_t)e * tc.P32;
+        F.ktot = tc.ktot + e;
+        F.values = nullptr;
+        F.err = &E.status[STAT_ERR];
+        fill_table(F, E.N, E.eps, E.fc, fsm);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(&tc.state[e], TE_READY);
+            atomicAdd(&E.status[STAT_BUILT], 1u);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t entry, double *values)
+{
+    extern __shared__ double fsm[];
+    FillJob F;
+    F.kind = kind;
+    F.prof[0] = prof.x; F.prof[1] = prof.y; F.prof[2] = prof.z; F.prof[3] = prof.w;
+    F.thr = E.tc.thr + (size_t)entry * E.tc.P;
+    F.sgn = E.tc.sgn + (size_t)entry * E.tc.P32;
+    F.ktot = E.tc.ktot + entry;
+    F.values = values;
+    F.err = &E.status[STAT_ERR];
+    fill_table(F, E.N, E.eps, E.fc, fsm);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+size_t fill_smem_bytes(int N)
+{
+    const int H = N / 2;
+    return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + 6 * N * N + 256 + 1);
+}
+
+size_t mw_smem_bytes(int N, int warps)
+{
+    return sizeof(uint32_t) * (256 + (size_t)warps * 3 * (N + 2) * 32);
+}
+
+cudaError_t set_kernel_attributes(int N, int mw_warps)
+{
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes(N));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fill_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes(N));
+    if (e != cudaSuccess) return e;
+    const int mws = (int)mw_smem_bytes(N, mw_warps);
+    e = cudaFuncSetAttribute(k_mw<QueueSource>, cudaFuncAttributeMaxDynamicSharedMemorySize, mws);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_mw<CubeSource>, cudaFuncAttributeMaxDynamicSharedMemorySize, mws);
+    return e;
+}
+
+cudaError_t launch_init_slots(const EngineView &E, cudaStream_t st)
+{
+    const int threads = 256;
+    const int blocks = (int)((E.NS + threads - 1) / threads);
+    k_init_slots<<<blocks, threads, 0, st>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geom(const EngineView &E, const LaunchShape &L, cudaStream_t st)
+{
+    const int threads = L.geom_threads;
+    const int blocks = (int)((E.NS + threads - 1) / threads);
+    if (E.fp32) k_geom<float><<<blocks, threads, 0, st>>>(E);
+    else k_geom<double><<<blocks, threads, 0, st>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(const EngineView &E, const LaunchShape &L, cudaStream_t st)
+{
+    k_fill<<<L.fill_ctas, 256, fill_smem_bytes(E.N), st>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mw(const EngineView &E, const LaunchShape &L, cudaStream_t st)
+{
+    QueueSource src;
+    src.q = E.mwq;
+    src.cnt = E.mwq_count;
+    src.head = E.mwq_head;
+    src.s = E.s;
+    src.NS = E.NS;
+    src.err = &E.status[STAT_ERR];
+    k_mw<QueueSource><<<L.sms * L.mw_ctas_per_sm, 32 * L.mw_warps, mw_smem_bytes(E.N, L.mw_warps), st>>>(
+        src, E.W, E.N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round(const EngineView &E, const LaunchShape &L, cudaStream_t st)
+{
+    cudaError_t e = launch_geom(E, L, st);
+    if (e != cudaSuccess) return e;
+    e = launch_fill(E, L, st);
+    if (e != cudaSuccess) return e;
+    e = launch_mw(E, L, st);
+    if (e != cudaSuccess) return e;
+    return launch_round_end(E, st);
+}
+
+cudaError_t launch_round_end(const EngineView &E, cudaStream_t st)
+{
+    k_round_end<<<1, 32, 0, st>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4], uint32_t entry,
+                            double *values_out, cudaStream_t st)
+{
+    k_fill_one<<<1, 256, fill_smem_bytes(E.N), st>>>(E, kind, make_uint4(prof[0], prof[1], prof[2], prof[3]),
+                                                      entry, values_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uint64_t spc, uint32_t key0,
+                            uint32_t key1, const uint8_t *map, const uint32_t *W, uint32_t *d_exit,
+                            uint32_t *d_steps, unsigned long long *d_head, uint32_t *d_err,
+                            const LaunchShape &L, cudaStream_t st)
+{
+    CubeSource src;
+    src.err = d_err;
+    src.cubes = d_cubes;
+    src.n_cubes = n_cubes;
+    src.spc = spc;
+    src.total = n_cubes * spc;
+    src.head = d_head;
+    src.key0 = key0;
+    src.key1 = key1;
+    uint64_t mm = 0;
+    for (int i = 0; i < 16; i++) mm |= (uint64_t)(map[i] & 15u) << (4 * i);
+    src.mmap_lo = mm;
+    src.d_exit = d_exit;
+    src.d_steps = d_steps;
+    src.N = N;
+    const int threads = 32 * L.mw_warps;
+    k_mw<CubeSource><<<L.sms * L.mw_ctas_per_sm, threads, mw_smem_bytes(N, L.mw_warps), st>>>(src, W, N);
+    return cudaGetLastError();
+}
+
+}  // namespace frw

@@ -1,0 +1,978 @@
+// frw_runtime.cu -- host side of the C ABI in include/frw.h: context, material
+// registry, structure loading and validation, and the engine loop that drives
+// the device rounds (geometry -> table fill -> MicroWalk -> round end).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "frw.h"
+#include "frw_internal.h"
+
+using namespace frw;
+
+namespace {
+
+struct HostStructure {
+    int n_c = 0, n_b = 0;
+    std::vector<double> c_lo, c_hi;   // n_c x 3 (AoS, host copy for Gaussian set-up)
+    double dom_lo[3], dom_hi[3];
+    std::vector<void *> dev;          // device allocations of this structure
+    DevStructure d;
+    bool live = false;
+};
+
+}  // namespace
+
+struct frw_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    frw_options opt;
+    LaunchShape shape;
+    std::string last_error;
+    // materials (global ids)
+    std::vector<double> eps;
+    uint32_t W[16][16];
+    // device memory
+    std::vector<void *> allocs;
+    uint32_t NS = 0;
+    SlotArrays slots;
+    MWJob *mwq = nullptr;
+    uint32_t *mwq_ctr = nullptr;        // [2]: count, head
+    TableCache tc;
+    uint32_t *status = nullptr;
+    uint32_t *d_W = nullptr;
+    double *d_eps = nullptr;
+    FillConsts fc;
+    double *fc_buf = nullptr;
+    DevStructure *d_structs = nullptr;
+    int struct_cap = 0;
+    std::vector<HostStructure> structs;
+    uint32_t *h_status = nullptr;       // pinned
+};
+
+static const char *kErr[] = {"ok",
+                             "invalid argument",
+                             "out of device memory / admission refused",
+                             "timeout",
+                             "device error",
+                             "walk budget exhausted before the sigma target",
+                             "capacity exceeded",
+                             "not found"};
+
+static int fail(frw_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->last_error = msg;
+    return code;
+}
+
+static int cuda_fail(frw_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? FRW_ENOMEM : FRW_EDEVICE, m);
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <typename T> static int dalloc(frw_ctx *ctx, T **p, size_t count, std::vector<void *> &owner)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    owner.push_back(q);
+    *p = (T *)q;
+    return FRW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// quantised alpha of Eq. 6: W[v][i] = round(eps_i / (eps_i + eps_v) * 2^24), boundary 2^24
+static void rebuild_w(frw_ctx *ctx)
+{
+    for (int a = 0; a < 16; a++)
+        for (int b = 0; b < 16; b++) ctx->W[a][b] = 0;
+    const int n = (int)ctx->eps.size();
+    for (int v = 0; v < n; v++) {
+        for (int i = 0; i < n; i++) {
+            const double al = ctx->eps[i] / (ctx->eps[i] + ctx->eps[v]);
+            ctx->W[v][i] = (uint32_t)std::floor(al * 16777216.0 + 0.5);
+        }
+        ctx->W[v][BOUNDARY] = 16777216u;
+    }
+}
+
+// map a local permittivity table onto global material ids (exact equality merges)
+static int register_materials(frw_ctx *ctx, const double *eps_r, int n_mat, std::vector<uint8_t> &map)
+{
+    map.assign(16, 0);
+    std::vector<double> add = ctx->eps;
+    for (int i = 0; i < n_mat; i++) {
+        if (!(eps_r[i] > 0.0) || !std::isfinite(eps_r[i]))
+            return fail(ctx, FRW_EINVAL, "permittivity must be positive and finite");
+        int g = -1;
+        for (size_t j = 0; j < add.size(); j++)
+            if (add[j] == eps_r[i]) g = (int)j;
+        if (g < 0) {
+            if ((int)add.size() >= FRW_MAX_MATERIALS)
+                return fail(ctx, FRW_ECAPACITY, "more than 15 distinct permittivities in one context");
+            add.push_back(eps_r[i]);
+            g = (int)add.size() - 1;
+        }
+        map[i] = (uint8_t)g;
+    }
+    if (add.size() != ctx->eps.size()) {
+        ctx->eps = add;
+        rebuild_w(ctx);
+        double e16[16] = {0};
+        for (size_t j = 0; j < ctx->eps.size(); j++) e16[j] = ctx->eps[j];
+        CK(cudaMemcpyAsync(ctx->d_eps, e16, sizeof(e16), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_W, ctx->W, sizeof(ctx->W), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return FRW_OK;
+}
+
+static EngineView make_view(frw_ctx *ctx)
+{
+    EngineView E;
+    memset(&E, 0, sizeof(E));
+    E.N = ctx->opt.N;
+    E.hybrid = ctx->opt.hybrid;
+    E.max_hops = ctx->opt.max_hops;
+    E.fp32 = ctx->opt.precision == FRW_FP32_GEOM;
+    E.NS = ctx->NS;
+    E.s = ctx->slots;
+    E.structs = ctx->d_structs;
+    E.mwq = ctx->mwq;
+    E.mwq_count = ctx->mwq_ctr;
+    E.mwq_head = ctx->mwq_ctr + 1;
+    E.mwq_cap = ctx->NS;
+    E.tc = ctx->tc;
+    E.W = ctx->d_W;
+    E.eps = ctx->d_eps;
+    E.fc = ctx->fc;
+    E.status = ctx->status;
+    E.hop_budget = 32;
+    E.walk_budget = 4;
+    return E;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" void frw_default_options(frw_options *o)
+{
+    memset(o, 0, sizeof(*o));
+    o->N = 24;
+    o->precision = FRW_FP64_GEOM;
+    o->seed = 0;
+    o->first_cube_mode = FRW_FIRST_HYBRID;
+    o->hybrid = 1;
+    o->gauss_offset_frac = 0.5;
+    o->max_hops = 100000;
+}
+
+extern "C" const char *frw_strerror(int code)
+{
+    if (code < 0 || code > 7) return "unknown status";
+    return kErr[code];
+}
+
+extern "C" const char *frw_last_error(frw_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+extern "C" int frw_set_stream(frw_ctx *ctx, void *s)
+{
+    if (!ctx) return FRW_EINVAL;
+    ctx->stream = s ? (cudaStream_t)s : ctx->own_stream;
+    return FRW_OK;
+}
+
+extern "C" void frw_destroy(frw_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &s : ctx->structs)
+        for (void *p : s.dev) cudaFree(p);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+static int check_status(frw_ctx *ctx)
+{
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(uint32_t) * STAT_WORDS, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const uint32_t e = ctx->h_status[STAT_ERR];
+    if (e) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s)", e,
+                 (e & ERR_MWQ_OVERFLOW) ? "queue overflow " : "", (e & ERR_CACHE_FULL) ? "table cache full " : "",
+                 (e & ERR_FILL) ? "table fill check " : "", (e & ERR_SHRINK) ? "cube shrink limit " : "",
+                 (e & ERR_ACC_RANGE) ? "accumulator range " : "", (e & ERR_MW_STEPS) ? "MicroWalk step cap" : "");
+        return fail(ctx, (e & ERR_CACHE_FULL) ? FRW_ECAPACITY : FRW_EDEVICE, buf);
+    }
+    return FRW_OK;
+}
+
+extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
+{
+    if (!out) return FRW_EINVAL;
+    *out = nullptr;
+    frw_options opt;
+    if (opt_in) opt = *opt_in;
+    else frw_default_options(&opt);
+    if (opt.N < 2 || opt.N > FRW_MAX_N || (opt.N & 1)) return FRW_EINVAL;
+    if (opt.precision != FRW_FP64_GEOM && opt.precision != FRW_FP32_GEOM) return FRW_EINVAL;
+    if (!(opt.gauss_offset_frac > 0.0 && opt.gauss_offset_frac < 1.0)) return FRW_EINVAL;
+    if (opt.max_hops <= 0) return FRW_EINVAL;
+    frw_ctx *ctx = new frw_ctx();
+    ctx->opt = opt;
+    ctx->device = device;
+    cudaError_t ce = cudaSetDevice(device);
+    if (ce != cudaSuccess) {
+        int r = cuda_fail(ctx, ce, "cudaSetDevice");
+        delete ctx;
+        return r;
+    }
+    int rc = FRW_OK;
+    auto bail = [&](int code) {
+        frw_destroy(ctx);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(FRW_EDEVICE);
+    ctx->stream = ctx->own_stream;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    ctx->shape.sms = sms > 0 ? sms : 1;
+    ctx->shape.geom_threads = opt.geom_threads > 0 ? opt.geom_threads : 128;
+    ctx->shape.mw_warps = opt.mw_warps_per_cta > 0 ? opt.mw_warps_per_cta : 8;
+    ctx->shape.mw_ctas_per_sm = opt.mw_ctas_per_sm > 0 ? opt.mw_ctas_per_sm : 2;
+    ctx->shape.fill_ctas = ctx->shape.sms;
+    const int N = opt.N;
+    ctx->NS = opt.slots > 0 ? (uint32_t)opt.slots : (1u << 20);
+    uint32_t cap = opt.table_capacity > 0 ? (uint32_t)opt.table_capacity : (N <= 16 ? (1u << 16) : (1u << 14));
+    uint32_t c2 = 1;
+    while (c2 < cap) c2 <<= 1;
+    cap = c2;
+    auto &A = ctx->allocs;
+    const uint32_t NS = ctx->NS;
+    SlotArrays &S = ctx->slots;
+    if ((rc = dalloc(ctx, &S.state, NS, A)) || (rc = dalloc(ctx, &S.job, NS, A)) || (rc = dalloc(ctx, &S.hop, NS, A)) ||
+        (rc = dalloc(ctx, &S.exitnode, NS, A)) || (rc = dalloc(ctx, &S.cnt_sh, NS, A)) ||
+        (rc = dalloc(ctx, &S.cnt_mw, NS, A)) || (rc = dalloc(ctx, &S.branch, NS, A)) ||
+        (rc = dalloc(ctx, &S.walk, NS, A)) || (rc = dalloc(ctx, &S.steps, NS, A)) ||
+        (rc = dalloc(ctx, &S.pos, 3 * (size_t)NS, A)) || (rc = dalloc(ctx, &S.cube, 4 * (size_t)NS, A)) ||
+        (rc = dalloc(ctx, &S.omega, NS, A)) || (rc = dalloc(ctx, &ctx->mwq, NS, A)) ||
+        (rc = dalloc(ctx, &ctx->mwq_ctr, 2, A)) || (rc = dalloc(ctx, &ctx->status, STAT_WORDS, A)) ||
+        (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)))
+        return bail(rc);
+    TableCache &T = ctx->tc;
+    T.cap = cap;
+    T.P = 6u * N * N;
+    T.P32 = (T.P + 31) / 32;
+    if ((rc = dalloc(ctx, &T.keys, 5 * (size_t)cap, A)) || (rc = dalloc(ctx, &T.state, cap, A)) ||
+        (rc = dalloc(ctx, &T.thr, (size_t)(cap + 2) * T.P, A)) ||
+        (rc = dalloc(ctx, &T.sgn, (size_t)(cap + 2) * T.P32, A)) || (rc = dalloc(ctx, &T.ktot, cap + 2, A)) ||
+        (rc = dalloc(ctx, &T.fillq, cap, A)) || (rc = dalloc(ctx, &T.fillq_count, 2, A)))
+        return bail(rc);
+    T.fillq_head = T.fillq_count + 1;
+    // separable-solve constants: DST-II basis, eigenvalues, centre projections
+    {
+        std::vector<double> h((size_t)N * N + 3 * N);
+        const double pi = 3.14159265358979323846;
+        for (int p = 1; p <= N; p++) {
+            for (int i = 0; i < N; i++) {
+                double v;
+                if (p < N) v = std::sqrt(2.0 / N) * std::sin(pi * p * (i + 0.5) / N);
+                else v = ((i & 1) ? -1.0 : 1.0) / std::sqrt((double)N);
+                h[(size_t)(p - 1) * N + i] = v;
+            }
+            const double s = std::sin(pi * p / (2.0 * N));
+            h[(size_t)N * N + p - 1] = 4.0 * s * s;
+            const double u0 = h[(size_t)(p - 1) * N + N / 2 - 1], u1 = h[(size_t)(p - 1) * N + N / 2];
+            h[(size_t)N * N + N + p - 1] = 0.5 * (u0 + u1);
+            h[(size_t)N * N + 2 * N + p - 1] = u1 - u0;
+        }
+        if ((rc = dalloc(ctx, &ctx->fc_buf, h.size(), A))) return bail(rc);
+        if (cudaMemcpy(ctx->fc_buf, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(FRW_EDEVICE);
+        ctx->fc.u = ctx->fc_buf;
+        ctx->fc.lam = ctx->fc_buf + (size_t)N * N;
+        ctx->fc.a = ctx->fc_buf + (size_t)N * N + N;
+        ctx->fc.d = ctx->fc_buf + (size_t)N * N + 2 * N;
+    }
+    ctx->struct_cap = 64;
+    if ((rc = dalloc(ctx, &ctx->d_structs, ctx->struct_cap, A))) return bail(rc);
+    if (cudaMallocHost(&ctx->h_status, sizeof(uint32_t) * STAT_WORDS) != cudaSuccess) return bail(FRW_ENOMEM);
+    cudaError_t e2 = set_kernel_attributes(N, ctx->shape.mw_warps);
+    if (e2 != cudaSuccess) return bail(cuda_fail(ctx, e2, "cudaFuncSetAttribute"));
+    cudaMemsetAsync(T.state, 0, sizeof(uint32_t) * cap, ctx->stream);
+    cudaMemsetAsync(T.fillq_count, 0, sizeof(uint32_t) * 2, ctx->stream);
+    cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, ctx->stream);
+    cudaMemsetAsync(ctx->mwq_ctr, 0, sizeof(uint32_t) * 2, ctx->stream);
+    cudaMemsetAsync(ctx->d_W, 0, sizeof(uint32_t) * 256, ctx->stream);
+    cudaMemsetAsync(ctx->d_eps, 0, sizeof(double) * 16, ctx->stream);
+    // homogeneous tables (independent of the permittivity): SGF at entry cap, flux at cap + 1
+    EngineView E = make_view(ctx);
+    const uint32_t zero[4] = {0, 0, 0, 0};
+    if (launch_fill_one(E, TAB_SGF_HOM, zero, cap, nullptr, ctx->stream) != cudaSuccess ||
+        launch_fill_one(E, TAB_FLUX_HOM, zero, cap + 1, nullptr, ctx->stream) != cudaSuccess)
+        return bail(cuda_fail(ctx, cudaGetLastError(), "homogeneous table fill"));
+    rc = check_status(ctx);
+    if (rc) return bail(rc);
+    *out = ctx;
+    return FRW_OK;
+}
+
+// ---------------------------------------------------------------------------
+static bool box_ok(const frw_box &b)
+{
+    for (int a = 0; a < 3; a++)
+        if (!(b.lo[a] < b.hi[a]) || !std::isfinite(b.lo[a]) || !std::isfinite(b.hi[a])) return false;
+    return true;
+}
+
+static double box_gap(const double *lo1, const double *hi1, const double *lo2, const double *hi2)
+{
+    double d = 0.0;
+    for (int a = 0; a < 3; a++) {
+        const double t1 = lo2[a] - hi1[a], t2 = lo1[a] - hi2[a];
+        if (t1 > d) d = t1;
+        if (t2 > d) d = t2;
+    }
+    return d;
+}
+
+static float ulpf(float x)
+{
+    return std::nextafter(x, INFINITY) - x;
+}
+
+extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *conductors, int32_t n_cond,
+                                  const double *eps_r, int32_t n_mat, int32_t background_mat,
+                                  const frw_block *blocks, int32_t n_blocks, int32_t *structure_id)
+{
+    if (!ctx || !domain || !conductors || !eps_r || !structure_id) return FRW_EINVAL;
+    if (n_cond < 1 || n_mat < 1 || n_blocks < 0 || (n_blocks > 0 && !blocks))
+        return fail(ctx, FRW_EINVAL, "need at least one conductor and one material");
+    if (background_mat < 0 || background_mat >= n_mat) return fail(ctx, FRW_EINVAL, "background material out of range");
+    if (!box_ok(*domain)) return fail(ctx, FRW_EINVAL, "degenerate domain");
+    for (int k = 0; k < n_cond; k++) {
+        if (!box_ok(conductors[k])) return fail(ctx, FRW_EINVAL, "degenerate conductor box");
+        for (int a = 0; a < 3; a++)
+            if (!(conductors[k].lo[a] > domain->lo[a] && conductors[k].hi[a] < domain->hi[a]))
+                return fail(ctx, FRW_EINVAL, "conductor not strictly inside the domain");
+    }
+    for (int k = 0; k < n_cond; k++)
+        for (int l = k + 1; l < n_cond; l++)
+            if (!(box_gap(conductors[k].lo, conductors[k].hi, conductors[l].lo, conductors[l].hi) > 0.0))
+                return fail(ctx, FRW_EINVAL, "conductors touch or overlap");
+    for (int b = 0; b < n_blocks; b++) {
+        if (!box_ok({{blocks[b].lo[0], blocks[b].lo[1], blocks[b].lo[2]}, {blocks[b].hi[0], blocks[b].hi[1], blocks[b].hi[2]}}))
+            return fail(ctx, FRW_EINVAL, "degenerate dielectric block");
+        if (blocks[b].mat < 0 || blocks[b].mat >= n_mat) return fail(ctx, FRW_EINVAL, "block material out of range");
+    }
+    std::vector<uint8_t> map;
+    int rc = register_materials(ctx, eps_r, n_mat, map);
+    if (rc) return rc;
+    // slot in the structure table
+    int sid = -1;
+    for (size_t i = 0; i < ctx->structs.size(); i++)
+        if (!ctx->structs[i].live) sid = (int)i;
+    if (sid < 0) {
+        if ((int)ctx->structs.size() >= ctx->struct_cap) return fail(ctx, FRW_ECAPACITY, "too many structures");
+        ctx->structs.emplace_back();
+        sid = (int)ctx->structs.size() - 1;
+    }
+    HostStructure &H = ctx->structs[sid];
+    H = HostStructure();
+    H.n_c = n_cond;
+    H.n_b = n_blocks;
+    H.c_lo.resize(3 * (size_t)n_cond);
+    H.c_hi.resize(3 * (size_t)n_cond);
+    for (int k = 0; k < n_cond; k++)
+        for (int a = 0; a < 3; a++) {
+            H.c_lo[3 * k + a] = conductors[k].lo[a];
+            H.c_hi[3 * k + a] = conductors[k].hi[a];
+        }
+    DevStructure &D = H.d;
+    memset(&D, 0, sizeof(D));
+    D.n_c = n_cond;
+    D.n_b = n_blocks;
+    D.bg = map[background_mat];
+    double edge = 0.0, maxabs = 0.0;
+    for (int a = 0; a < 3; a++) {
+        D.dom_lo[a] = H.dom_lo[a] = domain->lo[a];
+        D.dom_hi[a] = H.dom_hi[a] = domain->hi[a];
+        D.dom_lo_f[a] = (float)domain->lo[a];
+        D.dom_hi_f[a] = (float)domain->hi[a];
+        edge = std::max(edge, domain->hi[a] - domain->lo[a]);
+        maxabs = std::max(maxabs, std::max(std::fabs(domain->lo[a]), std::fabs(domain->hi[a])));
+    }
+    D.tau = 1e-9 * edge;
+    const float m = 8.0f * ulpf((float)maxabs);
+    D.margin_f = m;
+    D.tau_f = std::max((float)(1e-9 * edge), 2.0f * m);
+    // SoA device copies
+    std::vector<double> clo(3 * (size_t)n_cond), chi(3 * (size_t)n_cond);
+    std::vector<float> clof(3 * (size_t)n_cond), chif(3 * (size_t)n_cond);
+    for (int k = 0; k < n_cond; k++)
+        for (int a = 0; a < 3; a++) {
+            clo[(size_t)a * n_cond + k] = conductors[k].lo[a];
+            chi[(size_t)a * n_cond + k] = conductors[k].hi[a];
+            clof[(size_t)a * n_cond + k] = (float)conductors[k].lo[a];
+            chif[(size_t)a * n_cond + k] = (float)conductors[k].hi[a];
+        }
+    std::vector<double> blo(3 * (size_t)n_blocks), bhi(3 * (size_t)n_blocks);
+    std::vector<float> blof(3 * (size_t)n_blocks), bhif(3 * (size_t)n_blocks);
+    std::vector<uint8_t> bm((size_t)n_blocks);
+    for (int b = 0; b < n_blocks; b++) {
+        for (int a = 0; a < 3; a++) {
+            blo[(size_t)a * n_blocks + b] = blocks[b].lo[a];
+            bhi[(size_t)a * n_blocks + b] = blocks[b].hi[a];
+            blof[(size_t)a * n_blocks + b] = (float)blocks[b].lo[a];
+            bhif[(size_t)a * n_blocks + b] = (float)blocks[b].hi[a];
+        }
+        bm[b] = map[blocks[b].mat];
+    }
+    auto up = [&](auto **dst, const auto &src) -> int {
+        using E = typename std::remove_reference<decltype(src)>::type::value_type;
+        E *p = nullptr;
+        int r = dalloc(ctx, &p, src.size(), H.dev);
+        if (r) return r;
+        if (!src.empty()) {
+            cudaError_t e = cudaMemcpyAsync(p, src.data(), src.size() * sizeof(E), cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "structure upload");
+        }
+        *dst = p;
+        return FRW_OK;
+    };
+    if ((rc = up((double **)&D.c_lo, clo)) || (rc = up((double **)&D.c_hi, chi)) ||
+        (rc = up((float **)&D.c_lo_f, clof)) || (rc = up((float **)&D.c_hi_f, chif)) ||
+        (rc = up((double **)&D.b_lo, blo)) || (rc = up((double **)&D.b_hi, bhi)) ||
+        (rc = up((float **)&D.b_lo_f, blof)) || (rc = up((float **)&D.b_hi_f, bhif)) ||
+        (rc = up((uint8_t **)&D.b_mat, bm))) {
+        for (void *p : H.dev) cudaFree(p);
+        H.dev.clear();
+        return rc;
+    }
+    CK(cudaMemcpyAsync(ctx->d_structs + sid, &D, sizeof(DevStructure), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    H.live = true;
+    *structure_id = sid;
+    return FRW_OK;
+}
+
+extern "C" int frw_unload_structure(frw_ctx *ctx, int32_t sid)
+{
+    if (!ctx) return FRW_EINVAL;
+    if (sid < 0 || sid >= (int)ctx->structs.size() || !ctx->structs[sid].live) return FRW_ENOTFOUND;
+    cudaStreamSynchronize(ctx->stream);
+    for (void *p : ctx->structs[sid].dev) cudaFree(p);
+    ctx->structs[sid] = HostStructure();
+    return FRW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian surface of a master (reading: box grown by frac x the smallest
+// L-infinity gap to another conductor or a wall; point uniform by area).
+static void gauss_setup(const HostStructure &H, int master, double frac, DevJob &J)
+{
+    const double *lo = &H.c_lo[3 * (size_t)master], *hi = &H.c_hi[3 * (size_t)master];
+    double gap = INFINITY;
+    for (int k = 0; k < H.n_c; k++) {
+        if (k == master) continue;
+        const double d = box_gap(lo, hi, &H.c_lo[3 * (size_t)k], &H.c_hi[3 * (size_t)k]);
+        if (d < gap) gap = d;
+    }
+    for (int a = 0; a < 3; a++) {
+        double t = lo[a] - H.dom_lo[a];
+        if (t < gap) gap = t;
+        t = H.dom_hi[a] - hi[a];
+        if (t < gap) gap = t;
+    }
+    const double dg = frac * gap;
+    for (int a = 0; a < 3; a++) {
+        J.g_lo[a] = lo[a] - dg;
+        J.g_hi[a] = hi[a] + dg;
+    }
+    const double ex = J.g_hi[0] - J.g_lo[0], ey = J.g_hi[1] - J.g_lo[1], ez = J.g_hi[2] - J.g_lo[2];
+    const double fa[6] = {ey * ez, ey * ez, ex * ez, ex * ez, ex * ey, ex * ey};
+    double acc = 0.0;
+    for (int f = 0; f < 6; f++) {
+        acc += fa[f];
+        J.cum[f] = acc;
+    }
+    J.area = acc;
+}
+
+typedef __int128 i128;
+
+static i128 rd128(const unsigned long long *p)
+{
+    const unsigned __int128 u = ((unsigned __int128)p[1] << 64) | (unsigned __int128)p[0];
+    return (i128)u;
+}
+
+struct JobRun {
+    frw_job desc;
+    uint64_t walk_begin = 0;         // first walk id (resume / shard offset)
+    int record = 0;                  // write per-walk records (job 0 only)
+    DevJob d;
+    uint64_t n_batches = 0;
+    uint64_t prefix = 0;             // complete batches examined so far
+    uint64_t used_batches = 0;       // batches in the estimate
+    bool converged = false;
+    bool done = false;
+    std::vector<i128> S1, S2;        // running prefix sums
+    uint64_t walks = 0;
+    uint64_t ex[ACC_EXTRA] = {0};
+};
+
+// relative standard error rule of the stop criterion
+static bool sigma_ok(const std::vector<i128> &S1, const std::vector<i128> &S2, uint64_t n, int nc, int master,
+                     double target)
+{
+    if (n < 2) return false;
+    const double nn = (double)n;
+    auto val = [&](int k, double *c, double *se) {
+        const double s1 = (double)S1[k] / ACC_S1_SCALE, s2 = (double)S2[k] / ACC_S2_SCALE;
+        *c = s1 / nn;
+        const double v = (s2 - s1 * s1 / nn) / (nn * (nn - 1.0));
+        *se = std::sqrt(v > 0 ? v : 0);
+    };
+    double ci, si;
+    val(master, &ci, &si);
+    if (!(ci != 0.0 && si <= target * std::fabs(ci))) return false;
+    int jb = -1;
+    double cb = 0.0;
+    for (int j = 0; j < nc; j++) {
+        if (j == master) continue;
+        double c, s;
+        val(j, &c, &s);
+        if (jb < 0 || std::fabs(c) > cb) {
+            jb = j;
+            cb = std::fabs(c);
+        }
+    }
+    if (jb >= 0) {
+        double c, s;
+        val(jb, &c, &s);
+        if (!(c != 0.0 && s <= target * std::fabs(c))) return false;
+    }
+    return true;
+}
+
+// Run a set of jobs to completion on the device.  Records (optional) are
+// written for job 0 only (frw_walk_records).
+static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, RecArrays *rec, frw_stats *stats_out)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const int nj = (int)jobs.size();
+    uint64_t total_walks = 0;
+    uint64_t acc_words = 0;
+    for (auto &j : jobs) {
+        const HostStructure &H = ctx->structs[j.desc.structure_id];
+        DevJob &d = j.d;
+        memset(&d, 0, sizeof(d));
+        d.sid = j.desc.structure_id;
+        d.master = j.desc.master;
+        d.n_c = H.n_c;
+        d.key0 = (uint32_t)ctx->opt.seed;
+        d.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ (uint32_t)j.desc.request_id;
+        gauss_setup(H, j.desc.master, ctx->opt.gauss_offset_frac, d);
+        d.walk_count = j.desc.walk_budget;
+        d.walk_begin = j.walk_begin;
+        d.record = j.record;
+        d.rec_base = 0;
+        d.batch = j.desc.batch ? j.desc.batch : 16384;
+        d.acc_stride = acc_stride_for(H.n_c);
+        d.acc_base = acc_words;
+        j.n_batches = (d.walk_count + d.batch - 1) / d.batch;
+        acc_words += j.n_batches * d.acc_stride;
+        total_walks += d.walk_count;
+        j.S1.assign(H.n_c + 1, 0);
+        j.S2.assign(H.n_c + 1, 0);
+    }
+    std::vector<void *> tmp;
+    auto cleanup = [&]() {
+        for (void *p : tmp) cudaFree(p);
+    };
+    DevJob *d_jobs = nullptr;
+    unsigned long long *d_next = nullptr, *d_acc = nullptr;
+    int *d_cancel = nullptr;
+    int rc;
+    if ((rc = dalloc(ctx, &d_jobs, nj, tmp)) || (rc = dalloc(ctx, &d_next, nj, tmp)) ||
+        (rc = dalloc(ctx, &d_cancel, nj, tmp)) || (rc = dalloc(ctx, &d_acc, std::max<uint64_t>(acc_words, 1), tmp))) {
+        cleanup();
+        return rc;
+    }
+    std::vector<DevJob> hj(nj);
+    for (int i = 0; i < nj; i++) hj[i] = jobs[i].d;
+    cudaStream_t st = ctx->stream;
+#define CKR(call)                                     \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            int r_ = cuda_fail(ctx, e_, #call);       \
+            cleanup();                                \
+            return r_;                                \
+        }                                             \
+    } while (0)
+    CKR(cudaMemcpyAsync(d_jobs, hj.data(), sizeof(DevJob) * nj, cudaMemcpyHostToDevice, st));
+    CKR(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long) * nj, st));
+    CKR(cudaMemsetAsync(d_cancel, 0, sizeof(int) * nj, st));
+    CKR(cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long) * std::max<uint64_t>(acc_words, 1), st));
+    CKR(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
+    CKR(cudaMemsetAsync(ctx->mwq_ctr, 0, sizeof(uint32_t) * 2, st));
+    CKR(cudaMemsetAsync(ctx->tc.fillq_count, 0, sizeof(uint32_t) * 2, st));
+    EngineView E = make_view(ctx);
+    uint64_t ns = std::max<uint64_t>(1024, ((total_walks + 255) / 256) * 256);
+    E.NS = (uint32_t)std::min<uint64_t>(ctx->NS, ns);
+    E.n_jobs = nj;
+    E.jobs = d_jobs;
+    E.job_next = d_next;
+    E.job_cancel = d_cancel;
+    E.acc = d_acc;
+    if (rec) E.rec = *rec;
+    CKR(launch_init_slots(E, st));
+    uint64_t rounds = 0;
+    std::vector<unsigned long long> hb;
+    bool any_sigma = false;
+    for (auto &j : jobs) any_sigma |= j.desc.sigma_target > 0.0;
+    for (;;) {
+        CKR(launch_round(E, ctx->shape, st));
+        rounds++;
+        rc = check_status(ctx);
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+        const bool finished = ctx->h_status[STAT_ACTIVE] == 0;
+        if (any_sigma) {
+            for (int i = 0; i < nj; i++) {
+                JobRun &j = jobs[i];
+                if (j.desc.sigma_target <= 0.0 || j.converged) continue;
+                const uint32_t strd = j.d.acc_stride;
+                const int nc1 = j.d.n_c + 1;
+                while (j.prefix < j.n_batches && !j.converged) {
+                    const uint64_t look = std::min<uint64_t>(8, j.n_batches - j.prefix);
+                    hb.resize(look * strd);
+                    CKR(cudaMemcpyAsync(hb.data(), d_acc + j.d.acc_base + j.prefix * strd,
+                                        sizeof(unsigned long long) * look * strd, cudaMemcpyDeviceToHost, st));
+                    CKR(cudaStreamSynchronize(st));
+                    uint64_t adv = 0;
+                    for (uint64_t b = 0; b < look; b++) {
+                        const unsigned long long *blk = hb.data() + b * strd;
+                        const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - (j.prefix + b) * j.d.batch);
+                        if (blk[4 * nc1] != bsz) break;
+                        for (int k = 0; k < nc1; k++) {
+                            j.S1[k] += rd128(blk + 2 * k);
+                            j.S2[k] += rd128(blk + 2 * nc1 + 2 * k);
+                        }
+                        for (int x = 0; x < ACC_EXTRA; x++) j.ex[x] += blk[4 * nc1 + x];
+                        j.walks += bsz;
+                        adv++;
+                        const bool full_batch = bsz == j.d.batch;
+                        if (full_batch && sigma_ok(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, j.desc.sigma_target)) {
+                            j.converged = true;
+                            break;
+                        }
+                    }
+                    j.prefix += adv;
+                    if (j.converged) {
+                        j.used_batches = j.prefix;
+                        const int one = 1;
+                        CKR(cudaMemcpyAsync(d_cancel + i, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+                        CKR(cudaStreamSynchronize(st));
+                    }
+                    if (adv < look) break;
+                }
+            }
+        }
+        if (finished) break;
+        if (rounds > 100000000ull) {
+            cleanup();
+            return fail(ctx, FRW_ETIMEOUT, "engine did not finish");
+        }
+    }
+    // budget-only jobs (and sigma jobs that never converged): take every batch
+    for (int i = 0; i < nj; i++) {
+        JobRun &j = jobs[i];
+        if (j.converged) continue;
+        const uint32_t strd = j.d.acc_stride;
+        const int nc1 = j.d.n_c + 1;
+        const uint64_t rest = j.n_batches - j.prefix;
+        if (rest) {
+            hb.resize(rest * strd);
+            CKR(cudaMemcpyAsync(hb.data(), d_acc + j.d.acc_base + j.prefix * strd,
+                                sizeof(unsigned long long) * rest * strd, cudaMemcpyDeviceToHost, st));
+            CKR(cudaStreamSynchronize(st));
+            for (uint64_t b = 0; b < rest; b++) {
+                const unsigned long long *blk = hb.data() + b * strd;
+                for (int k = 0; k < nc1; k++) {
+                    j.S1[k] += rd128(blk + 2 * k);
+                    j.S2[k] += rd128(blk + 2 * nc1 + 2 * k);
+                }
+                for (int x = 0; x < ACC_EXTRA; x++) j.ex[x] += blk[4 * nc1 + x];
+                j.walks += blk[4 * nc1];
+            }
+        }
+        j.used_batches = j.n_batches;
+        j.prefix = j.n_batches;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats_out) {
+        for (int i = 0; i < nj; i++) {
+            frw_stats &s = stats_out[i];
+            memset(&s, 0, sizeof(s));
+            const JobRun &j = jobs[i];
+            s.walks = j.walks;
+            s.hops = j.ex[1];
+            s.micro_steps = j.ex[2];
+            s.strat_hops = j.ex[3];
+            s.hom_hops = j.ex[4];
+            s.mw_hops = j.ex[5];
+            s.branch[0] = j.ex[6];
+            s.branch[1] = j.ex[7];
+            s.branch[2] = j.ex[8];
+            s.truncated = j.ex[9];
+            s.tables_built = ctx->h_status[STAT_BUILT];
+            s.rounds = rounds;
+            s.seconds = secs;
+        }
+    }
+    cleanup();
+    return FRW_OK;
+}
+
+static void row_from(const JobRun &j, double *C, double *se)
+{
+    const int nc1 = j.d.n_c + 1;
+    const double n = (double)j.walks;
+    for (int k = 0; k < nc1; k++) {
+        const double s1 = (double)j.S1[k] / ACC_S1_SCALE, s2 = (double)j.S2[k] / ACC_S2_SCALE;
+        if (C) C[k] = n > 0 ? s1 / n : 0.0;
+        if (se) {
+            const double v = n > 1 ? (s2 - s1 * s1 / n) / (n * (n - 1.0)) : 0.0;
+            se[k] = std::sqrt(v > 0 ? v : 0);
+        }
+    }
+}
+
+static int check_job(frw_ctx *ctx, const frw_job &j)
+{
+    if (j.structure_id < 0 || j.structure_id >= (int)ctx->structs.size() || !ctx->structs[j.structure_id].live)
+        return fail(ctx, FRW_ENOTFOUND, "unknown structure id");
+    if (j.master < 0 || j.master >= ctx->structs[j.structure_id].n_c) return fail(ctx, FRW_EINVAL, "master out of range");
+    if (!(j.sigma_target >= 0.0)) return fail(ctx, FRW_EINVAL, "negative sigma target");
+    return FRW_OK;
+}
+
+extern "C" int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs, double *C_rows,
+                                 double *stderr_rows, frw_stats *stats)
+{
+    if (!ctx || (n_jobs > 0 && !jobs) || n_jobs < 0) return FRW_EINVAL;
+    if (n_jobs == 0) return FRW_OK;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<JobRun> runs(n_jobs);
+    for (int i = 0; i < n_jobs; i++) {
+        int rc = check_job(ctx, jobs[i]);
+        if (rc) return rc;
+        runs[i].desc = jobs[i];
+    }
+    std::vector<frw_stats> st(n_jobs);
+    const bool any_walks = [&] {
+        for (int i = 0; i < n_jobs; i++)
+            if (jobs[i].walk_budget) return true;
+        return false;
+    }();
+    if (any_walks) {
+        int rc = run_jobs(ctx, runs, nullptr, st.data());
+        if (rc) return rc;
+    } else {
+        for (int i = 0; i < n_jobs; i++) {
+            runs[i].d.n_c = ctx->structs[jobs[i].structure_id].n_c;
+            runs[i].S1.assign(runs[i].d.n_c + 1, 0);
+            runs[i].S2.assign(runs[i].d.n_c + 1, 0);
+            memset(&st[i], 0, sizeof(frw_stats));
+        }
+    }
+    bool notconv = false;
+    size_t off = 0;
+    for (int i = 0; i < n_jobs; i++) {
+        const int nc1 = runs[i].d.n_c + 1;
+        row_from(runs[i], C_rows ? C_rows + off : nullptr, stderr_rows ? stderr_rows + off : nullptr);
+        off += nc1;
+        if (stats) stats[i] = st[i];
+        if (jobs[i].sigma_target > 0.0 && !runs[i].converged) notconv = true;
+    }
+    return notconv ? FRW_ENOTCONV : FRW_OK;
+}
+
+extern "C" int frw_extract(frw_ctx *ctx, int32_t sid, int32_t master, const frw_extract_params *p, double *C_row,
+                           double *stderr_row, frw_stats *stats)
+{
+    if (!ctx || !p) return FRW_EINVAL;
+    frw_job j;
+    j.structure_id = sid;
+    j.master = master;
+    j.walk_budget = p->walk_budget;
+    j.sigma_target = p->sigma_target;
+    j.request_id = p->request_id;
+    j.batch = p->batch;
+    if (p->walk_begin == 0) return frw_extract_batch(ctx, &j, 1, C_row, stderr_row, stats);
+    // shard / resume: walk ids start at walk_begin (batches and the stop rule count from there)
+    int rc = check_job(ctx, j);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<JobRun> runs(1);
+    runs[0].desc = j;
+    runs[0].walk_begin = p->walk_begin;
+    frw_stats st;
+    if (j.walk_budget) {
+        rc = run_jobs(ctx, runs, nullptr, &st);
+        if (rc) return rc;
+    } else {
+        runs[0].d.n_c = ctx->structs[sid].n_c;
+        runs[0].S1.assign(runs[0].d.n_c + 1, 0);
+        runs[0].S2.assign(runs[0].d.n_c + 1, 0);
+        memset(&st, 0, sizeof(st));
+    }
+    row_from(runs[0], C_row, stderr_row);
+    if (stats) *stats = st;
+    return (j.sigma_target > 0.0 && !runs[0].converged) ? FRW_ENOTCONV : FRW_OK;
+}
+
+extern "C" int frw_walk_records(frw_ctx *ctx, int32_t sid, int32_t master, uint64_t request_id, uint64_t walk_begin,
+                                uint64_t n_walks, double *omega, int32_t *electrode, uint32_t *hops,
+                                uint64_t *micro_steps, int32_t *branch)
+{
+    if (!ctx) return FRW_EINVAL;
+    frw_job j;
+    j.structure_id = sid;
+    j.master = master;
+    j.walk_budget = n_walks;
+    j.sigma_target = 0.0;
+    j.request_id = request_id;
+    j.batch = 0;
+    int rc = check_job(ctx, j);
+    if (rc) return rc;
+    if (n_walks == 0) return FRW_OK;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<void *> tmp;
+    RecArrays R;
+    if ((rc = dalloc(ctx, &R.omega, n_walks, tmp)) || (rc = dalloc(ctx, &R.k, n_walks, tmp)) ||
+        (rc = dalloc(ctx, &R.hops, n_walks, tmp)) || (rc = dalloc(ctx, &R.steps, n_walks, tmp)) ||
+        (rc = dalloc(ctx, &R.branch, n_walks, tmp))) {
+        for (void *p : tmp) cudaFree(p);
+        return rc;
+    }
+    std::vector<JobRun> runs(1);
+    runs[0].desc = j;
+    runs[0].record = 1;
+    runs[0].walk_begin = walk_begin;
+    frw_stats st;
+    rc = run_jobs(ctx, runs, &R, &st);
+    if (!rc) {
+        cudaError_t e = cudaSuccess;
+        if (omega && e == cudaSuccess) e = cudaMemcpy(omega, R.omega, sizeof(double) * n_walks, cudaMemcpyDeviceToHost);
+        if (electrode && e == cudaSuccess) e = cudaMemcpy(electrode, R.k, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost);
+        if (hops && e == cudaSuccess) e = cudaMemcpy(hops, R.hops, sizeof(uint32_t) * n_walks, cudaMemcpyDeviceToHost);
+        if (micro_steps && e == cudaSuccess) e = cudaMemcpy(micro_steps, R.steps, sizeof(uint64_t) * n_walks, cudaMemcpyDeviceToHost);
+        if (branch && e == cudaSuccess) e = cudaMemcpy(branch, R.branch, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "record copy");
+    }
+    for (void *p : tmp) cudaFree(p);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t *d_cubes,
+                                   const double *eps_r, int32_t n_mat, uint64_t samples_per_cube, uint64_t request_id,
+                                   uint32_t *d_exit, uint32_t *d_steps)
+{
+    if (!ctx || (n_cubes > 0 && !d_cubes) || !eps_r || n_mat < 1 || n_mat > FRW_MAX_MATERIALS) return FRW_EINVAL;
+    if (N != ctx->opt.N) return fail(ctx, FRW_EINVAL, "cube lattice edge must equal the context's N");
+    if (n_cubes <= 0 || samples_per_cube == 0) return FRW_OK;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<uint8_t> map;
+    int rc = register_materials(ctx, eps_r, n_mat, map);
+    if (rc) return rc;
+    std::vector<void *> tmp;
+    unsigned long long *d_head = nullptr;
+    if ((rc = dalloc(ctx, &d_head, 1, tmp))) return rc;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st);
+    const uint32_t key0 = (uint32_t)ctx->opt.seed, key1 = (uint32_t)(ctx->opt.seed >> 32) ^ (uint32_t)request_id;
+    if (e == cudaSuccess)
+        e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, map.data(), ctx->d_W, d_exit,
+                            d_steps, d_head, ctx->status + STAT_ERR, ctx->shape, st);
+    if (e != cudaSuccess) {
+        for (void *p : tmp) cudaFree(p);
+        return cuda_fail(ctx, e, "MicroWalk cube launch");
+    }
+    rc = check_status(ctx);
+    for (void *p : tmp) cudaFree(p);
+    return rc;
+}
+
+extern "C" int frw_table(frw_ctx *ctx, int32_t kind, const int32_t *profile, const double *eps_r, int32_t n_mat,
+                         uint32_t *thr, uint8_t *neg, double *total, double *values)
+{
+    if (!ctx || kind < 0 || kind > 4) return FRW_EINVAL;
+    const int N = ctx->opt.N;
+    const bool hom = (kind == TAB_SGF_HOM || kind == TAB_FLUX_HOM);
+    uint32_t prof[4] = {0, 0, 0, 0};
+    CK(cudaSetDevice(ctx->device));
+    if (!hom) {
+        if (!profile || !eps_r || n_mat < 1) return FRW_EINVAL;
+        std::vector<uint8_t> map;
+        int rc = register_materials(ctx, eps_r, n_mat, map);
+        if (rc) return rc;
+        for (int i = 0; i < N; i++) {
+            if (profile[i] < 0 || profile[i] >= n_mat) return fail(ctx, FRW_EINVAL, "profile material out of range");
+            prof[i >> 3] |= (uint32_t)map[profile[i]] << (4 * (i & 7));
+        }
+    }
+    std::vector<void *> tmp;
+    const size_t P = 6 * (size_t)N * N, P32 = (P + 31) / 32;
+    uint32_t *d_thr = nullptr, *d_sgn = nullptr;
+    double *d_k = nullptr, *d_v = nullptr;
+    int rc;
+    if ((rc = dalloc(ctx, &d_thr, P, tmp)) || (rc = dalloc(ctx, &d_sgn, P32, tmp)) || (rc = dalloc(ctx, &d_k, 1, tmp)) ||
+        (rc = dalloc(ctx, &d_v, P, tmp))) {
+        for (void *p : tmp) cudaFree(p);
+        return rc;
+    }
+    EngineView E = make_view(ctx);
+    E.tc.thr = d_thr;
+    E.tc.sgn = d_sgn;
+    E.tc.ktot = d_k;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st);
+    if (e == cudaSuccess) e = launch_fill_one(E, (uint32_t)kind, prof, 0, d_v, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    std::vector<uint32_t> hs(P32);
+    if (e == cudaSuccess && thr) e = cudaMemcpy(thr, d_thr, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), d_sgn, sizeof(uint32_t) * P32, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && total) e = cudaMemcpy(total, d_k, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && values) e = cudaMemcpy(values, d_v, sizeof(double) * P, cudaMemcpyDeviceToHost);
+    for (void *p : tmp) cudaFree(p);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "table fill");
+    if (neg)
+        for (size_t n = 0; n < P; n++) neg[n] = (hs[n >> 5] >> (n & 31)) & 1u;
+    return FRW_OK;
+}
