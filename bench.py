@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Throughput of the FRW + MicroWalk capacitance engine on the 3-layer
+interconnect workload (24 wires with 10 nm eps-7.0 shells in an eps-2.7 ILD plus
+12 eps-5 LDE blocks, lattice N = 24, the three layer masters, 0.5 % 1-sigma
+target, budget 1e7 walks per master).
+
+One step = one full extraction of the three capacitance rows: every row of the
+hot path (walk issue, Gaussian sampling, first cube and weight, cube sizing,
+hybrid dispatch, analytical route, MicroWalk, absorption, exact accumulation and
+the stop rule) runs on the GPU for every walk.  The structure is loaded once
+and stays resident in HBM; each step uses a fresh request id (new random walks).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_09730_gb300 import workloads as W  # noqa: E402
+
+METRIC = "FRW walks/s at 0.5% 1-sigma (interconnect, N=24)"
+UNIT = "walks/s"
+INT_OPS_PER_MICRO_STEP = 45   # algorithmic integer ops of one MicroWalk step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--N", type=int, default=24)
+    ap.add_argument("--sigma", type=float, default=0.005)
+    ap.add_argument("--budget", type=int, default=10_000_000)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(s, masters, N, seconds):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same
+    workload (walks of the first master until `seconds` of CPU time)."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    walks = 0
+    chunk = 200
+    i = 0
+    while time.perf_counter() - t0 < seconds:
+        O.frw_run(s, masters[i % len(masters)], chunk, N=N, seed=0, request=900 + i, records=False)
+        walks += chunk
+        i += 1
+    dt = time.perf_counter() - t0
+    return {"value": walks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{walks} walks ({i} chunks of {chunk}, masters {list(masters)}) of the same interconnect "
+                      f"structure at N={N}, FP64, single thread, {dt:.1f} s"}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    s = W.interconnect(0)
+    masters = list(s.masters)
+    from oracle import oracle as O
+    O.build()
+    per_step = 100
+    for w in range(a.warmup):
+        O.frw_run(s, masters[w % 3], 20, N=a.N, seed=0, request=500 + w, records=False)
+    t0 = time.perf_counter()
+    walks = 0
+    for k in range(a.steps):
+        O.frw_run(s, masters[k % 3], per_step, N=a.N, seed=0, request=600 + k, records=False)
+        walks += per_step
+    dt = time.perf_counter() - t0
+    v = walks / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"interconnect 3-layer/24-wire, N={a.N}, {per_step} walks per step (bounded sample)",
+                       "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{walks} walks in {a.steps} steps of {per_step}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def structure_bytes(s):
+    return (s.cond_lo.nbytes + s.cond_hi.nbytes + s.block_lo.nbytes + s.block_hi.nbytes + s.block_mat.nbytes +
+            s.eps.nbytes + 48 + 40 * len(s.masters))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    from paper_2507_09730_gb300 import binding as B
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = B.FRW_FP32_GEOM if a.precision == "fp32" else B.FRW_FP64_GEOM
+    ctx = B.Context(local, N=a.N, precision=prec, seed=0)
+    stream = torch.cuda.current_stream()
+    B.frw_set_stream(ctx.ctx, stream.cuda_stream)
+    s = W.interconnect(0)
+    sid = ctx.load(s)
+    masters = list(s.masters)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def jobs_for(step):
+        rq = 1_000_000 * (rank + 1) + step
+        return [dict(structure_id=sid, master=m, walk_budget=a.budget, sigma_target=a.sigma,
+                     request_id=rq * 4 + i, batch=a.batch) for i, m in enumerate(masters)]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for w in range(a.warmup):
+        ctx.extract_batch(jobs_for(10_000 + w))
+        flush.zero_()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    agg = dict(walks=0, micro=0, mw_ms=0.0, geom_ms=0.0, fill_ms=0.0, launches=0, hops=0, mw_hops=0, strat=0,
+               hom=0, rounds=0, tables=0, mw_jobs=0)
+    rows = None
+    ev0.record(stream)
+    for k in range(a.steps):
+        res, conv = ctx.extract_batch(jobs_for(k))
+        for C, se, st in res:
+            agg["walks"] += st["walks"]
+            agg["micro"] += st["micro_steps"]
+            agg["hops"] += st["hops"]
+            agg["mw_hops"] += st["mw_hops"]
+            agg["strat"] += st["strat_hops"]
+            agg["hom"] += st["hom_hops"]
+        st0 = res[0][2]
+        agg["mw_ms"] += st0["mw_ms"]
+        agg["geom_ms"] += st0["geom_ms"]
+        agg["fill_ms"] += st0["fill_ms"]
+        agg["launches"] += st0["launches"] + 1     # + the L2 flush
+        agg["rounds"] += st0["rounds"]
+        agg["tables"] += st0["tables_built"]
+        agg["mw_jobs"] += st0["mw_jobs"]
+        rows = res
+        flush.zero_()
+    ev1.record(stream)
+    ev1.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    clocks = clk.stop()
+    barrier()
+    t_all = elapsed
+    walks_all = agg["walks"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_all = float(t.item())
+        wt = torch.tensor([agg["walks"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(wt)
+        walks_all = int(wt.item())
+    value = walks_all / t_all
+
+    # end to end through the C ABI with host buffers: load (H2D), extract, rows back (D2H), unload
+    e2e = None
+    if not a.no_e2e:
+        h2d = structure_bytes(s)
+        d2h = 2 * 8 * (s.n_cond + 1) * len(masters) + 8 * 17 * len(masters)
+        barrier()
+        te0 = time.perf_counter()
+        ew = 0
+        for k in range(a.steps):
+            sid2 = ctx.load(s)
+            jb = jobs_for(50_000 + k)
+            for j in jb:
+                j["structure_id"] = sid2
+            res, _ = ctx.extract_batch(jb)
+            ew += sum(st["walks"] for _, _, st in res)
+            ctx.unload(sid2)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - te0
+        e2e = {"value": ew / te * (walks_all / max(1, agg["walks"])) if world > 1 else ew / te, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    pk, src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12          # Tint-op/s: 128 INT32 lanes per SM at max clock
+    mw_s = agg["mw_ms"] / 1e3
+    achieved = (INT_OPS_PER_MICRO_STEP * agg["micro"] / mw_s) / 1e12 if mw_s > 0 else None
+    roofline = {"kernel": "k_mw (MicroWalk)", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "Tint-op/s", "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
+                "peak_source": f"{n_sm} SMs x 128 INT32 lanes x {sm_max:.0f} MHz ({src} clock)",
+                "kernel_share": {"mw": agg["mw_ms"] / (1e3 * elapsed), "geom": agg["geom_ms"] / (1e3 * elapsed),
+                                 "fill": agg["fill_ms"] / (1e3 * elapsed)}}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * t_all / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "interconnect 3-layer/24-wire + shells + 12 LDE, N=%d, masters %s, sigma %.3g, "
+                                   "budget %d/master" % (a.N, masters, a.sigma, a.budget),
+                       "geometry": a.precision, "accumulate": "exact int128 (fp64 in/out)",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"weak x{world}"},
+            "micro_transitions_per_s": agg["micro"] * (walks_all / max(1, agg["walks"])) / t_all,
+            "hops_per_walk": agg["hops"] / max(1, agg["walks"]),
+            "mw_hop_fraction": agg["mw_hops"] / max(1, agg["hops"] - agg["walks"]),
+            "gpu_launches": agg["launches"], "roofline": roofline, "clocks": clocks}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not a.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(s, masters, a.N, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -114,6 +114,11 @@ typedef struct {
     uint64_t tables_built;     /* analytical tables filled on the device during the call */
     uint64_t rounds;           /* engine rounds (geometry + fill + MicroWalk launches) */
     double seconds;            /* wall time of the call */
+    double geom_ms;            /* device time of the geometry kernel (CUDA events, launch stream) */
+    double fill_ms;            /* ... of the table-fill kernel */
+    double mw_ms;              /* ... of the MicroWalk kernel */
+    uint64_t launches;         /* kernels launched by the call */
+    uint64_t mw_jobs;          /* MicroWalk transitions run by the MicroWalk kernel */
 } frw_stats;
 
 /* Fill *opt with defaults (N = 24, FP64 geometry, hybrid on, offset 0.5,

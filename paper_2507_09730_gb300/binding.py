@@ -51,7 +51,9 @@ class frw_job(ctypes.Structure):
 class frw_stats(ctypes.Structure):
     _fields_ = [("walks", c_uint64), ("hops", c_uint64), ("micro_steps", c_uint64), ("truncated", c_uint64),
                 ("branch", c_uint64 * 3), ("strat_hops", c_uint64), ("hom_hops", c_uint64),
-                ("mw_hops", c_uint64), ("tables_built", c_uint64), ("rounds", c_uint64), ("seconds", c_double)]
+                ("mw_hops", c_uint64), ("tables_built", c_uint64), ("rounds", c_uint64), ("seconds", c_double),
+                ("geom_ms", c_double), ("fill_ms", c_double), ("mw_ms", c_double), ("launches", c_uint64),
+                ("mw_jobs", c_uint64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "branch"}

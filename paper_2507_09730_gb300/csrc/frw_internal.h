@@ -49,6 +49,24 @@ struct DevStructure {
     const double *b_lo, *b_hi;
     const float *b_lo_f, *b_hi_f;
     const uint8_t *b_mat;
+    // index built at load time:
+    //  - uniform grid; each cell lists (ascending) every conductor that can be the
+    //    nearest electrode of some point of the cell (exact nearest query);
+    //  - per axis, slab prefix masks: L[a][s] = blocks with lo below the upper edge
+    //    of slab s, H[a][s] = blocks with hi above its lower edge, so that
+    //    L[a][slab(c+R)] & H[a][slab(c-R)] over the three axes is a superset of the
+    //    blocks meeting the cube [c-R, c+R], enumerated in priority order.
+    int gdim[3];
+    int sl_S, sl_words;
+    int pad2;
+    double g_org[3], g_inv[3];
+    float g_org_f[3], g_inv_f[3];
+    double sl_org[3], sl_inv[3];
+    float sl_org_f[3], sl_inv_f[3];
+    const uint32_t *g_off;     // [cells + 1]
+    const uint16_t *g_ids;
+    const uint32_t *sl_L;      // [3][S][words]
+    const uint32_t *sl_H;      // [3][S][words]
 };
 
 // One extraction job (request x master).
@@ -96,11 +114,16 @@ struct SlotArrays {
     double *omega;
 };
 
+// Per-walk records (one entry per walk id of every job of a run).  k starts at
+// REC_PENDING and is written last, when the walk finishes.
+constexpr int32_t REC_PENDING = (int32_t)0x80808080;
 struct RecArrays {
     double *omega;
     int32_t *k;
     uint32_t *hops;
-    uint64_t *steps;
+    uint32_t *steps;
+    uint32_t *cnt_sh;   // strat hops (low 16) | homogeneous hops (high 16)
+    uint32_t *cnt_mw;
     int32_t *branch;
 };
 
@@ -134,6 +157,7 @@ struct EngineView {
     const DevStructure *structs;
     const DevJob *jobs;
     unsigned long long *job_next;
+    unsigned long long *job_limit;   // issue limit per job (<= walk_count), set by the host
     int *job_cancel;
     unsigned long long *acc;
     RecArrays rec;
@@ -145,8 +169,10 @@ struct EngineView {
     const double *eps;     // [16]
     FillConsts fc;
     uint32_t *status;      // STAT_WORDS
-    int hop_budget;        // analytical hops per slot per round
-    int walk_budget;       // walks started per slot per round
+    // slots waiting for a walk (FRESH) or for a first-cube table (FIRST): read by
+    // the first-transition kernel from *_in, appended to *_out for the next round
+    uint32_t *fresh_in, *fresh_out;
+    uint32_t *fresh_in_count, *fresh_out_count;
 };
 
 // ---- launchers (frw_kernels.cu) ----
@@ -159,11 +185,17 @@ struct LaunchShape {
 };
 
 cudaError_t launch_init_slots(const EngineView &E, cudaStream_t st);
+cudaError_t launch_first(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 cudaError_t launch_round(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 cudaError_t launch_geom(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 cudaError_t launch_fill(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 cudaError_t launch_mw(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 cudaError_t launch_round_end(const EngineView &E, cudaStream_t st);
+// reduce batches [b0, b1) of job j from the walk records into the accumulator pool
+cudaError_t launch_reduce(const EngineView &E, int job, uint64_t b0, uint64_t b1, int nc, cudaStream_t st);
+// raise / set a job's issue limit (ids above the old limit that were claimed but
+// not run are handed out again) and put idle slots back to work
+cudaError_t launch_set_limit(const EngineView &E, int job, uint64_t limit, cudaStream_t st);
 // fill one table with an explicit key into entry `entry` of the cache arrays
 cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4],
                             uint32_t entry, double *values_out, cudaStream_t st);

@@ -14,12 +14,15 @@
 // No kernel waits on another kernel or on the host: ordering comes only from the
 // launch order on the stream.
 #include <cstdint>
+#include <cooperative_groups.h>
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 
 #include "frw_internal.h"
 
 namespace frw {
 
+namespace cg = cooperative_groups;
 #define FULL_MASK 0xffffffffu
 
 // ---------------------------------------------------------------------------
@@ -77,6 +80,11 @@ template <typename T> struct SView {
     T tau, margin;
     const T *clo, *chi, *blo, *bhi;
     const uint8_t *bmat;
+    int gdim[3], sl_S, sl_words;
+    T g_org[3], g_inv[3], sl_org[3], sl_inv[3];
+    const uint32_t *g_off;
+    const uint16_t *g_ids;
+    const uint32_t *sl_L, *sl_H;
 };
 
 template <typename T> __device__ __forceinline__ SView<T> sview(const DevStructure &S);
@@ -87,6 +95,12 @@ template <> __device__ __forceinline__ SView<double> sview<double>(const DevStru
     for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo[a]; v.dhi[a] = S.dom_hi[a]; }
     v.tau = S.tau; v.margin = 0.0;
     v.clo = S.c_lo; v.chi = S.c_hi; v.blo = S.b_lo; v.bhi = S.b_hi; v.bmat = S.b_mat;
+    for (int a = 0; a < 3; a++) {
+        v.gdim[a] = S.gdim[a]; v.g_org[a] = S.g_org[a]; v.g_inv[a] = S.g_inv[a];
+        v.sl_org[a] = S.sl_org[a]; v.sl_inv[a] = S.sl_inv[a];
+    }
+    v.sl_S = S.sl_S; v.sl_words = S.sl_words;
+    v.g_off = S.g_off; v.g_ids = S.g_ids; v.sl_L = S.sl_L; v.sl_H = S.sl_H;
     return v;
 }
 template <> __device__ __forceinline__ SView<float> sview<float>(const DevStructure &S)
@@ -96,11 +110,28 @@ template <> __device__ __forceinline__ SView<float> sview<float>(const DevStruct
     for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo_f[a]; v.dhi[a] = S.dom_hi_f[a]; }
     v.tau = S.tau_f; v.margin = S.margin_f;
     v.clo = S.c_lo_f; v.chi = S.c_hi_f; v.blo = S.b_lo_f; v.bhi = S.b_hi_f; v.bmat = S.b_mat;
+    for (int a = 0; a < 3; a++) {
+        v.gdim[a] = S.gdim[a]; v.g_org[a] = S.g_org_f[a]; v.g_inv[a] = S.g_inv_f[a];
+        v.sl_org[a] = S.sl_org_f[a]; v.sl_inv[a] = S.sl_inv_f[a];
+    }
+    v.sl_S = S.sl_S; v.sl_words = S.sl_words;
+    v.g_off = S.g_off; v.g_ids = S.g_ids; v.sl_L = S.sl_L; v.sl_H = S.sl_H;
     return v;
 }
 
+// cell / slab index of a coordinate (clamped; the host built the index with
+// margins that absorb the rounding of this computation)
+template <typename T> __device__ __forceinline__ int cell_of(T x, T org, T inv, int n)
+{
+    const T f = (x - org) * inv;
+    int i = (f > T(0)) ? (int)f : 0;
+    return i < n ? i : n - 1;
+}
+
 // L-infinity distance to the nearest electrode (conductor box or grounded wall);
-// who = conductor index (lowest index on ties) or n_c for the walls.
+// who = conductor index (lowest index on ties) or n_c for the walls.  The grid
+// cell of p lists, in ascending order, every conductor that can be nearest (or
+// tie) anywhere in the cell, so the result equals the scan over all conductors.
 template <typename T>
 __device__ T nearest_electrode(const SView<T> &S, const T p[3], int &who)
 {
@@ -108,7 +139,13 @@ __device__ T nearest_electrode(const SView<T> &S, const T p[3], int &who)
     T best = A::inf();
     int kb = -1;
     const int n = S.n_c;
-    for (int k = 0; k < n; k++) {
+    const int cx = cell_of(p[0], S.g_org[0], S.g_inv[0], S.gdim[0]);
+    const int cy = cell_of(p[1], S.g_org[1], S.g_inv[1], S.gdim[1]);
+    const int cz = cell_of(p[2], S.g_org[2], S.g_inv[2], S.gdim[2]);
+    const int cell = (cx * S.gdim[1] + cy) * S.gdim[2] + cz;
+    const uint32_t i0 = __ldg(&S.g_off[cell]), i1 = __ldg(&S.g_off[cell + 1]);
+    for (uint32_t i = i0; i < i1; i++) {
+        const int k = __ldg(&S.g_ids[i]);
         T d = T(0);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -179,7 +216,19 @@ __device__ void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeI
     int count = 0;
     int bg = S.bg;
     const int nb = S.n_b;
-    for (int b = 0; b < nb; b++) {
+    const int SS = S.sl_S, nw = S.sl_words;
+    const uint32_t *Lx = S.sl_L + (size_t)(0 * SS + cell_of(A::add(c[0], R), S.sl_org[0], S.sl_inv[0], SS)) * nw;
+    const uint32_t *Hx = S.sl_H + (size_t)(0 * SS + cell_of(A::sub(c[0], R), S.sl_org[0], S.sl_inv[0], SS)) * nw;
+    const uint32_t *Ly = S.sl_L + (size_t)(1 * SS + cell_of(A::add(c[1], R), S.sl_org[1], S.sl_inv[1], SS)) * nw;
+    const uint32_t *Hy = S.sl_H + (size_t)(1 * SS + cell_of(A::sub(c[1], R), S.sl_org[1], S.sl_inv[1], SS)) * nw;
+    const uint32_t *Lz = S.sl_L + (size_t)(2 * SS + cell_of(A::add(c[2], R), S.sl_org[2], S.sl_inv[2], SS)) * nw;
+    const uint32_t *Hz = S.sl_H + (size_t)(2 * SS + cell_of(A::sub(c[2], R), S.sl_org[2], S.sl_inv[2], SS)) * nw;
+    for (int wd = 0; wd < nw; wd++) {
+      uint32_t cand = __ldg(&Lx[wd]) & __ldg(&Hx[wd]) & __ldg(&Ly[wd]) & __ldg(&Hy[wd]) & __ldg(&Lz[wd]) &
+                      __ldg(&Hz[wd]);
+      while (cand) {
+        const int b = 32 * wd + __ffs(cand) - 1;
+        cand &= cand - 1u;
         T lo[3], hi[3];
         bool rej = false;
 #pragma unroll
@@ -206,6 +255,7 @@ __device__ void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeI
                                           ((uint32_t)r1[1] << 24),
                                       (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | ((uint32_t)m << 16));
         count++;
+      }
     }
     q.bg = bg;
     q.K = count;
@@ -324,7 +374,8 @@ __device__ int table_lookup(const TableCache &tc, uint32_t kind, const uint32_t 
     const uint32_t h = hash5(kind, prof);
     for (uint32_t probe = 0; probe < 64; probe++) {
         const uint32_t e = (h + probe) & (tc.cap - 1);
-        uint32_t st = ((volatile uint32_t *)tc.state)[e];
+        uint32_t st = cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(tc.state[e]).load(
+            cuda::memory_order_acquire);
         if (st == TE_EMPTY) {
             const uint32_t old = atomicCAS(&tc.state[e], TE_EMPTY, TE_CLAIMED);
             if (old == TE_EMPTY) {
@@ -339,7 +390,6 @@ __device__ int table_lookup(const TableCache &tc, uint32_t kind, const uint32_t 
             st = old;
         }
         if (st == TE_CLAIMED) return -1;
-        __threadfence();
         const volatile uint32_t *k = tc.keys + 5 * e;
         if (k[0] == kind && k[1] == prof[0] && k[2] == prof[1] && k[3] == prof[2] && k[4] == prof[3])
             return (st == TE_READY) ? (int)e : -1;
@@ -390,25 +440,6 @@ __device__ __forceinline__ void node_point(const T c[3], T R, int N, const int n
 }
 
 // ---------------------------------------------------------------------------
-// Exact 128-bit fixed-point accumulation (order-independent, so results are
-// bit-reproducible whatever the completion order of walks).
-__device__ __forceinline__ void acc_i128(unsigned long long *p, double v, double scale)
-{
-    const double s = rint(v * scale);
-    const double a = fabs(s);
-    const double ah = floor(a * 5.421010862427522e-20);   // * 2^-64
-    const double al = a - ah * 18446744073709551616.0;
-    unsigned long long lo = (unsigned long long)al, hi = (unsigned long long)ah;
-    if (s < 0) {
-        lo = ~lo + 1ull;
-        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
-    }
-    const unsigned long long old = atomicAdd(&p[0], lo);
-    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-    atomicAdd(&p[1], hi + carry);
-}
-
-// ---------------------------------------------------------------------------
 // Walk slot bookkeeping
 struct WalkState {
     uint32_t job, hop, cnt_sh, cnt_mw;
@@ -417,33 +448,18 @@ struct WalkState {
     double omega;
 };
 
+// A finished walk writes its record; batches are folded later by k_reduce, so
+// completion involves no shared counter.  k is written last.
 __device__ void finish_walk(const EngineView &E, const DevJob &J, const WalkState &w, int k)
 {
-    const uint64_t rel = w.walk - J.walk_begin;
-    const uint64_t g = rel / J.batch;
-    unsigned long long *acc = E.acc + J.acc_base + g * J.acc_stride;
-    const int nc1 = J.n_c + 1;
-    if (k >= 0) {
-        acc_i128(acc + 2 * k, w.omega, ACC_S1_SCALE);
-        acc_i128(acc + 2 * nc1 + 2 * k, w.omega * w.omega, ACC_S2_SCALE);
-    }
-    unsigned long long *ex = acc + 4 * nc1;
-    atomicAdd(&ex[0], 1ull);
-    atomicAdd(&ex[1], (unsigned long long)w.hop);
-    atomicAdd(&ex[2], (unsigned long long)w.steps);
-    atomicAdd(&ex[3], (unsigned long long)(w.cnt_sh & 0xffffu));
-    atomicAdd(&ex[4], (unsigned long long)(w.cnt_sh >> 16));
-    atomicAdd(&ex[5], (unsigned long long)w.cnt_mw);
-    if (w.branch >= 0 && w.branch < 3) atomicAdd(&ex[6 + w.branch], 1ull);
-    if (k < 0) atomicAdd(&ex[9], 1ull);
-    if (J.record) {
-        const uint64_t r = J.rec_base + rel;
-        E.rec.omega[r] = w.omega;
-        E.rec.k[r] = k;
-        E.rec.hops[r] = w.hop;
-        E.rec.steps[r] = w.steps;
-        E.rec.branch[r] = w.branch;
-    }
+    const uint64_t r = J.rec_base + (w.walk - J.walk_begin);
+    E.rec.omega[r] = w.omega;
+    E.rec.hops[r] = w.hop;
+    E.rec.steps[r] = (uint32_t)w.steps;
+    E.rec.cnt_sh[r] = w.cnt_sh;
+    E.rec.cnt_mw[r] = w.cnt_mw;
+    E.rec.branch[r] = w.branch;
+    E.rec.k[r] = k;
 }
 
 // First transition (hop 0): point on the Gaussian surface, first cube with the
@@ -544,155 +560,16 @@ __device__ bool first_transition(const EngineView &E, const DevJob &J, const SVi
 
 __device__ __forceinline__ uint32_t nib(uint32_t v, int i) { return (v >> (4 * i)) & 15u; }
 
-template <typename T>
-__device__ void process_slot(const EngineView &E, uint32_t s)
+__device__ __forceinline__ void append_fresh(const EngineView &E, uint32_t s)
 {
-    typedef Ar<T> A;
-    uint32_t st = E.s.state[s];
-    if (st == ST_IDLE) return;
-    const int N = E.N;
-    const uint32_t NS = E.NS;
-    WalkState w;
-    w.job = E.s.job[s];
-    w.hop = E.s.hop[s];
-    w.walk = E.s.walk[s];
-    w.steps = E.s.steps[s];
-    w.cnt_sh = E.s.cnt_sh[s];
-    w.cnt_mw = E.s.cnt_mw[s];
-    w.branch = E.s.branch[s];
-    w.omega = E.s.omega[s];
-    T pos[3] = {(T)E.s.pos[s], (T)E.s.pos[NS + s], (T)E.s.pos[2 * NS + s]};
-    int hop_budget = E.hop_budget, walk_budget = E.walk_budget;
-    bool dirty_pos = false;
-    for (;;) {
-        if (st != ST_FRESH && st != ST_IDLE && E.job_cancel[w.job]) st = ST_FRESH;
-        if (st == ST_FRESH) {
-            if (walk_budget-- <= 0) break;
-            bool found = false;
-            for (int t = 0; t < E.n_jobs; t++) {
-                const uint32_t jj = (w.job + t) % (uint32_t)E.n_jobs;
-                if (E.job_cancel[jj]) continue;
-                const DevJob &Jc = E.jobs[jj];
-                if (((volatile unsigned long long *)E.job_next)[jj] >= Jc.walk_count) continue;
-                const unsigned long long x = atomicAdd(&E.job_next[jj], 1ull);
-                if (x < Jc.walk_count) {
-                    w.job = jj;
-                    w.walk = Jc.walk_begin + x;
-                    found = true;
-                    break;
-                }
-            }
-            if (!found) { st = ST_IDLE; break; }
-            w.hop = 0; w.steps = 0; w.cnt_sh = 0; w.cnt_mw = 0; w.branch = -1; w.omega = 0.0;
-            st = ST_FIRST;
-        }
-        const DevJob &J = E.jobs[w.job];
-        const SView<T> S = sview<T>(E.structs[J.sid]);
-        if (st == ST_FIRST) {
-            if (!first_transition<T>(E, J, S, w, pos)) break;   // table not ready
-            dirty_pos = true;
-            w.hop = 1;
-            st = ST_HOP;
-        }
-        if (st == ST_MWDONE) {
-            const uint32_t en = E.s.exitnode[s];
-            const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
-            const T c[3] = {(T)E.s.cube[s], (T)E.s.cube[NS + s], (T)E.s.cube[2 * NS + s]};
-            const T R = (T)E.s.cube[3 * NS + s];
-            node_point(c, R, N, node, pos);
-            dirty_pos = true;
-            w.hop++;
-            st = ST_HOP;
-        }
-        if (st == ST_MW) break;
-        // st == ST_HOP
-        if (hop_budget-- <= 0) break;
-        int who;
-        const T d = nearest_electrode(S, pos, who);
-        if (d <= S.tau) {
-            finish_walk(E, J, w, who);
-            st = ST_FRESH;
-            continue;
-        }
-        if ((int)w.hop >= E.max_hops) {
-            finish_walk(E, J, w, -1);
-            st = ST_FRESH;
-            continue;
-        }
-        T R = E.fp32 ? A::sub(d, S.margin) : d;
-        CubeInfo q;
-        classify_cube(S, pos, R, N, q);
-        int guard = 0;
-        while (q.kind == CUBE_OVERFLOW && guard++ < 40) {
-            R = A::mul(R, T(0.5));
-            classify_cube(S, pos, R, N, q);
-        }
-        if (q.kind == CUBE_OVERFLOW) {      // unreachable in practice: count the walk as capped
-            atomicOr(&E.status[STAT_ERR], ERR_SHRINK);
-            finish_walk(E, J, w, -1);
-            st = ST_FRESH;
-            continue;
-        }
-        const uint4 hb = philox10((uint32_t)w.walk, (uint32_t)(w.walk >> 32), w.hop, 0u, J.key0, J.key1);
-        if (E.hybrid && q.kind == CUBE_HOM) {
-            const int m = sample_thr(E.tc.thr + (size_t)E.tc.cap * E.tc.P, (int)E.tc.P, hb.x);
-            int fr[3] = {0, 1, 2}, node[3];
-            panel_node(N, fr, m, node);
-            node_point(pos, R, N, node, pos);
-            dirty_pos = true;
-            w.hop++;
-            w.cnt_sh += 1u << 16;
-            continue;
-        }
-        if (E.hybrid && q.kind == CUBE_STRAT) {
-            const int e = table_lookup(E.tc, TAB_SGF, q.prof);
-            if (e < 0) {
-                if (e == -2) atomicOr(&E.status[STAT_ERR], ERR_CACHE_FULL);
-                break;   // retry this hop next round
-            }
-            const int m = sample_thr(E.tc.thr + (size_t)e * E.tc.P, (int)E.tc.P, hb.x);
-            int fr[3], node[3];
-            frame_sgf(q.axis, fr);
-            panel_node(N, fr, m, node);
-            node_point(pos, R, N, node, pos);
-            dirty_pos = true;
-            w.hop++;
-            w.cnt_sh += 1u;
-            continue;
-        }
-        // MicroWalk job (Algorithm 3) for this cube
-        const uint32_t qi = atomicAdd(E.mwq_count, 1u);
-        if (qi >= E.mwq_cap) {
-            atomicOr(&E.status[STAT_ERR], ERR_MWQ_OVERFLOW);
-            break;
-        }
-        MWJob *jb = E.mwq + qi;
-        const uint32_t s3 = hb.x >> 29;
-        const uint32_t c0 = (uint32_t)(N / 2 - 1);
-        const uint32_t start = (c0 + (s3 & 1u)) | ((c0 + ((s3 >> 1) & 1u)) << 8) | ((c0 + ((s3 >> 2) & 1u)) << 16);
-        // material nibble map: slot 0 boundary, 1 background, 2 + t listed block t
-        uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)q.bg << 4);
-        for (int t = 0; t < q.K; t++) mm |= (uint64_t)rng_mat(q.rng[t]) << (4 * (t + 2));
-        jb->slot = s;
-        jb->hop = w.hop;
-        jb->walk_lo = (uint32_t)w.walk;
-        jb->walk_hi = (uint32_t)(w.walk >> 32);
-        jb->start = start;
-        jb->K = (uint32_t)q.K;
-        jb->mm_lo = (uint32_t)mm;
-        jb->mm_hi = (uint32_t)(mm >> 32);
-        jb->key0 = J.key0;
-        jb->key1 = J.key1;
-        for (int t = 0; t < q.K; t++) jb->rng[t] = q.rng[t];
-        E.s.cube[s] = (double)pos[0];
-        E.s.cube[NS + s] = (double)pos[1];
-        E.s.cube[2 * NS + s] = (double)pos[2];
-        E.s.cube[3 * NS + s] = (double)R;
-        w.cnt_mw++;
-        st = ST_MW;
-        break;
-    }
-    E.s.state[s] = st;
+    cg::coalesced_group g = cg::coalesced_threads();
+    uint32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(E.fresh_out_count, (uint32_t)g.size());
+    E.fresh_out[g.shfl(base, 0) + g.thread_rank()] = s;
+}
+
+__device__ __forceinline__ void store_walk(const EngineView &E, uint32_t s, const WalkState &w)
+{
     E.s.job[s] = w.job;
     E.s.hop[s] = w.hop;
     E.s.walk[s] = w.walk;
@@ -701,19 +578,221 @@ __device__ void process_slot(const EngineView &E, uint32_t s)
     E.s.cnt_mw[s] = w.cnt_mw;
     E.s.branch[s] = w.branch;
     E.s.omega[s] = w.omega;
-    if (dirty_pos) {
-        E.s.pos[s] = (double)pos[0];
-        E.s.pos[NS + s] = (double)pos[1];
-        E.s.pos[2 * NS + s] = (double)pos[2];
+}
+
+__device__ __forceinline__ void load_walk(const EngineView &E, uint32_t s, WalkState &w)
+{
+    w.job = E.s.job[s];
+    w.hop = E.s.hop[s];
+    w.walk = E.s.walk[s];
+    w.steps = E.s.steps[s];
+    w.cnt_sh = E.s.cnt_sh[s];
+    w.cnt_mw = E.s.cnt_mw[s];
+    w.branch = E.s.branch[s];
+    w.omega = E.s.omega[s];
+}
+
+// Slot waiting for a walk or for a first-cube table: take a walk id (one atomic
+// per group of lanes asking the same job), then make the first transition.
+template <typename T>
+__device__ void first_slot(const EngineView &E, uint32_t s)
+{
+    uint32_t st = E.s.state[s];
+    WalkState w;
+    load_walk(E, s, w);
+    if (st == ST_FIRST && E.job_cancel[w.job]) st = ST_FRESH;
+    if (st == ST_FRESH) {
+        bool found = false;
+        for (int t = 0; t < E.n_jobs; t++) {
+            const uint32_t jj = (w.job + t) % (uint32_t)E.n_jobs;
+            if (E.job_cancel[jj]) continue;
+            const DevJob &Jc = E.jobs[jj];
+            const uint64_t lim = ((volatile uint64_t *)E.job_limit)[jj];
+            if (((volatile unsigned long long *)E.job_next)[jj] >= lim) continue;
+            cg::coalesced_group g = cg::coalesced_threads();
+            cg::coalesced_group same = cg::labeled_partition(g, (int)jj);
+            unsigned long long base = 0;
+            if (same.thread_rank() == 0) base = atomicAdd(&E.job_next[jj], (unsigned long long)same.size());
+            base = same.shfl(base, 0);
+            const unsigned long long x = base + same.thread_rank();
+            if (x < lim) {
+                w.job = jj;
+                w.walk = Jc.walk_begin + x;
+                found = true;
+                break;
+            }
+        }
+        if (!found) {
+            E.s.state[s] = ST_IDLE;
+            return;
+        }
+        w.hop = 0; w.steps = 0; w.cnt_sh = 0; w.cnt_mw = 0; w.branch = -1; w.omega = 0.0;
+        st = ST_FIRST;
     }
-    if (st != ST_IDLE) atomicAdd(&E.status[STAT_ACTIVE_CTR], 1u);
+    const DevJob &J = E.jobs[w.job];
+    const SView<T> S = sview<T>(E.structs[J.sid]);
+    T pos[3];
+    if (first_transition<T>(E, J, S, w, pos)) {
+        w.hop = 1;
+        st = ST_HOP;
+        E.s.pos[s] = (double)pos[0];
+        E.s.pos[E.NS + s] = (double)pos[1];
+        E.s.pos[2 * E.NS + s] = (double)pos[2];
+    } else {
+        append_fresh(E, s);   // table not ready: retry next round with the same draws
+    }
+    E.s.state[s] = st;
+    store_walk(E, s, w);
 }
 
 template <typename T>
+__global__ void __launch_bounds__(128) k_first(EngineView E)
+{
+    const uint32_t n = min(*E.fresh_in_count, E.NS);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        first_slot<T>(E, E.fresh_in[i]);
+}
+
+// One geometry step of one walk (Algorithm 1 inner loop): absorption test, cube
+// sizing, classification, then the analytical route in place or a MicroWalk job.
+// Returns whether the slot is still in use.
+template <typename T>
+__device__ bool step_slot(const EngineView &E, uint32_t s)
+{
+    typedef Ar<T> A;
+    uint32_t st = E.s.state[s];
+    if (st == ST_IDLE) return false;
+    if (st != ST_HOP && st != ST_MWDONE) return true;     // FRESH / FIRST: handled by k_first
+    const int N = E.N;
+    const uint32_t NS = E.NS;
+    WalkState w;
+    load_walk(E, s, w);
+    if (E.job_cancel[w.job]) {
+        E.s.state[s] = ST_FRESH;
+        append_fresh(E, s);
+        return true;
+    }
+    const DevJob &J = E.jobs[w.job];
+    const SView<T> S = sview<T>(E.structs[J.sid]);
+    T pos[3];
+    if (st == ST_MWDONE) {
+        const uint32_t en = E.s.exitnode[s];
+        const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
+        const T c[3] = {(T)E.s.cube[s], (T)E.s.cube[NS + s], (T)E.s.cube[2 * NS + s]};
+        const T R = (T)E.s.cube[3 * NS + s];
+        node_point(c, R, N, node, pos);
+        w.hop++;
+    } else {
+        pos[0] = (T)E.s.pos[s];
+        pos[1] = (T)E.s.pos[NS + s];
+        pos[2] = (T)E.s.pos[2 * NS + s];
+    }
+    bool moved = (st == ST_MWDONE);
+    st = ST_HOP;
+    int who;
+    const T d = nearest_electrode(S, pos, who);
+    if (d <= S.tau || (int)w.hop >= E.max_hops) {
+        finish_walk(E, J, w, d <= S.tau ? who : -1);
+        E.s.state[s] = ST_FRESH;
+        append_fresh(E, s);
+        return true;
+    }
+    T R = E.fp32 ? A::sub(d, S.margin) : d;
+    CubeInfo q;
+    classify_cube(S, pos, R, N, q);
+    int guard = 0;
+    while (q.kind == CUBE_OVERFLOW && guard++ < 40) {
+        R = A::mul(R, T(0.5));
+        classify_cube(S, pos, R, N, q);
+    }
+    if (q.kind == CUBE_OVERFLOW) {        // unreachable in practice: count the walk as capped
+        atomicOr(&E.status[STAT_ERR], ERR_SHRINK);
+        finish_walk(E, J, w, -1);
+        E.s.state[s] = ST_FRESH;
+        append_fresh(E, s);
+        return true;
+    }
+    const uint4 hb = philox10((uint32_t)w.walk, (uint32_t)(w.walk >> 32), w.hop, 0u, J.key0, J.key1);
+    bool analytic = false;
+    int m = 0, fr[3] = {0, 1, 2};
+    if (E.hybrid && q.kind == CUBE_HOM) {
+        m = sample_thr(E.tc.thr + (size_t)E.tc.cap * E.tc.P, (int)E.tc.P, hb.x);
+        analytic = true;
+        w.cnt_sh += 1u << 16;
+    } else if (E.hybrid && q.kind == CUBE_STRAT) {
+        const int e = table_lookup(E.tc, TAB_SGF, q.prof);
+        if (e < 0) {
+            if (e == -2) atomicOr(&E.status[STAT_ERR], ERR_CACHE_FULL);
+            // retry this hop next round (same draws)
+            if (moved) {
+                E.s.pos[s] = (double)pos[0];
+                E.s.pos[NS + s] = (double)pos[1];
+                E.s.pos[2 * NS + s] = (double)pos[2];
+            }
+            E.s.state[s] = ST_HOP;
+            store_walk(E, s, w);
+            return true;
+        }
+        m = sample_thr(E.tc.thr + (size_t)e * E.tc.P, (int)E.tc.P, hb.x);
+        frame_sgf(q.axis, fr);
+        analytic = true;
+        w.cnt_sh += 1u;
+    }
+    if (analytic) {
+        int node[3];
+        panel_node(N, fr, m, node);
+        node_point(pos, R, N, node, pos);
+        w.hop++;
+        E.s.pos[s] = (double)pos[0];
+        E.s.pos[NS + s] = (double)pos[1];
+        E.s.pos[2 * NS + s] = (double)pos[2];
+        E.s.state[s] = ST_HOP;
+        store_walk(E, s, w);
+        return true;
+    }
+    // MicroWalk job (Algorithm 3) for this cube
+    uint32_t qi;
+    {
+        cg::coalesced_group g = cg::coalesced_threads();
+        uint32_t base = 0;
+        if (g.thread_rank() == 0) base = atomicAdd(E.mwq_count, (uint32_t)g.size());
+        qi = g.shfl(base, 0) + g.thread_rank();
+    }
+    if (qi >= E.mwq_cap) {
+        atomicOr(&E.status[STAT_ERR], ERR_MWQ_OVERFLOW);
+        return true;
+    }
+    MWJob *jb = E.mwq + qi;
+    const uint32_t s3 = hb.x >> 29;
+    const uint32_t c0 = (uint32_t)(N / 2 - 1);
+    const uint32_t start = (c0 + (s3 & 1u)) | ((c0 + ((s3 >> 1) & 1u)) << 8) | ((c0 + ((s3 >> 2) & 1u)) << 16);
+    // material nibble map: slot 0 boundary, 1 background, 2 + t listed block t
+    uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)q.bg << 4);
+    for (int t = 0; t < q.K; t++) mm |= (uint64_t)rng_mat(q.rng[t]) << (4 * (t + 2));
+    uint4 *dst = reinterpret_cast<uint4 *>(jb);
+    dst[0] = make_uint4(s, w.hop, (uint32_t)w.walk, (uint32_t)(w.walk >> 32));
+    dst[1] = make_uint4(start, (uint32_t)q.K, (uint32_t)mm, (uint32_t)(mm >> 32));
+    dst[2] = make_uint4(J.key0, J.key1, 0u, 0u);
+    for (int t = 0; t < q.K; t++) jb->rng[t] = q.rng[t];
+    E.s.cube[s] = (double)pos[0];
+    E.s.cube[NS + s] = (double)pos[1];
+    E.s.cube[2 * NS + s] = (double)pos[2];
+    E.s.cube[3 * NS + s] = (double)R;
+    w.cnt_mw++;
+    E.s.state[s] = ST_MW;
+    store_walk(E, s, w);
+    return true;
+}
+
+// One lane per slot; the slot count is a multiple of the block size, so every
+// lane of a warp reaches the ballot.
+template <typename T>
 __global__ void __launch_bounds__(256) k_geom(EngineView E)
 {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < E.NS; s += stride) process_slot<T>(E, s);
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = (s < E.NS) ? step_slot<T>(E, s) : false;
+    const uint32_t b = __ballot_sync(FULL_MASK, act);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&E.status[STAT_ACTIVE_CTR], (uint32_t)__popc(b));
 }
 
 __global__ void k_init_slots(EngineView E)
@@ -728,6 +807,11 @@ __global__ void k_init_slots(EngineView E)
         E.s.cnt_mw[s] = 0;
         E.s.branch[s] = -1;
         E.s.omega[s] = 0.0;
+        E.fresh_in[s] = s;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *E.fresh_in_count = E.NS;
+        *E.fresh_out_count = 0;
     }
 }
 
@@ -741,6 +825,7 @@ __global__ void k_round_end(EngineView E)
         *E.mwq_head = 0;
         *E.tc.fillq_count = 0;
         *E.tc.fillq_head = 0;
+        *E.fresh_in_count = 0;     // consumed; becomes next round's output list
     }
 }
 
@@ -1201,6 +1286,109 @@ __global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t ent
 }
 
 // ---------------------------------------------------------------------------
+// Batch reduction: one CTA per batch folds the batch's walk records into its
+// accumulator block (S1, S2 per electrode as exact 128-bit fixed point, counters).
+// Integer sums are order-independent, so the result does not depend on which walk
+// finished first.  done = number of finished walks of the batch.
+__device__ __forceinline__ void smem_add128(unsigned long long *p, unsigned long long lo, unsigned long long hi)
+{
+    const unsigned long long old = atomicAdd(&p[0], lo);
+    atomicAdd(&p[1], hi + ((old + lo < old) ? 1ull : 0ull));
+}
+
+__device__ __forceinline__ void to_fixed128(double v, double scale, unsigned long long &lo, unsigned long long &hi)
+{
+    const double s = rint(v * scale);
+    const double a = fabs(s);
+    const double ah = floor(a * 5.421010862427522e-20);   // * 2^-64
+    const double al = a - ah * 18446744073709551616.0;
+    lo = (unsigned long long)al;
+    hi = (unsigned long long)ah;
+    if (s < 0) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce(EngineView E, int job, uint64_t b0)
+{
+    extern __shared__ unsigned long long acc_sm[];
+    const DevJob &J = E.jobs[job];
+    const int nc1 = J.n_c + 1;
+    const uint32_t words = J.acc_stride;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) acc_sm[i] = 0ull;
+    __syncthreads();
+    const uint64_t b = b0 + blockIdx.x;
+    const uint64_t w0 = b * J.batch;
+    const uint64_t w1 = min(w0 + J.batch, J.walk_count);
+    unsigned long long *ex = acc_sm + 4 * nc1;
+    unsigned long long loc[ACC_EXTRA];
+    for (int x = 0; x < ACC_EXTRA; x++) loc[x] = 0ull;
+    for (uint64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+        const uint64_t r = J.rec_base + w;
+        const int k = E.rec.k[r];
+        if (k == REC_PENDING) continue;
+        loc[0]++;
+        loc[1] += E.rec.hops[r];
+        loc[2] += E.rec.steps[r];
+        const uint32_t sh = E.rec.cnt_sh[r];
+        loc[3] += sh & 0xffffu;
+        loc[4] += sh >> 16;
+        loc[5] += E.rec.cnt_mw[r];
+        const int br = E.rec.branch[r];
+        if (br >= 0 && br < 3) loc[6 + br]++;
+        if (k < 0) {
+            loc[9]++;
+            continue;
+        }
+        const double om = E.rec.omega[r];
+        unsigned long long lo, hi;
+        to_fixed128(om, ACC_S1_SCALE, lo, hi);
+        smem_add128(acc_sm + 2 * k, lo, hi);
+        to_fixed128(om * om, ACC_S2_SCALE, lo, hi);
+        smem_add128(acc_sm + 2 * nc1 + 2 * k, lo, hi);
+    }
+    for (int x = 0; x < ACC_EXTRA; x++) {
+        unsigned long long v = loc[x];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL_MASK, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&ex[x], v);
+    }
+    __syncthreads();
+    unsigned long long *out = E.acc + J.acc_base + b * words;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) out[i] = acc_sm[i];
+}
+
+__global__ void k_set_limit(EngineView E, int job, uint64_t limit)
+{
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) {
+        unsigned long long nx = E.job_next[job];
+        const unsigned long long old = E.job_limit[job];
+        if (nx > old) nx = old;                 // ids claimed past the old limit were not run
+        E.job_next[job] = nx;
+        E.job_limit[job] = limit > nx ? limit : nx;   // never below what was issued
+    }
+    if (s < E.NS && E.s.state[s] == ST_IDLE) {
+        E.s.state[s] = ST_FRESH;
+        E.fresh_out[atomicAdd(E.fresh_out_count, 1u)] = s;
+    }
+}
+
+cudaError_t launch_set_limit(const EngineView &E, int job, uint64_t limit, cudaStream_t st)
+{
+    k_set_limit<<<(E.NS + 255) / 256, 256, 0, st>>>(E, job, limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const EngineView &E, int job, uint64_t b0, uint64_t b1, int nc, cudaStream_t st)
+{
+    if (b1 <= b0) return cudaSuccess;
+    const size_t smem = sizeof(unsigned long long) * acc_stride_for(nc);
+    k_reduce<<<(unsigned)(b1 - b0), 256, smem, st>>>(E, job, b0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 size_t fill_smem_bytes(int N)
 {
@@ -1224,6 +1412,8 @@ cudaError_t set_kernel_attributes(int N, int mw_warps)
     e = cudaFuncSetAttribute(k_mw<QueueSource>, cudaFuncAttributeMaxDynamicSharedMemorySize, mws);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_mw<CubeSource>, cudaFuncAttributeMaxDynamicSharedMemorySize, mws);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     return e;
 }
 
@@ -1232,6 +1422,14 @@ cudaError_t launch_init_slots(const EngineView &E, cudaStream_t st)
     const int threads = 256;
     const int blocks = (int)((E.NS + threads - 1) / threads);
     k_init_slots<<<blocks, threads, 0, st>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_first(const EngineView &E, const LaunchShape &L, cudaStream_t st)
+{
+    const int blocks = L.sms * 8;
+    if (E.fp32) k_first<float><<<blocks, 128, 0, st>>>(E);
+    else k_first<double><<<blocks, 128, 0, st>>>(E);
     return cudaGetLastError();
 }
 
@@ -1266,7 +1464,9 @@ cudaError_t launch_mw(const EngineView &E, const LaunchShape &L, cudaStream_t st
 
 cudaError_t launch_round(const EngineView &E, const LaunchShape &L, cudaStream_t st)
 {
-    cudaError_t e = launch_geom(E, L, st);
+    cudaError_t e = launch_first(E, L, st);
+    if (e != cudaSuccess) return e;
+    e = launch_geom(E, L, st);
     if (e != cudaSuccess) return e;
     e = launch_fill(E, L, st);
     if (e != cudaSuccess) return e;

@@ -56,6 +56,12 @@ struct frw_ctx {
     int struct_cap = 0;
     std::vector<HostStructure> structs;
     uint32_t *h_status = nullptr;       // pinned
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t *fresh[2] = {nullptr, nullptr};   // slot lists of the first-transition kernel
+    uint32_t *fresh_ctr = nullptr;             // [2] counts
+    RecArrays rec;                      // per-walk records (grown on demand)
+    uint64_t rec_cap = 0;
+    std::vector<void *> rec_allocs;
 };
 
 static const char *kErr[] = {"ok",
@@ -162,8 +168,10 @@ static EngineView make_view(frw_ctx *ctx)
     E.eps = ctx->d_eps;
     E.fc = ctx->fc;
     E.status = ctx->status;
-    E.hop_budget = 32;
-    E.walk_budget = 4;
+    E.fresh_in = ctx->fresh[0];
+    E.fresh_out = ctx->fresh[1];
+    E.fresh_in_count = ctx->fresh_ctr;
+    E.fresh_out_count = ctx->fresh_ctr + 1;
     return E;
 }
 
@@ -203,7 +211,10 @@ extern "C" void frw_destroy(frw_ctx *ctx)
     for (auto &s : ctx->structs)
         for (void *p : s.dev) cudaFree(p);
     for (void *p : ctx->allocs) cudaFree(p);
+    for (void *p : ctx->rec_allocs) cudaFree(p);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -275,7 +286,9 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         (rc = dalloc(ctx, &S.pos, 3 * (size_t)NS, A)) || (rc = dalloc(ctx, &S.cube, 4 * (size_t)NS, A)) ||
         (rc = dalloc(ctx, &S.omega, NS, A)) || (rc = dalloc(ctx, &ctx->mwq, NS, A)) ||
         (rc = dalloc(ctx, &ctx->mwq_ctr, 2, A)) || (rc = dalloc(ctx, &ctx->status, STAT_WORDS, A)) ||
-        (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)))
+        (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)) ||
+        (rc = dalloc(ctx, &ctx->fresh[0], NS, A)) || (rc = dalloc(ctx, &ctx->fresh[1], NS, A)) ||
+        (rc = dalloc(ctx, &ctx->fresh_ctr, 2, A)))
         return bail(rc);
     TableCache &T = ctx->tc;
     T.cap = cap;
@@ -315,6 +328,8 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->struct_cap = 64;
     if ((rc = dalloc(ctx, &ctx->d_structs, ctx->struct_cap, A))) return bail(rc);
     if (cudaMallocHost(&ctx->h_status, sizeof(uint32_t) * STAT_WORDS) != cudaSuccess) return bail(FRW_ENOMEM);
+    for (auto &e : ctx->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(FRW_EDEVICE);
     cudaError_t e2 = set_kernel_attributes(N, ctx->shape.mw_warps);
     if (e2 != cudaSuccess) return bail(cuda_fail(ctx, e2, "cudaFuncSetAttribute"));
     cudaMemsetAsync(T.state, 0, sizeof(uint32_t) * cap, ctx->stream);
@@ -357,6 +372,90 @@ static double box_gap(const double *lo1, const double *hi1, const double *lo2, c
 static float ulpf(float x)
 {
     return std::nextafter(x, INFINITY) - x;
+}
+
+// ---------------------------------------------------------------------------
+// Structure index (a0).  Nearest-conductor grid: for each cell (grown by 2 % of
+// its width to absorb rounding of the device's cell computation), keep every
+// conductor whose smallest possible distance to the cell does not exceed an upper
+// bound on the nearest-electrode distance anywhere in the cell.  Block slabs:
+// prefix masks per axis (see DevStructure).
+struct IndexHost {
+    int gdim[3];
+    double g_org[3], g_inv[3];
+    std::vector<uint32_t> g_off;
+    std::vector<uint16_t> g_ids;
+    int S, words;
+    double sl_org[3], sl_inv[3];
+    std::vector<uint32_t> L, H;
+};
+
+static void build_index(const frw_box &dom, const frw_box *cond, int nc, const frw_block *blk, int nb, IndexHost &X)
+{
+    double ext[3], vol = 1.0, edge = 0.0;
+    for (int a = 0; a < 3; a++) {
+        ext[a] = dom.hi[a] - dom.lo[a];
+        vol *= ext[a];
+        edge = std::max(edge, ext[a]);
+    }
+    const double target = std::min(262144.0, std::max(4096.0, 4194304.0 / std::max(1, nc)));
+    const double h = std::cbrt(vol / target);
+    for (int a = 0; a < 3; a++) {
+        X.gdim[a] = (int)std::min(512.0, std::max(1.0, std::ceil(ext[a] / h)));
+        X.g_org[a] = dom.lo[a];
+        X.g_inv[a] = X.gdim[a] / ext[a];
+    }
+    const size_t cells = (size_t)X.gdim[0] * X.gdim[1] * X.gdim[2];
+    X.g_off.assign(cells + 1, 0);
+    X.g_ids.clear();
+    std::vector<double> dmin(nc);
+    for (int i = 0; i < X.gdim[0]; i++)
+        for (int j = 0; j < X.gdim[1]; j++)
+            for (int k = 0; k < X.gdim[2]; k++) {
+                const int ii[3] = {i, j, k};
+                double lo[3], hi[3];
+                for (int a = 0; a < 3; a++) {
+                    const double w = ext[a] / X.gdim[a];
+                    lo[a] = dom.lo[a] + ii[a] * w - 0.02 * w;
+                    hi[a] = dom.lo[a] + (ii[a] + 1) * w + 0.02 * w;
+                }
+                // upper bound on the nearest-electrode distance over the cell
+                double U = INFINITY;
+                for (int a = 0; a < 3; a++) U = std::min(U, std::min(hi[a] - dom.lo[a], dom.hi[a] - lo[a]));
+                for (int c = 0; c < nc; c++) {
+                    double dmax = 0.0, dm = 0.0;
+                    for (int a = 0; a < 3; a++) {
+                        dmax = std::max(dmax, std::max(cond[c].lo[a] - lo[a], hi[a] - cond[c].hi[a]));
+                        dm = std::max(dm, std::max(cond[c].lo[a] - hi[a], lo[a] - cond[c].hi[a]));
+                    }
+                    dmin[c] = dm;
+                    U = std::min(U, dmax);
+                }
+                const double tol = 1e-6 * edge;   // covers FP32 rounding of device distances
+                for (int c = 0; c < nc; c++)
+                    if (dmin[c] <= U + tol) X.g_ids.push_back((uint16_t)c);
+                X.g_off[((size_t)i * X.gdim[1] + j) * X.gdim[2] + k + 1] = (uint32_t)X.g_ids.size();
+            }
+    // slabs
+    X.S = 256;
+    X.words = std::max(1, (nb + 31) / 32);
+    X.L.assign((size_t)3 * X.S * X.words, 0u);
+    X.H.assign((size_t)3 * X.S * X.words, 0u);
+    for (int a = 0; a < 3; a++) {
+        const double w = ext[a] / X.S, m = w / 64.0 + 1e-9 * edge;
+        X.sl_org[a] = dom.lo[a];
+        X.sl_inv[a] = X.S / ext[a];
+        for (int s2 = 0; s2 < X.S; s2++) {
+            const double top = (s2 == X.S - 1) ? INFINITY : dom.lo[a] + (s2 + 1) * w + m;
+            const double bot = (s2 == 0) ? -INFINITY : dom.lo[a] + s2 * w - m;
+            uint32_t *Lw = &X.L[((size_t)a * X.S + s2) * X.words];
+            uint32_t *Hw = &X.H[((size_t)a * X.S + s2) * X.words];
+            for (int b = 0; b < nb; b++) {
+                if (blk[b].lo[a] <= top) Lw[b >> 5] |= 1u << (b & 31);
+                if (blk[b].hi[a] >= bot) Hw[b >> 5] |= 1u << (b & 31);
+            }
+        }
+    }
 }
 
 extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *conductors, int32_t n_cond,
@@ -458,7 +557,24 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
         *dst = p;
         return FRW_OK;
     };
-    if ((rc = up((double **)&D.c_lo, clo)) || (rc = up((double **)&D.c_hi, chi)) ||
+    IndexHost X;
+    build_index(*domain, conductors, n_cond, blocks, n_blocks, X);
+    for (int a = 0; a < 3; a++) {
+        D.gdim[a] = X.gdim[a];
+        D.g_org[a] = X.g_org[a];
+        D.g_inv[a] = X.g_inv[a];
+        D.g_org_f[a] = (float)X.g_org[a];
+        D.g_inv_f[a] = (float)X.g_inv[a];
+        D.sl_org[a] = X.sl_org[a];
+        D.sl_inv[a] = X.sl_inv[a];
+        D.sl_org_f[a] = (float)X.sl_org[a];
+        D.sl_inv_f[a] = (float)X.sl_inv[a];
+    }
+    D.sl_S = X.S;
+    D.sl_words = X.words;
+    if ((rc = up((uint32_t **)&D.g_off, X.g_off)) || (rc = up((uint16_t **)&D.g_ids, X.g_ids)) ||
+        (rc = up((uint32_t **)&D.sl_L, X.L)) || (rc = up((uint32_t **)&D.sl_H, X.H)) ||
+        (rc = up((double **)&D.c_lo, clo)) || (rc = up((double **)&D.c_hi, chi)) ||
         (rc = up((float **)&D.c_lo_f, clof)) || (rc = up((float **)&D.c_hi_f, chif)) ||
         (rc = up((double **)&D.b_lo, blo)) || (rc = up((double **)&D.b_hi, bhi)) ||
         (rc = up((float **)&D.b_lo_f, blof)) || (rc = up((float **)&D.b_hi_f, bhif)) ||
@@ -528,23 +644,26 @@ static i128 rd128(const unsigned long long *p)
 struct JobRun {
     frw_job desc;
     uint64_t walk_begin = 0;         // first walk id (resume / shard offset)
-    int record = 0;                  // write per-walk records (job 0 only)
     DevJob d;
     uint64_t n_batches = 0;
-    uint64_t prefix = 0;             // complete batches examined so far
-    uint64_t used_batches = 0;       // batches in the estimate
+    uint64_t prefix = 0;             // complete batches folded into S1/S2 so far
+    uint64_t limit = 0;              // current issue limit (walks)
     bool converged = false;
-    bool done = false;
     std::vector<i128> S1, S2;        // running prefix sums
     uint64_t walks = 0;
     uint64_t ex[ACC_EXTRA] = {0};
+    unsigned long long *h_blocks = nullptr;   // pinned staging for batch blocks
+    uint64_t h_cap = 0;
 };
 
-// relative standard error rule of the stop criterion
-static bool sigma_ok(const std::vector<i128> &S1, const std::vector<i128> &S2, uint64_t n, int nc, int master,
-                     double target)
+// relative standard errors of C_ii and of the largest |C_ij| (j != i, ground
+// excluded) from exact prefix sums; the stop rule holds when both are <= target
+static void rel_errors(const std::vector<i128> &S1, const std::vector<i128> &S2, uint64_t n, int nc, int master,
+                       double *r_self, double *r_cpl)
 {
-    if (n < 2) return false;
+    *r_self = INFINITY;
+    *r_cpl = 0.0;
+    if (n < 2) return;
     const double nn = (double)n;
     auto val = [&](int k, double *c, double *se) {
         const double s1 = (double)S1[k] / ACC_S1_SCALE, s2 = (double)S2[k] / ACC_S2_SCALE;
@@ -554,34 +673,71 @@ static bool sigma_ok(const std::vector<i128> &S1, const std::vector<i128> &S2, u
     };
     double ci, si;
     val(master, &ci, &si);
-    if (!(ci != 0.0 && si <= target * std::fabs(ci))) return false;
+    *r_self = (ci != 0.0) ? si / std::fabs(ci) : INFINITY;
     int jb = -1;
     double cb = 0.0;
     for (int j = 0; j < nc; j++) {
         if (j == master) continue;
-        double c, s;
-        val(j, &c, &s);
+        double c, sj;
+        val(j, &c, &sj);
         if (jb < 0 || std::fabs(c) > cb) {
             jb = j;
             cb = std::fabs(c);
         }
     }
     if (jb >= 0) {
-        double c, s;
-        val(jb, &c, &s);
-        if (!(c != 0.0 && s <= target * std::fabs(c))) return false;
+        double c, sj;
+        val(jb, &c, &sj);
+        *r_cpl = (c != 0.0) ? sj / std::fabs(c) : INFINITY;
     }
-    return true;
 }
 
-// Run a set of jobs to completion on the device.  Records (optional) are
-// written for job 0 only (frw_walk_records).
-static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, RecArrays *rec, frw_stats *stats_out)
+static bool sigma_ok(const std::vector<i128> &S1, const std::vector<i128> &S2, uint64_t n, int nc, int master,
+                     double target)
+{
+    if (n < 2) return false;
+    double rs, rc;
+    rel_errors(S1, S2, n, nc, master, &rs, &rc);
+    return rs <= target && rc <= target;
+}
+
+static int ensure_records(frw_ctx *ctx, uint64_t n)
+{
+    if (n <= ctx->rec_cap) return FRW_OK;
+    if (n * 32ull > (64ull << 30)) return fail(ctx, FRW_ENOMEM, "walk budget too large for the record pool (64 GB)");
+    for (void *p : ctx->rec_allocs) cudaFree(p);
+    ctx->rec_allocs.clear();
+    ctx->rec_cap = 0;
+    RecArrays &R = ctx->rec;
+    int rc;
+    if ((rc = dalloc(ctx, &R.omega, n, ctx->rec_allocs)) || (rc = dalloc(ctx, &R.k, n, ctx->rec_allocs)) ||
+        (rc = dalloc(ctx, &R.hops, n, ctx->rec_allocs)) || (rc = dalloc(ctx, &R.steps, n, ctx->rec_allocs)) ||
+        (rc = dalloc(ctx, &R.cnt_sh, n, ctx->rec_allocs)) || (rc = dalloc(ctx, &R.cnt_mw, n, ctx->rec_allocs)) ||
+        (rc = dalloc(ctx, &R.branch, n, ctx->rec_allocs)))
+        return rc;
+    ctx->rec_cap = n;
+    return FRW_OK;
+}
+
+static void fold_block(JobRun &j, const unsigned long long *blk, uint64_t bsz)
+{
+    const int nc1 = j.d.n_c + 1;
+    for (int k = 0; k < nc1; k++) {
+        j.S1[k] += rd128(blk + 2 * k);
+        j.S2[k] += rd128(blk + 2 * nc1 + 2 * k);
+    }
+    for (int x = 0; x < ACC_EXTRA; x++) j.ex[x] += blk[4 * nc1 + x];
+    j.walks += bsz;
+}
+
+// Run a set of jobs to completion on the device.  Each round: geometry, table
+// fill, MicroWalk, round end (each bracketed by CUDA events), then for jobs with
+// a sigma target the next batches are reduced and checked in walk-id order.
+static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_out)
 {
     const auto t0 = std::chrono::steady_clock::now();
     const int nj = (int)jobs.size();
-    uint64_t total_walks = 0;
-    uint64_t acc_words = 0;
+    uint64_t total_walks = 0, acc_words = 0;
     for (auto &j : jobs) {
         const HostStructure &H = ctx->structs[j.desc.structure_id];
         DevJob &d = j.d;
@@ -594,32 +750,43 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, RecArrays *rec, frw
         gauss_setup(H, j.desc.master, ctx->opt.gauss_offset_frac, d);
         d.walk_count = j.desc.walk_budget;
         d.walk_begin = j.walk_begin;
-        d.record = j.record;
-        d.rec_base = 0;
         d.batch = j.desc.batch ? j.desc.batch : 16384;
         d.acc_stride = acc_stride_for(H.n_c);
         d.acc_base = acc_words;
+        d.rec_base = total_walks;
         j.n_batches = (d.walk_count + d.batch - 1) / d.batch;
         acc_words += j.n_batches * d.acc_stride;
         total_walks += d.walk_count;
         j.S1.assign(H.n_c + 1, 0);
         j.S2.assign(H.n_c + 1, 0);
+        j.limit = d.walk_count;
     }
+    int rc = ensure_records(ctx, total_walks);
+    if (rc) return rc;
     std::vector<void *> tmp;
     auto cleanup = [&]() {
         for (void *p : tmp) cudaFree(p);
+        for (auto &j : jobs)
+            if (j.h_blocks) {
+                cudaFreeHost(j.h_blocks);
+                j.h_blocks = nullptr;
+            }
     };
     DevJob *d_jobs = nullptr;
-    unsigned long long *d_next = nullptr, *d_acc = nullptr;
+    unsigned long long *d_next = nullptr, *d_acc = nullptr, *d_limit = nullptr;
     int *d_cancel = nullptr;
-    int rc;
     if ((rc = dalloc(ctx, &d_jobs, nj, tmp)) || (rc = dalloc(ctx, &d_next, nj, tmp)) ||
-        (rc = dalloc(ctx, &d_cancel, nj, tmp)) || (rc = dalloc(ctx, &d_acc, std::max<uint64_t>(acc_words, 1), tmp))) {
+        (rc = dalloc(ctx, &d_limit, nj, tmp)) || (rc = dalloc(ctx, &d_cancel, nj, tmp)) ||
+        (rc = dalloc(ctx, &d_acc, std::max<uint64_t>(acc_words, 1), tmp))) {
         cleanup();
         return rc;
     }
     std::vector<DevJob> hj(nj);
-    for (int i = 0; i < nj; i++) hj[i] = jobs[i].d;
+    std::vector<unsigned long long> hl(nj);
+    for (int i = 0; i < nj; i++) {
+        hj[i] = jobs[i].d;
+        hl[i] = jobs[i].d.walk_count;
+    }
     cudaStream_t st = ctx->stream;
 #define CKR(call)                                     \
     do {                                              \
@@ -631,9 +798,11 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, RecArrays *rec, frw
         }                                             \
     } while (0)
     CKR(cudaMemcpyAsync(d_jobs, hj.data(), sizeof(DevJob) * nj, cudaMemcpyHostToDevice, st));
+    CKR(cudaMemcpyAsync(d_limit, hl.data(), sizeof(unsigned long long) * nj, cudaMemcpyHostToDevice, st));
     CKR(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long) * nj, st));
     CKR(cudaMemsetAsync(d_cancel, 0, sizeof(int) * nj, st));
     CKR(cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long) * std::max<uint64_t>(acc_words, 1), st));
+    CKR(cudaMemsetAsync(ctx->rec.k, 0x80, sizeof(int32_t) * total_walks, st));
     CKR(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
     CKR(cudaMemsetAsync(ctx->mwq_ctr, 0, sizeof(uint32_t) * 2, st));
     CKR(cudaMemsetAsync(ctx->tc.fillq_count, 0, sizeof(uint32_t) * 2, st));
@@ -643,94 +812,144 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, RecArrays *rec, frw
     E.n_jobs = nj;
     E.jobs = d_jobs;
     E.job_next = d_next;
+    E.job_limit = d_limit;
     E.job_cancel = d_cancel;
     E.acc = d_acc;
-    if (rec) E.rec = *rec;
+    E.rec = ctx->rec;
     CKR(launch_init_slots(E, st));
-    uint64_t rounds = 0;
-    std::vector<unsigned long long> hb;
-    bool any_sigma = false;
-    for (auto &j : jobs) any_sigma |= j.desc.sigma_target > 0.0;
+    uint64_t rounds = 0, extra_launches = 0;
+    const EngineView E0 = E;
+    const uint64_t LOOK = 16;    // batches examined per sigma job per round
+    for (auto &j : jobs)
+        if (j.desc.sigma_target > 0.0) {
+            if (cudaMallocHost(&j.h_blocks, sizeof(unsigned long long) * LOOK * j.d.acc_stride) != cudaSuccess) {
+                cleanup();
+                return fail(ctx, FRW_ENOMEM, "pinned staging");
+            }
+            j.h_cap = LOOK;
+        }
+    double t_geom = 0.0, t_fill = 0.0, t_mw = 0.0;
     for (;;) {
-        CKR(launch_round(E, ctx->shape, st));
+        // fresh-slot lists alternate between rounds
+        E.fresh_in = E0.fresh_in;
+        E.fresh_out = E0.fresh_out;
+        E.fresh_in_count = E0.fresh_in_count;
+        E.fresh_out_count = E0.fresh_out_count;
+        if (rounds & 1) {
+            std::swap(E.fresh_in, E.fresh_out);
+            std::swap(E.fresh_in_count, E.fresh_out_count);
+        }
+        // one round, each launch bracketed by events on the launch stream
+        CKR(cudaEventRecord(ctx->ev[0], st));
+        CKR(launch_first(E, ctx->shape, st));
+        CKR(launch_geom(E, ctx->shape, st));
+        CKR(cudaEventRecord(ctx->ev[1], st));
+        CKR(launch_fill(E, ctx->shape, st));
+        CKR(cudaEventRecord(ctx->ev[2], st));
+        CKR(launch_mw(E, ctx->shape, st));
+        CKR(cudaEventRecord(ctx->ev[3], st));
+        CKR(launch_round_end(E, st));
         rounds++;
-        rc = check_status(ctx);
+        // fold the next batches of every unfinished sigma job
+        std::vector<uint64_t> look(nj, 0);
+        for (int i = 0; i < nj; i++) {
+            JobRun &j = jobs[i];
+            if (j.desc.sigma_target <= 0.0 || j.converged || j.prefix >= j.n_batches) continue;
+            look[i] = std::min<uint64_t>(LOOK, j.n_batches - j.prefix);
+            CKR(launch_reduce(E, i, j.prefix, j.prefix + look[i], j.d.n_c, st));
+            extra_launches++;
+            CKR(cudaMemcpyAsync(j.h_blocks, d_acc + j.d.acc_base + j.prefix * j.d.acc_stride,
+                                sizeof(unsigned long long) * look[i] * j.d.acc_stride, cudaMemcpyDeviceToHost, st));
+        }
+        rc = check_status(ctx);   // copies the status words and synchronises the stream
         if (rc) {
             cleanup();
             return rc;
         }
-        const bool finished = ctx->h_status[STAT_ACTIVE] == 0;
-        if (any_sigma) {
-            for (int i = 0; i < nj; i++) {
-                JobRun &j = jobs[i];
-                if (j.desc.sigma_target <= 0.0 || j.converged) continue;
-                const uint32_t strd = j.d.acc_stride;
-                const int nc1 = j.d.n_c + 1;
-                while (j.prefix < j.n_batches && !j.converged) {
-                    const uint64_t look = std::min<uint64_t>(8, j.n_batches - j.prefix);
-                    hb.resize(look * strd);
-                    CKR(cudaMemcpyAsync(hb.data(), d_acc + j.d.acc_base + j.prefix * strd,
-                                        sizeof(unsigned long long) * look * strd, cudaMemcpyDeviceToHost, st));
-                    CKR(cudaStreamSynchronize(st));
-                    uint64_t adv = 0;
-                    for (uint64_t b = 0; b < look; b++) {
-                        const unsigned long long *blk = hb.data() + b * strd;
-                        const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - (j.prefix + b) * j.d.batch);
-                        if (blk[4 * nc1] != bsz) break;
-                        for (int k = 0; k < nc1; k++) {
-                            j.S1[k] += rd128(blk + 2 * k);
-                            j.S2[k] += rd128(blk + 2 * nc1 + 2 * k);
-                        }
-                        for (int x = 0; x < ACC_EXTRA; x++) j.ex[x] += blk[4 * nc1 + x];
-                        j.walks += bsz;
-                        adv++;
-                        const bool full_batch = bsz == j.d.batch;
-                        if (full_batch && sigma_ok(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, j.desc.sigma_target)) {
-                            j.converged = true;
-                            break;
-                        }
-                    }
-                    j.prefix += adv;
-                    if (j.converged) {
-                        j.used_batches = j.prefix;
-                        const int one = 1;
-                        CKR(cudaMemcpyAsync(d_cancel + i, &one, sizeof(int), cudaMemcpyHostToDevice, st));
-                        CKR(cudaStreamSynchronize(st));
-                    }
-                    if (adv < look) break;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) t_geom += ms;
+        if (cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) == cudaSuccess) t_fill += ms;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) == cudaSuccess) t_mw += ms;
+        bool more = false;   // a sigma job still needs walks
+        for (int i = 0; i < nj; i++) {
+            JobRun &j = jobs[i];
+            if (!look[i]) continue;
+            const uint32_t strd = j.d.acc_stride;
+            const int nc1 = j.d.n_c + 1;
+            for (uint64_t b = 0; b < look[i] && !j.converged; b++) {
+                const unsigned long long *blk = j.h_blocks + b * strd;
+                const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - j.prefix * j.d.batch);
+                if (blk[4 * nc1] != bsz) break;
+                fold_block(j, blk, bsz);
+                j.prefix++;
+                if (bsz == j.d.batch && sigma_ok(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, j.desc.sigma_target))
+                    j.converged = true;
+            }
+            if (j.converged) {
+                const int one = 1;
+                CKR(cudaMemcpyAsync(d_cancel + i, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+                continue;
+            }
+            if (j.prefix >= j.n_batches) continue;   // budget exhausted
+            more = true;
+            // predictive issue limit: walks needed ~ n (r / target)^2, with margin,
+            // so that the in-flight pool does not overshoot the stopping point
+            if (j.walks >= j.d.batch) {
+                double rs, rcp;
+                rel_errors(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, &rs, &rcp);
+                const double r = std::max(rs, rcp) / j.desc.sigma_target;
+                double need = std::isfinite(r) ? (double)j.walks * r * r : (double)j.d.walk_count;
+                need = std::min<double>(need * 1.15 + 2.0 * j.d.batch, (double)j.d.walk_count);
+                uint64_t lim = ((uint64_t)need + j.d.batch - 1) / j.d.batch * j.d.batch;
+                lim = std::min<uint64_t>(std::max<uint64_t>(lim, (j.prefix + 1) * j.d.batch), j.d.walk_count);
+                if (lim != j.limit) {
+                    CKR(launch_set_limit(E, i, lim, st));
+                    extra_launches++;
+                    j.limit = lim;
                 }
             }
         }
-        if (finished) break;
+        if (ctx->h_status[STAT_ACTIVE] == 0 && !more) break;
+        if (ctx->h_status[STAT_ACTIVE] == 0 && more) {
+            // every slot idle but a sigma job is short of walks: lift its limit
+            for (int i = 0; i < nj; i++) {
+                JobRun &j = jobs[i];
+                if (j.desc.sigma_target <= 0.0 || j.converged || j.prefix >= j.n_batches) continue;
+                const uint64_t lim = std::min<uint64_t>(j.d.walk_count, std::max<uint64_t>(2 * j.limit, j.limit + j.d.batch));
+                CKR(launch_set_limit(E, i, lim, st));
+                extra_launches++;
+                j.limit = lim;
+            }
+        }
         if (rounds > 100000000ull) {
             cleanup();
             return fail(ctx, FRW_ETIMEOUT, "engine did not finish");
         }
     }
-    // budget-only jobs (and sigma jobs that never converged): take every batch
+    // jobs without a sigma target (or that ran out of budget): fold every batch
+    std::vector<unsigned long long> hb;
     for (int i = 0; i < nj; i++) {
         JobRun &j = jobs[i];
-        if (j.converged) continue;
+        if (j.converged || j.prefix >= j.n_batches) continue;
         const uint32_t strd = j.d.acc_stride;
-        const int nc1 = j.d.n_c + 1;
         const uint64_t rest = j.n_batches - j.prefix;
-        if (rest) {
-            hb.resize(rest * strd);
-            CKR(cudaMemcpyAsync(hb.data(), d_acc + j.d.acc_base + j.prefix * strd,
-                                sizeof(unsigned long long) * rest * strd, cudaMemcpyDeviceToHost, st));
-            CKR(cudaStreamSynchronize(st));
-            for (uint64_t b = 0; b < rest; b++) {
-                const unsigned long long *blk = hb.data() + b * strd;
-                for (int k = 0; k < nc1; k++) {
-                    j.S1[k] += rd128(blk + 2 * k);
-                    j.S2[k] += rd128(blk + 2 * nc1 + 2 * k);
-                }
-                for (int x = 0; x < ACC_EXTRA; x++) j.ex[x] += blk[4 * nc1 + x];
-                j.walks += blk[4 * nc1];
-            }
+        CKR(launch_reduce(E, i, j.prefix, j.n_batches, j.d.n_c, st));
+        extra_launches++;
+        hb.resize(rest * strd);
+        CKR(cudaMemcpyAsync(hb.data(), d_acc + j.d.acc_base + j.prefix * strd, sizeof(unsigned long long) * rest * strd,
+                            cudaMemcpyDeviceToHost, st));
+        CKR(cudaStreamSynchronize(st));
+        const int nc1 = j.d.n_c + 1;
+        for (uint64_t b = 0; b < rest; b++) {
+            const unsigned long long *blk = hb.data() + b * strd;
+            fold_block(j, blk, blk[4 * nc1]);
         }
-        j.used_batches = j.n_batches;
         j.prefix = j.n_batches;
+    }
+    rc = check_status(ctx);
+    if (rc) {
+        cleanup();
+        return rc;
     }
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats_out) {
@@ -751,6 +970,11 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, RecArrays *rec, frw
             s.tables_built = ctx->h_status[STAT_BUILT];
             s.rounds = rounds;
             s.seconds = secs;
+            s.geom_ms = t_geom;
+            s.fill_ms = t_fill;
+            s.mw_ms = t_mw;
+            s.launches = 1 + 5 * rounds + extra_launches;
+            s.mw_jobs = ctx->h_status[STAT_MWJOBS];
         }
     }
     cleanup();
@@ -799,7 +1023,7 @@ extern "C" int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jo
         return false;
     }();
     if (any_walks) {
-        int rc = run_jobs(ctx, runs, nullptr, st.data());
+        int rc = run_jobs(ctx, runs, st.data());
         if (rc) return rc;
     } else {
         for (int i = 0; i < n_jobs; i++) {
@@ -842,7 +1066,7 @@ extern "C" int frw_extract(frw_ctx *ctx, int32_t sid, int32_t master, const frw_
     runs[0].walk_begin = p->walk_begin;
     frw_stats st;
     if (j.walk_budget) {
-        rc = run_jobs(ctx, runs, nullptr, &st);
+        rc = run_jobs(ctx, runs, &st);
         if (rc) return rc;
     } else {
         runs[0].d.n_c = ctx->structs[sid].n_c;
@@ -871,31 +1095,25 @@ extern "C" int frw_walk_records(frw_ctx *ctx, int32_t sid, int32_t master, uint6
     if (rc) return rc;
     if (n_walks == 0) return FRW_OK;
     CK(cudaSetDevice(ctx->device));
-    std::vector<void *> tmp;
-    RecArrays R;
-    if ((rc = dalloc(ctx, &R.omega, n_walks, tmp)) || (rc = dalloc(ctx, &R.k, n_walks, tmp)) ||
-        (rc = dalloc(ctx, &R.hops, n_walks, tmp)) || (rc = dalloc(ctx, &R.steps, n_walks, tmp)) ||
-        (rc = dalloc(ctx, &R.branch, n_walks, tmp))) {
-        for (void *p : tmp) cudaFree(p);
-        return rc;
-    }
     std::vector<JobRun> runs(1);
     runs[0].desc = j;
-    runs[0].record = 1;
     runs[0].walk_begin = walk_begin;
     frw_stats st;
-    rc = run_jobs(ctx, runs, &R, &st);
-    if (!rc) {
-        cudaError_t e = cudaSuccess;
-        if (omega && e == cudaSuccess) e = cudaMemcpy(omega, R.omega, sizeof(double) * n_walks, cudaMemcpyDeviceToHost);
-        if (electrode && e == cudaSuccess) e = cudaMemcpy(electrode, R.k, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost);
-        if (hops && e == cudaSuccess) e = cudaMemcpy(hops, R.hops, sizeof(uint32_t) * n_walks, cudaMemcpyDeviceToHost);
-        if (micro_steps && e == cudaSuccess) e = cudaMemcpy(micro_steps, R.steps, sizeof(uint64_t) * n_walks, cudaMemcpyDeviceToHost);
-        if (branch && e == cudaSuccess) e = cudaMemcpy(branch, R.branch, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "record copy");
-    }
-    for (void *p : tmp) cudaFree(p);
-    return rc;
+    rc = run_jobs(ctx, runs, &st);
+    if (rc) return rc;
+    // records of job 0 start at index 0 of the record pool
+    const RecArrays &R = ctx->rec;
+    cudaStream_t s = ctx->stream;
+    std::vector<uint32_t> st32(micro_steps ? n_walks : 0);
+    if (omega) CK(cudaMemcpyAsync(omega, R.omega, sizeof(double) * n_walks, cudaMemcpyDeviceToHost, s));
+    if (electrode) CK(cudaMemcpyAsync(electrode, R.k, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost, s));
+    if (hops) CK(cudaMemcpyAsync(hops, R.hops, sizeof(uint32_t) * n_walks, cudaMemcpyDeviceToHost, s));
+    if (micro_steps) CK(cudaMemcpyAsync(st32.data(), R.steps, sizeof(uint32_t) * n_walks, cudaMemcpyDeviceToHost, s));
+    if (branch) CK(cudaMemcpyAsync(branch, R.branch, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (micro_steps)
+        for (uint64_t i = 0; i < n_walks; i++) micro_steps[i] = st32[i];
+    return FRW_OK;
 }
 
 // ---------------------------------------------------------------------------
