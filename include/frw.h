@@ -189,6 +189,31 @@ int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t 
                         const double *eps_r, int32_t n_mat, uint64_t samples_per_cube,
                         uint64_t request_id, uint32_t *d_exit, uint32_t *d_steps);
 
+/* Allocation-free variant of frw_microwalk_cubes (the paper has no counterpart:
+ * this is a deployment convenience).  Some callers cannot allocate device memory:
+ * a host application that owns all device memory through its own allocator, or a
+ * loop with a fixed device-memory budget that must not pay the device-wide
+ * synchronisation that cudaMalloc / cudaFree imply.  This entry point allocates
+ * nothing and needs no context: it runs on the current CUDA device and on
+ * `cuda_stream` (cudaStream_t as void*, NULL = the default stream), takes the same
+ * inputs and writes the same outputs as frw_microwalk_cubes (bit-identical for the
+ * same seed and request id), and keeps its scratch -- the job counter, an error
+ * word and the 16 x 16 jump-weight table, 1.25 KB in all -- in one fixed
+ * file-scope device array of 2 KB that every GPU loading the library holds until
+ * the process exits.
+ *   - The first call on a device looks up that array's device address (once per
+ *     device); make this first call before any stream capture.
+ *   - Every call shares the array: it zeroes the counter and error word and writes
+ *     the weight table before its launch, so calls in sequence are independent, but
+ *     calls that overlap on the GPU (other streams, other host threads) race.
+ *   - Limits: 2 <= N <= 32 even, at most 15 materials (n_mat > 15 returns
+ *     FRW_ECAPACITY: the weight table has 15 rows), at most 8 blocks per cube record.
+ *   - Blocks the calling thread until the launch has finished; FRW_EDEVICE if the
+ *     kernel's step cap was hit or a CUDA call failed. */
+int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int32_t *d_cubes, const double *eps_r,
+                                int32_t n_mat, uint64_t seed, uint64_t samples_per_cube, uint64_t request_id,
+                                uint32_t *d_exit, uint32_t *d_steps, void *cuda_stream);
+
 /* One analytical table computed on the device (Eq. 8 for SGF kinds; the
  * first-cube flux kernel for FLUX kinds) for the context's N: profile[N] = material
  * ids (into eps_r) of the layers along table axis t2 (ignored for HOM kinds).

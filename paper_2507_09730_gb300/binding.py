@@ -20,7 +20,7 @@ FRW_TAB_SGF, FRW_TAB_FLUX_PAR, FRW_TAB_FLUX_PERP, FRW_TAB_SGF_HOM, FRW_TAB_FLUX_
 
 EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream", "frw_load_structure",
            "frw_unload_structure", "frw_extract", "frw_extract_batch", "frw_walk_records",
-           "frw_microwalk_cubes", "frw_table", "frw_strerror", "frw_last_error")
+           "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error")
 
 
 class frw_box(ctypes.Structure):
@@ -94,6 +94,8 @@ def lib():
                                    P(c_int32), P(c_uint32), P(c_uint64), P(c_int32)]
     L.frw_microwalk_cubes.argtypes = [c_void_p, c_int32, c_int32, c_void_p, P(c_double), c_int32, c_uint64,
                                       c_uint64, c_void_p, c_void_p]
+    L.frw_microwalk_cubes_noalloc.argtypes = [c_int32, c_int32, c_void_p, P(c_double), c_int32, c_uint64, c_uint64,
+                                              c_uint64, c_void_p, c_void_p, c_void_p]
     L.frw_table.argtypes = [c_void_p, c_int32, P(c_int32), P(c_double), c_int32, P(c_uint32), P(c_uint8),
                             P(c_double), P(c_double)]
     L.frw_strerror.argtypes = [c_int]
@@ -240,6 +242,16 @@ def frw_microwalk_cubes(ctx, N: int, n_cubes: int, d_cubes_ptr: int, eps, sample
                                    int(samples_per_cube), int(request_id), c_void_p(d_exit_ptr or 0),
                                    c_void_p(d_steps_ptr or 0))
     _check(ctx, rc)
+
+
+def frw_microwalk_cubes_noalloc(N: int, n_cubes: int, d_cubes_ptr: int, eps, seed: int, samples_per_cube: int,
+                                request_id: int, d_exit_ptr: int, d_steps_ptr: int, stream_handle: int = 0) -> int:
+    """Allocation-free MicroWalk on the current device; returns the status code."""
+    e = np.ascontiguousarray(eps, np.float64)
+    return lib().frw_microwalk_cubes_noalloc(int(N), int(n_cubes), c_void_p(d_cubes_ptr), _ptr(e, c_double), len(e),
+                                             int(seed), int(samples_per_cube), int(request_id),
+                                             c_void_p(d_exit_ptr or 0), c_void_p(d_steps_ptr or 0),
+                                             c_void_p(stream_handle or 0))
 
 
 def frw_table(ctx, N: int, kind: int, profile=None, eps=None):

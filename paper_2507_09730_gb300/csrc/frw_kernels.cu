@@ -13,6 +13,7 @@
 //   k_round_end  resets the per-round queues and publishes the active-slot count.
 // No kernel waits on another kernel or on the host: ordering comes only from the
 // launch order on the stream.
+#include <cmath>
 #include <cstdint>
 #include <cooperative_groups.h>
 #include <cuda/atomic>
@@ -1515,3 +1516,96 @@ cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uin
 }
 
 }  // namespace frw
+
+// ---------------------------------------------------------------------------
+// Allocation-free MicroWalk entry point (see frw_microwalk_cubes_noalloc in frw.h).
+// Its scratch lives in this fixed device array; host code only ever uses the
+// address returned by cudaGetSymbolAddress for the current device.
+#include <mutex>
+
+#include "frw.h"
+
+namespace frw {
+namespace {
+
+constexpr int NOALLOC_WORDS = 512;                   // 2 KB
+constexpr int NOALLOC_W_OFFSET = 64;                 // weight table at word 64 (256 words)
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+uint32_t *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on `dev` (looked up once per device).
+cudaError_t noalloc_scratch(int dev, uint32_t **out)
+{
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace frw
+
+extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int32_t *d_cubes, const double *eps_r,
+                                           int32_t n_mat, uint64_t seed, uint64_t samples_per_cube,
+                                           uint64_t request_id, uint32_t *d_exit, uint32_t *d_steps,
+                                           void *cuda_stream)
+{
+    using namespace frw;
+    if (N < 2 || N > FRW_MAX_N || (N & 1) || n_cubes < 0 || !eps_r || n_mat < 1) return FRW_EINVAL;
+    if (n_mat > FRW_MAX_MATERIALS) return FRW_ECAPACITY;
+    for (int i = 0; i < n_mat; i++)
+        if (!(eps_r[i] > 0.0)) return FRW_EINVAL;
+    if (n_cubes == 0 || samples_per_cube == 0) return FRW_OK;
+    if (!d_cubes) return FRW_EINVAL;
+    if (samples_per_cube > UINT64_MAX / (uint64_t)n_cubes) return FRW_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FRW_EDEVICE;
+    uint32_t *scr = nullptr;
+    if (noalloc_scratch(dev, &scr) != cudaSuccess) return FRW_EDEVICE;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // jump weights of Eq. 6, quantised as in the context path
+    uint32_t W[256];
+    for (int i = 0; i < 256; i++) W[i] = 0;
+    for (int v = 0; v < n_mat; v++) {
+        for (int i = 0; i < n_mat; i++) {
+            const double al = eps_r[i] / (eps_r[i] + eps_r[v]);
+            W[v * 16 + i] = (uint32_t)std::floor(al * 16777216.0 + 0.5);
+        }
+        W[v * 16 + BOUNDARY] = 16777216u;
+    }
+    uint8_t map[16];
+    for (int i = 0; i < 16; i++) map[i] = (uint8_t)i;
+    LaunchShape L;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return FRW_EDEVICE;
+    L.sms = sms;
+    L.mw_warps = 8;
+    L.mw_ctas_per_sm = 2;
+    L.geom_threads = 128;
+    L.fill_ctas = sms;
+    if (cudaFuncSetAttribute(k_mw<CubeSource>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mw_smem_bytes(N, L.mw_warps)) != cudaSuccess)
+        return FRW_EDEVICE;
+    // counter and error word start at zero; the weight table is rewritten every call
+    if (cudaMemsetAsync(scr, 0, 4 * sizeof(uint32_t), st) != cudaSuccess) return FRW_EDEVICE;
+    if (cudaMemcpyAsync(scr + NOALLOC_W_OFFSET, W, sizeof(W), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return FRW_EDEVICE;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32) ^ (uint32_t)request_id;
+    if (launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, map, scr + NOALLOC_W_OFFSET,
+                        d_exit, d_steps, reinterpret_cast<unsigned long long *>(scr), scr + 2, L,
+                        st) != cudaSuccess)
+        return FRW_EDEVICE;
+    uint32_t err = 0;
+    if (cudaMemcpyAsync(&err, scr + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FRW_EDEVICE;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FRW_EDEVICE;
+    return err ? FRW_EDEVICE : FRW_OK;
+}
