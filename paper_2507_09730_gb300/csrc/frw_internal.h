@@ -21,11 +21,13 @@ enum : uint32_t { ST_IDLE = 0, ST_FRESH = 1, ST_FIRST = 2, ST_HOP = 3, ST_MW = 4
 // device error flags (status word 1)
 enum : uint32_t {
     ERR_MWQ_OVERFLOW = 1u, ERR_CACHE_FULL = 2u, ERR_FILL = 4u, ERR_SHRINK = 8u, ERR_ACC_RANGE = 16u,
-    ERR_MW_STEPS = 32u
+    ERR_MW_STEPS = 32u, ERR_IDLE_TIMEOUT = 64u, ERR_REDUCE_QUEUE = 128u
 };
 // status words
-enum { STAT_ACTIVE = 0, STAT_ERR = 1, STAT_BUILT = 2, STAT_MWJOBS = 3, STAT_ACTIVE_CTR = 4,
+enum { STAT_ACTIVE = 0, STAT_ERR = 1, STAT_BUILT = 2, STAT_MWJOBS = 3, STAT_EPOCHS = 4, STAT_SUSPENDED = 5,
        STAT_WORDS = 8 };
+// host control words read by the running walk kernel
+enum { CTRL_OPEN = 0, CTRL_ABORT = 1, CTRL_WORDS = 4 };
 
 // cube classes
 enum : int { CUBE_HOM = 0, CUBE_STRAT = 1, CUBE_NONSTRAT = 2, CUBE_OVERFLOW = 3 };
@@ -86,6 +88,7 @@ struct DevJob {
     uint32_t acc_stride;   // u64 words per batch
     uint32_t pad;
     uint64_t rec_base;     // offset of walk 0 in the record arrays
+    uint64_t batch_base;   // index of batch 0 in the run's batch arrays
 };
 
 // per-batch accumulator block (u64 words):
@@ -151,28 +154,31 @@ struct EngineView {
     int hybrid;
     int max_hops;
     int fp32;
-    uint32_t NS;           // slots
+    uint32_t NS;           // slots = grid x pool
+    uint32_t pool;         // slots per CTA of the walk kernel (multiple of its block size)
     int n_jobs;
+    int max_nc;            // largest conductor count over the jobs (reduction scratch)
     SlotArrays s;
     const DevStructure *structs;
     const DevJob *jobs;
-    unsigned long long *job_next;
-    unsigned long long *job_limit;   // issue limit per job (<= walk_count), set by the host
-    int *job_cancel;
-    unsigned long long *acc;
+    unsigned long long *job_next;    // next walk offset per job (claimed by compare-and-swap)
+    unsigned long long *job_limit;   // issue limit per job (<= walk_count), written by the host
+    int *job_cancel;                 // written by the host
+    unsigned long long *acc;         // batch accumulator blocks
+    uint32_t *batch_done;            // finished walks per batch
+    uint32_t *batch_ready;           // 1 once the batch block is written
+    uint32_t *rq, *rq_count, *rq_head;   // queue of completed batches awaiting reduction
+    uint32_t rq_cap;
     RecArrays rec;
-    MWJob *mwq;
-    uint32_t *mwq_count, *mwq_head;
-    uint32_t mwq_cap;
+    MWJob *mwq;                      // one MicroWalk job record per slot
     TableCache tc;
     const uint32_t *W;     // [16][16]
     const double *eps;     // [16]
     FillConsts fc;
     uint32_t *status;      // STAT_WORDS
-    // slots waiting for a walk (FRESH) or for a first-cube table (FIRST): read by
-    // the first-transition kernel from *_in, appended to *_out for the next round
-    uint32_t *fresh_in, *fresh_out;
-    uint32_t *fresh_in_count, *fresh_out_count;
+    uint32_t *ctrl;        // CTRL_WORDS (host -> device)
+    unsigned long long *cycles;   // [4] SM cycles spent in geometry / fill / reduce / MicroWalk phases
+    double idle_timeout_s; // idle wait limit of the walk kernel
 };
 
 // ---- launchers (frw_kernels.cu) ----
@@ -184,18 +190,10 @@ struct LaunchShape {
     int sms;
 };
 
-cudaError_t launch_init_slots(const EngineView &E, cudaStream_t st);
-cudaError_t launch_first(const EngineView &E, const LaunchShape &L, cudaStream_t st);
-cudaError_t launch_round(const EngineView &E, const LaunchShape &L, cudaStream_t st);
-cudaError_t launch_geom(const EngineView &E, const LaunchShape &L, cudaStream_t st);
-cudaError_t launch_fill(const EngineView &E, const LaunchShape &L, cudaStream_t st);
-cudaError_t launch_mw(const EngineView &E, const LaunchShape &L, cudaStream_t st);
-cudaError_t launch_round_end(const EngineView &E, cudaStream_t st);
-// reduce batches [b0, b1) of job j from the walk records into the accumulator pool
-cudaError_t launch_reduce(const EngineView &E, int job, uint64_t b0, uint64_t b1, int nc, cudaStream_t st);
-// raise / set a job's issue limit (ids above the old limit that were claimed but
-// not run are handed out again) and put idle slots back to work
-cudaError_t launch_set_limit(const EngineView &E, int job, uint64_t limit, cudaStream_t st);
+// the persistent walk kernel: runs every job of the view to completion
+cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st);
+size_t walk_smem_bytes(int N, int max_nc);
+int walk_pool_slots();
 // fill one table with an explicit key into entry `entry` of the cache arrays
 cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4],
                             uint32_t entry, double *values_out, cudaStream_t st);
@@ -206,6 +204,6 @@ cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uin
                             const uint32_t *W, uint32_t *d_exit, uint32_t *d_steps,
                             unsigned long long *d_head, uint32_t *d_err, const LaunchShape &L,
                             cudaStream_t st);
-cudaError_t set_kernel_attributes(int N, int mw_warps);
+cudaError_t set_kernel_attributes(int N, int mw_warps, int max_nc);
 
 }  // namespace frw

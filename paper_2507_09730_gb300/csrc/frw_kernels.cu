@@ -1,18 +1,14 @@
 // frw_kernels.cu -- sm_103a kernels of the FRW + MicroWalk engine.
 //
-// One engine round is four launches on one stream:
-//   k_geom   one lane per walk slot: issues walks, makes the first transition,
-//            sizes transition cubes, classifies them (hybrid dispatch), samples the
-//            analytical route in place and hands non-stratified cubes to MicroWalk;
-//            requests missing analytical tables.
-//   k_fill   one CTA per requested table: the exact FD surface Green's function (or
-//            first-cube flux kernel) of a layered lattice by separation of variables.
-//   k_mw     persistent MicroWalk kernel (Algorithm 3): each lane runs one lattice
-//            walk at a time and refills from the device job queue at 4-step group
-//            boundaries, so walks of uneven length do not idle the warp.
-//   k_round_end  resets the per-round queues and publishes the active-slot count.
-// No kernel waits on another kernel or on the host: ordering comes only from the
-// launch order on the stream.
+//   k_walk      the persistent walk kernel: every CTA owns a pool of walk slots and
+//               cycles through geometry (walk issue, first transition, cube sizing,
+//               hybrid dispatch, analytical route), table fill, batch reduction and
+//               MicroWalk (Algorithm 3) phases, with no global barrier;
+//   k_fill_one  one analytical table for an explicit key (context set-up, frw_table);
+//   k_mw        the MicroWalk loop over stand-alone cubes (frw_microwalk_cubes).
+// No CTA waits for another CTA; the only wait is the bounded idle wait of k_walk
+// for host control words.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cooperative_groups.h>
@@ -370,7 +366,15 @@ __device__ __forceinline__ uint32_t hash5(uint32_t k, const uint32_t p[4])
     return h;
 }
 
-__device__ int table_lookup(const TableCache &tc, uint32_t kind, const uint32_t prof[4])
+// CTA-local list of cache entries claimed during the geometry phase; the CTA
+// fills them itself in its fill phase.
+struct FillList {
+    uint32_t *list;
+    uint32_t *count;
+    uint32_t cap;
+};
+
+__device__ int table_lookup(const TableCache &tc, uint32_t kind, const uint32_t prof[4], const FillList &fl)
 {
     const uint32_t h = hash5(kind, prof);
     for (uint32_t probe = 0; probe < 64; probe++) {
@@ -378,16 +382,19 @@ __device__ int table_lookup(const TableCache &tc, uint32_t kind, const uint32_t 
         uint32_t st = cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(tc.state[e]).load(
             cuda::memory_order_acquire);
         if (st == TE_EMPTY) {
+            // claim only if this CTA has room to fill the entry in this epoch
+            const uint32_t li = atomicAdd(fl.count, 1u);
+            if (li >= fl.cap) return -1;
             const uint32_t old = atomicCAS(&tc.state[e], TE_EMPTY, TE_CLAIMED);
             if (old == TE_EMPTY) {
                 uint32_t *k = tc.keys + 5 * e;
                 k[0] = kind; k[1] = prof[0]; k[2] = prof[1]; k[3] = prof[2]; k[4] = prof[3];
                 __threadfence();
                 atomicExch(&tc.state[e], TE_REQUESTED);
-                const uint32_t qi = atomicAdd(tc.fillq_count, 1u);
-                if (qi < tc.cap) tc.fillq[qi] = e;
+                fl.list[li] = e;
                 return -1;
             }
+            fl.list[li] = 0xffffffffu;   // slot taken by another claimant: nothing to fill
             st = old;
         }
         if (st == TE_CLAIMED) return -1;
@@ -449,18 +456,33 @@ struct WalkState {
     double omega;
 };
 
-// A finished walk writes its record; batches are folded later by k_reduce, so
-// completion involves no shared counter.  k is written last.
+// A finished walk writes its record (electrode k last, with release order) and
+// counts itself in its batch; the group of lanes that completes a batch queues
+// it for reduction.
 __device__ void finish_walk(const EngineView &E, const DevJob &J, const WalkState &w, int k)
 {
-    const uint64_t r = J.rec_base + (w.walk - J.walk_begin);
+    const uint64_t rel = w.walk - J.walk_begin;
+    const uint64_t r = J.rec_base + rel;
     E.rec.omega[r] = w.omega;
     E.rec.hops[r] = w.hop;
     E.rec.steps[r] = (uint32_t)w.steps;
     E.rec.cnt_sh[r] = w.cnt_sh;
     E.rec.cnt_mw[r] = w.cnt_mw;
     E.rec.branch[r] = w.branch;
-    E.rec.k[r] = k;
+    cuda::atomic_ref<int32_t, cuda::thread_scope_device>(E.rec.k[r]).store(k, cuda::memory_order_release);
+    const uint64_t bi = rel / J.batch;
+    const uint64_t g = J.batch_base + bi;
+    const uint32_t bsz = (uint32_t)min(J.batch, J.walk_count - bi * J.batch);
+    cg::coalesced_group grp = cg::coalesced_threads();
+    cg::coalesced_group same = cg::labeled_partition(grp, (unsigned long long)g);
+    if (same.thread_rank() == 0) {
+        const uint32_t old = atomicAdd(&E.batch_done[g], (uint32_t)same.size());
+        if (old + (uint32_t)same.size() == bsz) {
+            const uint32_t qi = atomicAdd(E.rq_count, 1u);
+            if (qi < E.rq_cap) E.rq[qi] = (uint32_t)g;
+            else atomicOr(&E.status[STAT_ERR], ERR_REDUCE_QUEUE);
+        }
+    }
 }
 
 // First transition (hop 0): point on the Gaussian surface, first cube with the
@@ -468,7 +490,7 @@ __device__ void finish_walk(const EngineView &E, const DevJob &J, const WalkStat
 // Returns false when a table is not ready yet (retry next round, same draws).
 template <typename T>
 __device__ bool first_transition(const EngineView &E, const DevJob &J, const SView<T> &S, WalkState &w,
-                                 T pos[3])
+                                 T pos[3], const FillList &fl)
 {
     typedef Ar<T> A;
     const int N = E.N;
@@ -537,7 +559,7 @@ __device__ bool first_transition(const EngineView &E, const DevJob &J, const SVi
         frame_sgf(na, fr);
     } else {
         const uint32_t kind = (qq.axis == na) ? TAB_FLUX_PAR : TAB_FLUX_PERP;
-        const int e = table_lookup(tc, kind, qq.prof);
+        const int e = table_lookup(tc, kind, qq.prof, fl);
         if (e < 0) {
             if (e == -2) atomicOr(&E.status[STAT_ERR], ERR_CACHE_FULL);
             return false;
@@ -560,14 +582,6 @@ __device__ bool first_transition(const EngineView &E, const DevJob &J, const SVi
 }
 
 __device__ __forceinline__ uint32_t nib(uint32_t v, int i) { return (v >> (4 * i)) & 15u; }
-
-__device__ __forceinline__ void append_fresh(const EngineView &E, uint32_t s)
-{
-    cg::coalesced_group g = cg::coalesced_threads();
-    uint32_t base = 0;
-    if (g.thread_rank() == 0) base = atomicAdd(E.fresh_out_count, (uint32_t)g.size());
-    E.fresh_out[g.shfl(base, 0) + g.thread_rank()] = s;
-}
 
 __device__ __forceinline__ void store_walk(const EngineView &E, uint32_t s, const WalkState &w)
 {
@@ -593,38 +607,88 @@ __device__ __forceinline__ void load_walk(const EngineView &E, uint32_t s, WalkS
     w.omega = E.s.omega[s];
 }
 
-// Slot waiting for a walk or for a first-cube table: take a walk id (one atomic
-// per group of lanes asking the same job), then make the first transition.
-template <typename T>
-__device__ void first_slot(const EngineView &E, uint32_t s)
+__device__ __forceinline__ bool job_open(const EngineView &E, int j)
 {
-    uint32_t st = E.s.state[s];
-    WalkState w;
-    load_walk(E, s, w);
-    if (st == ST_FIRST && E.job_cancel[w.job]) st = ST_FRESH;
-    if (st == ST_FRESH) {
-        bool found = false;
-        for (int t = 0; t < E.n_jobs; t++) {
-            const uint32_t jj = (w.job + t) % (uint32_t)E.n_jobs;
-            if (E.job_cancel[jj]) continue;
-            const DevJob &Jc = E.jobs[jj];
-            const uint64_t lim = ((volatile uint64_t *)E.job_limit)[jj];
-            if (((volatile unsigned long long *)E.job_next)[jj] >= lim) continue;
-            cg::coalesced_group g = cg::coalesced_threads();
-            cg::coalesced_group same = cg::labeled_partition(g, (int)jj);
-            unsigned long long base = 0;
-            if (same.thread_rank() == 0) base = atomicAdd(&E.job_next[jj], (unsigned long long)same.size());
-            base = same.shfl(base, 0);
-            const unsigned long long x = base + same.thread_rank();
-            if (x < lim) {
-                w.job = jj;
-                w.walk = Jc.walk_begin + x;
-                found = true;
+    return !((volatile int *)E.job_cancel)[j] &&
+           ((volatile unsigned long long *)E.job_next)[j] < ((volatile unsigned long long *)E.job_limit)[j];
+}
+
+// Walk ids are claimed per CTA, once per epoch, for exactly the number of free
+// slots (one compare-and-swap per job on the job's counter, which therefore never
+// passes the issue limit the host may move while the kernel runs); free slots then
+// take ids from the CTA's claimed ranges through a shared-memory counter.
+constexpr int ISSUE_MAX_JOBS = 64;     // claimed ranges per CTA and epoch
+struct IssueRanges {
+    uint32_t n;                        // number of ranges
+    uint32_t pos;                      // next id to hand out (over the concatenated ranges)
+    uint32_t total;
+    uint32_t job[ISSUE_MAX_JOBS];
+    unsigned long long lo[ISSUE_MAX_JOBS];
+    uint32_t cnt[ISSUE_MAX_JOBS];
+};
+
+// thread 0: claim up to `want` ids over the open jobs, starting at job `first`
+__device__ void claim_ids(const EngineView &E, IssueRanges &ir, uint32_t want, uint32_t first)
+{
+    ir.n = 0;
+    ir.pos = 0;
+    ir.total = 0;
+    if (want == 0 || E.n_jobs == 0) return;
+    for (int t = 0; t < E.n_jobs && ir.total < want && ir.n < ISSUE_MAX_JOBS; t++) {
+        const uint32_t jj = (first + (uint32_t)t) % (uint32_t)E.n_jobs;
+        if (((volatile int *)E.job_cancel)[jj]) continue;
+        const unsigned long long lim = ((volatile unsigned long long *)E.job_limit)[jj];
+        for (int tries = 0; tries < 64; tries++) {
+            const unsigned long long c = ((volatile unsigned long long *)E.job_next)[jj];
+            if (c >= lim) break;
+            const unsigned long long take = min((unsigned long long)(want - ir.total), lim - c);
+            if (atomicCAS(&E.job_next[jj], c, c + take) == c) {
+                ir.job[ir.n] = jj;
+                ir.lo[ir.n] = c;
+                ir.cnt[ir.n] = (uint32_t)take;
+                ir.n++;
+                ir.total += (uint32_t)take;
                 break;
             }
         }
-        if (!found) {
+    }
+}
+
+// a free slot takes the next claimed id (false when the CTA's ranges are used up)
+__device__ bool issue_walk(const EngineView &E, IssueRanges &ir, WalkState &w)
+{
+    const uint32_t i = atomicAdd(&ir.pos, 1u);
+    if (i >= ir.total) return false;
+    uint32_t r = 0, off = i;
+    while (off >= ir.cnt[r]) {
+        off -= ir.cnt[r];
+        r++;
+    }
+    const uint32_t jj = ir.job[r];
+    w.job = jj;
+    w.walk = E.jobs[jj].walk_begin + ir.lo[r] + off;
+    return true;
+}
+
+// Geometry-phase work of one slot: a new walk and its first transition if the
+// slot is free, then one step of the walk (Algorithm 1 inner loop): absorption
+// test, cube sizing, classification, then the analytical route in place or a
+// MicroWalk job queued for this CTA.
+template <typename T>
+__device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const FillList &fl, uint16_t *qlist,
+                         uint32_t *q_count, IssueRanges &ir)
+{
+    typedef Ar<T> A;
+    const int N = E.N;
+    const uint32_t NS = E.NS;
+    uint32_t st = E.s.state[s];
+    WalkState w;
+    load_walk(E, s, w);
+    if (st != ST_FRESH && ((volatile int *)E.job_cancel)[w.job]) st = ST_FRESH;   // drop the walk
+    if (st == ST_FRESH) {
+        if (!issue_walk(E, ir, w)) {
             E.s.state[s] = ST_IDLE;
+            E.s.job[s] = w.job;
             return;
         }
         w.hop = 0; w.steps = 0; w.cnt_sh = 0; w.cnt_mw = 0; w.branch = -1; w.omega = 0.0;
@@ -633,70 +697,32 @@ __device__ void first_slot(const EngineView &E, uint32_t s)
     const DevJob &J = E.jobs[w.job];
     const SView<T> S = sview<T>(E.structs[J.sid]);
     T pos[3];
-    if (first_transition<T>(E, J, S, w, pos)) {
+    if (st == ST_FIRST) {
+        if (!first_transition<T>(E, J, S, w, pos, fl)) {   // table not ready: retry next epoch
+            E.s.state[s] = ST_FIRST;
+            store_walk(E, s, w);
+            return;
+        }
         w.hop = 1;
-        st = ST_HOP;
-        E.s.pos[s] = (double)pos[0];
-        E.s.pos[E.NS + s] = (double)pos[1];
-        E.s.pos[2 * E.NS + s] = (double)pos[2];
-    } else {
-        append_fresh(E, s);   // table not ready: retry next round with the same draws
-    }
-    E.s.state[s] = st;
-    store_walk(E, s, w);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(128) k_first(EngineView E)
-{
-    const uint32_t n = min(*E.fresh_in_count, E.NS);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        first_slot<T>(E, E.fresh_in[i]);
-}
-
-// One geometry step of one walk (Algorithm 1 inner loop): absorption test, cube
-// sizing, classification, then the analytical route in place or a MicroWalk job.
-// Returns whether the slot is still in use.
-template <typename T>
-__device__ bool step_slot(const EngineView &E, uint32_t s)
-{
-    typedef Ar<T> A;
-    uint32_t st = E.s.state[s];
-    if (st == ST_IDLE) return false;
-    if (st != ST_HOP && st != ST_MWDONE) return true;     // FRESH / FIRST: handled by k_first
-    const int N = E.N;
-    const uint32_t NS = E.NS;
-    WalkState w;
-    load_walk(E, s, w);
-    if (E.job_cancel[w.job]) {
-        E.s.state[s] = ST_FRESH;
-        append_fresh(E, s);
-        return true;
-    }
-    const DevJob &J = E.jobs[w.job];
-    const SView<T> S = sview<T>(E.structs[J.sid]);
-    T pos[3];
-    if (st == ST_MWDONE) {
+    } else if (st == ST_MWDONE) {
         const uint32_t en = E.s.exitnode[s];
         const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
         const T c[3] = {(T)E.s.cube[s], (T)E.s.cube[NS + s], (T)E.s.cube[2 * NS + s]};
         const T R = (T)E.s.cube[3 * NS + s];
         node_point(c, R, N, node, pos);
         w.hop++;
-    } else {
+    } else {   // ST_HOP
         pos[0] = (T)E.s.pos[s];
         pos[1] = (T)E.s.pos[NS + s];
         pos[2] = (T)E.s.pos[2 * NS + s];
     }
-    bool moved = (st == ST_MWDONE);
-    st = ST_HOP;
     int who;
     const T d = nearest_electrode(S, pos, who);
     if (d <= S.tau || (int)w.hop >= E.max_hops) {
         finish_walk(E, J, w, d <= S.tau ? who : -1);
         E.s.state[s] = ST_FRESH;
-        append_fresh(E, s);
-        return true;
+        E.s.job[s] = w.job;
+        return;
     }
     T R = E.fp32 ? A::sub(d, S.margin) : d;
     CubeInfo q;
@@ -710,60 +736,42 @@ __device__ bool step_slot(const EngineView &E, uint32_t s)
         atomicOr(&E.status[STAT_ERR], ERR_SHRINK);
         finish_walk(E, J, w, -1);
         E.s.state[s] = ST_FRESH;
-        append_fresh(E, s);
-        return true;
+        E.s.job[s] = w.job;
+        return;
     }
     const uint4 hb = philox10((uint32_t)w.walk, (uint32_t)(w.walk >> 32), w.hop, 0u, J.key0, J.key1);
-    bool analytic = false;
-    int m = 0, fr[3] = {0, 1, 2};
+    int m = -1, fr[3] = {0, 1, 2};
+    bool wait = false;
     if (E.hybrid && q.kind == CUBE_HOM) {
         m = sample_thr(E.tc.thr + (size_t)E.tc.cap * E.tc.P, (int)E.tc.P, hb.x);
-        analytic = true;
         w.cnt_sh += 1u << 16;
     } else if (E.hybrid && q.kind == CUBE_STRAT) {
-        const int e = table_lookup(E.tc, TAB_SGF, q.prof);
+        const int e = table_lookup(E.tc, TAB_SGF, q.prof, fl);
         if (e < 0) {
             if (e == -2) atomicOr(&E.status[STAT_ERR], ERR_CACHE_FULL);
-            // retry this hop next round (same draws)
-            if (moved) {
-                E.s.pos[s] = (double)pos[0];
-                E.s.pos[NS + s] = (double)pos[1];
-                E.s.pos[2 * NS + s] = (double)pos[2];
-            }
-            E.s.state[s] = ST_HOP;
-            store_walk(E, s, w);
-            return true;
+            wait = true;                   // retry this hop next epoch (same draws)
+        } else {
+            m = sample_thr(E.tc.thr + (size_t)e * E.tc.P, (int)E.tc.P, hb.x);
+            frame_sgf(q.axis, fr);
+            w.cnt_sh += 1u;
         }
-        m = sample_thr(E.tc.thr + (size_t)e * E.tc.P, (int)E.tc.P, hb.x);
-        frame_sgf(q.axis, fr);
-        analytic = true;
-        w.cnt_sh += 1u;
     }
-    if (analytic) {
-        int node[3];
-        panel_node(N, fr, m, node);
-        node_point(pos, R, N, node, pos);
-        w.hop++;
+    if (wait || m >= 0) {
+        if (m >= 0) {
+            int node[3];
+            panel_node(N, fr, m, node);
+            node_point(pos, R, N, node, pos);
+            w.hop++;
+        }
         E.s.pos[s] = (double)pos[0];
         E.s.pos[NS + s] = (double)pos[1];
         E.s.pos[2 * NS + s] = (double)pos[2];
         E.s.state[s] = ST_HOP;
         store_walk(E, s, w);
-        return true;
+        return;
     }
-    // MicroWalk job (Algorithm 3) for this cube
-    uint32_t qi;
-    {
-        cg::coalesced_group g = cg::coalesced_threads();
-        uint32_t base = 0;
-        if (g.thread_rank() == 0) base = atomicAdd(E.mwq_count, (uint32_t)g.size());
-        qi = g.shfl(base, 0) + g.thread_rank();
-    }
-    if (qi >= E.mwq_cap) {
-        atomicOr(&E.status[STAT_ERR], ERR_MWQ_OVERFLOW);
-        return true;
-    }
-    MWJob *jb = E.mwq + qi;
+    // MicroWalk job (Algorithm 3) for this cube, recorded with the slot
+    MWJob *jb = E.mwq + s;
     const uint32_t s3 = hb.x >> 29;
     const uint32_t c0 = (uint32_t)(N / 2 - 1);
     const uint32_t start = (c0 + (s3 & 1u)) | ((c0 + ((s3 >> 1) & 1u)) << 8) | ((c0 + ((s3 >> 2) & 1u)) << 16);
@@ -773,7 +781,7 @@ __device__ bool step_slot(const EngineView &E, uint32_t s)
     uint4 *dst = reinterpret_cast<uint4 *>(jb);
     dst[0] = make_uint4(s, w.hop, (uint32_t)w.walk, (uint32_t)(w.walk >> 32));
     dst[1] = make_uint4(start, (uint32_t)q.K, (uint32_t)mm, (uint32_t)(mm >> 32));
-    dst[2] = make_uint4(J.key0, J.key1, 0u, 0u);
+    dst[2] = make_uint4(J.key0, J.key1, 0u, 0u);      // pad0 = steps already taken (resume)
     for (int t = 0; t < q.K; t++) jb->rng[t] = q.rng[t];
     E.s.cube[s] = (double)pos[0];
     E.s.cube[NS + s] = (double)pos[1];
@@ -782,51 +790,11 @@ __device__ bool step_slot(const EngineView &E, uint32_t s)
     w.cnt_mw++;
     E.s.state[s] = ST_MW;
     store_walk(E, s, w);
-    return true;
-}
-
-// One lane per slot; the slot count is a multiple of the block size, so every
-// lane of a warp reaches the ballot.
-template <typename T>
-__global__ void __launch_bounds__(256) k_geom(EngineView E)
-{
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = (s < E.NS) ? step_slot<T>(E, s) : false;
-    const uint32_t b = __ballot_sync(FULL_MASK, act);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&E.status[STAT_ACTIVE_CTR], (uint32_t)__popc(b));
-}
-
-__global__ void k_init_slots(EngineView E)
-{
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < E.NS; s += stride) {
-        E.s.state[s] = ST_FRESH;
-        E.s.job[s] = E.n_jobs > 0 ? s % (uint32_t)E.n_jobs : 0u;
-        E.s.hop[s] = 0;
-        E.s.steps[s] = 0;
-        E.s.cnt_sh[s] = 0;
-        E.s.cnt_mw[s] = 0;
-        E.s.branch[s] = -1;
-        E.s.omega[s] = 0.0;
-        E.fresh_in[s] = s;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *E.fresh_in_count = E.NS;
-        *E.fresh_out_count = 0;
-    }
-}
-
-__global__ void k_round_end(EngineView E)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        E.status[STAT_ACTIVE] = E.status[STAT_ACTIVE_CTR];
-        E.status[STAT_ACTIVE_CTR] = 0;
-        E.status[STAT_MWJOBS] += *E.mwq_count;
-        *E.mwq_count = 0;
-        *E.mwq_head = 0;
-        *E.tc.fillq_count = 0;
-        *E.tc.fillq_head = 0;
-        *E.fresh_in_count = 0;     // consumed; becomes next round's output list
+    {
+        cg::coalesced_group g = cg::coalesced_threads();
+        uint32_t base = 0;
+        if (g.thread_rank() == 0) base = atomicAdd(q_count, (uint32_t)g.size());
+        qlist[g.shfl(base, 0) + g.thread_rank()] = (uint16_t)o;
     }
 }
 
@@ -879,52 +847,6 @@ __device__ __forceinline__ bool mw_step(const uint32_t *__restrict__ M, const ui
 struct MWLane {
     uint32_t walk_lo, walk_hi, hop, key0, key1, tag;
     uint64_t mm;
-};
-
-// Job source: the engine's per-round queue.
-struct QueueSource {
-    const MWJob *q;
-    const uint32_t *cnt;
-    uint32_t *head;
-    uint32_t *err;
-    SlotArrays s;
-    uint32_t NS;
-    __device__ uint64_t grab(uint32_t n) const { return atomicAdd(head, n); }
-    __device__ bool valid(uint64_t j) const { return j < (uint64_t)min(*cnt, NS); }
-    __device__ void overrun() const { atomicOr(err, ERR_MW_STEPS); }
-    __device__ void build(uint64_t j, uint32_t *Mcol, int NP2, int N, int lane) const
-    {
-        const MWJob &b = q[j];
-        const int K = (int)b.K;
-        for (int row = lane; row < 3 * NP2; row += 32) {
-            const int a = row / NP2;
-            const int c = row - a * NP2 - 1;
-            uint32_t m = 0;
-            if (c >= 0 && c < N) {
-                m = 1u;
-                for (int t = 0; t < K; t++) {
-                    const uint2 r = b.rng[t];
-                    if (rng_lo(r, a) <= c && c < rng_hi(r, a)) m |= 2u << t;
-                }
-            }
-            Mcol[row * 32] = m;
-        }
-    }
-    __device__ void load(uint64_t j, MWLane &L, int &x, int &y, int &z) const
-    {
-        const MWJob &b = q[j];
-        L.walk_lo = b.walk_lo; L.walk_hi = b.walk_hi; L.hop = b.hop;
-        L.key0 = b.key0; L.key1 = b.key1; L.tag = b.slot;
-        L.mm = (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32);
-        x = (int)(b.start & 255u); y = (int)((b.start >> 8) & 255u); z = (int)((b.start >> 16) & 255u);
-    }
-    __device__ void finish(const MWLane &L, int x, int y, int z, uint32_t steps) const
-    {
-        const uint32_t sl = L.tag;
-        s.exitnode[sl] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
-        s.steps[sl] += steps;
-        s.state[sl] = ST_MWDONE;
-    }
 };
 
 // Job source: stand-alone cubes given as integer voxel ranges (64 int32 per cube).
@@ -1238,40 +1160,6 @@ __device__ void fill_table(const FillJob &F, int N, const double *__restrict__ e
     }
 }
 
-__global__ void k_fill(EngineView E)
-{
-    extern __shared__ double fsm[];
-    __shared__ uint32_t e_sh;
-    const TableCache &tc = E.tc;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t qi = atomicAdd(tc.fillq_head, 1u);
-            const uint32_t cnt = min(*tc.fillq_count, tc.cap);
-            e_sh = (qi < cnt) ? tc.fillq[qi] : 0xffffffffu;
-        }
-        __syncthreads();
-        const uint32_t e = e_sh;
-        if (e == 0xffffffffu) break;
-        FillJob F;
-        const uint32_t *k = tc.keys + 5 * e;
-        F.kind = k[0];
-        F.prof[0] = k[1]; F.prof[1] = k[2]; F.prof[2] = k[3]; F.prof[3] = k[4];
-        F.thr = tc.thr + (size_t)e * tc.P;
-        F.sgn = tc.sgn + (size_t)e * tc.P32;
-        F.ktot = tc.ktot + e;
-        F.values = nullptr;
-        F.err = &E.status[STAT_ERR];
-        fill_table(F, E.N, E.eps, E.fc, fsm);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicExch(&tc.state[e], TE_READY);
-            atomicAdd(&E.status[STAT_BUILT], 1u);
-        }
-        __syncthreads();
-    }
-}
-
 __global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t entry, double *values)
 {
     extern __shared__ double fsm[];
@@ -1311,15 +1199,23 @@ __device__ __forceinline__ void to_fixed128(double v, double scale, unsigned lon
     }
 }
 
-__global__ void __launch_bounds__(256) k_reduce(EngineView E, int job, uint64_t b0)
+// CTA-cooperative reduction of one complete batch g into its accumulator block;
+// sets batch_ready[g] (release) once the block is written.
+__device__ void reduce_batch(const EngineView &E, uint32_t g, unsigned long long *acc_sm)
 {
-    extern __shared__ unsigned long long acc_sm[];
-    const DevJob &J = E.jobs[job];
+    int j = 0;
+    for (; j < E.n_jobs; j++) {
+        const DevJob &Jc = E.jobs[j];
+        const uint64_t nb = (Jc.walk_count + Jc.batch - 1) / Jc.batch;
+        if (g >= Jc.batch_base && g < Jc.batch_base + nb) break;
+    }
+    if (j == E.n_jobs) return;
+    const DevJob &J = E.jobs[j];
     const int nc1 = J.n_c + 1;
     const uint32_t words = J.acc_stride;
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) acc_sm[i] = 0ull;
     __syncthreads();
-    const uint64_t b = b0 + blockIdx.x;
+    const uint64_t b = g - J.batch_base;
     const uint64_t w0 = b * J.batch;
     const uint64_t w1 = min(w0 + J.batch, J.walk_count);
     unsigned long long *ex = acc_sm + 4 * nc1;
@@ -1327,7 +1223,7 @@ __global__ void __launch_bounds__(256) k_reduce(EngineView E, int job, uint64_t 
     for (int x = 0; x < ACC_EXTRA; x++) loc[x] = 0ull;
     for (uint64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
         const uint64_t r = J.rec_base + w;
-        const int k = E.rec.k[r];
+        const int k = cuda::atomic_ref<int32_t, cuda::thread_scope_device>(E.rec.k[r]).load(cuda::memory_order_acquire);
         if (k == REC_PENDING) continue;
         loc[0]++;
         loc[1] += E.rec.hops[r];
@@ -1357,40 +1253,63 @@ __global__ void __launch_bounds__(256) k_reduce(EngineView E, int job, uint64_t 
     __syncthreads();
     unsigned long long *out = E.acc + J.acc_base + b * words;
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) out[i] = acc_sm[i];
-}
-
-__global__ void k_set_limit(EngineView E, int job, uint64_t limit)
-{
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s == 0) {
-        unsigned long long nx = E.job_next[job];
-        const unsigned long long old = E.job_limit[job];
-        if (nx > old) nx = old;                 // ids claimed past the old limit were not run
-        E.job_next[job] = nx;
-        E.job_limit[job] = limit > nx ? limit : nx;   // never below what was issued
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(E.batch_ready[g]).store(1u, cuda::memory_order_release);
     }
-    if (s < E.NS && E.s.state[s] == ST_IDLE) {
-        E.s.state[s] = ST_FRESH;
-        E.fresh_out[atomicAdd(E.fresh_out_count, 1u)] = s;
+    __syncthreads();
+}
+
+// Take one completed batch from the reduction queue (compare-and-swap on the
+// head; an entry is taken only once its index has been written).
+__device__ uint32_t take_batch(const EngineView &E)
+{
+    for (int tries = 0; tries < 64; tries++) {
+        const uint32_t h = *(volatile uint32_t *)E.rq_head;
+        const uint32_t c = min(*(volatile uint32_t *)E.rq_count, E.rq_cap);
+        if (h >= c) return 0xffffffffu;
+        const uint32_t item = *(volatile uint32_t *)(E.rq + h);
+        if (item == 0xffffffffu) return 0xffffffffu;     // not written yet: next epoch
+        if (atomicCAS(E.rq_head, h, h + 1u) == h) return item;
     }
-}
-
-cudaError_t launch_set_limit(const EngineView &E, int job, uint64_t limit, cudaStream_t st)
-{
-    k_set_limit<<<(E.NS + 255) / 256, 256, 0, st>>>(E, job, limit);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reduce(const EngineView &E, int job, uint64_t b0, uint64_t b1, int nc, cudaStream_t st)
-{
-    if (b1 <= b0) return cudaSuccess;
-    const size_t smem = sizeof(unsigned long long) * acc_stride_for(nc);
-    k_reduce<<<(unsigned)(b1 - b0), 256, smem, st>>>(E, job, b0);
-    return cudaGetLastError();
+    return 0xffffffffu;
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// The persistent walk kernel.  Each CTA owns a pool of walk slots and cycles, on
+// its own, through four phases per epoch (no CTA ever waits for another):
+//   geometry  every slot that is not in MicroWalk makes one step: a free slot takes
+//             a walk id and makes the first transition; a walk at a point sizes its
+//             cube, classifies it, and either samples the analytical route in place
+//             or records a MicroWalk job in the CTA's queue;
+//   fill      the CTA fills the analytical tables it claimed (separable FD solve);
+//   reduce    completed batches queued by any CTA are folded into accumulators;
+//   MicroWalk each warp runs the CTA's queued lattice walks (Algorithm 3), one per
+//             lane, refilling lanes at 4-step boundaries; once the queue is empty a
+//             warp with few lanes left suspends them (node and step count saved, so
+//             the Philox stream continues unchanged) and they resume next epoch.
+// The kernel exits when its pool is empty, no walk can be issued and the host has
+// closed the run; an idle wait is bounded by E.idle_timeout_s.
+constexpr int WALK_THREADS = 256;
+constexpr int WALK_WARPS = WALK_THREADS / 32;
+constexpr int POOL_MAX = 4096;
+constexpr int FILL_MAX = 128;
+constexpr int SUSPEND_LANES = 8;
+constexpr uint32_t SUSPEND_MIN_STEPS = 64;    // progress a job makes in an epoch before it may be suspended
+constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // ... and only if this much geometry work is waiting
+
+struct WalkShared {
+    uint32_t W[256];
+    uint32_t q_count, q_head, s_count, g_count;
+    uint32_t f_count, active, issuable, stop;
+    uint32_t red, finished, n_free, rr;
+    IssueRanges ir;
+    uint32_t fill[FILL_MAX];
+    uint16_t qlist[2][POOL_MAX];
+    uint16_t glist[POOL_MAX];
+};
+
 size_t fill_smem_bytes(int N)
 {
     const int H = N / 2;
@@ -1402,84 +1321,300 @@ size_t mw_smem_bytes(int N, int warps)
     return sizeof(uint32_t) * (256 + (size_t)warps * 3 * (N + 2) * 32);
 }
 
-cudaError_t set_kernel_attributes(int N, int mw_warps)
+size_t walk_smem_bytes(int N, int max_nc)
 {
-    cudaError_t e;
-    e = cudaFuncSetAttribute(k_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes(N));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_fill_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fill_smem_bytes(N));
-    if (e != cudaSuccess) return e;
-    const int mws = (int)mw_smem_bytes(N, mw_warps);
-    e = cudaFuncSetAttribute(k_mw<QueueSource>, cudaFuncAttributeMaxDynamicSharedMemorySize, mws);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_mw<CubeSource>, cudaFuncAttributeMaxDynamicSharedMemorySize, mws);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    return e;
+    const size_t masks = sizeof(uint32_t) * (size_t)WALK_WARPS * 3 * (N + 2) * 32;
+    const size_t fill = fill_smem_bytes(N);
+    const size_t red = sizeof(unsigned long long) * acc_stride_for(max_nc);
+    return std::max(masks, std::max(fill, red));
 }
 
-cudaError_t launch_init_slots(const EngineView &E, cudaStream_t st)
+int walk_pool_slots() { return POOL_MAX; }
+
+template <typename T>
+__global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
 {
-    const int threads = 256;
-    const int blocks = (int)((E.NS + threads - 1) / threads);
-    k_init_slots<<<blocks, threads, 0, st>>>(E);
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ WalkShared sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N = E.N, NP2 = N + 2;
+    const uint32_t P = E.pool;
+    const uint32_t base = blockIdx.x * P;
+    for (int i = tid; i < 256; i += WALK_THREADS) sh.W[i] = E.W[i];
+    for (uint32_t o = tid; o < P; o += WALK_THREADS) {
+        const uint32_t s = base + o;
+        E.s.state[s] = ST_FRESH;
+        E.s.job[s] = E.n_jobs > 0 ? s % (uint32_t)E.n_jobs : 0u;
+    }
+    if (tid == 0) {
+        sh.q_count = 0; sh.q_head = 0; sh.s_count = 0; sh.stop = 0;
+        sh.rr = blockIdx.x % (uint32_t)(E.n_jobs > 0 ? E.n_jobs : 1);
+    }
+    __syncthreads();
+    int cur = 0;
+    unsigned long long idle_t0 = 0, cyc[4] = {0, 0, 0, 0};
+    uint32_t epochs = 0;
+    for (;;) {
+        const long long c0 = clock64();
+        // ---------------- geometry phase ----------------
+        if (tid == 0) {
+            sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0;
+            uint32_t iss = 0;
+            for (int j = 0; j < E.n_jobs; j++)
+                if (job_open(E, j)) iss = 1;
+            sh.issuable = iss;
+        }
+        __syncthreads();
+        const bool iss = sh.issuable != 0;
+        for (uint32_t o = tid; o < P; o += WALK_THREADS) {     // P is a multiple of the block size
+            const uint32_t s = base + o;
+            uint32_t st = E.s.state[s];
+            if (st == ST_IDLE && iss) {
+                st = ST_FRESH;
+                E.s.state[s] = ST_FRESH;
+            }
+            const bool act = st != ST_IDLE;
+            const bool need = act && st != ST_MW;
+            uint32_t wj = 0;
+            if (st != ST_FRESH && st != ST_IDLE) wj = E.s.job[s];
+            const bool free_slot = st == ST_FRESH || (act && st != ST_MW && ((volatile int *)E.job_cancel)[wj]);
+            const uint32_t ba = __ballot_sync(FULL_MASK, act), bn = __ballot_sync(FULL_MASK, need);
+            const uint32_t bf = __ballot_sync(FULL_MASK, free_slot);
+            uint32_t gb = 0;
+            if (lane == 0) {
+                if (ba) atomicAdd(&sh.active, (uint32_t)__popc(ba));
+                if (bn) gb = atomicAdd(&sh.g_count, (uint32_t)__popc(bn));
+                if (bf) atomicAdd(&sh.n_free, (uint32_t)__popc(bf));
+            }
+            gb = __shfl_sync(FULL_MASK, gb, 0);
+            if (need) sh.glist[gb + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)o;
+        }
+        if (tid == 0) {
+            claim_ids(E, sh.ir, sh.n_free, sh.rr);
+            sh.rr = E.n_jobs > 0 ? (sh.rr + 1u) % (uint32_t)E.n_jobs : 0u;
+        }
+        __syncthreads();
+        {
+            const uint32_t ng = sh.g_count;
+            const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
+            uint16_t *ql = sh.qlist[cur];
+            for (uint32_t i = tid; i < ng; i += WALK_THREADS) {
+                const uint32_t o = sh.glist[i];
+                geo_slot<T>(E, base + o, o, fl, ql, &sh.q_count, sh.ir);
+            }
+        }
+        __syncthreads();
+        const long long c1 = clock64();
+        // ---------------- fill phase ----------------
+        const uint32_t nf = min(sh.f_count, (uint32_t)FILL_MAX);
+        for (uint32_t f = 0; f < nf; f++) {
+            const uint32_t e = sh.fill[f];
+            if (e == 0xffffffffu) continue;
+            FillJob F;
+            const uint32_t *k = E.tc.keys + 5 * e;
+            F.kind = k[0];
+            F.prof[0] = k[1]; F.prof[1] = k[2]; F.prof[2] = k[3]; F.prof[3] = k[4];
+            F.thr = E.tc.thr + (size_t)e * E.tc.P;
+            F.sgn = E.tc.sgn + (size_t)e * E.tc.P32;
+            F.ktot = E.tc.ktot + e;
+            F.values = nullptr;
+            F.err = &E.status[STAT_ERR];
+            fill_table(F, N, E.eps, E.fc, reinterpret_cast<double *>(dsm));
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(&E.tc.state[e], TE_READY);
+                atomicAdd(&E.status[STAT_BUILT], 1u);
+            }
+            __syncthreads();
+        }
+        const long long c2 = clock64();
+        // ---------------- reduction phase ----------------
+        for (;;) {
+            if (tid == 0) sh.red = take_batch(E);
+            __syncthreads();
+            const uint32_t g = sh.red;
+            __syncthreads();
+            if (g == 0xffffffffu) break;
+            reduce_batch(E, g, reinterpret_cast<unsigned long long *>(dsm));
+        }
+        const long long c3 = clock64();
+        // ---------------- MicroWalk phase ----------------
+        {
+            uint32_t *Mw = reinterpret_cast<uint32_t *>(dsm) + (size_t)warp * 3 * NP2 * 32;
+            const uint32_t *M = Mw + lane;
+            const uint32_t qn = sh.q_count;
+            const uint16_t *ql = sh.qlist[cur];
+            uint16_t *sl = sh.qlist[cur ^ 1];
+            bool active = false, exhausted = false;
+            int x = 0, y = 0, z = 0;
+            uint32_t t = 0, t_in = 0, my_o = 0;
+            MWLane L;
+            L.walk_lo = L.walk_hi = L.hop = L.key0 = L.key1 = L.tag = 0;
+            L.mm = 0;
+            for (;;) {
+                const bool need = !active && !exhausted;
+                const uint32_t bal = __ballot_sync(FULL_MASK, need);
+                if (bal) {
+                    const int leader = __ffs(bal) - 1;
+                    uint32_t b0 = 0;
+                    if (lane == leader) b0 = atomicAdd(&sh.q_head, (uint32_t)__popc(bal));
+                    b0 = __shfl_sync(FULL_MASK, b0, leader);
+                    const uint32_t myj = b0 + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+                    const bool got = need && myj < qn;
+                    if (need && !got) exhausted = true;
+                    const uint32_t oj = got ? (uint32_t)ql[myj] : 0u;
+                    uint32_t todo = __ballot_sync(FULL_MASK, got);
+                    while (todo) {
+                        const int r = __ffs(todo) - 1;
+                        todo &= todo - 1u;
+                        const uint32_t orr = __shfl_sync(FULL_MASK, oj, r);
+                        const MWJob &b = E.mwq[base + orr];
+                        const int K = min((int)b.K, KMAX);
+                        for (int row = lane; row < 3 * NP2; row += 32) {
+                            const int a = row / NP2;
+                            const int c = row - a * NP2 - 1;
+                            uint32_t m = 0;
+                            if (c >= 0 && c < N) {
+                                m = 1u;
+                                for (int q = 0; q < K; q++) {
+                                    const uint2 rr = b.rng[q];
+                                    if (rng_lo(rr, a) <= c && c < rng_hi(rr, a)) m |= 2u << q;
+                                }
+                            }
+                            Mw[row * 32 + r] = m;
+                        }
+                    }
+                    __syncwarp();
+                    if (got) {
+                        const MWJob &b = E.mwq[base + oj];
+                        L.walk_lo = b.walk_lo; L.walk_hi = b.walk_hi; L.hop = b.hop;
+                        L.key0 = b.key0; L.key1 = b.key1; L.tag = b.slot;
+                        L.mm = (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32);
+                        x = (int)(b.start & 255u); y = (int)((b.start >> 8) & 255u); z = (int)((b.start >> 16) & 255u);
+                        t = b.pad0;
+                        t_in = t;
+                        my_o = oj;
+                        active = true;
+                    }
+                }
+                const uint32_t ab = __ballot_sync(FULL_MASK, active);
+                if (ab == 0u) break;
+                // Suspend the few lanes left once the queue is empty, if every one of
+                // them has made progress this epoch and the CTA has other work
+                // waiting (so every job advances every epoch: no livelock).
+                const bool qexh = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.q_head >= qn), 0) != 0u;
+                const bool progressed = __all_sync(FULL_MASK, !active || t - t_in >= SUSPEND_MIN_STEPS);
+                const bool other_work = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.finished >=
+                                                                           SUSPEND_MIN_FINISHED || sh.issuable), 0) != 0u;
+                if (qexh && progressed && other_work && __popc(ab) <= SUSPEND_LANES) {
+                    if (active) {
+                        MWJob &b = E.mwq[base + my_o];
+                        b.start = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16);
+                        b.pad0 = t;
+                        sl[atomicAdd(&sh.s_count, 1u)] = (uint16_t)my_o;
+                        active = false;
+                    }
+                    break;
+                }
+                if (active) {
+                    const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
+                    const uint32_t words[4] = {blk.x, blk.y, blk.z, blk.w};
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (active) {
+                            if (mw_step(M, sh.W, NP2, N, x, y, z, L.mm, words[k])) {
+                                const uint32_t sl2 = L.tag;
+                                E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+                                E.s.steps[sl2] += t + (uint32_t)k + 1u;
+                                E.s.state[sl2] = ST_MWDONE;
+                                active = false;
+                                atomicAdd(&sh.finished, 1u);
+                            }
+                        }
+                    }
+                    t += 4;
+                    if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
+                        atomicOr(&E.status[STAT_ERR], ERR_MW_STEPS);
+                        const uint32_t sl2 = L.tag;
+                        E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+                        E.s.steps[sl2] += t;
+                        E.s.state[sl2] = ST_MWDONE;
+                        active = false;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        const long long c4 = clock64();
+        epochs++;
+        if (tid == 0) {
+            cyc[0] += (unsigned long long)(c1 - c0);
+            cyc[1] += (unsigned long long)(c2 - c1);
+            cyc[2] += (unsigned long long)(c3 - c2);
+            cyc[3] += (unsigned long long)(c4 - c3);
+            if (sh.s_count) atomicAdd(&E.status[STAT_SUSPENDED], sh.s_count);
+            const bool idle = sh.active == 0u && sh.issuable == 0u && sh.s_count == 0u;
+            sh.q_count = sh.s_count;
+            sh.q_head = 0;
+            sh.s_count = 0;
+            uint32_t stop = 0;
+            if (*(volatile uint32_t *)&E.ctrl[CTRL_ABORT]) stop = 1;
+            if (*(volatile uint32_t *)&E.status[STAT_ERR]) stop = 1;   // any device error ends the run
+            if (idle) {
+                if (*(volatile uint32_t *)&E.ctrl[CTRL_OPEN] == 0u) {
+                    stop = 1;
+                } else {
+                    unsigned long long now;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                    if (idle_t0 == 0) idle_t0 = now;
+                    else if ((double)(now - idle_t0) * 1e-9 > E.idle_timeout_s) {
+                        atomicOr(&E.status[STAT_ERR], ERR_IDLE_TIMEOUT);
+                        stop = 1;
+                    }
+                    __nanosleep(20000);
+                }
+            } else {
+                idle_t0 = 0;
+            }
+            sh.stop = stop;
+        }
+        cur ^= 1;
+        __syncthreads();
+        if (sh.stop) break;
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 4; i++) atomicAdd(&E.cycles[i], cyc[i]);
+        atomicMax(&E.status[STAT_EPOCHS], epochs);
+    }
+}
+
+cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st)
+{
+    (void)L;
+    const size_t smem = walk_smem_bytes(E.N, E.max_nc);
+    const unsigned grid = E.NS / E.pool;
+    if (E.fp32) {
+        cudaError_t e = cudaFuncSetAttribute(k_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_walk<float><<<grid, WALK_THREADS, smem, st>>>(E);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_walk<double><<<grid, WALK_THREADS, smem, st>>>(E);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_first(const EngineView &E, const LaunchShape &L, cudaStream_t st)
+cudaError_t set_kernel_attributes(int N, int mw_warps, int max_nc)
 {
-    const int blocks = L.sms * 8;
-    if (E.fp32) k_first<float><<<blocks, 128, 0, st>>>(E);
-    else k_first<double><<<blocks, 128, 0, st>>>(E);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_geom(const EngineView &E, const LaunchShape &L, cudaStream_t st)
-{
-    const int threads = L.geom_threads;
-    const int blocks = (int)((E.NS + threads - 1) / threads);
-    if (E.fp32) k_geom<float><<<blocks, threads, 0, st>>>(E);
-    else k_geom<double><<<blocks, threads, 0, st>>>(E);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fill(const EngineView &E, const LaunchShape &L, cudaStream_t st)
-{
-    k_fill<<<L.fill_ctas, 256, fill_smem_bytes(E.N), st>>>(E);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mw(const EngineView &E, const LaunchShape &L, cudaStream_t st)
-{
-    QueueSource src;
-    src.q = E.mwq;
-    src.cnt = E.mwq_count;
-    src.head = E.mwq_head;
-    src.s = E.s;
-    src.NS = E.NS;
-    src.err = &E.status[STAT_ERR];
-    k_mw<QueueSource><<<L.sms * L.mw_ctas_per_sm, 32 * L.mw_warps, mw_smem_bytes(E.N, L.mw_warps), st>>>(
-        src, E.W, E.N);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_round(const EngineView &E, const LaunchShape &L, cudaStream_t st)
-{
-    cudaError_t e = launch_first(E, L, st);
+    (void)max_nc;
+    cudaError_t e = cudaFuncSetAttribute(k_fill_one, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fill_smem_bytes(N));
     if (e != cudaSuccess) return e;
-    e = launch_geom(E, L, st);
-    if (e != cudaSuccess) return e;
-    e = launch_fill(E, L, st);
-    if (e != cudaSuccess) return e;
-    e = launch_mw(E, L, st);
-    if (e != cudaSuccess) return e;
-    return launch_round_end(E, st);
-}
-
-cudaError_t launch_round_end(const EngineView &E, cudaStream_t st)
-{
-    k_round_end<<<1, 32, 0, st>>>(E);
-    return cudaGetLastError();
+    return cudaFuncSetAttribute(k_mw<CubeSource>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mw_smem_bytes(N, mw_warps));
 }
 
 cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4], uint32_t entry,

@@ -5,9 +5,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -44,8 +46,7 @@ struct frw_ctx {
     std::vector<void *> allocs;
     uint32_t NS = 0;
     SlotArrays slots;
-    MWJob *mwq = nullptr;
-    uint32_t *mwq_ctr = nullptr;        // [2]: count, head
+    MWJob *mwq = nullptr;               // one MicroWalk job record per slot
     TableCache tc;
     uint32_t *status = nullptr;
     uint32_t *d_W = nullptr;
@@ -57,8 +58,10 @@ struct frw_ctx {
     std::vector<HostStructure> structs;
     uint32_t *h_status = nullptr;       // pinned
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    uint32_t *fresh[2] = {nullptr, nullptr};   // slot lists of the first-transition kernel
-    uint32_t *fresh_ctr = nullptr;             // [2] counts
+    cudaStream_t aux = nullptr;                // control / monitoring copies during a run
+    uint32_t *ctrl = nullptr;                  // device control words
+    unsigned long long *cycles = nullptr;      // phase cycle counters
+    int grid = 0;                              // walk-kernel CTAs
     RecArrays rec;                      // per-walk records (grown on demand)
     uint64_t rec_cap = 0;
     std::vector<void *> rec_allocs;
@@ -157,21 +160,18 @@ static EngineView make_view(frw_ctx *ctx)
     E.max_hops = ctx->opt.max_hops;
     E.fp32 = ctx->opt.precision == FRW_FP32_GEOM;
     E.NS = ctx->NS;
+    E.pool = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
     E.s = ctx->slots;
     E.structs = ctx->d_structs;
     E.mwq = ctx->mwq;
-    E.mwq_count = ctx->mwq_ctr;
-    E.mwq_head = ctx->mwq_ctr + 1;
-    E.mwq_cap = ctx->NS;
     E.tc = ctx->tc;
     E.W = ctx->d_W;
     E.eps = ctx->d_eps;
     E.fc = ctx->fc;
     E.status = ctx->status;
-    E.fresh_in = ctx->fresh[0];
-    E.fresh_out = ctx->fresh[1];
-    E.fresh_in_count = ctx->fresh_ctr;
-    E.fresh_out_count = ctx->fresh_ctr + 1;
+    E.ctrl = ctx->ctrl;
+    E.cycles = ctx->cycles;
+    E.idle_timeout_s = 10.0;
     return E;
 }
 
@@ -216,6 +216,7 @@ extern "C" void frw_destroy(frw_ctx *ctx)
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
     delete ctx;
 }
 
@@ -262,6 +263,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         return code;
     };
     if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(FRW_EDEVICE);
+    if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess) return bail(FRW_EDEVICE);
     ctx->stream = ctx->own_stream;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -271,7 +273,16 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->shape.mw_ctas_per_sm = opt.mw_ctas_per_sm > 0 ? opt.mw_ctas_per_sm : 2;
     ctx->shape.fill_ctas = ctx->shape.sms;
     const int N = opt.N;
-    ctx->NS = opt.slots > 0 ? (uint32_t)opt.slots : (1u << 20);
+    // walk kernel: CTAs resident at once (2 per SM), each with a pool of slots
+    ctx->grid = 2 * ctx->shape.sms;
+    {
+        uint64_t want = opt.slots > 0 ? (uint64_t)opt.slots : (1ull << 20);
+        uint64_t pool = (want + ctx->grid - 1) / ctx->grid;
+        pool = ((pool + 255) / 256) * 256;
+        if (pool < 256) pool = 256;
+        if (pool > (uint64_t)walk_pool_slots()) pool = walk_pool_slots();
+        ctx->NS = (uint32_t)(pool * ctx->grid);
+    }
     uint32_t cap = opt.table_capacity > 0 ? (uint32_t)opt.table_capacity : (N <= 16 ? (1u << 16) : (1u << 14));
     uint32_t c2 = 1;
     while (c2 < cap) c2 <<= 1;
@@ -285,10 +296,9 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         (rc = dalloc(ctx, &S.walk, NS, A)) || (rc = dalloc(ctx, &S.steps, NS, A)) ||
         (rc = dalloc(ctx, &S.pos, 3 * (size_t)NS, A)) || (rc = dalloc(ctx, &S.cube, 4 * (size_t)NS, A)) ||
         (rc = dalloc(ctx, &S.omega, NS, A)) || (rc = dalloc(ctx, &ctx->mwq, NS, A)) ||
-        (rc = dalloc(ctx, &ctx->mwq_ctr, 2, A)) || (rc = dalloc(ctx, &ctx->status, STAT_WORDS, A)) ||
+        (rc = dalloc(ctx, &ctx->status, STAT_WORDS, A)) ||
         (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)) ||
-        (rc = dalloc(ctx, &ctx->fresh[0], NS, A)) || (rc = dalloc(ctx, &ctx->fresh[1], NS, A)) ||
-        (rc = dalloc(ctx, &ctx->fresh_ctr, 2, A)))
+        (rc = dalloc(ctx, &ctx->ctrl, CTRL_WORDS, A)) || (rc = dalloc(ctx, &ctx->cycles, 4, A)))
         return bail(rc);
     TableCache &T = ctx->tc;
     T.cap = cap;
@@ -330,12 +340,11 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     if (cudaMallocHost(&ctx->h_status, sizeof(uint32_t) * STAT_WORDS) != cudaSuccess) return bail(FRW_ENOMEM);
     for (auto &e : ctx->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(FRW_EDEVICE);
-    cudaError_t e2 = set_kernel_attributes(N, ctx->shape.mw_warps);
+    cudaError_t e2 = set_kernel_attributes(N, ctx->shape.mw_warps, 0);
     if (e2 != cudaSuccess) return bail(cuda_fail(ctx, e2, "cudaFuncSetAttribute"));
     cudaMemsetAsync(T.state, 0, sizeof(uint32_t) * cap, ctx->stream);
     cudaMemsetAsync(T.fillq_count, 0, sizeof(uint32_t) * 2, ctx->stream);
     cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, ctx->stream);
-    cudaMemsetAsync(ctx->mwq_ctr, 0, sizeof(uint32_t) * 2, ctx->stream);
     cudaMemsetAsync(ctx->d_W, 0, sizeof(uint32_t) * 256, ctx->stream);
     cudaMemsetAsync(ctx->d_eps, 0, sizeof(double) * 16, ctx->stream);
     // homogeneous tables (independent of the permittivity): SGF at entry cap, flux at cap + 1
@@ -654,6 +663,7 @@ struct JobRun {
     uint64_t ex[ACC_EXTRA] = {0};
     unsigned long long *h_blocks = nullptr;   // pinned staging for batch blocks
     uint64_t h_cap = 0;
+    unsigned long long h_limit = 0;           // host copy of the issue limit (copy source)
 };
 
 // relative standard errors of C_ii and of the largest |C_ij| (j != i, ground
@@ -730,14 +740,25 @@ static void fold_block(JobRun &j, const unsigned long long *blk, uint64_t bsz)
     j.walks += bsz;
 }
 
-// Run a set of jobs to completion on the device.  Each round: geometry, table
-// fill, MicroWalk, round end (each bracketed by CUDA events), then for jobs with
-// a sigma target the next batches are reduced and checked in walk-id order.
+// Wall-clock limit of one run (seconds; environment FRW_RUN_TIMEOUT_S, default 3600).
+static double run_timeout_s()
+{
+    const char *v = std::getenv("FRW_RUN_TIMEOUT_S");
+    const double t = v ? std::atof(v) : 0.0;
+    return t > 0.0 ? t : 3600.0;
+}
+
+// Run a set of jobs to completion: one launch of the persistent walk kernel.
+// For jobs with a sigma target the host follows completed batches in walk-id
+// order from a second stream (copy engines only), cancels a job when its stop rule
+// holds, moves its issue limit to the predicted need, and closes the run when
+// every such job is decided.
 static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_out)
 {
     const auto t0 = std::chrono::steady_clock::now();
     const int nj = (int)jobs.size();
-    uint64_t total_walks = 0, acc_words = 0;
+    uint64_t total_walks = 0, acc_words = 0, total_batches = 0;
+    int max_nc = 1;
     for (auto &j : jobs) {
         const HostStructure &H = ctx->structs[j.desc.structure_id];
         DevJob &d = j.d;
@@ -754,16 +775,21 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
         d.acc_stride = acc_stride_for(H.n_c);
         d.acc_base = acc_words;
         d.rec_base = total_walks;
+        d.batch_base = total_batches;
         j.n_batches = (d.walk_count + d.batch - 1) / d.batch;
         acc_words += j.n_batches * d.acc_stride;
         total_walks += d.walk_count;
+        total_batches += j.n_batches;
+        max_nc = std::max(max_nc, H.n_c);
         j.S1.assign(H.n_c + 1, 0);
         j.S2.assign(H.n_c + 1, 0);
         j.limit = d.walk_count;
     }
+    if (total_batches >= 0xffffffffull) return fail(ctx, FRW_EINVAL, "too many batches");
     int rc = ensure_records(ctx, total_walks);
     if (rc) return rc;
     std::vector<void *> tmp;
+    uint32_t *h_flags = nullptr;
     auto cleanup = [&]() {
         for (void *p : tmp) cudaFree(p);
         for (auto &j : jobs)
@@ -771,23 +797,30 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
                 cudaFreeHost(j.h_blocks);
                 j.h_blocks = nullptr;
             }
+        if (h_flags) cudaFreeHost(h_flags);
     };
     DevJob *d_jobs = nullptr;
     unsigned long long *d_next = nullptr, *d_acc = nullptr, *d_limit = nullptr;
     int *d_cancel = nullptr;
+    uint32_t *d_done = nullptr, *d_ready = nullptr, *d_rq = nullptr, *d_rqc = nullptr;
     if ((rc = dalloc(ctx, &d_jobs, nj, tmp)) || (rc = dalloc(ctx, &d_next, nj, tmp)) ||
         (rc = dalloc(ctx, &d_limit, nj, tmp)) || (rc = dalloc(ctx, &d_cancel, nj, tmp)) ||
-        (rc = dalloc(ctx, &d_acc, std::max<uint64_t>(acc_words, 1), tmp))) {
+        (rc = dalloc(ctx, &d_acc, std::max<uint64_t>(acc_words, 1), tmp)) ||
+        (rc = dalloc(ctx, &d_done, std::max<uint64_t>(total_batches, 1), tmp)) ||
+        (rc = dalloc(ctx, &d_ready, std::max<uint64_t>(total_batches, 1), tmp)) ||
+        (rc = dalloc(ctx, &d_rq, std::max<uint64_t>(total_batches, 1), tmp)) || (rc = dalloc(ctx, &d_rqc, 2, tmp))) {
         cleanup();
         return rc;
     }
     std::vector<DevJob> hj(nj);
     std::vector<unsigned long long> hl(nj);
+    bool any_sigma = false;
     for (int i = 0; i < nj; i++) {
         hj[i] = jobs[i].d;
         hl[i] = jobs[i].d.walk_count;
+        any_sigma |= jobs[i].desc.sigma_target > 0.0 && jobs[i].n_batches > 0;
     }
-    cudaStream_t st = ctx->stream;
+    cudaStream_t st = ctx->stream, ax = ctx->aux;
 #define CKR(call)                                     \
     do {                                              \
         cudaError_t e_ = (call);                      \
@@ -797,29 +830,42 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             return r_;                                \
         }                                             \
     } while (0)
+    const uint32_t ctrl0[CTRL_WORDS] = {any_sigma ? 1u : 0u, 0u, 0u, 0u};
     CKR(cudaMemcpyAsync(d_jobs, hj.data(), sizeof(DevJob) * nj, cudaMemcpyHostToDevice, st));
     CKR(cudaMemcpyAsync(d_limit, hl.data(), sizeof(unsigned long long) * nj, cudaMemcpyHostToDevice, st));
+    CKR(cudaMemcpyAsync(ctx->ctrl, ctrl0, sizeof(ctrl0), cudaMemcpyHostToDevice, st));
     CKR(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long) * nj, st));
     CKR(cudaMemsetAsync(d_cancel, 0, sizeof(int) * nj, st));
     CKR(cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long) * std::max<uint64_t>(acc_words, 1), st));
-    CKR(cudaMemsetAsync(ctx->rec.k, 0x80, sizeof(int32_t) * total_walks, st));
+    CKR(cudaMemsetAsync(d_done, 0, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
+    CKR(cudaMemsetAsync(d_ready, 0, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
+    CKR(cudaMemsetAsync(d_rq, 0xff, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
+    CKR(cudaMemsetAsync(d_rqc, 0, sizeof(uint32_t) * 2, st));
+    CKR(cudaMemsetAsync(ctx->rec.k, 0x80, sizeof(int32_t) * std::max<uint64_t>(total_walks, 1), st));
     CKR(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
-    CKR(cudaMemsetAsync(ctx->mwq_ctr, 0, sizeof(uint32_t) * 2, st));
-    CKR(cudaMemsetAsync(ctx->tc.fillq_count, 0, sizeof(uint32_t) * 2, st));
+    CKR(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 4, st));
     EngineView E = make_view(ctx);
-    uint64_t ns = std::max<uint64_t>(1024, ((total_walks + 255) / 256) * 256);
-    E.NS = (uint32_t)std::min<uint64_t>(ctx->NS, ns);
     E.n_jobs = nj;
+    E.max_nc = max_nc;
     E.jobs = d_jobs;
     E.job_next = d_next;
     E.job_limit = d_limit;
     E.job_cancel = d_cancel;
     E.acc = d_acc;
+    E.batch_done = d_done;
+    E.batch_ready = d_ready;
+    E.rq = d_rq;
+    E.rq_count = d_rqc;
+    E.rq_head = d_rqc + 1;
+    E.rq_cap = (uint32_t)std::max<uint64_t>(total_batches, 1);
     E.rec = ctx->rec;
-    CKR(launch_init_slots(E, st));
-    uint64_t rounds = 0, extra_launches = 0;
-    const EngineView E0 = E;
-    const uint64_t LOOK = 16;    // batches examined per sigma job per round
+    // fewer slots for small runs
+    {
+        const uint64_t per = std::max<uint64_t>(256, ((total_walks / ctx->grid + 255) / 256) * 256);
+        E.pool = (uint32_t)std::min<uint64_t>(E.pool, per);
+        E.NS = E.pool * ctx->grid;
+    }
+    const uint64_t LOOK = 16;   // batches followed per sigma job per poll
     for (auto &j : jobs)
         if (j.desc.sigma_target > 0.0) {
             if (cudaMallocHost(&j.h_blocks, sizeof(unsigned long long) * LOOK * j.d.acc_stride) != cudaSuccess) {
@@ -828,103 +874,108 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             }
             j.h_cap = LOOK;
         }
-    double t_geom = 0.0, t_fill = 0.0, t_mw = 0.0;
+    if (cudaMallocHost(&h_flags, sizeof(uint32_t) * (LOOK + STAT_WORDS)) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, FRW_ENOMEM, "pinned staging");
+    }
+    CKR(cudaEventRecord(ctx->ev[0], st));
+    CKR(launch_walk(E, ctx->shape, st));
+    CKR(cudaEventRecord(ctx->ev[1], st));
+    bool open = any_sigma;
+    uint32_t dev_err = 0;
+    const double limit_s = run_timeout_s();
+    bool timed_out = false;
     for (;;) {
-        // fresh-slot lists alternate between rounds
-        E.fresh_in = E0.fresh_in;
-        E.fresh_out = E0.fresh_out;
-        E.fresh_in_count = E0.fresh_in_count;
-        E.fresh_out_count = E0.fresh_out_count;
-        if (rounds & 1) {
-            std::swap(E.fresh_in, E.fresh_out);
-            std::swap(E.fresh_in_count, E.fresh_out_count);
+        const bool finished = cudaEventQuery(ctx->ev[1]) == cudaSuccess;
+        if (finished) break;
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) {
+            // give up: the kernel stops at its next epoch boundary
+            static const uint32_t abort1 = 1;
+            CKR(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
+            CKR(cudaStreamSynchronize(ax));
+            timed_out = true;
+            break;
         }
-        // one round, each launch bracketed by events on the launch stream
-        CKR(cudaEventRecord(ctx->ev[0], st));
-        CKR(launch_first(E, ctx->shape, st));
-        CKR(launch_geom(E, ctx->shape, st));
-        CKR(cudaEventRecord(ctx->ev[1], st));
-        CKR(launch_fill(E, ctx->shape, st));
-        CKR(cudaEventRecord(ctx->ev[2], st));
-        CKR(launch_mw(E, ctx->shape, st));
-        CKR(cudaEventRecord(ctx->ev[3], st));
-        CKR(launch_round_end(E, st));
-        rounds++;
-        // fold the next batches of every unfinished sigma job
-        std::vector<uint64_t> look(nj, 0);
-        for (int i = 0; i < nj; i++) {
+        if (!open) {
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+            continue;
+        }
+        // device error flags
+        CKR(cudaMemcpyAsync(h_flags + LOOK, ctx->status, sizeof(uint32_t) * STAT_WORDS, cudaMemcpyDeviceToHost, ax));
+        CKR(cudaStreamSynchronize(ax));
+        dev_err = h_flags[LOOK + STAT_ERR];
+        bool undecided = false;
+        for (int i = 0; i < nj && !dev_err; i++) {
             JobRun &j = jobs[i];
             if (j.desc.sigma_target <= 0.0 || j.converged || j.prefix >= j.n_batches) continue;
-            look[i] = std::min<uint64_t>(LOOK, j.n_batches - j.prefix);
-            CKR(launch_reduce(E, i, j.prefix, j.prefix + look[i], j.d.n_c, st));
-            extra_launches++;
-            CKR(cudaMemcpyAsync(j.h_blocks, d_acc + j.d.acc_base + j.prefix * j.d.acc_stride,
-                                sizeof(unsigned long long) * look[i] * j.d.acc_stride, cudaMemcpyDeviceToHost, st));
-        }
-        rc = check_status(ctx);   // copies the status words and synchronises the stream
-        if (rc) {
-            cleanup();
-            return rc;
-        }
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) t_geom += ms;
-        if (cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) == cudaSuccess) t_fill += ms;
-        if (cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]) == cudaSuccess) t_mw += ms;
-        bool more = false;   // a sigma job still needs walks
-        for (int i = 0; i < nj; i++) {
-            JobRun &j = jobs[i];
-            if (!look[i]) continue;
             const uint32_t strd = j.d.acc_stride;
-            const int nc1 = j.d.n_c + 1;
-            for (uint64_t b = 0; b < look[i] && !j.converged; b++) {
-                const unsigned long long *blk = j.h_blocks + b * strd;
-                const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - j.prefix * j.d.batch);
-                if (blk[4 * nc1] != bsz) break;
-                fold_block(j, blk, bsz);
-                j.prefix++;
-                if (bsz == j.d.batch && sigma_ok(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, j.desc.sigma_target))
-                    j.converged = true;
+            const uint64_t look = std::min<uint64_t>(LOOK, j.n_batches - j.prefix);
+            CKR(cudaMemcpyAsync(h_flags, d_ready + j.d.batch_base + j.prefix, sizeof(uint32_t) * look,
+                                cudaMemcpyDeviceToHost, ax));
+            CKR(cudaStreamSynchronize(ax));
+            uint64_t nready = 0;
+            while (nready < look && h_flags[nready]) nready++;
+            if (nready) {
+                CKR(cudaMemcpyAsync(j.h_blocks, d_acc + j.d.acc_base + j.prefix * strd,
+                                    sizeof(unsigned long long) * nready * strd, cudaMemcpyDeviceToHost, ax));
+                CKR(cudaStreamSynchronize(ax));
+                for (uint64_t b = 0; b < nready && !j.converged; b++) {
+                    const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - j.prefix * j.d.batch);
+                    fold_block(j, j.h_blocks + b * strd, bsz);
+                    j.prefix++;
+                    if (bsz == j.d.batch && sigma_ok(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, j.desc.sigma_target))
+                        j.converged = true;
+                }
             }
             if (j.converged) {
-                const int one = 1;
-                CKR(cudaMemcpyAsync(d_cancel + i, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+                static const int one = 1;
+                CKR(cudaMemcpyAsync(d_cancel + i, &one, sizeof(int), cudaMemcpyHostToDevice, ax));
                 continue;
             }
-            if (j.prefix >= j.n_batches) continue;   // budget exhausted
-            more = true;
-            // predictive issue limit: walks needed ~ n (r / target)^2, with margin,
-            // so that the in-flight pool does not overshoot the stopping point
+            if (j.prefix >= j.n_batches) continue;
+            undecided = true;
+            // predictive issue limit: walks needed ~ n (r / target)^2 with margin, so that
+            // the in-flight pool does not run far past the stopping point
+            uint64_t lim = j.limit;
             if (j.walks >= j.d.batch) {
                 double rs, rcp;
                 rel_errors(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, &rs, &rcp);
                 const double r = std::max(rs, rcp) / j.desc.sigma_target;
                 double need = std::isfinite(r) ? (double)j.walks * r * r : (double)j.d.walk_count;
                 need = std::min<double>(need * 1.15 + 2.0 * j.d.batch, (double)j.d.walk_count);
-                uint64_t lim = ((uint64_t)need + j.d.batch - 1) / j.d.batch * j.d.batch;
-                lim = std::min<uint64_t>(std::max<uint64_t>(lim, (j.prefix + 1) * j.d.batch), j.d.walk_count);
-                if (lim != j.limit) {
-                    CKR(launch_set_limit(E, i, lim, st));
-                    extra_launches++;
-                    j.limit = lim;
-                }
+                lim = ((uint64_t)need + j.d.batch - 1) / j.d.batch * j.d.batch;
             }
-        }
-        if (ctx->h_status[STAT_ACTIVE] == 0 && !more) break;
-        if (ctx->h_status[STAT_ACTIVE] == 0 && more) {
-            // every slot idle but a sigma job is short of walks: lift its limit
-            for (int i = 0; i < nj; i++) {
-                JobRun &j = jobs[i];
-                if (j.desc.sigma_target <= 0.0 || j.converged || j.prefix >= j.n_batches) continue;
-                const uint64_t lim = std::min<uint64_t>(j.d.walk_count, std::max<uint64_t>(2 * j.limit, j.limit + j.d.batch));
-                CKR(launch_set_limit(E, i, lim, st));
-                extra_launches++;
+            lim = std::min<uint64_t>(std::max<uint64_t>(lim, (j.prefix + 1) * j.d.batch), j.d.walk_count);
+            if (lim != j.limit) {
                 j.limit = lim;
+                j.h_limit = lim;
+                CKR(cudaMemcpyAsync(d_limit + i, &j.h_limit, sizeof(unsigned long long), cudaMemcpyHostToDevice, ax));
             }
         }
-        if (rounds > 100000000ull) {
-            cleanup();
-            return fail(ctx, FRW_ETIMEOUT, "engine did not finish");
+        if (dev_err) {
+            static const uint32_t abort1 = 1;
+            CKR(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
+            break;
         }
+        if (!undecided) {
+            static const uint32_t zero = 0;
+            CKR(cudaMemcpyAsync(ctx->ctrl + CTRL_OPEN, &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
+            CKR(cudaStreamSynchronize(ax));
+            open = false;
+            continue;
+        }
+        CKR(cudaStreamSynchronize(ax));
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    CKR(cudaStreamSynchronize(st));
+    rc = check_status(ctx);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    if (timed_out) {
+        cleanup();
+        return fail(ctx, FRW_ETIMEOUT, "run exceeded its wall-clock limit (FRW_RUN_TIMEOUT_S)");
     }
     // jobs without a sigma target (or that ran out of budget): fold every batch
     std::vector<unsigned long long> hb;
@@ -933,8 +984,6 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
         if (j.converged || j.prefix >= j.n_batches) continue;
         const uint32_t strd = j.d.acc_stride;
         const uint64_t rest = j.n_batches - j.prefix;
-        CKR(launch_reduce(E, i, j.prefix, j.n_batches, j.d.n_c, st));
-        extra_launches++;
         hb.resize(rest * strd);
         CKR(cudaMemcpyAsync(hb.data(), d_acc + j.d.acc_base + j.prefix * strd, sizeof(unsigned long long) * rest * strd,
                             cudaMemcpyDeviceToHost, st));
@@ -942,15 +991,20 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
         const int nc1 = j.d.n_c + 1;
         for (uint64_t b = 0; b < rest; b++) {
             const unsigned long long *blk = hb.data() + b * strd;
-            fold_block(j, blk, blk[4 * nc1]);
+            const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - (j.prefix + b) * j.d.batch);
+            if (blk[4 * nc1] != bsz) {
+                cleanup();
+                return fail(ctx, FRW_EDEVICE, "a batch was not reduced");
+            }
+            fold_block(j, blk, bsz);
         }
         j.prefix = j.n_batches;
     }
-    rc = check_status(ctx);
-    if (rc) {
-        cleanup();
-        return rc;
-    }
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, ctx->ev[0], ctx->ev[1]);
+    unsigned long long cyc[4] = {0, 0, 0, 0};
+    CKR(cudaMemcpy(cyc, ctx->cycles, sizeof(cyc), cudaMemcpyDeviceToHost));
+    const double ctot = (double)(cyc[0] + cyc[1] + cyc[2] + cyc[3]);
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats_out) {
         for (int i = 0; i < nj; i++) {
@@ -968,13 +1022,13 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             s.branch[2] = j.ex[8];
             s.truncated = j.ex[9];
             s.tables_built = ctx->h_status[STAT_BUILT];
-            s.rounds = rounds;
+            s.rounds = ctx->h_status[STAT_EPOCHS];
             s.seconds = secs;
-            s.geom_ms = t_geom;
-            s.fill_ms = t_fill;
-            s.mw_ms = t_mw;
-            s.launches = 1 + 5 * rounds + extra_launches;
-            s.mw_jobs = ctx->h_status[STAT_MWJOBS];
+            s.geom_ms = ctot > 0 ? kms * (double)cyc[0] / ctot : 0.0;
+            s.fill_ms = ctot > 0 ? kms * (double)(cyc[1] + cyc[2]) / ctot : 0.0;
+            s.mw_ms = ctot > 0 ? kms * (double)cyc[3] / ctot : 0.0;
+            s.launches = 1;
+            s.mw_jobs = j.ex[5];
         }
     }
     cleanup();
