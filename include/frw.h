@@ -119,6 +119,7 @@ typedef struct {
     double mw_ms;              /* ... of the MicroWalk kernel */
     uint64_t launches;         /* kernels launched by the call */
     uint64_t mw_jobs;          /* MicroWalk transitions run by the MicroWalk kernel */
+    uint64_t walks_issued;     /* walk ids started (>= walks: a sigma-target run stops mid-flight) */
 } frw_stats;
 
 /* Fill *opt with defaults (N = 24, FP64 geometry, hybrid on, offset 0.5,

@@ -11,6 +11,7 @@ constexpr int KMAX = 14;                 // blocks per transition cube (mask bit
 constexpr int BOUNDARY = 15;             // material id of absorbing boundary nodes
 constexpr int NMAT = 16;                 // material slots (15 real + boundary)
 constexpr double EPS0 = 8.8541878128e-3; // fF / um
+constexpr int GUIDE = 2048;              // guide-table buckets of the inverse-CDF sampler (2^11)
 
 // analytical table kinds (same numbering as the ABI's FRW_TAB_*)
 enum : uint32_t { TAB_SGF = 0, TAB_FLUX_PAR = 1, TAB_FLUX_PERP = 2, TAB_SGF_HOM = 3, TAB_FLUX_HOM = 4 };
@@ -89,6 +90,15 @@ struct DevJob {
     uint32_t pad;
     uint64_t rec_base;     // offset of walk 0 in the record arrays
     uint64_t batch_base;   // index of batch 0 in the run's batch arrays
+    double sigma;          // relative standard-error target (0: budget only)
+};
+
+// Device-side state of a job's stop rule (followed in walk-id order).
+struct JobState {
+    unsigned long long prefix;     // complete batches folded so far
+    unsigned long long used;       // walks in the estimate once decided
+    uint32_t decided;              // 1: converged, 2: budget exhausted
+    uint32_t lock;
 };
 
 // per-batch accumulator block (u64 words):
@@ -138,6 +148,7 @@ struct TableCache {
     uint32_t *state;       // [cap]
     uint32_t *thr;         // [cap + 2][P]; entries cap, cap+1 = homogeneous SGF / flux
     uint32_t *sgn;         // [cap + 2][P32]
+    uint16_t *guide;       // [cap + 2][GUIDE]: first panel whose threshold exceeds each bucket start
     double *ktot;          // [cap + 2]
     uint32_t *fillq;       // [cap]
     uint32_t *fillq_count, *fillq_head;
@@ -163,7 +174,10 @@ struct EngineView {
     const DevJob *jobs;
     unsigned long long *job_next;    // next walk offset per job (claimed by compare-and-swap)
     unsigned long long *job_limit;   // issue limit per job (<= walk_count), written by the host
-    int *job_cancel;                 // written by the host
+    int *job_cancel;                 // set when the stop rule holds (or by the host)
+    JobState *jstate;                // per job
+    unsigned long long *jsum;        // per job: running prefix sums, acc_stride words each
+    unsigned long long *jsum_off;    // per job: offset of its running sums
     unsigned long long *acc;         // batch accumulator blocks
     uint32_t *batch_done;            // finished walks per batch
     uint32_t *batch_ready;           // 1 once the batch block is written
@@ -177,7 +191,7 @@ struct EngineView {
     FillConsts fc;
     uint32_t *status;      // STAT_WORDS
     uint32_t *ctrl;        // CTRL_WORDS (host -> device)
-    unsigned long long *cycles;   // [4] SM cycles spent in geometry / fill / reduce / MicroWalk phases
+    unsigned long long *cycles;   // [5] CTA cycles: geometry busy, fill, reduce, MicroWalk busy, total
     double idle_timeout_s; // idle wait limit of the walk kernel
 };
 

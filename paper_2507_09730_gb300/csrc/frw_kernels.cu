@@ -405,7 +405,18 @@ __device__ int table_lookup(const TableCache &tc, uint32_t kind, const uint32_t 
     return -2;
 }
 
-// smallest n in [0, P-1] with u < thr[n] (thr[P-1] counts as 2^32)
+// smallest n in [0, P-1] with u < thr[n] (thr[P-1] counts as 2^32).  The guide
+// table gives, for the bucket of u (its top 11 bits), the first panel whose
+// threshold exceeds the bucket's start; no earlier panel can be the answer, so a
+// short forward scan from there returns exactly the inverse-CDF sample.
+__device__ __forceinline__ int sample_guided(const uint32_t *__restrict__ thr, const uint16_t *__restrict__ guide,
+                                             int P, uint32_t u)
+{
+    int n = __ldg(&guide[u >> 21]);
+    while (n < P - 1 && !(u < __ldg(&thr[n]))) n++;
+    return n;
+}
+
 __device__ __forceinline__ int sample_thr(const uint32_t *__restrict__ thr, int P, uint32_t u)
 {
     int lo = 0, hi = P - 1;
@@ -543,6 +554,7 @@ __device__ bool first_transition(const EngineView &E, const DevJob &J, const SVi
     const CubeInfo &qq = use_qc ? qc : q;
     const uint32_t *thr;
     const uint32_t *sgn;
+    const uint16_t *guide;
     double keff;
     int fr[3];
     const TableCache &tc = E.tc;
@@ -550,11 +562,13 @@ __device__ bool first_transition(const EngineView &E, const DevJob &J, const SVi
         const double em = mean_eps(q, N, E.eps);
         thr = tc.thr + (size_t)(tc.cap + 1) * tc.P;
         sgn = tc.sgn + (size_t)(tc.cap + 1) * tc.P32;
+        guide = tc.guide + (size_t)(tc.cap + 1) * GUIDE;
         keff = __dmul_rn(em, tc.ktot[tc.cap + 1]);
         frame_sgf(na, fr);
     } else if (qq.kind == CUBE_HOM) {
         thr = tc.thr + (size_t)(tc.cap + 1) * tc.P;
         sgn = tc.sgn + (size_t)(tc.cap + 1) * tc.P32;
+        guide = tc.guide + (size_t)(tc.cap + 1) * GUIDE;
         keff = __dmul_rn(E.eps[qq.bg], tc.ktot[tc.cap + 1]);
         frame_sgf(na, fr);
     } else {
@@ -566,11 +580,12 @@ __device__ bool first_transition(const EngineView &E, const DevJob &J, const SVi
         }
         thr = tc.thr + (size_t)e * tc.P;
         sgn = tc.sgn + (size_t)e * tc.P32;
+        guide = tc.guide + (size_t)e * GUIDE;
         keff = tc.ktot[e];
         if (kind == TAB_FLUX_PAR) frame_sgf(na, fr);
         else frame_perp(na, qq.axis, fr);
     }
-    const int m = sample_thr(thr, (int)tc.P, b1.z);
+    const int m = sample_guided(thr, guide, (int)tc.P, b1.z);
     const double sg = ((__ldg(&sgn[m >> 5]) >> (m & 31)) & 1u) ? -1.0 : 1.0;
     int node[3];
     panel_node(N, fr, m, node);
@@ -670,6 +685,8 @@ __device__ bool issue_walk(const EngineView &E, IssueRanges &ir, WalkState &w)
     return true;
 }
 
+constexpr int HOPS_PER_EPOCH = 8;     // analytical hops one walk may take per epoch
+
 // Geometry-phase work of one slot: a new walk and its first transition if the
 // slot is free, then one step of the walk (Algorithm 1 inner loop): absorption
 // test, cube sizing, classification, then the analytical route in place or a
@@ -681,7 +698,8 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
     typedef Ar<T> A;
     const int N = E.N;
     const uint32_t NS = E.NS;
-    uint32_t st = E.s.state[s];
+    uint32_t st = *(volatile uint32_t *)&E.s.state[s];
+    __threadfence_block();   // pairs with the MicroWalk warps' fence before they publish ST_MWDONE
     WalkState w;
     load_walk(E, s, w);
     if (st != ST_FRESH && ((volatile int *)E.job_cancel)[w.job]) st = ST_FRESH;   // drop the walk
@@ -716,6 +734,10 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         pos[1] = (T)E.s.pos[NS + s];
         pos[2] = (T)E.s.pos[2 * NS + s];
     }
+  T R;
+  CubeInfo q;
+  uint4 hb;
+  for (int hops_here = 0;; hops_here++) {
     int who;
     const T d = nearest_electrode(S, pos, who);
     if (d <= S.tau || (int)w.hop >= E.max_hops) {
@@ -724,8 +746,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         E.s.job[s] = w.job;
         return;
     }
-    T R = E.fp32 ? A::sub(d, S.margin) : d;
-    CubeInfo q;
+    R = E.fp32 ? A::sub(d, S.margin) : d;
     classify_cube(S, pos, R, N, q);
     int guard = 0;
     while (q.kind == CUBE_OVERFLOW && guard++ < 40) {
@@ -739,11 +760,11 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         E.s.job[s] = w.job;
         return;
     }
-    const uint4 hb = philox10((uint32_t)w.walk, (uint32_t)(w.walk >> 32), w.hop, 0u, J.key0, J.key1);
+    hb = philox10((uint32_t)w.walk, (uint32_t)(w.walk >> 32), w.hop, 0u, J.key0, J.key1);
     int m = -1, fr[3] = {0, 1, 2};
     bool wait = false;
     if (E.hybrid && q.kind == CUBE_HOM) {
-        m = sample_thr(E.tc.thr + (size_t)E.tc.cap * E.tc.P, (int)E.tc.P, hb.x);
+        m = sample_guided(E.tc.thr + (size_t)E.tc.cap * E.tc.P, E.tc.guide + (size_t)E.tc.cap * GUIDE, (int)E.tc.P, hb.x);
         w.cnt_sh += 1u << 16;
     } else if (E.hybrid && q.kind == CUBE_STRAT) {
         const int e = table_lookup(E.tc, TAB_SGF, q.prof, fl);
@@ -751,18 +772,19 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
             if (e == -2) atomicOr(&E.status[STAT_ERR], ERR_CACHE_FULL);
             wait = true;                   // retry this hop next epoch (same draws)
         } else {
-            m = sample_thr(E.tc.thr + (size_t)e * E.tc.P, (int)E.tc.P, hb.x);
+            m = sample_guided(E.tc.thr + (size_t)e * E.tc.P, E.tc.guide + (size_t)e * GUIDE, (int)E.tc.P, hb.x);
             frame_sgf(q.axis, fr);
             w.cnt_sh += 1u;
         }
     }
+    if (m >= 0) {
+        int node[3];
+        panel_node(N, fr, m, node);
+        node_point(pos, R, N, node, pos);
+        w.hop++;
+        if (hops_here + 1 < HOPS_PER_EPOCH) continue;   // next hop of the same walk in this epoch
+    }
     if (wait || m >= 0) {
-        if (m >= 0) {
-            int node[3];
-            panel_node(N, fr, m, node);
-            node_point(pos, R, N, node, pos);
-            w.hop++;
-        }
         E.s.pos[s] = (double)pos[0];
         E.s.pos[NS + s] = (double)pos[1];
         E.s.pos[2 * NS + s] = (double)pos[2];
@@ -770,6 +792,8 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         store_walk(E, s, w);
         return;
     }
+    break;
+  }
     // MicroWalk job (Algorithm 3) for this cube, recorded with the slot
     MWJob *jb = E.mwq + s;
     const uint32_t s3 = hb.x >> 29;
@@ -992,6 +1016,7 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
 struct FillJob {
     uint32_t kind;
     uint32_t prof[4];
+    uint16_t *guide;
     uint32_t *thr;
     uint32_t *sgn;
     double *ktot;
@@ -1158,6 +1183,19 @@ __device__ void fill_table(const FillJob &F, int N, const double *__restrict__ e
         if (!flux && fabs(total - 1.0) > 1e-9) atomicOr(F.err, ERR_FILL);
         if (!(total > 0.0)) atomicOr(F.err, ERR_FILL);
     }
+    __syncthreads();
+    // guide table: first panel with threshold > bucket start (binary search)
+    for (int k = tid; k < GUIDE; k += nt) {
+        const uint32_t start = (uint32_t)k << 21;
+        int lo = 0, hi = P - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (F.thr[mid] > start) hi = mid;
+            else lo = mid + 1;
+        }
+        F.guide[k] = (uint16_t)lo;
+    }
+    __syncthreads();
 }
 
 __global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t entry, double *values)
@@ -1168,6 +1206,7 @@ __global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t ent
     F.prof[0] = prof.x; F.prof[1] = prof.y; F.prof[2] = prof.z; F.prof[3] = prof.w;
     F.thr = E.tc.thr + (size_t)entry * E.tc.P;
     F.sgn = E.tc.sgn + (size_t)entry * E.tc.P32;
+    F.guide = E.tc.guide + (size_t)entry * GUIDE;
     F.ktot = E.tc.ktot + entry;
     F.values = values;
     F.err = &E.status[STAT_ERR];
@@ -1261,6 +1300,129 @@ __device__ void reduce_batch(const EngineView &E, uint32_t g, unsigned long long
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Stop rule on the device (Sec. IV: standard error below the target on C_ii and on
+// the largest |C_ij|, j != i, ground excluded, re-chosen at every check), evaluated
+// at every full batch of the completed prefix of walk ids, so the decision does
+// not depend on the order in which walks finish.
+__device__ __forceinline__ double i128_to_double(unsigned long long lo, unsigned long long hi)
+{
+    const bool neg = (long long)hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const double v = (double)hi * 18446744073709551616.0 + (double)lo;
+    return neg ? -v : v;
+}
+
+__device__ __forceinline__ void add128(unsigned long long *d, const unsigned long long *a)
+{
+    const unsigned long long lo = d[0] + a[0];
+    d[1] = d[1] + a[1] + (lo < d[0] ? 1ull : 0ull);
+    d[0] = lo;
+}
+
+__device__ void rel_errors_dev(const unsigned long long *sum, int nc, int master, double n, double *rs, double *rc)
+{
+    const int nc1 = nc + 1;
+    auto val = [&](int k, double *c, double *se) {
+        const double s1 = i128_to_double(sum[2 * k], sum[2 * k + 1]) / ACC_S1_SCALE;
+        const double s2 = i128_to_double(sum[2 * nc1 + 2 * k], sum[2 * nc1 + 2 * k + 1]) / ACC_S2_SCALE;
+        *c = s1 / n;
+        const double v = (s2 - s1 * s1 / n) / (n * (n - 1.0));
+        *se = sqrt(v > 0 ? v : 0.0);
+    };
+    double ci, si;
+    val(master, &ci, &si);
+    *rs = (ci != 0.0) ? si / fabs(ci) : __longlong_as_double(0x7ff0000000000000ll);
+    *rc = 0.0;
+    int jb = -1;
+    double cb = 0.0;
+    for (int j = 0; j < nc; j++) {
+        if (j == master) continue;
+        double c, sj;
+        val(j, &c, &sj);
+        if (jb < 0 || fabs(c) > cb) {
+            jb = j;
+            cb = fabs(c);
+        }
+    }
+    if (jb >= 0) {
+        double c, sj;
+        val(jb, &c, &sj);
+        *rc = (c != 0.0) ? sj / fabs(c) : __longlong_as_double(0x7ff0000000000000ll);
+    }
+}
+
+// One thread: advance the completed prefix of every undecided sigma job (try-lock
+// per job, bounded work), apply the stop rule, and steer the job's issue limit to
+// the predicted need (n (r / target)^2 with margin) so the pool does not run far
+// past the stopping point.
+__device__ void advance_sigma_jobs(const EngineView &E)
+{
+    for (int j = 0; j < E.n_jobs; j++) {
+        const DevJob &J = E.jobs[j];
+        if (!(J.sigma > 0.0)) continue;
+        JobState &S = E.jstate[j];
+        if (*(volatile uint32_t *)&S.decided) continue;
+        if (atomicCAS(&S.lock, 0u, 1u) != 0u) continue;
+        __threadfence();
+        unsigned long long *sum = E.jsum + E.jsum_off[j];
+        const int nc1 = J.n_c + 1;
+        const uint64_t nb = (J.walk_count + J.batch - 1) / J.batch;
+        unsigned long long prefix = *(volatile unsigned long long *)&S.prefix;
+        bool changed = false;
+        uint32_t decided = 0;
+        for (int it = 0; it < 64; it++) {
+            if (prefix >= nb) {
+                decided = 2;
+                break;
+            }
+            const uint64_t g = J.batch_base + prefix;
+            if (!cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(E.batch_ready[g]).load(cuda::memory_order_acquire))
+                break;
+            const unsigned long long *blk = E.acc + J.acc_base + prefix * J.acc_stride;
+            for (int w = 0; w < 4 * nc1; w += 2) add128(sum + w, blk + w);
+            for (int x = 0; x < ACC_EXTRA; x++) sum[4 * nc1 + x] += blk[4 * nc1 + x];
+            const uint64_t bsz = min((uint64_t)J.batch, (uint64_t)(J.walk_count - prefix * J.batch));
+            prefix++;
+            changed = true;
+            const double n = (double)min((uint64_t)(prefix * J.batch), (uint64_t)J.walk_count);
+            if (bsz == J.batch && n >= 2.0) {
+                double rs, rc;
+                rel_errors_dev(sum, J.n_c, J.master, n, &rs, &rc);
+                if (rs <= J.sigma && rc <= J.sigma) {
+                    decided = 1;
+                    S.used = (unsigned long long)n;
+                    atomicExch(&E.job_cancel[j], 1);
+                    break;
+                }
+            }
+        }
+        if (decided == 2) S.used = J.walk_count;
+        S.prefix = prefix;
+        if (!decided && changed) {
+            const double n = (double)min((uint64_t)(prefix * J.batch), (uint64_t)J.walk_count);
+            unsigned long long lim = J.walk_count;
+            if (n >= (double)J.batch) {
+                double rs, rc;
+                rel_errors_dev(sum, J.n_c, J.master, n, &rs, &rc);
+                const double r = fmax(rs, rc) / J.sigma;
+                double need = isfinite(r) ? n * r * r : (double)J.walk_count;
+                need = fmin(need * 1.15 + 2.0 * (double)J.batch, (double)J.walk_count);
+                lim = ((unsigned long long)need + J.batch - 1) / J.batch * J.batch;
+            }
+            lim = max(lim, (unsigned long long)((prefix + 1) * J.batch));
+            lim = min(lim, (unsigned long long)J.walk_count);
+            atomicExch(&E.job_limit[j], lim);
+        }
+        __threadfence();
+        if (decided) atomicExch(&S.decided, decided);
+        atomicExch(&S.lock, 0u);
+    }
+}
+
 // Take one completed batch from the reduction queue (compare-and-swap on the
 // head; an entry is taken only once its index has been written).
 __device__ uint32_t take_batch(const EngineView &E)
@@ -1289,10 +1451,11 @@ __device__ uint32_t take_batch(const EngineView &E)
 //             lane, refilling lanes at 4-step boundaries; once the queue is empty a
 //             warp with few lanes left suspends them (node and step count saved, so
 //             the Philox stream continues unchanged) and they resume next epoch.
-// The kernel exits when its pool is empty, no walk can be issued and the host has
-// closed the run; an idle wait is bounded by E.idle_timeout_s.
+// The kernel exits when its pool is empty, no walk can be issued and every stop
+// rule is decided; an idle wait is bounded by E.idle_timeout_s.
 constexpr int WALK_THREADS = 256;
 constexpr int WALK_WARPS = WALK_THREADS / 32;
+constexpr int MW_WARPS = WALK_WARPS;
 constexpr int POOL_MAX = 4096;
 constexpr int FILL_MAX = 128;
 constexpr int SUSPEND_LANES = 8;
@@ -1304,6 +1467,7 @@ struct WalkShared {
     uint32_t q_count, q_head, s_count, g_count;
     uint32_t f_count, active, issuable, stop;
     uint32_t red, finished, n_free, rr;
+    uint32_t q_next, pad2[3];
     IssueRanges ir;
     uint32_t fill[FILL_MAX];
     uint16_t qlist[2][POOL_MAX];
@@ -1323,7 +1487,7 @@ size_t mw_smem_bytes(int N, int warps)
 
 size_t walk_smem_bytes(int N, int max_nc)
 {
-    const size_t masks = sizeof(uint32_t) * (size_t)WALK_WARPS * 3 * (N + 2) * 32;
+    const size_t masks = sizeof(uint32_t) * (size_t)MW_WARPS * 3 * (N + 2) * 32;
     const size_t fill = fill_smem_bytes(N);
     const size_t red = sizeof(unsigned long long) * acc_stride_for(max_nc);
     return std::max(masks, std::max(fill, red));
@@ -1347,16 +1511,17 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
         E.s.job[s] = E.n_jobs > 0 ? s % (uint32_t)E.n_jobs : 0u;
     }
     if (tid == 0) {
-        sh.q_count = 0; sh.q_head = 0; sh.s_count = 0; sh.stop = 0;
+        sh.q_count = 0; sh.q_head = 0; sh.s_count = 0; sh.stop = 0; sh.q_next = 0;
+        sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0; sh.red = 0;
+        sh.issuable = 0;
         sh.rr = blockIdx.x % (uint32_t)(E.n_jobs > 0 ? E.n_jobs : 1);
     }
     __syncthreads();
     int cur = 0;
-    unsigned long long idle_t0 = 0, cyc[4] = {0, 0, 0, 0};
+    unsigned long long idle_t0 = 0, cyc[5] = {0, 0, 0, 0, 0};
     uint32_t epochs = 0;
     for (;;) {
         const long long c0 = clock64();
-        // ---------------- geometry phase ----------------
         if (tid == 0) {
             sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0;
             uint32_t iss = 0;
@@ -1365,87 +1530,60 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
             sh.issuable = iss;
         }
         __syncthreads();
-        const bool iss = sh.issuable != 0;
-        for (uint32_t o = tid; o < P; o += WALK_THREADS) {     // P is a multiple of the block size
-            const uint32_t s = base + o;
-            uint32_t st = E.s.state[s];
-            if (st == ST_IDLE && iss) {
-                st = ST_FRESH;
-                E.s.state[s] = ST_FRESH;
-            }
-            const bool act = st != ST_IDLE;
-            const bool need = act && st != ST_MW;
-            uint32_t wj = 0;
-            if (st != ST_FRESH && st != ST_IDLE) wj = E.s.job[s];
-            const bool free_slot = st == ST_FRESH || (act && st != ST_MW && ((volatile int *)E.job_cancel)[wj]);
-            const uint32_t ba = __ballot_sync(FULL_MASK, act), bn = __ballot_sync(FULL_MASK, need);
-            const uint32_t bf = __ballot_sync(FULL_MASK, free_slot);
-            uint32_t gb = 0;
-            if (lane == 0) {
-                if (ba) atomicAdd(&sh.active, (uint32_t)__popc(ba));
-                if (bn) gb = atomicAdd(&sh.g_count, (uint32_t)__popc(bn));
-                if (bf) atomicAdd(&sh.n_free, (uint32_t)__popc(bf));
-            }
-            gb = __shfl_sync(FULL_MASK, gb, 0);
-            if (need) sh.glist[gb + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)o;
-        }
-        if (tid == 0) {
-            claim_ids(E, sh.ir, sh.n_free, sh.rr);
-            sh.rr = E.n_jobs > 0 ? (sh.rr + 1u) % (uint32_t)E.n_jobs : 0u;
-        }
-        __syncthreads();
+        // Two warp groups run concurrently in every epoch.  Geometry warps step every
+        // slot that is not in MicroWalk (and queue new MicroWalk jobs for the next
+        // epoch); MicroWalk warps run the jobs queued by the previous epoch.  The
+        // groups touch disjoint slots; both append to the next epoch's queue.
+        uint16_t *q_now = sh.qlist[cur];
+        uint16_t *q_next = sh.qlist[cur ^ 1];
         {
-            const uint32_t ng = sh.g_count;
-            const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
-            uint16_t *ql = sh.qlist[cur];
-            for (uint32_t i = tid; i < ng; i += WALK_THREADS) {
-                const uint32_t o = sh.glist[i];
-                geo_slot<T>(E, base + o, o, fl, ql, &sh.q_count, sh.ir);
+            // ---------------- geometry ----------------
+            const bool iss = sh.issuable != 0;
+            for (uint32_t o = tid; o < P; o += WALK_THREADS) {   // P is a multiple of WALK_THREADS
+                const uint32_t s = base + o;
+                uint32_t st = E.s.state[s];
+                if (st == ST_IDLE && iss) {
+                    st = ST_FRESH;
+                    E.s.state[s] = ST_FRESH;
+                }
+                const bool act = st != ST_IDLE;
+                const bool need = act && st != ST_MW;
+                uint32_t wj = 0;
+                if (st != ST_FRESH && st != ST_IDLE && st != ST_MW) wj = E.s.job[s];
+                const bool free_slot =
+                    st == ST_FRESH || (need && st != ST_FRESH && ((volatile int *)E.job_cancel)[wj]);
+                const uint32_t ba = __ballot_sync(FULL_MASK, act), bn = __ballot_sync(FULL_MASK, need);
+                const uint32_t bf = __ballot_sync(FULL_MASK, free_slot);
+                uint32_t gb = 0;
+                if (lane == 0) {
+                    if (ba) atomicAdd(&sh.active, (uint32_t)__popc(ba));
+                    if (bn) gb = atomicAdd(&sh.g_count, (uint32_t)__popc(bn));
+                    if (bf) atomicAdd(&sh.n_free, (uint32_t)__popc(bf));
+                }
+                gb = __shfl_sync(FULL_MASK, gb, 0);
+                if (need) sh.glist[gb + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)o;
             }
-        }
-        __syncthreads();
-        const long long c1 = clock64();
-        // ---------------- fill phase ----------------
-        const uint32_t nf = min(sh.f_count, (uint32_t)FILL_MAX);
-        for (uint32_t f = 0; f < nf; f++) {
-            const uint32_t e = sh.fill[f];
-            if (e == 0xffffffffu) continue;
-            FillJob F;
-            const uint32_t *k = E.tc.keys + 5 * e;
-            F.kind = k[0];
-            F.prof[0] = k[1]; F.prof[1] = k[2]; F.prof[2] = k[3]; F.prof[3] = k[4];
-            F.thr = E.tc.thr + (size_t)e * E.tc.P;
-            F.sgn = E.tc.sgn + (size_t)e * E.tc.P32;
-            F.ktot = E.tc.ktot + e;
-            F.values = nullptr;
-            F.err = &E.status[STAT_ERR];
-            fill_table(F, N, E.eps, E.fc, reinterpret_cast<double *>(dsm));
             __syncthreads();
             if (tid == 0) {
-                __threadfence();
-                atomicExch(&E.tc.state[e], TE_READY);
-                atomicAdd(&E.status[STAT_BUILT], 1u);
+                claim_ids(E, sh.ir, sh.n_free, sh.rr);
+                sh.rr = E.n_jobs > 0 ? (sh.rr + 1u) % (uint32_t)E.n_jobs : 0u;
             }
             __syncthreads();
+            const uint32_t ng = sh.g_count;
+            const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
+            for (uint32_t i = tid; i < ng; i += WALK_THREADS) {
+                const uint32_t o = sh.glist[i];
+                geo_slot<T>(E, base + o, o, fl, q_now, &sh.q_count, sh.ir);
+            }
         }
-        const long long c2 = clock64();
-        // ---------------- reduction phase ----------------
-        for (;;) {
-            if (tid == 0) sh.red = take_batch(E);
-            __syncthreads();
-            const uint32_t g = sh.red;
-            __syncthreads();
-            if (g == 0xffffffffu) break;
-            reduce_batch(E, g, reinterpret_cast<unsigned long long *>(dsm));
-        }
-        const long long c3 = clock64();
-        // ---------------- MicroWalk phase ----------------
+        __syncthreads();
+        const long long cg1 = clock64();
         {
-            uint32_t *Mw = reinterpret_cast<uint32_t *>(dsm) + (size_t)warp * 3 * NP2 * 32;
+            // ---------------- MicroWalk ----------------
+            const int mwarp = warp;
+            uint32_t *Mw = reinterpret_cast<uint32_t *>(dsm) + (size_t)mwarp * 3 * NP2 * 32;
             const uint32_t *M = Mw + lane;
             const uint32_t qn = sh.q_count;
-            const uint16_t *ql = sh.qlist[cur];
-            uint16_t *sl = sh.qlist[cur ^ 1];
             bool active = false, exhausted = false;
             int x = 0, y = 0, z = 0;
             uint32_t t = 0, t_in = 0, my_o = 0;
@@ -1463,7 +1601,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
                     const uint32_t myj = b0 + (uint32_t)__popc(bal & ((1u << lane) - 1u));
                     const bool got = need && myj < qn;
                     if (need && !got) exhausted = true;
-                    const uint32_t oj = got ? (uint32_t)ql[myj] : 0u;
+                    const uint32_t oj = got ? (uint32_t)q_now[myj] : 0u;
                     uint32_t todo = __ballot_sync(FULL_MASK, got);
                     while (todo) {
                         const int r = __ffs(todo) - 1;
@@ -1512,7 +1650,8 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
                         MWJob &b = E.mwq[base + my_o];
                         b.start = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16);
                         b.pad0 = t;
-                        sl[atomicAdd(&sh.s_count, 1u)] = (uint16_t)my_o;
+                        q_next[atomicAdd(&sh.q_next, 1u)] = (uint16_t)my_o;
+                        atomicAdd(&sh.s_count, 1u);
                         active = false;
                     }
                     break;
@@ -1527,6 +1666,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
                                 const uint32_t sl2 = L.tag;
                                 E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
                                 E.s.steps[sl2] += t + (uint32_t)k + 1u;
+                                __threadfence_block();      // exit data before the state (read by geometry warps)
                                 E.s.state[sl2] = ST_MWDONE;
                                 active = false;
                                 atomicAdd(&sh.finished, 1u);
@@ -1539,6 +1679,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
                         const uint32_t sl2 = L.tag;
                         E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
                         E.s.steps[sl2] += t;
+                        __threadfence_block();
                         E.s.state[sl2] = ST_MWDONE;
                         active = false;
                     }
@@ -1547,23 +1688,66 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
             }
         }
         __syncthreads();
-        const long long c4 = clock64();
+        const long long c1 = clock64();
+        if (tid == 0) {
+            cyc[0] += (unsigned long long)(cg1 - c0);
+            cyc[3] += (unsigned long long)(c1 - cg1);
+        }
+        // ---------------- fill phase ----------------
+        const uint32_t nf = min(sh.f_count, (uint32_t)FILL_MAX);
+        for (uint32_t f = 0; f < nf; f++) {
+            const uint32_t e = sh.fill[f];
+            if (e == 0xffffffffu) continue;
+            FillJob F;
+            const uint32_t *k = E.tc.keys + 5 * e;
+            F.kind = k[0];
+            F.prof[0] = k[1]; F.prof[1] = k[2]; F.prof[2] = k[3]; F.prof[3] = k[4];
+            F.thr = E.tc.thr + (size_t)e * E.tc.P;
+            F.sgn = E.tc.sgn + (size_t)e * E.tc.P32;
+            F.guide = E.tc.guide + (size_t)e * GUIDE;
+            F.ktot = E.tc.ktot + e;
+            F.values = nullptr;
+            F.err = &E.status[STAT_ERR];
+            fill_table(F, N, E.eps, E.fc, reinterpret_cast<double *>(dsm));
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicExch(&E.tc.state[e], TE_READY);
+                atomicAdd(&E.status[STAT_BUILT], 1u);
+            }
+            __syncthreads();
+        }
+        const long long c2 = clock64();
+        // ---------------- reduction phase ----------------
+        for (;;) {
+            if (tid == 0) sh.red = take_batch(E);
+            __syncthreads();
+            const uint32_t g = sh.red;
+            __syncthreads();
+            if (g == 0xffffffffu) break;
+            reduce_batch(E, g, reinterpret_cast<unsigned long long *>(dsm));
+        }
+        if (tid == 0) advance_sigma_jobs(E);
+        const long long c3 = clock64();
         epochs++;
         if (tid == 0) {
-            cyc[0] += (unsigned long long)(c1 - c0);
             cyc[1] += (unsigned long long)(c2 - c1);
             cyc[2] += (unsigned long long)(c3 - c2);
-            cyc[3] += (unsigned long long)(c4 - c3);
+            cyc[4] += (unsigned long long)(c3 - c0);
             if (sh.s_count) atomicAdd(&E.status[STAT_SUSPENDED], sh.s_count);
-            const bool idle = sh.active == 0u && sh.issuable == 0u && sh.s_count == 0u;
-            sh.q_count = sh.s_count;
+            const bool idle = sh.active == 0u && sh.issuable == 0u && sh.q_next == 0u;
+            sh.q_count = sh.q_next;
+            sh.q_next = 0;
             sh.q_head = 0;
             sh.s_count = 0;
             uint32_t stop = 0;
             if (*(volatile uint32_t *)&E.ctrl[CTRL_ABORT]) stop = 1;
             if (*(volatile uint32_t *)&E.status[STAT_ERR]) stop = 1;   // any device error ends the run
+            bool undecided = false;
+            for (int j = 0; j < E.n_jobs; j++)
+                if (E.jobs[j].sigma > 0.0 && *(volatile uint32_t *)&E.jstate[j].decided == 0u) undecided = true;
             if (idle) {
-                if (*(volatile uint32_t *)&E.ctrl[CTRL_OPEN] == 0u) {
+                if (!undecided && *(volatile uint32_t *)&E.ctrl[CTRL_OPEN] == 0u) {
                     stop = 1;
                 } else {
                     unsigned long long now;
@@ -1585,7 +1769,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
         if (sh.stop) break;
     }
     if (tid == 0) {
-        for (int i = 0; i < 4; i++) atomicAdd(&E.cycles[i], cyc[i]);
+        for (int i = 0; i < 5; i++) atomicAdd(&E.cycles[i], cyc[i]);
         atomicMax(&E.status[STAT_EPOCHS], epochs);
     }
 }

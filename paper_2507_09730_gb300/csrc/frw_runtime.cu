@@ -298,7 +298,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         (rc = dalloc(ctx, &S.omega, NS, A)) || (rc = dalloc(ctx, &ctx->mwq, NS, A)) ||
         (rc = dalloc(ctx, &ctx->status, STAT_WORDS, A)) ||
         (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)) ||
-        (rc = dalloc(ctx, &ctx->ctrl, CTRL_WORDS, A)) || (rc = dalloc(ctx, &ctx->cycles, 4, A)))
+        (rc = dalloc(ctx, &ctx->ctrl, CTRL_WORDS, A)) || (rc = dalloc(ctx, &ctx->cycles, 8, A)))
         return bail(rc);
     TableCache &T = ctx->tc;
     T.cap = cap;
@@ -307,6 +307,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     if ((rc = dalloc(ctx, &T.keys, 5 * (size_t)cap, A)) || (rc = dalloc(ctx, &T.state, cap, A)) ||
         (rc = dalloc(ctx, &T.thr, (size_t)(cap + 2) * T.P, A)) ||
         (rc = dalloc(ctx, &T.sgn, (size_t)(cap + 2) * T.P32, A)) || (rc = dalloc(ctx, &T.ktot, cap + 2, A)) ||
+        (rc = dalloc(ctx, &T.guide, (size_t)(cap + 2) * GUIDE, A)) ||
         (rc = dalloc(ctx, &T.fillq, cap, A)) || (rc = dalloc(ctx, &T.fillq_count, 2, A)))
         return bail(rc);
     T.fillq_head = T.fillq_count + 1;
@@ -776,6 +777,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
         d.acc_base = acc_words;
         d.rec_base = total_walks;
         d.batch_base = total_batches;
+        d.sigma = j.desc.sigma_target;
         j.n_batches = (d.walk_count + d.batch - 1) / d.batch;
         acc_words += j.n_batches * d.acc_stride;
         total_walks += d.walk_count;
@@ -803,22 +805,48 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     unsigned long long *d_next = nullptr, *d_acc = nullptr, *d_limit = nullptr;
     int *d_cancel = nullptr;
     uint32_t *d_done = nullptr, *d_ready = nullptr, *d_rq = nullptr, *d_rqc = nullptr;
+    JobState *d_js = nullptr;
+    unsigned long long *d_jsum = nullptr, *d_jsoff = nullptr;
     if ((rc = dalloc(ctx, &d_jobs, nj, tmp)) || (rc = dalloc(ctx, &d_next, nj, tmp)) ||
         (rc = dalloc(ctx, &d_limit, nj, tmp)) || (rc = dalloc(ctx, &d_cancel, nj, tmp)) ||
         (rc = dalloc(ctx, &d_acc, std::max<uint64_t>(acc_words, 1), tmp)) ||
         (rc = dalloc(ctx, &d_done, std::max<uint64_t>(total_batches, 1), tmp)) ||
         (rc = dalloc(ctx, &d_ready, std::max<uint64_t>(total_batches, 1), tmp)) ||
-        (rc = dalloc(ctx, &d_rq, std::max<uint64_t>(total_batches, 1), tmp)) || (rc = dalloc(ctx, &d_rqc, 2, tmp))) {
+        (rc = dalloc(ctx, &d_rq, std::max<uint64_t>(total_batches, 1), tmp)) || (rc = dalloc(ctx, &d_rqc, 2, tmp)) ||
+        (rc = dalloc(ctx, &d_js, nj, tmp)) || (rc = dalloc(ctx, &d_jsoff, nj, tmp))) {
         cleanup();
         return rc;
     }
+    // slots for this run (fewer for small runs)
+    uint32_t run_pool;
+    {
+        const uint32_t pool0 = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
+        const uint64_t per = std::max<uint64_t>(256, ((total_walks / ctx->grid + 255) / 256) * 256);
+        run_pool = (uint32_t)std::min<uint64_t>(pool0, per);
+    }
+    const uint64_t run_slots = (uint64_t)run_pool * ctx->grid;
+    int n_sigma = 0;
+    for (auto &j : jobs) n_sigma += j.desc.sigma_target > 0.0 ? 1 : 0;
     std::vector<DevJob> hj(nj);
-    std::vector<unsigned long long> hl(nj);
-    bool any_sigma = false;
+    std::vector<unsigned long long> hl(nj), hjo(nj);
+    uint64_t jsum_words = 0;
     for (int i = 0; i < nj; i++) {
         hj[i] = jobs[i].d;
         hl[i] = jobs[i].d.walk_count;
-        any_sigma |= jobs[i].desc.sigma_target > 0.0 && jobs[i].n_batches > 0;
+        if (jobs[i].desc.sigma_target > 0.0) {
+            // first wave: this job's share of the slot pool; the device then steers
+            // the limit from the completed prefix (predicted need)
+            const uint64_t b = jobs[i].d.batch;
+            uint64_t first = std::max<uint64_t>(4 * b, run_slots / (uint64_t)n_sigma);
+            first = (first + b - 1) / b * b;
+            hl[i] = std::min<uint64_t>(first, jobs[i].d.walk_count);
+        }
+        hjo[i] = jsum_words;
+        jsum_words += jobs[i].d.acc_stride;
+    }
+    if ((rc = dalloc(ctx, &d_jsum, std::max<uint64_t>(jsum_words, 1), tmp))) {
+        cleanup();
+        return rc;
     }
     cudaStream_t st = ctx->stream, ax = ctx->aux;
 #define CKR(call)                                     \
@@ -830,7 +858,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             return r_;                                \
         }                                             \
     } while (0)
-    const uint32_t ctrl0[CTRL_WORDS] = {any_sigma ? 1u : 0u, 0u, 0u, 0u};
+    const uint32_t ctrl0[CTRL_WORDS] = {0u, 0u, 0u, 0u};
     CKR(cudaMemcpyAsync(d_jobs, hj.data(), sizeof(DevJob) * nj, cudaMemcpyHostToDevice, st));
     CKR(cudaMemcpyAsync(d_limit, hl.data(), sizeof(unsigned long long) * nj, cudaMemcpyHostToDevice, st));
     CKR(cudaMemcpyAsync(ctx->ctrl, ctrl0, sizeof(ctrl0), cudaMemcpyHostToDevice, st));
@@ -841,9 +869,12 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     CKR(cudaMemsetAsync(d_ready, 0, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
     CKR(cudaMemsetAsync(d_rq, 0xff, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
     CKR(cudaMemsetAsync(d_rqc, 0, sizeof(uint32_t) * 2, st));
+    CKR(cudaMemsetAsync(d_js, 0, sizeof(JobState) * nj, st));
+    CKR(cudaMemsetAsync(d_jsum, 0, sizeof(unsigned long long) * std::max<uint64_t>(jsum_words, 1), st));
+    CKR(cudaMemcpyAsync(d_jsoff, hjo.data(), sizeof(unsigned long long) * nj, cudaMemcpyHostToDevice, st));
     CKR(cudaMemsetAsync(ctx->rec.k, 0x80, sizeof(int32_t) * std::max<uint64_t>(total_walks, 1), st));
     CKR(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
-    CKR(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 4, st));
+    CKR(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, st));
     EngineView E = make_view(ctx);
     E.n_jobs = nj;
     E.max_nc = max_nc;
@@ -851,6 +882,9 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     E.job_next = d_next;
     E.job_limit = d_limit;
     E.job_cancel = d_cancel;
+    E.jstate = d_js;
+    E.jsum = d_jsum;
+    E.jsum_off = d_jsoff;
     E.acc = d_acc;
     E.batch_done = d_done;
     E.batch_ready = d_ready;
@@ -859,112 +893,22 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     E.rq_head = d_rqc + 1;
     E.rq_cap = (uint32_t)std::max<uint64_t>(total_batches, 1);
     E.rec = ctx->rec;
-    // fewer slots for small runs
-    {
-        const uint64_t per = std::max<uint64_t>(256, ((total_walks / ctx->grid + 255) / 256) * 256);
-        E.pool = (uint32_t)std::min<uint64_t>(E.pool, per);
-        E.NS = E.pool * ctx->grid;
-    }
-    const uint64_t LOOK = 16;   // batches followed per sigma job per poll
-    for (auto &j : jobs)
-        if (j.desc.sigma_target > 0.0) {
-            if (cudaMallocHost(&j.h_blocks, sizeof(unsigned long long) * LOOK * j.d.acc_stride) != cudaSuccess) {
-                cleanup();
-                return fail(ctx, FRW_ENOMEM, "pinned staging");
-            }
-            j.h_cap = LOOK;
-        }
-    if (cudaMallocHost(&h_flags, sizeof(uint32_t) * (LOOK + STAT_WORDS)) != cudaSuccess) {
-        cleanup();
-        return fail(ctx, FRW_ENOMEM, "pinned staging");
-    }
+    E.pool = run_pool;
+    E.NS = (uint32_t)run_slots;
     CKR(cudaEventRecord(ctx->ev[0], st));
     CKR(launch_walk(E, ctx->shape, st));
     CKR(cudaEventRecord(ctx->ev[1], st));
-    bool open = any_sigma;
-    uint32_t dev_err = 0;
+    // wait for the kernel (which applies the stop rules itself) under a wall-clock guard
     const double limit_s = run_timeout_s();
     bool timed_out = false;
-    for (;;) {
-        const bool finished = cudaEventQuery(ctx->ev[1]) == cudaSuccess;
-        if (finished) break;
+    while (cudaEventQuery(ctx->ev[1]) == cudaErrorNotReady) {
         if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) {
-            // give up: the kernel stops at its next epoch boundary
-            static const uint32_t abort1 = 1;
+            static const uint32_t abort1 = 1;   // the kernel stops at its next epoch boundary
             CKR(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
             CKR(cudaStreamSynchronize(ax));
             timed_out = true;
             break;
         }
-        if (!open) {
-            std::this_thread::sleep_for(std::chrono::microseconds(100));
-            continue;
-        }
-        // device error flags
-        CKR(cudaMemcpyAsync(h_flags + LOOK, ctx->status, sizeof(uint32_t) * STAT_WORDS, cudaMemcpyDeviceToHost, ax));
-        CKR(cudaStreamSynchronize(ax));
-        dev_err = h_flags[LOOK + STAT_ERR];
-        bool undecided = false;
-        for (int i = 0; i < nj && !dev_err; i++) {
-            JobRun &j = jobs[i];
-            if (j.desc.sigma_target <= 0.0 || j.converged || j.prefix >= j.n_batches) continue;
-            const uint32_t strd = j.d.acc_stride;
-            const uint64_t look = std::min<uint64_t>(LOOK, j.n_batches - j.prefix);
-            CKR(cudaMemcpyAsync(h_flags, d_ready + j.d.batch_base + j.prefix, sizeof(uint32_t) * look,
-                                cudaMemcpyDeviceToHost, ax));
-            CKR(cudaStreamSynchronize(ax));
-            uint64_t nready = 0;
-            while (nready < look && h_flags[nready]) nready++;
-            if (nready) {
-                CKR(cudaMemcpyAsync(j.h_blocks, d_acc + j.d.acc_base + j.prefix * strd,
-                                    sizeof(unsigned long long) * nready * strd, cudaMemcpyDeviceToHost, ax));
-                CKR(cudaStreamSynchronize(ax));
-                for (uint64_t b = 0; b < nready && !j.converged; b++) {
-                    const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - j.prefix * j.d.batch);
-                    fold_block(j, j.h_blocks + b * strd, bsz);
-                    j.prefix++;
-                    if (bsz == j.d.batch && sigma_ok(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, j.desc.sigma_target))
-                        j.converged = true;
-                }
-            }
-            if (j.converged) {
-                static const int one = 1;
-                CKR(cudaMemcpyAsync(d_cancel + i, &one, sizeof(int), cudaMemcpyHostToDevice, ax));
-                continue;
-            }
-            if (j.prefix >= j.n_batches) continue;
-            undecided = true;
-            // predictive issue limit: walks needed ~ n (r / target)^2 with margin, so that
-            // the in-flight pool does not run far past the stopping point
-            uint64_t lim = j.limit;
-            if (j.walks >= j.d.batch) {
-                double rs, rcp;
-                rel_errors(j.S1, j.S2, j.walks, j.d.n_c, j.d.master, &rs, &rcp);
-                const double r = std::max(rs, rcp) / j.desc.sigma_target;
-                double need = std::isfinite(r) ? (double)j.walks * r * r : (double)j.d.walk_count;
-                need = std::min<double>(need * 1.15 + 2.0 * j.d.batch, (double)j.d.walk_count);
-                lim = ((uint64_t)need + j.d.batch - 1) / j.d.batch * j.d.batch;
-            }
-            lim = std::min<uint64_t>(std::max<uint64_t>(lim, (j.prefix + 1) * j.d.batch), j.d.walk_count);
-            if (lim != j.limit) {
-                j.limit = lim;
-                j.h_limit = lim;
-                CKR(cudaMemcpyAsync(d_limit + i, &j.h_limit, sizeof(unsigned long long), cudaMemcpyHostToDevice, ax));
-            }
-        }
-        if (dev_err) {
-            static const uint32_t abort1 = 1;
-            CKR(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
-            break;
-        }
-        if (!undecided) {
-            static const uint32_t zero = 0;
-            CKR(cudaMemcpyAsync(ctx->ctrl + CTRL_OPEN, &zero, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
-            CKR(cudaStreamSynchronize(ax));
-            open = false;
-            continue;
-        }
-        CKR(cudaStreamSynchronize(ax));
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
     CKR(cudaStreamSynchronize(st));
@@ -977,11 +921,20 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
         cleanup();
         return fail(ctx, FRW_ETIMEOUT, "run exceeded its wall-clock limit (FRW_RUN_TIMEOUT_S)");
     }
-    // jobs without a sigma target (or that ran out of budget): fold every batch
+    std::vector<JobState> hjs(nj);
+    CKR(cudaMemcpy(hjs.data(), d_js, sizeof(JobState) * nj, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nj; i++) {
+        JobRun &j = jobs[i];
+        if (j.desc.sigma_target > 0.0 && hjs[i].decided == 1) {
+            j.converged = true;
+            j.n_batches = (hjs[i].used + j.d.batch - 1) / j.d.batch;   // fold exactly the decided prefix
+        }
+    }
+    // fold the batches of every job's estimate (all of them, or the decided prefix)
     std::vector<unsigned long long> hb;
     for (int i = 0; i < nj; i++) {
         JobRun &j = jobs[i];
-        if (j.converged || j.prefix >= j.n_batches) continue;
+        if (j.prefix >= j.n_batches) continue;
         const uint32_t strd = j.d.acc_stride;
         const uint64_t rest = j.n_batches - j.prefix;
         hb.resize(rest * strd);
@@ -1002,9 +955,11 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     }
     float kms = 0.f;
     cudaEventElapsedTime(&kms, ctx->ev[0], ctx->ev[1]);
-    unsigned long long cyc[4] = {0, 0, 0, 0};
+    std::vector<unsigned long long> issued(nj);
+    CKR(cudaMemcpy(issued.data(), d_next, sizeof(unsigned long long) * nj, cudaMemcpyDeviceToHost));
+    unsigned long long cyc[5] = {0, 0, 0, 0, 0};
     CKR(cudaMemcpy(cyc, ctx->cycles, sizeof(cyc), cudaMemcpyDeviceToHost));
-    const double ctot = (double)(cyc[0] + cyc[1] + cyc[2] + cyc[3]);
+    const double ctot = (double)cyc[4];   // phases overlap: busy shares of the kernel's CTA time
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats_out) {
         for (int i = 0; i < nj; i++) {
@@ -1029,6 +984,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             s.mw_ms = ctot > 0 ? kms * (double)cyc[3] / ctot : 0.0;
             s.launches = 1;
             s.mw_jobs = j.ex[5];
+            s.walks_issued = issued[i];
         }
     }
     cleanup();
