@@ -86,9 +86,9 @@ typedef struct {
     int32_t max_hops;          /* hop cap; a capped walk counts with zero contribution */
     int32_t slots;             /* walks in flight on the device (0: default) */
     int32_t table_capacity;    /* analytical-table cache entries (0: default) */
-    int32_t mw_warps_per_cta;  /* MicroWalk kernel launch shape (0: default) */
-    int32_t mw_ctas_per_sm;    /* (0: default) */
-    int32_t geom_threads;      /* geometry kernel block size (0: default) */
+    int32_t mw_warps_per_cta;  /* stand-alone MicroWalk kernel: warps per CTA, 1..16 (0: 16) */
+    int32_t mw_ctas_per_sm;    /* stand-alone MicroWalk kernel: CTAs per SM, 1..32 (0: 2) */
+    int32_t geom_threads;      /* ignored (kept for layout) */
     int32_t reserved[6];
 } frw_options;
 

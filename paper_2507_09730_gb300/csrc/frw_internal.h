@@ -189,6 +189,7 @@ struct EngineView {
     const uint32_t *W;     // [16][16]
     const double *eps;     // [16]
     FillConsts fc;
+    double *fill_scratch;  // per walk-kernel CTA: 6N^2 doubles of table-fill scratch
     uint32_t *status;      // STAT_WORDS
     uint32_t *ctrl;        // CTRL_WORDS (host -> device)
     unsigned long long *cycles;   // [5] CTA cycles: geometry busy, fill, reduce, MicroWalk busy, total

@@ -836,27 +836,55 @@ __device__ __forceinline__ int mat_of(uint64_t mm, uint32_t mask)
     return (int)((mm >> (4 * slot)) & 15ull);
 }
 
-// One step of the lattice walk: weights W[mv][m_k] of Eq. 6 (quantised), integer
-// prefix sums, neighbour chosen by (u * S) >> 32.  Returns true on reaching a
-// boundary node.
-__device__ __forceinline__ bool mw_step(const uint32_t *__restrict__ M, const uint32_t *__restrict__ Wsm,
-                                        int NP2, int N, int &x, int &y, int &z, uint64_t mm, uint32_t u)
+// Lattice masks: 16-bit rows, laid out [row][lane] (row R = a * (N + 2) + c + 1 for
+// axis a, coordinate c = -1..N), so the 32 lanes of a warp read one row as 64
+// contiguous bytes, with no bank conflict.  Bit 0: inside the cube; bit q + 1:
+// inside listed block q (q < 14).
+__device__ __forceinline__ int mask_rows(int N) { return 3 * (N + 2); }
+
+// Build lane r's mask column (all 32 lanes cooperate): blocks given as voxel
+// ranges [lo, hi) per axis through rng(q, a, lo, hi).
+template <class RangeFn>
+__device__ __forceinline__ void build_masks(uint16_t *Mw, int r, int N, int lane, int K, RangeFn rng)
 {
-    const uint32_t *Mx = M;
-    const uint32_t *My = M + NP2 * 32;
-    const uint32_t *Mz = M + 2 * NP2 * 32;
-    const uint32_t xm = Mx[x * 32], x0 = Mx[(x + 1) * 32], xp = Mx[(x + 2) * 32];
-    const uint32_t ym = My[y * 32], y0 = My[(y + 1) * 32], yp = My[(y + 2) * 32];
-    const uint32_t zm = Mz[z * 32], z0 = Mz[(z + 1) * 32], zp = Mz[(z + 2) * 32];
+    const int NP2 = N + 2;
+    for (int row = lane; row < 3 * NP2; row += 32) {
+        const int a = row / NP2;
+        const int c = row - a * NP2 - 1;
+        uint32_t m = 0;
+        if (c >= 0 && c < N) {
+            m = 1u;
+            for (int q = 0; q < K; q++) {
+                int lo, hi;
+                rng(q, a, lo, hi);
+                if (lo <= c && c < hi) m |= 2u << q;
+            }
+        }
+        Mw[row * 32 + r] = (uint16_t)m;
+    }
+}
+
+// One step of the lattice walk: weights W[mv][m_k] of Eq. 6 (quantised; one copy
+// of the 16 x 16 table per lane, so lookups never conflict), integer prefix sums,
+// neighbour chosen by (u * S) >> 32.  Returns true on reaching a boundary node.
+// M points at the lane's column (Mw + lane), Wl at the lane's table (Wrep + lane).
+__device__ __forceinline__ bool mw_step(const uint16_t *__restrict__ M, const uint32_t *__restrict__ Wl, int N,
+                                        int &x, int &y, int &z, uint64_t mm, uint32_t u)
+{
+    const int AR = (N + 2) * 32;
+    const uint16_t *Mx = M + x * 32, *My = M + AR + y * 32, *Mz = M + 2 * AR + z * 32;
+    const uint32_t xm = Mx[0], x0 = Mx[32], xp = Mx[64];
+    const uint32_t ym = My[0], y0 = My[32], yp = My[64];
+    const uint32_t zm = Mz[0], z0 = Mz[32], zp = Mz[64];
     const uint32_t yz = y0 & z0, xz = x0 & z0, xy = x0 & y0;
     const int mv = mat_of(mm, xy & z0);
-    const uint32_t *Wr = Wsm + mv * 16;
-    const uint32_t w0 = Wr[mat_of(mm, xm & yz)];
-    const uint32_t w1 = Wr[mat_of(mm, xp & yz)];
-    const uint32_t w2 = Wr[mat_of(mm, ym & xz)];
-    const uint32_t w3 = Wr[mat_of(mm, yp & xz)];
-    const uint32_t w4 = Wr[mat_of(mm, zm & xy)];
-    const uint32_t w5 = Wr[mat_of(mm, zp & xy)];
+    const uint32_t *Wr = Wl + mv * 16 * 32;
+    const uint32_t w0 = Wr[mat_of(mm, xm & yz) * 32];
+    const uint32_t w1 = Wr[mat_of(mm, xp & yz) * 32];
+    const uint32_t w2 = Wr[mat_of(mm, ym & xz) * 32];
+    const uint32_t w3 = Wr[mat_of(mm, yp & xz) * 32];
+    const uint32_t w4 = Wr[mat_of(mm, zm & xy) * 32];
+    const uint32_t w5 = Wr[mat_of(mm, zp & xy) * 32];
     const uint32_t p0 = w0, p1 = p0 + w1, p2 = p1 + w2, p3 = p2 + w3, p4 = p3 + w4, p5 = p4 + w5;
     const uint32_t r = __umulhi(u, p5);
     const int k = (int)(r >= p0) + (int)(r >= p1) + (int)(r >= p2) + (int)(r >= p3) + (int)(r >= p4);
@@ -866,6 +894,12 @@ __device__ __forceinline__ bool mw_step(const uint32_t *__restrict__ M, const ui
     y += (ax == 1) ? d : 0;
     z += (ax == 2) ? d : 0;
     return ((unsigned)x >= (unsigned)N) | ((unsigned)y >= (unsigned)N) | ((unsigned)z >= (unsigned)N);
+}
+
+// replicate the 16 x 16 weight table once per lane: Wrep[entry * 32 + lane]
+__device__ __forceinline__ void replicate_w(uint32_t *Wrep, const uint32_t *__restrict__ Wg)
+{
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) Wrep[i] = Wg[i >> 5];
 }
 
 struct MWLane {
@@ -887,21 +921,14 @@ struct CubeSource {
     __device__ void overrun() const { atomicOr(err, ERR_MW_STEPS); }
     __device__ bool valid(uint64_t j) const { return j < total; }
     __device__ int gmat(int local) const { return (int)((mmap_lo >> (4 * (local & 15))) & 15ull); }
-    __device__ void build(uint64_t j, uint32_t *Mcol, int NP2, int N_, int lane) const
+    __device__ void build(uint64_t j, uint16_t *Mw, int r, int N_, int lane) const
     {
         const int32_t *c = cubes + (j / spc) * 64;
         const int K = min(max(c[1], 0), 8);   // a 64-word record holds at most 8 blocks
-        for (int row = lane; row < 3 * NP2; row += 32) {
-            const int a = row / NP2;
-            const int cc = row - a * NP2 - 1;
-            uint32_t m = 0;
-            if (cc >= 0 && cc < N_) {
-                m = 1u;
-                for (int t = 0; t < K; t++)
-                    if (c[2 + 7 * t + 2 * a] <= cc && cc < c[3 + 7 * t + 2 * a]) m |= 2u << t;
-            }
-            Mcol[row * 32] = m;
-        }
+        build_masks(Mw, r, N_, lane, K, [&](int q, int a, int &lo, int &hi) {
+            lo = c[2 + 7 * q + 2 * a];
+            hi = c[3 + 7 * q + 2 * a];
+        });
     }
     __device__ void load(uint64_t j, MWLane &L, int &x, int &y, int &z) const
     {
@@ -937,13 +964,13 @@ template <class Src>
 __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict__ Wg, int N)
 {
     extern __shared__ uint32_t smem[];
-    uint32_t *Wsm = smem;
-    const int NP2 = N + 2;
+    uint32_t *Wrep = smem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *Mw = smem + 256 + (size_t)warp * 3 * NP2 * 32;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) Wsm[i] = Wg[i];
+    uint16_t *Mw = reinterpret_cast<uint16_t *>(smem + 256 * 32) + (size_t)warp * mask_rows(N) * 32;
+    replicate_w(Wrep, Wg);
     __syncthreads();
-    const uint32_t *M = Mw + lane;
+    const uint16_t *M = Mw + lane;
+    const uint32_t *Wl = Wrep + lane;
     bool active = false, exhausted = false;
     int x = 0, y = 0, z = 0;
     uint32_t t = 0;
@@ -966,7 +993,7 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
                 const int r = __ffs(todo) - 1;
                 todo &= todo - 1u;
                 const uint64_t jr = __shfl_sync(FULL_MASK, myj, r);
-                src.build(jr, Mw + r, NP2, N, lane);
+                src.build(jr, Mw, r, N, lane);
             }
             __syncwarp();
             if (got) {
@@ -982,7 +1009,7 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 if (active) {
-                    if (mw_step(M, Wsm, NP2, N, x, y, z, L.mm, words[k])) {
+                    if (mw_step(M, Wl, N, x, y, z, L.mm, words[k])) {
                         src.finish(L, x, y, z, t + (uint32_t)k + 1u);
                         active = false;
                     }
@@ -1021,6 +1048,7 @@ struct FillJob {
     uint32_t *sgn;
     double *ktot;
     double *values;        // optional raw panel values (canonical order)
+    double *V;             // scratch for the 6N^2 panel values (global memory)
     uint32_t *err;
 };
 
@@ -1032,8 +1060,8 @@ __device__ void fill_table(const FillJob &F, int N, const double *__restrict__ e
     double *ek = sm;                 // N
     double *yh = ek + MAXN;          // M * N
     double *Z = yh + M * N;          // N * N
-    double *V = Z + MAXN * MAXN;     // P
-    double *red = V + P;             // nt
+    double *red = Z + MAXN * MAXN;   // nt + 1
+    double *V = F.V;                 // P, global scratch
     const uint32_t kind = F.kind;
     const bool hom = (kind == TAB_SGF_HOM || kind == TAB_FLUX_HOM);
     const bool perp = (kind == TAB_FLUX_PERP);
@@ -1210,6 +1238,7 @@ __global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t ent
     F.ktot = E.tc.ktot + entry;
     F.values = values;
     F.err = &E.status[STAT_ERR];
+    F.V = E.fill_scratch;
     fill_table(F, E.N, E.eps, E.fc, fsm);
 }
 
@@ -1463,7 +1492,7 @@ constexpr uint32_t SUSPEND_MIN_STEPS = 64;    // progress a job makes in an epoc
 constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // ... and only if this much geometry work is waiting
 
 struct WalkShared {
-    uint32_t W[256];
+    uint32_t g_head, pad3[3];
     uint32_t q_count, q_head, s_count, g_count;
     uint32_t f_count, active, issuable, stop;
     uint32_t red, finished, n_free, rr;
@@ -1477,34 +1506,41 @@ struct WalkShared {
 size_t fill_smem_bytes(int N)
 {
     const int H = N / 2;
-    return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + 6 * N * N + 256 + 1);
+    return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + 256 + 1);
 }
 
 size_t mw_smem_bytes(int N, int warps)
 {
-    return sizeof(uint32_t) * (256 + (size_t)warps * 3 * (N + 2) * 32);
+    return sizeof(uint32_t) * 256 * 32 + sizeof(uint16_t) * (size_t)warps * 3 * (N + 2) * 32;
 }
 
-size_t walk_smem_bytes(int N, int max_nc)
+// dynamic shared memory of the walk kernel: the per-lane weight table, then one
+// region shared in turn by the MicroWalk masks, the table fill and the reduction
+size_t walk_scratch_bytes(int N, int max_nc)
 {
-    const size_t masks = sizeof(uint32_t) * (size_t)MW_WARPS * 3 * (N + 2) * 32;
+    const size_t masks = sizeof(uint16_t) * (size_t)MW_WARPS * 3 * (N + 2) * 32;
     const size_t fill = fill_smem_bytes(N);
     const size_t red = sizeof(unsigned long long) * acc_stride_for(max_nc);
     return std::max(masks, std::max(fill, red));
 }
+
+size_t walk_smem_bytes(int N, int max_nc) { return sizeof(uint32_t) * 256 * 32 + walk_scratch_bytes(N, max_nc); }
 
 int walk_pool_slots() { return POOL_MAX; }
 
 template <typename T>
 __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
 {
-    extern __shared__ __align__(16) unsigned char dsm[];
+    extern __shared__ __align__(16) unsigned char dsm_all[];
     __shared__ WalkShared sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int N = E.N, NP2 = N + 2;
+    const int N = E.N;
     const uint32_t P = E.pool;
     const uint32_t base = blockIdx.x * P;
-    for (int i = tid; i < 256; i += WALK_THREADS) sh.W[i] = E.W[i];
+    uint32_t *Wrep = reinterpret_cast<uint32_t *>(dsm_all);
+    unsigned char *dsm = dsm_all + sizeof(uint32_t) * 256 * 32;
+    double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.tc.P;
+    replicate_w(Wrep, E.W);
     for (uint32_t o = tid; o < P; o += WALK_THREADS) {
         const uint32_t s = base + o;
         E.s.state[s] = ST_FRESH;
@@ -1523,7 +1559,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
     for (;;) {
         const long long c0 = clock64();
         if (tid == 0) {
-            sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0;
+            sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0; sh.g_head = 0;
             uint32_t iss = 0;
             for (int j = 0; j < E.n_jobs; j++)
                 if (job_open(E, j)) iss = 1;
@@ -1571,7 +1607,11 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
             __syncthreads();
             const uint32_t ng = sh.g_count;
             const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
-            for (uint32_t i = tid; i < ng; i += WALK_THREADS) {
+            // dynamic distribution: slot steps differ a lot in cost (first transitions,
+            // chains of analytical hops), so threads take the next slot when free
+            for (;;) {
+                const uint32_t i = atomicAdd(&sh.g_head, 1u);
+                if (i >= ng) break;
                 const uint32_t o = sh.glist[i];
                 geo_slot<T>(E, base + o, o, fl, q_now, &sh.q_count, sh.ir);
             }
@@ -1581,8 +1621,9 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
         {
             // ---------------- MicroWalk ----------------
             const int mwarp = warp;
-            uint32_t *Mw = reinterpret_cast<uint32_t *>(dsm) + (size_t)mwarp * 3 * NP2 * 32;
-            const uint32_t *M = Mw + lane;
+            uint16_t *Mw = reinterpret_cast<uint16_t *>(dsm) + (size_t)mwarp * mask_rows(N) * 32;
+            const uint16_t *M = Mw + lane;
+            const uint32_t *Wl = Wrep + lane;
             const uint32_t qn = sh.q_count;
             bool active = false, exhausted = false;
             int x = 0, y = 0, z = 0;
@@ -1609,19 +1650,11 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
                         const uint32_t orr = __shfl_sync(FULL_MASK, oj, r);
                         const MWJob &b = E.mwq[base + orr];
                         const int K = min((int)b.K, KMAX);
-                        for (int row = lane; row < 3 * NP2; row += 32) {
-                            const int a = row / NP2;
-                            const int c = row - a * NP2 - 1;
-                            uint32_t m = 0;
-                            if (c >= 0 && c < N) {
-                                m = 1u;
-                                for (int q = 0; q < K; q++) {
-                                    const uint2 rr = b.rng[q];
-                                    if (rng_lo(rr, a) <= c && c < rng_hi(rr, a)) m |= 2u << q;
-                                }
-                            }
-                            Mw[row * 32 + r] = m;
-                        }
+                        build_masks(Mw, r, N, lane, K, [&](int q, int a, int &lo, int &hi) {
+                            const uint2 rr = b.rng[q];
+                            lo = rng_lo(rr, a);
+                            hi = rng_hi(rr, a);
+                        });
                     }
                     __syncwarp();
                     if (got) {
@@ -1662,7 +1695,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         if (active) {
-                            if (mw_step(M, sh.W, NP2, N, x, y, z, L.mm, words[k])) {
+                            if (mw_step(M, Wl, N, x, y, z, L.mm, words[k])) {
                                 const uint32_t sl2 = L.tag;
                                 E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
                                 E.s.steps[sl2] += t + (uint32_t)k + 1u;
@@ -1708,6 +1741,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
             F.ktot = E.tc.ktot + e;
             F.values = nullptr;
             F.err = &E.status[STAT_ERR];
+            F.V = fill_v;
             fill_table(F, N, E.eps, E.fc, reinterpret_cast<double *>(dsm));
             __syncthreads();
             if (tid == 0) {
@@ -1907,7 +1941,7 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return FRW_EDEVICE;
     L.sms = sms;
-    L.mw_warps = 8;
+    L.mw_warps = 16;
     L.mw_ctas_per_sm = 2;
     L.geom_threads = 128;
     L.fill_ctas = sms;

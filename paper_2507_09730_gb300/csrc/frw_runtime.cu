@@ -62,6 +62,7 @@ struct frw_ctx {
     uint32_t *ctrl = nullptr;                  // device control words
     unsigned long long *cycles = nullptr;      // phase cycle counters
     int grid = 0;                              // walk-kernel CTAs
+    double *fill_scratch = nullptr;            // per CTA table-fill scratch
     RecArrays rec;                      // per-walk records (grown on demand)
     uint64_t rec_cap = 0;
     std::vector<void *> rec_allocs;
@@ -169,6 +170,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.eps = ctx->d_eps;
     E.fc = ctx->fc;
     E.status = ctx->status;
+    E.fill_scratch = ctx->fill_scratch;
     E.ctrl = ctx->ctrl;
     E.cycles = ctx->cycles;
     E.idle_timeout_s = 10.0;
@@ -248,6 +250,8 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     if (opt.precision != FRW_FP64_GEOM && opt.precision != FRW_FP32_GEOM) return FRW_EINVAL;
     if (!(opt.gauss_offset_frac > 0.0 && opt.gauss_offset_frac < 1.0)) return FRW_EINVAL;
     if (opt.max_hops <= 0) return FRW_EINVAL;
+    if (opt.mw_warps_per_cta < 0 || opt.mw_warps_per_cta > 16 || opt.mw_ctas_per_sm < 0 || opt.mw_ctas_per_sm > 32)
+        return FRW_EINVAL;
     frw_ctx *ctx = new frw_ctx();
     ctx->opt = opt;
     ctx->device = device;
@@ -269,7 +273,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     ctx->shape.sms = sms > 0 ? sms : 1;
     ctx->shape.geom_threads = opt.geom_threads > 0 ? opt.geom_threads : 128;
-    ctx->shape.mw_warps = opt.mw_warps_per_cta > 0 ? opt.mw_warps_per_cta : 8;
+    ctx->shape.mw_warps = opt.mw_warps_per_cta > 0 ? opt.mw_warps_per_cta : 16;
     ctx->shape.mw_ctas_per_sm = opt.mw_ctas_per_sm > 0 ? opt.mw_ctas_per_sm : 2;
     ctx->shape.fill_ctas = ctx->shape.sms;
     const int N = opt.N;
@@ -298,7 +302,8 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         (rc = dalloc(ctx, &S.omega, NS, A)) || (rc = dalloc(ctx, &ctx->mwq, NS, A)) ||
         (rc = dalloc(ctx, &ctx->status, STAT_WORDS, A)) ||
         (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)) ||
-        (rc = dalloc(ctx, &ctx->ctrl, CTRL_WORDS, A)) || (rc = dalloc(ctx, &ctx->cycles, 8, A)))
+        (rc = dalloc(ctx, &ctx->ctrl, CTRL_WORDS, A)) || (rc = dalloc(ctx, &ctx->cycles, 8, A)) ||
+        (rc = dalloc(ctx, &ctx->fill_scratch, (size_t)ctx->grid * 6 * N * N, A)))
         return bail(rc);
     TableCache &T = ctx->tc;
     T.cap = cap;
