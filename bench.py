@@ -167,6 +167,18 @@ def run_reference(a):
     return 0
 
 
+# DRAM bytes (read + write) per walk of the walk kernel, from one ncu capture of
+# this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
+# launch started.  None once the kernel has changed since the capture.
+DRAM_BYTES_PER_WALK = 3876.0
+
+
+def traffic_per_launch(agg, n_launch):
+    if DRAM_BYTES_PER_WALK is None:
+        return None
+    return DRAM_BYTES_PER_WALK * agg["issued"] / n_launch
+
+
 def structure_bytes(s):
     return (s.cond_lo.nbytes + s.cond_hi.nbytes + s.block_lo.nbytes + s.block_hi.nbytes + s.block_mat.nbytes +
             s.eps.nbytes + 48 + 40 * len(s.masters))
@@ -210,14 +222,15 @@ def main():
     clk = ClockSampler(local)
     clk.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    agg = dict(walks=0, micro=0, mw_ms=0.0, geom_ms=0.0, fill_ms=0.0, launches=0, hops=0, mw_hops=0, strat=0,
-               hom=0, rounds=0, tables=0, mw_jobs=0)
+    agg = dict(walks=0, micro=0, mw_ms=0.0, geom_ms=0.0, fill_ms=0.0, kernel_ms=0.0, launches=0, hops=0, mw_hops=0,
+               strat=0, hom=0, rounds=0, tables=0, mw_jobs=0, walk_launches=0, issued=0)
     rows = None
     ev0.record(stream)
     for k in range(a.steps):
         res, conv = ctx.extract_batch(jobs_for(k))
         for C, se, st in res:
             agg["walks"] += st["walks"]
+            agg["issued"] += st["walks_issued"]
             agg["micro"] += st["micro_steps"]
             agg["hops"] += st["hops"]
             agg["mw_hops"] += st["mw_hops"]
@@ -227,6 +240,8 @@ def main():
         agg["mw_ms"] += st0["mw_ms"]
         agg["geom_ms"] += st0["geom_ms"]
         agg["fill_ms"] += st0["fill_ms"]
+        agg["kernel_ms"] += st0["kernel_ms"]
+        agg["walk_launches"] += st0["launches"]
         agg["launches"] += st0["launches"] + 1     # + the L2 flush
         agg["rounds"] += st0["rounds"]
         agg["tables"] += st0["tables_built"]
@@ -275,13 +290,24 @@ def main():
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12          # Tint-op/s: 128 INT32 lanes per SM at max clock
+    # dominant kernel: the persistent walk kernel (one launch per step); algorithmic work =
+    # the MicroWalk lattice steps it ran x INT_OPS_PER_MICRO_STEP, over its event-timed duration
+    k_s = agg["kernel_ms"] / 1e3
+    ops = INT_OPS_PER_MICRO_STEP * agg["micro"]
+    achieved = ops / k_s / 1e12 if k_s > 0 else None
     mw_s = agg["mw_ms"] / 1e3
-    achieved = (INT_OPS_PER_MICRO_STEP * agg["micro"] / mw_s) / 1e12 if mw_s > 0 else None
-    roofline = {"kernel": "k_mw (MicroWalk)", "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "Tint-op/s", "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
-                "peak_source": f"{n_sm} SMs x 128 INT32 lanes x {sm_max:.0f} MHz ({src} clock)",
-                "kernel_share": {"mw": agg["mw_ms"] / (1e3 * elapsed), "geom": agg["geom_ms"] / (1e3 * elapsed),
-                                 "fill": agg["fill_ms"] / (1e3 * elapsed)}}
+    mw_ach = ops / mw_s / 1e12 if mw_s > 0 else None
+    n_l = max(1, agg["walk_launches"])
+    roofline = {"kernel": "k_walk (persistent: geometry, table fill, reduction, MicroWalk)", "bound": "alu",
+                "achieved": achieved, "peak": alu_peak, "unit": "Tint-op/s",
+                "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic_per_launch(agg, n_l),
+                "peak_source": f"{n_sm} SMs x 128 INT32 lanes x {sm_max:.0f} MHz ({src} max clock)",
+                "launch_ms": agg["kernel_ms"] / n_l, "walks_per_launch": agg["walks"] / n_l,
+                "micro_steps_per_launch": agg["micro"] / n_l,
+                "phase_share": {"mw": agg["mw_ms"] / max(1e-9, agg["kernel_ms"]),
+                                "geom": agg["geom_ms"] / max(1e-9, agg["kernel_ms"]),
+                                "fill": agg["fill_ms"] / max(1e-9, agg["kernel_ms"])},
+                "mw_phase": {"achieved": mw_ach, "frac": (mw_ach / alu_peak) if mw_ach else None}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * t_all / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",

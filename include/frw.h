@@ -112,14 +112,16 @@ typedef struct {
     uint64_t hom_hops;         /* ... homogeneous cube */
     uint64_t mw_hops;          /* later hops through MicroWalk */
     uint64_t tables_built;     /* analytical tables filled on the device during the call */
-    uint64_t rounds;           /* engine rounds (geometry + fill + MicroWalk launches) */
+    uint64_t rounds;           /* epochs of the persistent walk kernel (largest over its CTAs) */
     double seconds;            /* wall time of the call */
-    double geom_ms;            /* device time of the geometry kernel (CUDA events, launch stream) */
-    double fill_ms;            /* ... of the table-fill kernel */
-    double mw_ms;              /* ... of the MicroWalk kernel */
-    uint64_t launches;         /* kernels launched by the call */
-    uint64_t mw_jobs;          /* MicroWalk transitions run by the MicroWalk kernel */
+    double geom_ms;            /* walk-kernel time in its geometry phase: kernel_ms x that phase's
+                                  share of the CTAs' busy cycles */
+    double fill_ms;            /* ... in its table-fill and batch-reduction phases */
+    double mw_ms;              /* ... in its MicroWalk phase */
+    uint64_t launches;         /* kernels launched by the call (memsets not counted) */
+    uint64_t mw_jobs;          /* MicroWalk transitions */
     uint64_t walks_issued;     /* walk ids started (>= walks: a sigma-target run stops mid-flight) */
+    double kernel_ms;          /* device time of the walk kernel (CUDA events on the launch stream) */
 } frw_stats;
 
 /* Fill *opt with defaults (N = 24, FP64 geometry, hybrid on, offset 0.5,

@@ -25,6 +25,11 @@ namespace cg = cooperative_groups;
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 Philox bijection,
 // multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+// Functions that run once per walk, per batch or per epoch, or that would be
+// inlined in several places, stay out of line: the persistent walk kernel's hot
+// loops then fit the instruction cache.
+#define FRW_OUTLINE __noinline__
+
 __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                           uint32_t k0, uint32_t k1)
 {
@@ -130,7 +135,7 @@ template <typename T> __device__ __forceinline__ int cell_of(T x, T org, T inv, 
 // cell of p lists, in ascending order, every conductor that can be nearest (or
 // tie) anywhere in the cell, so the result equals the scan over all conductors.
 template <typename T>
-__device__ T nearest_electrode(const SView<T> &S, const T p[3], int &who)
+__device__ FRW_OUTLINE T nearest_electrode(const SView<T> &S, const T p[3], int &who)
 {
     typedef Ar<T> A;
     T best = A::inf();
@@ -199,7 +204,7 @@ __device__ __forceinline__ int rng_mat(const uint2 r) { return (int)((r.y >> 16)
 // centre inside), list reset by a block covering every voxel, and the class:
 // homogeneous, layered along one axis, non-stratified, or too many blocks.
 template <typename T>
-__device__ void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeInfo &q)
+__device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeInfo &q)
 {
     typedef Ar<T> A;
     const T h = A::div(A::mul(T(2), R), T(N));
@@ -300,7 +305,7 @@ __device__ void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeI
 
 // Volume-mean permittivity of the cube's lattice: constant-mask runs per axis,
 // material of each run triple by the last listed block containing it.
-__device__ double mean_eps(const CubeInfo &q, int N, const double *eps)
+__device__ FRW_OUTLINE double mean_eps(const CubeInfo &q, int N, const double *eps)
 {
     int cut[3][2 * KMAX + 2];
     int ncut[3];
@@ -470,7 +475,7 @@ struct WalkState {
 // A finished walk writes its record (electrode k last, with release order) and
 // counts itself in its batch; the group of lanes that completes a batch queues
 // it for reduction.
-__device__ void finish_walk(const EngineView &E, const DevJob &J, const WalkState &w, int k)
+__device__ FRW_OUTLINE void finish_walk(const EngineView &E, const DevJob &J, const WalkState &w, int k)
 {
     const uint64_t rel = w.walk - J.walk_begin;
     const uint64_t r = J.rec_base + rel;
@@ -500,7 +505,7 @@ __device__ void finish_walk(const EngineView &E, const DevJob &J, const WalkStat
 // special treatment, weight omega (Algorithm 1; flux reading of FirstTransition).
 // Returns false when a table is not ready yet (retry next round, same draws).
 template <typename T>
-__device__ bool first_transition(const EngineView &E, const DevJob &J, const SView<T> &S, WalkState &w,
+__device__ FRW_OUTLINE bool first_transition(const EngineView &E, const DevJob &J, const SView<T> &S, WalkState &w,
                                  T pos[3], const FillList &fl)
 {
     typedef Ar<T> A;
@@ -643,7 +648,7 @@ struct IssueRanges {
 };
 
 // thread 0: claim up to `want` ids over the open jobs, starting at job `first`
-__device__ void claim_ids(const EngineView &E, IssueRanges &ir, uint32_t want, uint32_t first)
+__device__ FRW_OUTLINE void claim_ids(const EngineView &E, IssueRanges &ir, uint32_t want, uint32_t first)
 {
     ir.n = 0;
     ir.pos = 0;
@@ -670,7 +675,7 @@ __device__ void claim_ids(const EngineView &E, IssueRanges &ir, uint32_t want, u
 }
 
 // a free slot takes the next claimed id (false when the CTA's ranges are used up)
-__device__ bool issue_walk(const EngineView &E, IssueRanges &ir, WalkState &w)
+__device__ FRW_OUTLINE bool issue_walk(const EngineView &E, IssueRanges &ir, WalkState &w)
 {
     const uint32_t i = atomicAdd(&ir.pos, 1u);
     if (i >= ir.total) return false;
@@ -828,7 +833,6 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
 // for every listed block whose range on axis a contains c; rows c = -1 and c = N
 // are 0 (boundary).  The material of node (x, y, z) is given by the highest set
 // bit of mask(0,x) & mask(1,y) & mask(2,z) through a 16-entry nibble map.
-// Layout [row][lane] keeps every lane in its own bank.
 
 __device__ __forceinline__ int mat_of(uint64_t mm, uint32_t mask)
 {
@@ -1052,7 +1056,7 @@ struct FillJob {
     uint32_t *err;
 };
 
-__device__ void fill_table(const FillJob &F, int N, const double *__restrict__ eps, const FillConsts &C,
+__device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__restrict__ eps, const FillConsts &C,
                            double *sm)
 {
     const int H = N / 2, M = H * H, P = 6 * N * N;
@@ -1269,7 +1273,7 @@ __device__ __forceinline__ void to_fixed128(double v, double scale, unsigned lon
 
 // CTA-cooperative reduction of one complete batch g into its accumulator block;
 // sets batch_ready[g] (release) once the block is written.
-__device__ void reduce_batch(const EngineView &E, uint32_t g, unsigned long long *acc_sm)
+__device__ FRW_OUTLINE void reduce_batch(const EngineView &E, uint32_t g, unsigned long long *acc_sm)
 {
     int j = 0;
     for (; j < E.n_jobs; j++) {
@@ -1388,7 +1392,7 @@ __device__ void rel_errors_dev(const unsigned long long *sum, int nc, int master
 // per job, bounded work), apply the stop rule, and steer the job's issue limit to
 // the predicted need (n (r / target)^2 with margin) so the pool does not run far
 // past the stopping point.
-__device__ void advance_sigma_jobs(const EngineView &E)
+__device__ FRW_OUTLINE void advance_sigma_jobs(const EngineView &E)
 {
     for (int j = 0; j < E.n_jobs; j++) {
         const DevJob &J = E.jobs[j];
@@ -1439,7 +1443,7 @@ __device__ void advance_sigma_jobs(const EngineView &E)
                 rel_errors_dev(sum, J.n_c, J.master, n, &rs, &rc);
                 const double r = fmax(rs, rc) / J.sigma;
                 double need = isfinite(r) ? n * r * r : (double)J.walk_count;
-                need = fmin(need * 1.15 + 2.0 * (double)J.batch, (double)J.walk_count);
+                need = fmin(need * 1.05 + 2.0 * (double)J.batch, (double)J.walk_count);
                 lim = ((unsigned long long)need + J.batch - 1) / J.batch * J.batch;
             }
             lim = max(lim, (unsigned long long)((prefix + 1) * J.batch));
@@ -1454,7 +1458,7 @@ __device__ void advance_sigma_jobs(const EngineView &E)
 
 // Take one completed batch from the reduction queue (compare-and-swap on the
 // head; an entry is taken only once its index has been written).
-__device__ uint32_t take_batch(const EngineView &E)
+__device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 {
     for (int tries = 0; tries < 64; tries++) {
         const uint32_t h = *(volatile uint32_t *)E.rq_head;

@@ -990,6 +990,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             s.launches = 1;
             s.mw_jobs = j.ex[5];
             s.walks_issued = issued[i];
+            s.kernel_ms = kms;
         }
     }
     cleanup();
