@@ -118,23 +118,42 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def cpu_baseline(s, masters, N, seconds):
-    """The oracle as it stands, single-threaded, on a bounded sample of the same
-    workload (walks of the first master until `seconds` of CPU time)."""
+def oracle_walks(s, masters, N, seconds, threads, base_request, chunk=200, chunks=None):
+    """Run the oracle as it stands on `threads` host threads, for about `seconds`
+    or for exactly `chunks` chunks per thread: thread t takes chunks of `chunk`
+    walks from its own walk-id range (ids t * 10^9 + ...), masters in turn.
+    ctypes releases the GIL during each oracle call, so the threads run in
+    parallel.  Returns (walks, seconds)."""
+    import concurrent.futures as cf
     from oracle import oracle as O
     O.build()
+
+    def worker(t, t0):
+        walks, i = 0, 0
+        while (i < chunks) if chunks is not None else (time.perf_counter() - t0 < seconds):
+            O.frw_run(s, masters[i % len(masters)], chunk, N=N, seed=0, request=base_request,
+                      walk_begin=t * 10**9 + i * chunk, records=False)
+            walks += chunk
+            i += 1
+        return walks
+
     t0 = time.perf_counter()
-    walks = 0
-    chunk = 200
-    i = 0
-    while time.perf_counter() - t0 < seconds:
-        O.frw_run(s, masters[i % len(masters)], chunk, N=N, seed=0, request=900 + i, records=False)
-        walks += chunk
-        i += 1
-    dt = time.perf_counter() - t0
-    return {"value": walks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{walks} walks ({i} chunks of {chunk}, masters {list(masters)}) of the same interconnect "
-                      f"structure at N={N}, FP64, single thread, {dt:.1f} s"}
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        total = sum(ex.map(worker, range(threads), [t0] * threads))
+    return total, time.perf_counter() - t0
+
+
+def cpu_baseline(s, masters, N, seconds):
+    """The oracle as it stands on a bounded sample of the same workload: first one
+    thread, then every host core over disjoint walk-id ranges."""
+    cores = os.cpu_count() or 1
+    w1, t1 = oracle_walks(s, masters, N, seconds / 3, 1, 900)
+    wn, tn = oracle_walks(s, masters, N, 2 * seconds / 3, cores, 901)
+    return {"value": wn / tn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": w1 / t1,
+            "sample": f"{wn} walks on {cores} threads in {tn:.1f} s (chunks of 200 walks, disjoint walk-id ranges, "
+                      f"masters {list(masters)}) of the same interconnect structure at N={N}, FP64; "
+                      f"single thread: {w1} walks in {t1:.1f} s"}
 
 
 def run_reference(a):
@@ -145,38 +164,29 @@ def run_reference(a):
     masters = list(s.masters)
     from oracle import oracle as O
     O.build()
-    per_step = 100
+    cores = os.cpu_count() or 1
+    per_thread = 200     # one step: one chunk of 200 walks per host thread (a few seconds)
     for w in range(a.warmup):
-        O.frw_run(s, masters[w % 3], 20, N=a.N, seed=0, request=500 + w, records=False)
+        oracle_walks(s, masters, a.N, None, cores, 500 + w, chunk=20, chunks=1)
     t0 = time.perf_counter()
     walks = 0
     for k in range(a.steps):
-        O.frw_run(s, masters[k % 3], per_step, N=a.N, seed=0, request=600 + k, records=False)
-        walks += per_step
+        n, _ = oracle_walks(s, masters, a.N, None, cores, 600 + k, chunk=per_thread, chunks=1)
+        walks += n
     dt = time.perf_counter() - t0
     v = walks / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"interconnect 3-layer/24-wire, N={a.N}, {per_step} walks per step (bounded sample)",
+            "config": {"workload": f"interconnect 3-layer/24-wire + shells + 12 LDE, N={a.N}, masters {masters}; "
+                                   f"bounded sample: {per_thread} walks per host thread per step",
                        "precision": "fp64"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{walks} walks in {a.steps} steps of {per_step}"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{walks} walks in {a.steps} steps on {cores} threads "
+                                       f"({per_thread} walks per thread per step, disjoint walk-id ranges)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-# DRAM bytes (read + write) per walk of the walk kernel, from one ncu capture of
-# this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
-# launch started.  None once the kernel has changed since the capture.
-DRAM_BYTES_PER_WALK = 3876.0
-
-
-def traffic_per_launch(agg, n_launch):
-    if DRAM_BYTES_PER_WALK is None:
-        return None
-    return DRAM_BYTES_PER_WALK * agg["issued"] / n_launch
 
 
 def structure_bytes(s):
