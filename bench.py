@@ -165,7 +165,8 @@ def run_reference(a):
     from oracle import oracle as O
     O.build()
     cores = os.cpu_count() or 1
-    per_thread = 200     # one step: one chunk of 200 walks per host thread (a few seconds)
+    # one step: one chunk of walks per host thread (200: a few seconds)
+    per_thread = int(os.environ.get("FRW_BENCH_REF_WALKS", "200"))
     for w in range(a.warmup):
         oracle_walks(s, masters, a.N, None, cores, 500 + w, chunk=20, chunks=1)
     t0 = time.perf_counter()
@@ -187,6 +188,18 @@ def run_reference(a):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# DRAM bytes (read + write) per walk of the walk kernel, from one ncu capture of
+# this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
+# launch started.  None once the kernel has changed since the capture.
+DRAM_BYTES_PER_WALK = None
+
+
+def traffic_per_launch(agg, n_launch):
+    if DRAM_BYTES_PER_WALK is None:
+        return None
+    return DRAM_BYTES_PER_WALK * agg["issued"] / n_launch
 
 
 def structure_bytes(s):

@@ -89,7 +89,10 @@ typedef struct {
     int32_t mw_warps_per_cta;  /* stand-alone MicroWalk kernel: warps per CTA, 1..16 (0: 16) */
     int32_t mw_ctas_per_sm;    /* stand-alone MicroWalk kernel: CTAs per SM, 1..32 (0: 2) */
     int32_t geom_threads;      /* ignored (kept for layout) */
-    int32_t reserved[6];
+    int32_t serve_jobs;        /* serving: job-table entries of one run (0: 4096) */
+    int32_t serve_arena_mb;    /* serving: MB of per-walk records of one run, 32 B per walk of
+                                  budget; also sizes its batch arenas (0: 4096) */
+    int32_t reserved[4];
 } frw_options;
 
 /* One extraction: a row of the capacitance matrix for one master conductor. */
@@ -172,6 +175,34 @@ typedef struct {
 
 int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs, double *C_rows,
                       double *stderr_rows, frw_stats *stats);
+
+/* Serving (the paper has no counterpart: a deployment form of Algorithm 1's
+ * extraction).  frw_submit queues one extraction and returns at once with a
+ * ticket; a scheduler thread of the context admits queued requests, in arrival
+ * order, into the running persistent walk kernel whenever the run's job table and
+ * arenas have room for the request's walk budget (admission by memory: 32 B of
+ * records per walk of budget plus its batch accumulators).  Admitted requests'
+ * walks interleave on the device with those of earlier requests, and each request
+ * completes as soon as its own stop rule holds.  A request that can never fit the
+ * serving arena (options serve_arena_mb / serve_jobs) completes with FRW_ENOMEM.
+ * Results are identical to frw_extract of the same job (same seed and request_id),
+ * whatever else is running.  frw_submit, frw_poll and frw_wait may be called from
+ * any host thread.  While a serving run is on the device, frw_extract*,
+ * frw_walk_records and frw_unload_structure wait for it to end (it ends after
+ * 0.5 s without requests).
+ *   frw_submit: job as in frw_extract_batch; *ticket receives the request's id.
+ *   frw_poll:   *done = 1 once the request has completed (FRW_ENOTFOUND for an
+ *               unknown or already collected ticket).
+ *   frw_wait:   blocks until completion (timeout_s < 0: no limit; FRW_ETIMEOUT if
+ *               the limit passes first, the ticket stays valid), then fills C_row /
+ *               stderr_row (n_cond + 1 doubles each, host) and stats (may be NULL;
+ *               stats->seconds = time from submission to completion) and releases
+ *               the ticket.  Returns the request's status (FRW_OK, FRW_ENOTCONV with
+ *               results filled, or an error). */
+int frw_submit(frw_ctx *ctx, const frw_job *job, uint64_t *ticket);
+int frw_poll(frw_ctx *ctx, uint64_t ticket, int32_t *done);
+int frw_wait(frw_ctx *ctx, uint64_t ticket, double timeout_s, double *C_row, double *stderr_row,
+             frw_stats *stats);
 
 /* Per-walk records of walks walk_begin .. walk_begin + n_walks - 1 (host arrays of
  * n_walks entries each; any may be NULL): weight omega, electrode reached

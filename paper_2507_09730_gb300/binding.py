@@ -20,7 +20,8 @@ FRW_TAB_SGF, FRW_TAB_FLUX_PAR, FRW_TAB_FLUX_PERP, FRW_TAB_SGF_HOM, FRW_TAB_FLUX_
 
 EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream", "frw_load_structure",
            "frw_unload_structure", "frw_extract", "frw_extract_batch", "frw_walk_records",
-           "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error")
+           "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
+           "frw_submit", "frw_poll", "frw_wait")
 
 
 class frw_box(ctypes.Structure):
@@ -35,7 +36,8 @@ class frw_options(ctypes.Structure):
     _fields_ = [("N", c_int32), ("precision", c_int32), ("seed", c_uint64), ("first_cube_mode", c_int32),
                 ("hybrid", c_int32), ("gauss_offset_frac", c_double), ("max_hops", c_int32),
                 ("slots", c_int32), ("table_capacity", c_int32), ("mw_warps_per_cta", c_int32),
-                ("mw_ctas_per_sm", c_int32), ("geom_threads", c_int32), ("reserved", c_int32 * 6)]
+                ("mw_ctas_per_sm", c_int32), ("geom_threads", c_int32), ("serve_jobs", c_int32),
+                ("serve_arena_mb", c_int32), ("reserved", c_int32 * 4)]
 
 
 class frw_extract_params(ctypes.Structure):
@@ -98,6 +100,9 @@ def lib():
                                               c_uint64, c_void_p, c_void_p, c_void_p]
     L.frw_table.argtypes = [c_void_p, c_int32, P(c_int32), P(c_double), c_int32, P(c_uint32), P(c_uint8),
                             P(c_double), P(c_double)]
+    L.frw_submit.argtypes = [c_void_p, POINTER(frw_job), POINTER(c_uint64)]
+    L.frw_poll.argtypes = [c_void_p, c_uint64, POINTER(c_int32)]
+    L.frw_wait.argtypes = [c_void_p, c_uint64, c_double, P(c_double), P(c_double), POINTER(frw_stats)]
     L.frw_strerror.argtypes = [c_int]
     L.frw_strerror.restype = ctypes.c_char_p
     L.frw_last_error.argtypes = [c_void_p]
@@ -210,6 +215,33 @@ def frw_extract_batch(ctx, jobs, n_conds):
     return out, rc == FRW_OK
 
 
+def frw_submit(ctx, job) -> int:
+    """Queue one extraction (dict as in frw_extract_batch); returns its ticket."""
+    j = frw_job(int(job["structure_id"]), int(job["master"]), int(job["walk_budget"]),
+                float(job.get("sigma_target", 0.0)), int(job.get("request_id", 0)), int(job.get("batch", 0)))
+    t = c_uint64(0)
+    _check(ctx, lib().frw_submit(ctx, ctypes.byref(j), ctypes.byref(t)))
+    return int(t.value)
+
+
+def frw_poll(ctx, ticket: int) -> bool:
+    d = c_int32(0)
+    _check(ctx, lib().frw_poll(ctx, int(ticket), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def frw_wait(ctx, ticket: int, n_cond: int, timeout_s: float = -1.0):
+    """-> (C, stderr, stats, converged), or None if timeout_s passed first."""
+    C = np.zeros(n_cond + 1)
+    se = np.zeros(n_cond + 1)
+    st = frw_stats()
+    rc = lib().frw_wait(ctx, int(ticket), float(timeout_s), _ptr(C, c_double), _ptr(se, c_double), ctypes.byref(st))
+    if rc == FRW_ETIMEOUT:
+        return None
+    _check(ctx, rc, (FRW_OK, FRW_ENOTCONV))
+    return C, se, st.as_dict(), rc == FRW_OK
+
+
 def frw_walk_records(ctx, sid: int, master: int, request_id: int, walk_begin: int, n_walks: int):
     n = int(n_walks)
     om = np.zeros(n)
@@ -283,6 +315,7 @@ class Context:
         self.N = self.options.N
         self.ctx = frw_create(device, self.options)
         self._n_cond = {}
+        self._tickets = {}
 
     def close(self):
         if self.ctx:
@@ -316,6 +349,20 @@ class Context:
 
     def extract_batch(self, jobs):
         return frw_extract_batch(self.ctx, jobs, [self._n_cond.get(j["structure_id"], 0) for j in jobs])
+
+    def submit(self, job) -> int:
+        t = frw_submit(self.ctx, job)
+        self._tickets[t] = self._n_cond.get(job["structure_id"], 0)
+        return t
+
+    def poll(self, ticket) -> bool:
+        return frw_poll(self.ctx, ticket)
+
+    def wait(self, ticket, timeout_s=-1.0):
+        r = frw_wait(self.ctx, ticket, self._tickets[ticket], timeout_s)
+        if r is not None:
+            self._tickets.pop(ticket, None)
+        return r
 
     def walk_records(self, sid, master, n_walks, request_id=0, walk_begin=0):
         return frw_walk_records(self.ctx, sid, master, request_id, walk_begin, n_walks)

@@ -73,7 +73,9 @@ struct DevStructure {
 };
 
 // One extraction job (request x master).
-struct DevJob {
+// 256-byte aligned: the host publishes jobs into a running kernel, and no cache
+// line of a job may be shared with another job's.
+struct alignas(256) DevJob {
     int sid;               // index into the structure table
     int master;
     int n_c;
@@ -93,12 +95,24 @@ struct DevJob {
     double sigma;          // relative standard-error target (0: budget only)
 };
 
-// Device-side state of a job's stop rule (followed in walk-id order).
+// Device-side state of a job (followed in walk-id order): its completed batches
+// are folded, in order, into its running sums; the job is decided when its stop
+// rule holds or its budget is used up.
 struct JobState {
     unsigned long long prefix;     // complete batches folded so far
     unsigned long long used;       // walks in the estimate once decided
     uint32_t decided;              // 1: converged, 2: budget exhausted
-    uint32_t lock;
+    uint32_t lock;                 // held by the thread folding batches
+    uint32_t pending;              // set by a thread that found the lock held
+    uint32_t pad;
+};
+
+// job-table control words (device memory)
+enum {
+    JC_PUBLISHED = 0,   // jobs 0 .. published-1 are visible to the kernel (host-written)
+    JC_DECIDED = 1,     // number of decided jobs (device counter)
+    JC_LOW = 2,         // every job below this index is decided (device, monotone)
+    JC_WORDS = 4
 };
 
 // per-batch accumulator block (u64 words):
@@ -167,8 +181,8 @@ struct EngineView {
     int fp32;
     uint32_t NS;           // slots = grid x pool
     uint32_t pool;         // slots per CTA of the walk kernel (multiple of its block size)
-    int n_jobs;
-    int max_nc;            // largest conductor count over the jobs (reduction scratch)
+    int n_jobs;            // job-table capacity
+    int max_nc;            // largest conductor count a job of this run may have (reduction scratch)
     SlotArrays s;
     const DevStructure *structs;
     const DevJob *jobs;
@@ -176,6 +190,8 @@ struct EngineView {
     unsigned long long *job_limit;   // issue limit per job (<= walk_count), written by the host
     int *job_cancel;                 // set when the stop rule holds (or by the host)
     JobState *jstate;                // per job
+    uint32_t *jctl;                  // JC_WORDS job-table control words
+    uint32_t *batch_job;             // job of each batch
     unsigned long long *jsum;        // per job: running prefix sums, acc_stride words each
     unsigned long long *jsum_off;    // per job: offset of its running sums
     unsigned long long *acc;         // batch accumulator blocks

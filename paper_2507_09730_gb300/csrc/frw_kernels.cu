@@ -635,9 +635,11 @@ __device__ __forceinline__ bool job_open(const EngineView &E, int j)
 
 // Walk ids are claimed per CTA, once per epoch, for exactly the number of free
 // slots (one compare-and-swap per job on the job's counter, which therefore never
-// passes the issue limit the host may move while the kernel runs); free slots then
-// take ids from the CTA's claimed ranges through a shared-memory counter.
+// passes the issue limit the stop rule may move while the kernel runs); free slots
+// then take ids from the CTA's claimed ranges through a shared-memory counter.
+// Jobs are served oldest first: the scan starts at the lowest undecided job.
 constexpr int ISSUE_MAX_JOBS = 64;     // claimed ranges per CTA and epoch
+constexpr uint32_t JOB_WINDOW = 256;   // jobs a CTA looks at per epoch
 struct IssueRanges {
     uint32_t n;                        // number of ranges
     uint32_t pos;                      // next id to hand out (over the concatenated ranges)
@@ -647,31 +649,75 @@ struct IssueRanges {
     uint32_t cnt[ISSUE_MAX_JOBS];
 };
 
-// thread 0: claim up to `want` ids over the open jobs, starting at job `first`
-__device__ FRW_OUTLINE void claim_ids(const EngineView &E, IssueRanges &ir, uint32_t want, uint32_t first)
+// one warp: claim up to `want` ids over the open jobs among [lo, pub)
+__device__ FRW_OUTLINE void claim_ids(const EngineView &E, IssueRanges &ir, uint32_t want, uint32_t lo, uint32_t pub)
 {
-    ir.n = 0;
-    ir.pos = 0;
-    ir.total = 0;
-    if (want == 0 || E.n_jobs == 0) return;
-    for (int t = 0; t < E.n_jobs && ir.total < want && ir.n < ISSUE_MAX_JOBS; t++) {
-        const uint32_t jj = (first + (uint32_t)t) % (uint32_t)E.n_jobs;
-        if (((volatile int *)E.job_cancel)[jj]) continue;
-        const unsigned long long lim = ((volatile unsigned long long *)E.job_limit)[jj];
-        for (int tries = 0; tries < 64; tries++) {
-            const unsigned long long c = ((volatile unsigned long long *)E.job_next)[jj];
-            if (c >= lim) break;
-            const unsigned long long take = min((unsigned long long)(want - ir.total), lim - c);
-            if (atomicCAS(&E.job_next[jj], c, c + take) == c) {
-                ir.job[ir.n] = jj;
-                ir.lo[ir.n] = c;
-                ir.cnt[ir.n] = (uint32_t)take;
-                ir.n++;
-                ir.total += (uint32_t)take;
-                break;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        ir.n = 0;
+        ir.pos = 0;
+        ir.total = 0;
+    }
+    __syncwarp();
+    if (want == 0 || pub <= lo) return;
+    const uint32_t span = min(pub - lo, JOB_WINDOW);
+    for (uint32_t c = 0; c < span; c += 32) {
+        const uint32_t jj = lo + c + (uint32_t)lane;
+        const bool open = c + (uint32_t)lane < span && job_open(E, (int)jj);
+        uint32_t bal = __ballot_sync(FULL_MASK, open);
+        if (lane == 0) {
+            while (bal && ir.total < want && ir.n < ISSUE_MAX_JOBS) {
+                const uint32_t j = lo + c + (uint32_t)(__ffs(bal) - 1);
+                bal &= bal - 1u;
+                const unsigned long long lim = ((volatile unsigned long long *)E.job_limit)[j];
+                for (int tries = 0; tries < 64; tries++) {
+                    const unsigned long long cur = ((volatile unsigned long long *)E.job_next)[j];
+                    if (cur >= lim) break;
+                    const unsigned long long take = min((unsigned long long)(want - ir.total), lim - cur);
+                    if (atomicCAS(&E.job_next[j], cur, cur + take) == cur) {
+                        ir.job[ir.n] = j;
+                        ir.lo[ir.n] = cur;
+                        ir.cnt[ir.n] = (uint32_t)take;
+                        ir.n++;
+                        ir.total += (uint32_t)take;
+                        break;
+                    }
+                }
             }
         }
+        const uint32_t done = __shfl_sync(FULL_MASK, lane == 0 ? (uint32_t)(ir.total >= want || ir.n >= ISSUE_MAX_JOBS) : 0u, 0);
+        if (done) break;
     }
+    __syncwarp();
+}
+
+// one warp, at the start of an epoch: move the job table's low-water mark past the
+// leading decided jobs and tell whether any job in the window can take new walks
+__device__ FRW_OUTLINE void scan_jobs(const EngineView &E, uint32_t &lo_out, uint32_t &pub_out, uint32_t &open_out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t pub = *(volatile uint32_t *)&E.jctl[JC_PUBLISHED];
+    const uint32_t lo0 = *(volatile uint32_t *)&E.jctl[JC_LOW];
+    __threadfence();   // jobs below `pub` were written before it (host copies in stream order)
+    uint32_t lo = lo0;
+    for (int k = 0; k < 8 && lo < pub; k++) {
+        const uint32_t j = lo + (uint32_t)lane;
+        const bool dec = j < pub && *(volatile uint32_t *)&E.jstate[j].decided != 0u;
+        const uint32_t bal = __ballot_sync(FULL_MASK, dec);
+        const uint32_t lead = (bal == FULL_MASK) ? 32u : (uint32_t)(__ffs(~bal) - 1);
+        lo += lead;
+        if (lead < 32u) break;
+    }
+    if (lane == 0 && lo > lo0) atomicMax(&E.jctl[JC_LOW], lo);
+    uint32_t open = 0;
+    const uint32_t span = pub > lo ? min(pub - lo, JOB_WINDOW) : 0u;
+    for (uint32_t c = 0; c < span && !open; c += 32) {
+        const uint32_t jj = lo + c + (uint32_t)lane;
+        open = __ballot_sync(FULL_MASK, c + (uint32_t)lane < span && job_open(E, (int)jj)) != 0u;
+    }
+    lo_out = lo;
+    pub_out = pub;
+    open_out = open;
 }
 
 // a free slot takes the next claimed id (false when the CTA's ranges are used up)
@@ -1275,14 +1321,7 @@ __device__ __forceinline__ void to_fixed128(double v, double scale, unsigned lon
 // sets batch_ready[g] (release) once the block is written.
 __device__ FRW_OUTLINE void reduce_batch(const EngineView &E, uint32_t g, unsigned long long *acc_sm)
 {
-    int j = 0;
-    for (; j < E.n_jobs; j++) {
-        const DevJob &Jc = E.jobs[j];
-        const uint64_t nb = (Jc.walk_count + Jc.batch - 1) / Jc.batch;
-        if (g >= Jc.batch_base && g < Jc.batch_base + nb) break;
-    }
-    if (j == E.n_jobs) return;
-    const DevJob &J = E.jobs[j];
+    const DevJob &J = E.jobs[__ldcg(E.batch_job + g)];
     const int nc1 = J.n_c + 1;
     const uint32_t words = J.acc_stride;
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) acc_sm[i] = 0ull;
@@ -1388,71 +1427,97 @@ __device__ void rel_errors_dev(const unsigned long long *sum, int nc, int master
     }
 }
 
-// One thread: advance the completed prefix of every undecided sigma job (try-lock
-// per job, bounded work), apply the stop rule, and steer the job's issue limit to
-// the predicted need (n (r / target)^2 with margin) so the pool does not run far
-// past the stopping point.
-__device__ FRW_OUTLINE void advance_sigma_jobs(const EngineView &E)
+// Fold the completed prefix of job j's batches, in walk-id order, into its running
+// sums; decide the job when its stop rule holds (sigma jobs, checked at every full
+// batch) or its budget is used up; steer a sigma job's issue limit to the
+// predicted need (n (r / target)^2 + 5 % + 2 batches) so that the pool does not run
+// far past the stopping point.  Caller holds the job's lock.
+__device__ void advance_locked(const EngineView &E, uint32_t j, JobState &S)
 {
-    for (int j = 0; j < E.n_jobs; j++) {
-        const DevJob &J = E.jobs[j];
-        if (!(J.sigma > 0.0)) continue;
-        JobState &S = E.jstate[j];
-        if (*(volatile uint32_t *)&S.decided) continue;
-        if (atomicCAS(&S.lock, 0u, 1u) != 0u) continue;
-        __threadfence();
-        unsigned long long *sum = E.jsum + E.jsum_off[j];
-        const int nc1 = J.n_c + 1;
-        const uint64_t nb = (J.walk_count + J.batch - 1) / J.batch;
-        unsigned long long prefix = *(volatile unsigned long long *)&S.prefix;
-        bool changed = false;
-        uint32_t decided = 0;
-        for (int it = 0; it < 64; it++) {
-            if (prefix >= nb) {
-                decided = 2;
+    const DevJob &J = E.jobs[j];
+    unsigned long long *sum = E.jsum + __ldcg(E.jsum_off + j);
+    const int nc1 = J.n_c + 1;
+    const uint64_t nb = (J.walk_count + J.batch - 1) / J.batch;
+    unsigned long long prefix = *(volatile unsigned long long *)&S.prefix;
+    bool changed = false, capped = true;
+    uint32_t decided = 0;
+    for (int it = 0; it < 4096; it++) {
+        if (prefix >= nb) {
+            capped = false;
+            break;
+        }
+        const uint64_t g = J.batch_base + prefix;
+        if (!cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(E.batch_ready[g]).load(cuda::memory_order_acquire)) {
+            capped = false;
+            break;
+        }
+        const unsigned long long *blk = E.acc + J.acc_base + prefix * J.acc_stride;
+        for (int w = 0; w < 4 * nc1; w += 2) add128(sum + w, blk + w);
+        for (int x = 0; x < ACC_EXTRA; x++) sum[4 * nc1 + x] += blk[4 * nc1 + x];
+        const uint64_t bsz = min((uint64_t)J.batch, (uint64_t)(J.walk_count - prefix * J.batch));
+        prefix++;
+        changed = true;
+        const double n = (double)min((uint64_t)(prefix * J.batch), (uint64_t)J.walk_count);
+        if (J.sigma > 0.0 && bsz == J.batch && n >= 2.0) {
+            double rs, rc;
+            rel_errors_dev(sum, J.n_c, J.master, n, &rs, &rc);
+            if (rs <= J.sigma && rc <= J.sigma) {
+                decided = 1;
+                S.used = (unsigned long long)n;
+                atomicExch(&E.job_cancel[j], 1);
+                capped = false;
                 break;
             }
-            const uint64_t g = J.batch_base + prefix;
-            if (!cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(E.batch_ready[g]).load(cuda::memory_order_acquire))
-                break;
-            const unsigned long long *blk = E.acc + J.acc_base + prefix * J.acc_stride;
-            for (int w = 0; w < 4 * nc1; w += 2) add128(sum + w, blk + w);
-            for (int x = 0; x < ACC_EXTRA; x++) sum[4 * nc1 + x] += blk[4 * nc1 + x];
-            const uint64_t bsz = min((uint64_t)J.batch, (uint64_t)(J.walk_count - prefix * J.batch));
-            prefix++;
-            changed = true;
-            const double n = (double)min((uint64_t)(prefix * J.batch), (uint64_t)J.walk_count);
-            if (bsz == J.batch && n >= 2.0) {
-                double rs, rc;
-                rel_errors_dev(sum, J.n_c, J.master, n, &rs, &rc);
-                if (rs <= J.sigma && rc <= J.sigma) {
-                    decided = 1;
-                    S.used = (unsigned long long)n;
-                    atomicExch(&E.job_cancel[j], 1);
-                    break;
-                }
-            }
         }
-        if (decided == 2) S.used = J.walk_count;
-        S.prefix = prefix;
-        if (!decided && changed) {
-            const double n = (double)min((uint64_t)(prefix * J.batch), (uint64_t)J.walk_count);
-            unsigned long long lim = J.walk_count;
-            if (n >= (double)J.batch) {
-                double rs, rc;
-                rel_errors_dev(sum, J.n_c, J.master, n, &rs, &rc);
-                const double r = fmax(rs, rc) / J.sigma;
-                double need = isfinite(r) ? n * r * r : (double)J.walk_count;
-                need = fmin(need * 1.05 + 2.0 * (double)J.batch, (double)J.walk_count);
-                lim = ((unsigned long long)need + J.batch - 1) / J.batch * J.batch;
-            }
-            lim = max(lim, (unsigned long long)((prefix + 1) * J.batch));
-            lim = min(lim, (unsigned long long)J.walk_count);
-            atomicExch(&E.job_limit[j], lim);
+    }
+    if (!decided && prefix >= nb) {
+        decided = 2;
+        S.used = J.walk_count;
+    }
+    S.prefix = prefix;
+    if (capped) atomicExch(&S.pending, 1u);   // bounded work per round: the caller takes another
+    if (J.sigma > 0.0 && !decided && changed) {
+        const double n = (double)min((uint64_t)(prefix * J.batch), (uint64_t)J.walk_count);
+        unsigned long long lim = J.walk_count;
+        if (n >= (double)J.batch) {
+            double rs, rc;
+            rel_errors_dev(sum, J.n_c, J.master, n, &rs, &rc);
+            const double r = fmax(rs, rc) / J.sigma;
+            double need = isfinite(r) ? n * r * r : (double)J.walk_count;
+            need = fmin(need * 1.05 + 2.0 * (double)J.batch, (double)J.walk_count);
+            lim = ((unsigned long long)need + J.batch - 1) / J.batch * J.batch;
         }
+        lim = max(lim, (unsigned long long)((prefix + 1) * J.batch));
+        lim = min(lim, (unsigned long long)J.walk_count);
+        atomicExch(&E.job_limit[j], lim);
+    }
+    if (decided) {
         __threadfence();
-        if (decided) atomicExch(&S.decided, decided);
+        atomicExch(&S.decided, decided);
+        atomicAdd(&E.jctl[JC_DECIDED], 1u);
+    }
+}
+
+// One thread, after reducing a batch of job j: run advance_locked under the job's
+// try-lock.  A thread that finds the lock held leaves a pending mark, which the
+// holder sees after unlocking and takes the lock again for; every round either
+// returns or was asked for by another thread, so the loop ends.
+__device__ FRW_OUTLINE void advance_job(const EngineView &E, uint32_t j)
+{
+    JobState &S = E.jstate[j];
+    atomicExch(&S.pending, 1u);
+    __threadfence();
+    for (int round = 0; round < (1 << 20); round++) {
+        if (*(volatile uint32_t *)&S.decided) return;
+        if (atomicCAS(&S.lock, 0u, 1u) != 0u) return;
+        __threadfence();
+        atomicExch(&S.pending, 0u);
+        __threadfence();
+        if (!*(volatile uint32_t *)&S.decided) advance_locked(E, j, S);
+        __threadfence();
         atomicExch(&S.lock, 0u);
+        __threadfence();
+        if (*(volatile uint32_t *)&S.pending == 0u) return;
     }
 }
 
@@ -1499,7 +1564,8 @@ struct WalkShared {
     uint32_t g_head, pad3[3];
     uint32_t q_count, q_head, s_count, g_count;
     uint32_t f_count, active, issuable, stop;
-    uint32_t red, finished, n_free, rr;
+    uint32_t red, finished, n_free, j_lo;
+    uint32_t j_pub, pad4[3];
     uint32_t q_next, pad2[3];
     IssueRanges ir;
     uint32_t fill[FILL_MAX];
@@ -1548,13 +1614,14 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
     for (uint32_t o = tid; o < P; o += WALK_THREADS) {
         const uint32_t s = base + o;
         E.s.state[s] = ST_FRESH;
-        E.s.job[s] = E.n_jobs > 0 ? s % (uint32_t)E.n_jobs : 0u;
+        E.s.job[s] = 0u;
     }
     if (tid == 0) {
         sh.q_count = 0; sh.q_head = 0; sh.s_count = 0; sh.stop = 0; sh.q_next = 0;
         sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0; sh.red = 0;
         sh.issuable = 0;
-        sh.rr = blockIdx.x % (uint32_t)(E.n_jobs > 0 ? E.n_jobs : 1);
+        sh.j_lo = 0;
+        sh.j_pub = 0;
     }
     __syncthreads();
     int cur = 0;
@@ -1562,12 +1629,15 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
     uint32_t epochs = 0;
     for (;;) {
         const long long c0 = clock64();
-        if (tid == 0) {
-            sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0; sh.g_head = 0;
-            uint32_t iss = 0;
-            for (int j = 0; j < E.n_jobs; j++)
-                if (job_open(E, j)) iss = 1;
-            sh.issuable = iss;
+        if (warp == 0) {
+            uint32_t lo, pub, open;
+            scan_jobs(E, lo, pub, open);
+            if (lane == 0) {
+                sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0; sh.g_head = 0;
+                sh.issuable = open;
+                sh.j_lo = lo;
+                sh.j_pub = pub;
+            }
         }
         __syncthreads();
         // Two warp groups run concurrently in every epoch.  Geometry warps step every
@@ -1604,10 +1674,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
                 if (need) sh.glist[gb + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)o;
             }
             __syncthreads();
-            if (tid == 0) {
-                claim_ids(E, sh.ir, sh.n_free, sh.rr);
-                sh.rr = E.n_jobs > 0 ? (sh.rr + 1u) % (uint32_t)E.n_jobs : 0u;
-            }
+            if (warp == 0) claim_ids(E, sh.ir, sh.n_free, sh.j_lo, sh.j_pub);
             __syncthreads();
             const uint32_t ng = sh.g_count;
             const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
@@ -1764,8 +1831,8 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
             __syncthreads();
             if (g == 0xffffffffu) break;
             reduce_batch(E, g, reinterpret_cast<unsigned long long *>(dsm));
+            if (tid == 0) advance_job(E, __ldcg(E.batch_job + g));
         }
-        if (tid == 0) advance_sigma_jobs(E);
         const long long c3 = clock64();
         epochs++;
         if (tid == 0) {
@@ -1781,9 +1848,8 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
             uint32_t stop = 0;
             if (*(volatile uint32_t *)&E.ctrl[CTRL_ABORT]) stop = 1;
             if (*(volatile uint32_t *)&E.status[STAT_ERR]) stop = 1;   // any device error ends the run
-            bool undecided = false;
-            for (int j = 0; j < E.n_jobs; j++)
-                if (E.jobs[j].sigma > 0.0 && *(volatile uint32_t *)&E.jstate[j].decided == 0u) undecided = true;
+            const bool undecided =
+                *(volatile uint32_t *)&E.jctl[JC_DECIDED] < *(volatile uint32_t *)&E.jctl[JC_PUBLISHED];
             if (idle) {
                 if (!undecided && *(volatile uint32_t *)&E.ctrl[CTRL_OPEN] == 0u) {
                     stop = 1;

@@ -1,13 +1,17 @@
 // frw_runtime.cu -- host side of the C ABI in include/frw.h: context, material
-// registry, structure loading and validation, and the engine loop that drives
-// the device rounds (geometry -> table fill -> MicroWalk -> round end).
+// registry, structure loading and validation, runs of the persistent walk kernel
+// (closed runs for frw_extract*, open runs fed by the serving loop).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -23,12 +27,28 @@ namespace {
 
 struct HostStructure {
     int n_c = 0, n_b = 0;
+    int mat_need = 0;                 // 1 + the largest global material id it uses
     std::vector<double> c_lo, c_hi;   // n_c x 3 (AoS, host copy for Gaussian set-up)
     double dom_lo[3], dom_hi[3];
     std::vector<void *> dev;          // device allocations of this structure
     DevStructure d;
     bool live = false;
 };
+
+// Job table and arenas of the persistent walk kernel (device), owned by the
+// context and grown on demand between runs.
+struct RunBufs {
+    uint32_t jcap = 0;
+    uint64_t bcap = 0, acap = 0, scap = 0;
+    DevJob *jobs = nullptr;
+    unsigned long long *next = nullptr, *limit = nullptr, *jsum = nullptr, *jsoff = nullptr, *acc = nullptr;
+    int *cancel = nullptr;
+    JobState *js = nullptr;
+    uint32_t *done = nullptr, *ready = nullptr, *bjob = nullptr, *rq = nullptr, *rqc = nullptr, *jctl = nullptr;
+    std::vector<void *> allocs;
+};
+
+struct Server;
 
 }  // namespace
 
@@ -66,6 +86,10 @@ struct frw_ctx {
     RecArrays rec;                      // per-walk records (grown on demand)
     uint64_t rec_cap = 0;
     std::vector<void *> rec_allocs;
+    RunBufs rb;                         // job table and arenas
+    std::mutex engine_mu;               // held for the whole of a run (closed or serving)
+    std::mutex struct_mu;               // guards the host structure table against the serving thread
+    Server *srv = nullptr;              // serving loop (started by the first frw_submit)
 };
 
 static const char *kErr[] = {"ok",
@@ -205,15 +229,19 @@ extern "C" int frw_set_stream(frw_ctx *ctx, void *s)
     return FRW_OK;
 }
 
+static void stop_server(frw_ctx *ctx);
+
 extern "C" void frw_destroy(frw_ctx *ctx)
 {
     if (!ctx) return;
+    stop_server(ctx);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto &s : ctx->structs)
         for (void *p : s.dev) cudaFree(p);
     for (void *p : ctx->allocs) cudaFree(p);
     for (void *p : ctx->rec_allocs) cudaFree(p);
+    for (void *p : ctx->rb.allocs) cudaFree(p);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -222,11 +250,11 @@ extern "C" void frw_destroy(frw_ctx *ctx)
     delete ctx;
 }
 
-static int check_status(frw_ctx *ctx)
+static int check_status(frw_ctx *ctx, cudaStream_t st = nullptr)
 {
-    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(uint32_t) * STAT_WORDS, cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (!st) st = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status, sizeof(uint32_t) * STAT_WORDS, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     const uint32_t e = ctx->h_status[STAT_ERR];
     if (e) {
         char buf[160];
@@ -341,7 +369,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         ctx->fc.a = ctx->fc_buf + (size_t)N * N + N;
         ctx->fc.d = ctx->fc_buf + (size_t)N * N + 2 * N;
     }
-    ctx->struct_cap = 64;
+    ctx->struct_cap = 256;
     if ((rc = dalloc(ctx, &ctx->d_structs, ctx->struct_cap, A))) return bail(rc);
     if (cudaMallocHost(&ctx->h_status, sizeof(uint32_t) * STAT_WORDS) != cudaSuccess) return bail(FRW_ENOMEM);
     for (auto &e : ctx->ev)
@@ -497,9 +525,12 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
             return fail(ctx, FRW_EINVAL, "degenerate dielectric block");
         if (blocks[b].mat < 0 || blocks[b].mat >= n_mat) return fail(ctx, FRW_EINVAL, "block material out of range");
     }
+    std::lock_guard<std::mutex> lk(ctx->struct_mu);
     std::vector<uint8_t> map;
     int rc = register_materials(ctx, eps_r, n_mat, map);
     if (rc) return rc;
+    int mat_need = 0;
+    for (int i = 0; i < n_mat; i++) mat_need = std::max(mat_need, (int)map[i] + 1);
     // slot in the structure table
     int sid = -1;
     for (size_t i = 0; i < ctx->structs.size(); i++)
@@ -512,6 +543,7 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
     HostStructure &H = ctx->structs[sid];
     H = HostStructure();
     H.n_c = n_cond;
+    H.mat_need = mat_need;
     H.n_b = n_blocks;
     H.c_lo.resize(3 * (size_t)n_cond);
     H.c_hi.resize(3 * (size_t)n_cond);
@@ -608,6 +640,8 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
 extern "C" int frw_unload_structure(frw_ctx *ctx, int32_t sid)
 {
     if (!ctx) return FRW_EINVAL;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);   // no run on the device meanwhile
+    std::lock_guard<std::mutex> lk(ctx->struct_mu);
     if (sid < 0 || sid >= (int)ctx->structs.size() || !ctx->structs[sid].live) return FRW_ENOTFOUND;
     cudaStreamSynchronize(ctx->stream);
     for (void *p : ctx->structs[sid].dev) cudaFree(p);
@@ -661,61 +695,14 @@ struct JobRun {
     uint64_t walk_begin = 0;         // first walk id (resume / shard offset)
     DevJob d;
     uint64_t n_batches = 0;
-    uint64_t prefix = 0;             // complete batches folded into S1/S2 so far
-    uint64_t limit = 0;              // current issue limit (walks)
+    uint64_t sum_off = 0;            // u64 offset of the job's running sums
+    uint64_t first_limit = 0;        // issue limit at publication
     bool converged = false;
-    std::vector<i128> S1, S2;        // running prefix sums
+    std::vector<i128> S1, S2;        // exact sums of the estimate
     uint64_t walks = 0;
+    uint64_t issued = 0;
     uint64_t ex[ACC_EXTRA] = {0};
-    unsigned long long *h_blocks = nullptr;   // pinned staging for batch blocks
-    uint64_t h_cap = 0;
-    unsigned long long h_limit = 0;           // host copy of the issue limit (copy source)
 };
-
-// relative standard errors of C_ii and of the largest |C_ij| (j != i, ground
-// excluded) from exact prefix sums; the stop rule holds when both are <= target
-static void rel_errors(const std::vector<i128> &S1, const std::vector<i128> &S2, uint64_t n, int nc, int master,
-                       double *r_self, double *r_cpl)
-{
-    *r_self = INFINITY;
-    *r_cpl = 0.0;
-    if (n < 2) return;
-    const double nn = (double)n;
-    auto val = [&](int k, double *c, double *se) {
-        const double s1 = (double)S1[k] / ACC_S1_SCALE, s2 = (double)S2[k] / ACC_S2_SCALE;
-        *c = s1 / nn;
-        const double v = (s2 - s1 * s1 / nn) / (nn * (nn - 1.0));
-        *se = std::sqrt(v > 0 ? v : 0);
-    };
-    double ci, si;
-    val(master, &ci, &si);
-    *r_self = (ci != 0.0) ? si / std::fabs(ci) : INFINITY;
-    int jb = -1;
-    double cb = 0.0;
-    for (int j = 0; j < nc; j++) {
-        if (j == master) continue;
-        double c, sj;
-        val(j, &c, &sj);
-        if (jb < 0 || std::fabs(c) > cb) {
-            jb = j;
-            cb = std::fabs(c);
-        }
-    }
-    if (jb >= 0) {
-        double c, sj;
-        val(jb, &c, &sj);
-        *r_cpl = (c != 0.0) ? sj / std::fabs(c) : INFINITY;
-    }
-}
-
-static bool sigma_ok(const std::vector<i128> &S1, const std::vector<i128> &S2, uint64_t n, int nc, int master,
-                     double target)
-{
-    if (n < 2) return false;
-    double rs, rc;
-    rel_errors(S1, S2, n, nc, master, &rs, &rc);
-    return rs <= target && rc <= target;
-}
 
 static int ensure_records(frw_ctx *ctx, uint64_t n)
 {
@@ -735,15 +722,178 @@ static int ensure_records(frw_ctx *ctx, uint64_t n)
     return FRW_OK;
 }
 
-static void fold_block(JobRun &j, const unsigned long long *blk, uint64_t bsz)
+// job table and arenas, grown (never while a run is on the device) to at least the
+// given capacities
+static int ensure_runbufs(frw_ctx *ctx, uint32_t jcap, uint64_t bcap, uint64_t acap, uint64_t scap)
+{
+    RunBufs &B = ctx->rb;
+    if (jcap <= B.jcap && bcap <= B.bcap && acap <= B.acap && scap <= B.scap) return FRW_OK;
+    jcap = std::max(jcap, B.jcap);
+    bcap = std::max(bcap, B.bcap);
+    acap = std::max(acap, B.acap);
+    scap = std::max(scap, B.scap);
+    for (void *p : B.allocs) cudaFree(p);
+    B = RunBufs();
+    int rc;
+    if ((rc = dalloc(ctx, &B.jobs, jcap, B.allocs)) || (rc = dalloc(ctx, &B.next, jcap, B.allocs)) ||
+        (rc = dalloc(ctx, &B.limit, jcap, B.allocs)) || (rc = dalloc(ctx, &B.cancel, jcap, B.allocs)) ||
+        (rc = dalloc(ctx, &B.js, jcap, B.allocs)) || (rc = dalloc(ctx, &B.jsoff, jcap, B.allocs)) ||
+        (rc = dalloc(ctx, &B.jsum, scap, B.allocs)) || (rc = dalloc(ctx, &B.acc, acap, B.allocs)) ||
+        (rc = dalloc(ctx, &B.done, bcap, B.allocs)) || (rc = dalloc(ctx, &B.ready, bcap, B.allocs)) ||
+        (rc = dalloc(ctx, &B.bjob, bcap, B.allocs)) || (rc = dalloc(ctx, &B.rq, bcap, B.allocs)) ||
+        (rc = dalloc(ctx, &B.rqc, 2, B.allocs)) || (rc = dalloc(ctx, &B.jctl, JC_WORDS, B.allocs))) {
+        for (void *p : B.allocs) cudaFree(p);
+        B = RunBufs();
+        return rc;
+    }
+    B.jcap = jcap;
+    B.bcap = bcap;
+    B.acap = acap;
+    B.scap = scap;
+    return FRW_OK;
+}
+
+// Bump allocation of a run's arenas.
+struct Arena {
+    uint32_t jobs = 0;
+    uint64_t walks = 0, batches = 0, acc = 0, sums = 0;
+};
+
+// words of a job's running sums, rounded to whole 128-byte lines (no line is
+// shared between jobs)
+static uint64_t sum_words(int n_c) { return (acc_stride_for(n_c) + 15u) / 16u * 16u; }
+
+// Fill a job's descriptor and place it at the arena's current ends.
+static void place_job(frw_ctx *ctx, JobRun &j, Arena &A)
+{
+    const HostStructure &H = ctx->structs[j.desc.structure_id];
+    DevJob &d = j.d;
+    memset(&d, 0, sizeof(d));
+    d.sid = j.desc.structure_id;
+    d.master = j.desc.master;
+    d.n_c = H.n_c;
+    d.key0 = (uint32_t)ctx->opt.seed;
+    d.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ (uint32_t)j.desc.request_id;
+    gauss_setup(H, j.desc.master, ctx->opt.gauss_offset_frac, d);
+    d.walk_count = j.desc.walk_budget;
+    d.walk_begin = j.walk_begin;
+    d.batch = j.desc.batch ? j.desc.batch : 16384;
+    d.acc_stride = acc_stride_for(H.n_c);
+    d.sigma = j.desc.sigma_target;
+    j.n_batches = (d.walk_count + d.batch - 1) / d.batch;
+    d.acc_base = A.acc;
+    d.rec_base = A.walks;
+    d.batch_base = A.batches;
+    j.sum_off = A.sums;
+    A.acc += j.n_batches * d.acc_stride;
+    A.walks += d.walk_count;
+    A.batches += j.n_batches;
+    A.sums += sum_words(H.n_c);
+    A.jobs++;
+    j.S1.assign(H.n_c + 1, 0);
+    j.S2.assign(H.n_c + 1, 0);
+}
+
+// Zero a run's job table and arenas up to the given sizes (stream order).
+static cudaError_t zero_run(frw_ctx *ctx, uint32_t jobs, const Arena &A, cudaStream_t st)
+{
+    RunBufs &B = ctx->rb;
+    const uint64_t nb = std::max<uint64_t>(A.batches, 1);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(B.next, 0, sizeof(unsigned long long) * std::max<uint32_t>(jobs, 1), st)) ||
+        (e = cudaMemsetAsync(B.cancel, 0, sizeof(int) * std::max<uint32_t>(jobs, 1), st)) ||
+        (e = cudaMemsetAsync(B.js, 0, sizeof(JobState) * std::max<uint32_t>(jobs, 1), st)) ||
+        (e = cudaMemsetAsync(B.jsum, 0, sizeof(unsigned long long) * std::max<uint64_t>(A.sums, 1), st)) ||
+        (e = cudaMemsetAsync(B.acc, 0, sizeof(unsigned long long) * std::max<uint64_t>(A.acc, 1), st)) ||
+        (e = cudaMemsetAsync(B.done, 0, sizeof(uint32_t) * nb, st)) ||
+        (e = cudaMemsetAsync(B.ready, 0, sizeof(uint32_t) * nb, st)) ||
+        (e = cudaMemsetAsync(B.rq, 0xff, sizeof(uint32_t) * nb, st)) ||
+        (e = cudaMemsetAsync(B.rqc, 0, sizeof(uint32_t) * 2, st)) ||
+        (e = cudaMemsetAsync(B.jctl, 0, sizeof(uint32_t) * JC_WORDS, st)) ||
+        (e = cudaMemsetAsync(ctx->rec.k, 0x80, sizeof(int32_t) * std::max<uint64_t>(A.walks, 1), st)))
+        return e;
+    return cudaSuccess;
+}
+
+// Write jobs[j0 .. j0 + n) (table indices j0 ..) and then publish them: the kernel
+// sees a job only once the published count covers it (copies in stream order).
+// Host buffers must stay valid until the stream has run the copies.
+struct PublishStage {
+    std::vector<DevJob> d;
+    std::vector<unsigned long long> lim, off;
+    std::vector<uint32_t> bjob;
+    uint32_t pub = 0;
+};
+
+static cudaError_t publish_jobs(frw_ctx *ctx, JobRun *const *jobs, uint32_t j0, uint32_t n, PublishStage &P,
+                                cudaStream_t st)
+{
+    RunBufs &B = ctx->rb;
+    if (n == 0) return cudaSuccess;
+    P.d.resize(n);
+    P.lim.resize(n);
+    P.off.resize(n);
+    P.bjob.clear();
+    const uint64_t b0 = jobs[0]->d.batch_base;
+    for (uint32_t i = 0; i < n; i++) {
+        const JobRun &j = *jobs[i];
+        P.d[i] = j.d;
+        P.lim[i] = j.first_limit;
+        P.off[i] = j.sum_off;
+        for (uint64_t b = 0; b < j.n_batches; b++) P.bjob.push_back(j0 + i);
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(B.jobs + j0, P.d.data(), sizeof(DevJob) * n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(B.limit + j0, P.lim.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(B.jsoff + j0, P.off.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st)))
+        return e;
+    if (!P.bjob.empty() &&
+        (e = cudaMemcpyAsync(B.bjob + b0, P.bjob.data(), sizeof(uint32_t) * P.bjob.size(), cudaMemcpyHostToDevice, st)))
+        return e;
+    P.pub = j0 + n;
+    return cudaMemcpyAsync(B.jctl + JC_PUBLISHED, &P.pub, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+}
+
+// Read a decided job's sums and counters back (stream order) and fill its result.
+static void take_result(JobRun &j, const JobState &S, const unsigned long long *sum, unsigned long long issued)
 {
     const int nc1 = j.d.n_c + 1;
     for (int k = 0; k < nc1; k++) {
-        j.S1[k] += rd128(blk + 2 * k);
-        j.S2[k] += rd128(blk + 2 * nc1 + 2 * k);
+        j.S1[k] = rd128(sum + 2 * k);
+        j.S2[k] = rd128(sum + 2 * nc1 + 2 * k);
     }
-    for (int x = 0; x < ACC_EXTRA; x++) j.ex[x] += blk[4 * nc1 + x];
-    j.walks += bsz;
+    for (int x = 0; x < ACC_EXTRA; x++) j.ex[x] = sum[4 * nc1 + x];
+    j.walks = S.used;
+    j.converged = S.decided == 1u;
+    j.issued = issued;
+}
+
+static void fill_stats(frw_stats &s, const JobRun &j)
+{
+    memset(&s, 0, sizeof(s));
+    s.walks = j.walks;
+    s.hops = j.ex[1];
+    s.micro_steps = j.ex[2];
+    s.strat_hops = j.ex[3];
+    s.hom_hops = j.ex[4];
+    s.mw_hops = j.ex[5];
+    s.branch[0] = j.ex[6];
+    s.branch[1] = j.ex[7];
+    s.branch[2] = j.ex[8];
+    s.truncated = j.ex[9];
+    s.mw_jobs = j.ex[5];
+    s.walks_issued = j.issued;
+}
+
+// first issue limit of a sigma job: its share of the slot pool (the device then
+// steers the limit from the completed prefix), at least 4 batches
+static uint64_t first_wave(const JobRun &j, uint64_t slots, int n_sigma)
+{
+    if (!(j.desc.sigma_target > 0.0)) return j.d.walk_count;
+    const uint64_t b = j.d.batch;
+    uint64_t first = std::max<uint64_t>(4 * b, slots / (uint64_t)std::max(1, n_sigma));
+    first = (first + b - 1) / b * b;
+    return std::min<uint64_t>(first, j.d.walk_count);
 }
 
 // Wall-clock limit of one run (seconds; environment FRW_RUN_TIMEOUT_S, default 3600).
@@ -754,233 +904,119 @@ static double run_timeout_s()
     return t > 0.0 ? t : 3600.0;
 }
 
-// Run a set of jobs to completion: one launch of the persistent walk kernel.
-// For jobs with a sigma target the host follows completed batches in walk-id
-// order from a second stream (copy engines only), cancels a job when its stop rule
-// holds, moves its issue limit to the predicted need, and closes the run when
-// every such job is decided.
+static EngineView run_view(frw_ctx *ctx, uint32_t jcap, int max_nc, uint32_t pool, uint64_t batches)
+{
+    EngineView E = make_view(ctx);
+    RunBufs &B = ctx->rb;
+    E.n_jobs = (int)jcap;
+    E.max_nc = max_nc;
+    E.jobs = B.jobs;
+    E.job_next = B.next;
+    E.job_limit = B.limit;
+    E.job_cancel = B.cancel;
+    E.jstate = B.js;
+    E.jctl = B.jctl;
+    E.batch_job = B.bjob;
+    E.jsum = B.jsum;
+    E.jsum_off = B.jsoff;
+    E.acc = B.acc;
+    E.batch_done = B.done;
+    E.batch_ready = B.ready;
+    E.rq = B.rq;
+    E.rq_count = B.rqc;
+    E.rq_head = B.rqc + 1;
+    E.rq_cap = (uint32_t)std::max<uint64_t>(batches, 1);
+    E.rec = ctx->rec;
+    E.pool = pool;
+    E.NS = pool * (uint32_t)ctx->grid;
+    return E;
+}
+
+// Run a set of jobs to completion: one launch of the persistent walk kernel with
+// every job published before it starts.  The kernel applies each job's stop rule
+// and folds its batches; the host reads the decided sums back.  The caller holds
+// the engine lock.
 static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_out)
 {
     const auto t0 = std::chrono::steady_clock::now();
-    const int nj = (int)jobs.size();
-    uint64_t total_walks = 0, acc_words = 0, total_batches = 0;
-    int max_nc = 1;
+    std::vector<JobRun *> live;
     for (auto &j : jobs) {
         const HostStructure &H = ctx->structs[j.desc.structure_id];
-        DevJob &d = j.d;
-        memset(&d, 0, sizeof(d));
-        d.sid = j.desc.structure_id;
-        d.master = j.desc.master;
-        d.n_c = H.n_c;
-        d.key0 = (uint32_t)ctx->opt.seed;
-        d.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ (uint32_t)j.desc.request_id;
-        gauss_setup(H, j.desc.master, ctx->opt.gauss_offset_frac, d);
-        d.walk_count = j.desc.walk_budget;
-        d.walk_begin = j.walk_begin;
-        d.batch = j.desc.batch ? j.desc.batch : 16384;
-        d.acc_stride = acc_stride_for(H.n_c);
-        d.acc_base = acc_words;
-        d.rec_base = total_walks;
-        d.batch_base = total_batches;
-        d.sigma = j.desc.sigma_target;
-        j.n_batches = (d.walk_count + d.batch - 1) / d.batch;
-        acc_words += j.n_batches * d.acc_stride;
-        total_walks += d.walk_count;
-        total_batches += j.n_batches;
-        max_nc = std::max(max_nc, H.n_c);
         j.S1.assign(H.n_c + 1, 0);
         j.S2.assign(H.n_c + 1, 0);
-        j.limit = d.walk_count;
+        j.d.n_c = H.n_c;
+        if (j.desc.walk_budget) live.push_back(&j);
     }
-    if (total_batches >= 0xffffffffull) return fail(ctx, FRW_EINVAL, "too many batches");
-    int rc = ensure_records(ctx, total_walks);
+    if (stats_out)
+        for (size_t i = 0; i < jobs.size(); i++) memset(&stats_out[i], 0, sizeof(frw_stats));
+    if (live.empty()) return FRW_OK;
+    const uint32_t nj = (uint32_t)live.size();
+    Arena A;
+    int max_nc = 1;
+    for (JobRun *j : live) {
+        place_job(ctx, *j, A);
+        max_nc = std::max(max_nc, j->d.n_c);
+    }
+    if (A.batches >= 0xffffffffull) return fail(ctx, FRW_EINVAL, "too many batches");
+    int rc = ensure_records(ctx, A.walks);
     if (rc) return rc;
-    std::vector<void *> tmp;
-    uint32_t *h_flags = nullptr;
-    auto cleanup = [&]() {
-        for (void *p : tmp) cudaFree(p);
-        for (auto &j : jobs)
-            if (j.h_blocks) {
-                cudaFreeHost(j.h_blocks);
-                j.h_blocks = nullptr;
-            }
-        if (h_flags) cudaFreeHost(h_flags);
-    };
-    DevJob *d_jobs = nullptr;
-    unsigned long long *d_next = nullptr, *d_acc = nullptr, *d_limit = nullptr;
-    int *d_cancel = nullptr;
-    uint32_t *d_done = nullptr, *d_ready = nullptr, *d_rq = nullptr, *d_rqc = nullptr;
-    JobState *d_js = nullptr;
-    unsigned long long *d_jsum = nullptr, *d_jsoff = nullptr;
-    if ((rc = dalloc(ctx, &d_jobs, nj, tmp)) || (rc = dalloc(ctx, &d_next, nj, tmp)) ||
-        (rc = dalloc(ctx, &d_limit, nj, tmp)) || (rc = dalloc(ctx, &d_cancel, nj, tmp)) ||
-        (rc = dalloc(ctx, &d_acc, std::max<uint64_t>(acc_words, 1), tmp)) ||
-        (rc = dalloc(ctx, &d_done, std::max<uint64_t>(total_batches, 1), tmp)) ||
-        (rc = dalloc(ctx, &d_ready, std::max<uint64_t>(total_batches, 1), tmp)) ||
-        (rc = dalloc(ctx, &d_rq, std::max<uint64_t>(total_batches, 1), tmp)) || (rc = dalloc(ctx, &d_rqc, 2, tmp)) ||
-        (rc = dalloc(ctx, &d_js, nj, tmp)) || (rc = dalloc(ctx, &d_jsoff, nj, tmp))) {
-        cleanup();
-        return rc;
-    }
+    if ((rc = ensure_runbufs(ctx, nj, A.batches, A.acc, A.sums))) return rc;
     // slots for this run (fewer for small runs)
-    uint32_t run_pool;
-    {
-        const uint32_t pool0 = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
-        const uint64_t per = std::max<uint64_t>(256, ((total_walks / ctx->grid + 255) / 256) * 256);
-        run_pool = (uint32_t)std::min<uint64_t>(pool0, per);
-    }
+    const uint32_t pool0 = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
+    const uint64_t per = std::max<uint64_t>(256, ((A.walks / ctx->grid + 255) / 256) * 256);
+    const uint32_t run_pool = (uint32_t)std::min<uint64_t>(pool0, per);
     const uint64_t run_slots = (uint64_t)run_pool * ctx->grid;
     int n_sigma = 0;
-    for (auto &j : jobs) n_sigma += j.desc.sigma_target > 0.0 ? 1 : 0;
-    std::vector<DevJob> hj(nj);
-    std::vector<unsigned long long> hl(nj), hjo(nj);
-    uint64_t jsum_words = 0;
-    for (int i = 0; i < nj; i++) {
-        hj[i] = jobs[i].d;
-        hl[i] = jobs[i].d.walk_count;
-        if (jobs[i].desc.sigma_target > 0.0) {
-            // first wave: this job's share of the slot pool; the device then steers
-            // the limit from the completed prefix (predicted need)
-            const uint64_t b = jobs[i].d.batch;
-            uint64_t first = std::max<uint64_t>(4 * b, run_slots / (uint64_t)n_sigma);
-            first = (first + b - 1) / b * b;
-            hl[i] = std::min<uint64_t>(first, jobs[i].d.walk_count);
-        }
-        hjo[i] = jsum_words;
-        jsum_words += jobs[i].d.acc_stride;
-    }
-    if ((rc = dalloc(ctx, &d_jsum, std::max<uint64_t>(jsum_words, 1), tmp))) {
-        cleanup();
-        return rc;
-    }
+    for (JobRun *j : live) n_sigma += j->desc.sigma_target > 0.0 ? 1 : 0;
+    for (JobRun *j : live) j->first_limit = first_wave(*j, run_slots, n_sigma);
     cudaStream_t st = ctx->stream, ax = ctx->aux;
-#define CKR(call)                                     \
-    do {                                              \
-        cudaError_t e_ = (call);                      \
-        if (e_ != cudaSuccess) {                      \
-            int r_ = cuda_fail(ctx, e_, #call);       \
-            cleanup();                                \
-            return r_;                                \
-        }                                             \
-    } while (0)
+    PublishStage P;
     const uint32_t ctrl0[CTRL_WORDS] = {0u, 0u, 0u, 0u};
-    CKR(cudaMemcpyAsync(d_jobs, hj.data(), sizeof(DevJob) * nj, cudaMemcpyHostToDevice, st));
-    CKR(cudaMemcpyAsync(d_limit, hl.data(), sizeof(unsigned long long) * nj, cudaMemcpyHostToDevice, st));
-    CKR(cudaMemcpyAsync(ctx->ctrl, ctrl0, sizeof(ctrl0), cudaMemcpyHostToDevice, st));
-    CKR(cudaMemsetAsync(d_next, 0, sizeof(unsigned long long) * nj, st));
-    CKR(cudaMemsetAsync(d_cancel, 0, sizeof(int) * nj, st));
-    CKR(cudaMemsetAsync(d_acc, 0, sizeof(unsigned long long) * std::max<uint64_t>(acc_words, 1), st));
-    CKR(cudaMemsetAsync(d_done, 0, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
-    CKR(cudaMemsetAsync(d_ready, 0, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
-    CKR(cudaMemsetAsync(d_rq, 0xff, sizeof(uint32_t) * std::max<uint64_t>(total_batches, 1), st));
-    CKR(cudaMemsetAsync(d_rqc, 0, sizeof(uint32_t) * 2, st));
-    CKR(cudaMemsetAsync(d_js, 0, sizeof(JobState) * nj, st));
-    CKR(cudaMemsetAsync(d_jsum, 0, sizeof(unsigned long long) * std::max<uint64_t>(jsum_words, 1), st));
-    CKR(cudaMemcpyAsync(d_jsoff, hjo.data(), sizeof(unsigned long long) * nj, cudaMemcpyHostToDevice, st));
-    CKR(cudaMemsetAsync(ctx->rec.k, 0x80, sizeof(int32_t) * std::max<uint64_t>(total_walks, 1), st));
-    CKR(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
-    CKR(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, st));
-    EngineView E = make_view(ctx);
-    E.n_jobs = nj;
-    E.max_nc = max_nc;
-    E.jobs = d_jobs;
-    E.job_next = d_next;
-    E.job_limit = d_limit;
-    E.job_cancel = d_cancel;
-    E.jstate = d_js;
-    E.jsum = d_jsum;
-    E.jsum_off = d_jsoff;
-    E.acc = d_acc;
-    E.batch_done = d_done;
-    E.batch_ready = d_ready;
-    E.rq = d_rq;
-    E.rq_count = d_rqc;
-    E.rq_head = d_rqc + 1;
-    E.rq_cap = (uint32_t)std::max<uint64_t>(total_batches, 1);
-    E.rec = ctx->rec;
-    E.pool = run_pool;
-    E.NS = (uint32_t)run_slots;
-    CKR(cudaEventRecord(ctx->ev[0], st));
-    CKR(launch_walk(E, ctx->shape, st));
-    CKR(cudaEventRecord(ctx->ev[1], st));
+    CK(zero_run(ctx, nj, A, st));
+    CK(cudaMemcpyAsync(ctx->ctrl, ctrl0, sizeof(ctrl0), cudaMemcpyHostToDevice, st));
+    CK(publish_jobs(ctx, live.data(), 0, nj, P, st));
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
+    CK(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, st));
+    const EngineView E = run_view(ctx, nj, max_nc, run_pool, A.batches);
+    CK(cudaEventRecord(ctx->ev[0], st));
+    CK(launch_walk(E, ctx->shape, st));
+    CK(cudaEventRecord(ctx->ev[1], st));
     // wait for the kernel (which applies the stop rules itself) under a wall-clock guard
     const double limit_s = run_timeout_s();
     bool timed_out = false;
     while (cudaEventQuery(ctx->ev[1]) == cudaErrorNotReady) {
         if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) {
             static const uint32_t abort1 = 1;   // the kernel stops at its next epoch boundary
-            CKR(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
-            CKR(cudaStreamSynchronize(ax));
+            CK(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ax));
+            CK(cudaStreamSynchronize(ax));
             timed_out = true;
             break;
         }
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    CKR(cudaStreamSynchronize(st));
+    CK(cudaStreamSynchronize(st));
     rc = check_status(ctx);
-    if (rc) {
-        cleanup();
-        return rc;
-    }
-    if (timed_out) {
-        cleanup();
-        return fail(ctx, FRW_ETIMEOUT, "run exceeded its wall-clock limit (FRW_RUN_TIMEOUT_S)");
-    }
+    if (rc) return rc;
+    if (timed_out) return fail(ctx, FRW_ETIMEOUT, "run exceeded its wall-clock limit (FRW_RUN_TIMEOUT_S)");
     std::vector<JobState> hjs(nj);
-    CKR(cudaMemcpy(hjs.data(), d_js, sizeof(JobState) * nj, cudaMemcpyDeviceToHost));
-    for (int i = 0; i < nj; i++) {
-        JobRun &j = jobs[i];
-        if (j.desc.sigma_target > 0.0 && hjs[i].decided == 1) {
-            j.converged = true;
-            j.n_batches = (hjs[i].used + j.d.batch - 1) / j.d.batch;   // fold exactly the decided prefix
-        }
-    }
-    // fold the batches of every job's estimate (all of them, or the decided prefix)
-    std::vector<unsigned long long> hb;
-    for (int i = 0; i < nj; i++) {
-        JobRun &j = jobs[i];
-        if (j.prefix >= j.n_batches) continue;
-        const uint32_t strd = j.d.acc_stride;
-        const uint64_t rest = j.n_batches - j.prefix;
-        hb.resize(rest * strd);
-        CKR(cudaMemcpyAsync(hb.data(), d_acc + j.d.acc_base + j.prefix * strd, sizeof(unsigned long long) * rest * strd,
-                            cudaMemcpyDeviceToHost, st));
-        CKR(cudaStreamSynchronize(st));
-        const int nc1 = j.d.n_c + 1;
-        for (uint64_t b = 0; b < rest; b++) {
-            const unsigned long long *blk = hb.data() + b * strd;
-            const uint64_t bsz = std::min<uint64_t>(j.d.batch, j.d.walk_count - (j.prefix + b) * j.d.batch);
-            if (blk[4 * nc1] != bsz) {
-                cleanup();
-                return fail(ctx, FRW_EDEVICE, "a batch was not reduced");
-            }
-            fold_block(j, blk, bsz);
-        }
-        j.prefix = j.n_batches;
+    std::vector<unsigned long long> hsum(A.sums), hnext(nj);
+    CK(cudaMemcpy(hjs.data(), ctx->rb.js, sizeof(JobState) * nj, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hsum.data(), ctx->rb.jsum, sizeof(unsigned long long) * A.sums, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(hnext.data(), ctx->rb.next, sizeof(unsigned long long) * nj, cudaMemcpyDeviceToHost));
+    for (uint32_t i = 0; i < nj; i++) {
+        if (hjs[i].decided == 0u) return fail(ctx, FRW_EDEVICE, "a job was not decided when the kernel ended");
+        take_result(*live[i], hjs[i], hsum.data() + live[i]->sum_off, hnext[i]);
     }
     float kms = 0.f;
     cudaEventElapsedTime(&kms, ctx->ev[0], ctx->ev[1]);
-    std::vector<unsigned long long> issued(nj);
-    CKR(cudaMemcpy(issued.data(), d_next, sizeof(unsigned long long) * nj, cudaMemcpyDeviceToHost));
     unsigned long long cyc[5] = {0, 0, 0, 0, 0};
-    CKR(cudaMemcpy(cyc, ctx->cycles, sizeof(cyc), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cyc, ctx->cycles, sizeof(cyc), cudaMemcpyDeviceToHost));
     const double ctot = (double)cyc[4];   // phases overlap: busy shares of the kernel's CTA time
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats_out) {
-        for (int i = 0; i < nj; i++) {
+        for (size_t i = 0; i < jobs.size(); i++) {
             frw_stats &s = stats_out[i];
-            memset(&s, 0, sizeof(s));
-            const JobRun &j = jobs[i];
-            s.walks = j.walks;
-            s.hops = j.ex[1];
-            s.micro_steps = j.ex[2];
-            s.strat_hops = j.ex[3];
-            s.hom_hops = j.ex[4];
-            s.mw_hops = j.ex[5];
-            s.branch[0] = j.ex[6];
-            s.branch[1] = j.ex[7];
-            s.branch[2] = j.ex[8];
-            s.truncated = j.ex[9];
+            fill_stats(s, jobs[i]);
             s.tables_built = ctx->h_status[STAT_BUILT];
             s.rounds = ctx->h_status[STAT_EPOCHS];
             s.seconds = secs;
@@ -988,12 +1024,9 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             s.fill_ms = ctot > 0 ? kms * (double)(cyc[1] + cyc[2]) / ctot : 0.0;
             s.mw_ms = ctot > 0 ? kms * (double)cyc[3] / ctot : 0.0;
             s.launches = 1;
-            s.mw_jobs = j.ex[5];
-            s.walks_issued = issued[i];
             s.kernel_ms = kms;
         }
     }
-    cleanup();
     return FRW_OK;
 }
 
@@ -1025,6 +1058,7 @@ extern "C" int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jo
 {
     if (!ctx || (n_jobs > 0 && !jobs) || n_jobs < 0) return FRW_EINVAL;
     if (n_jobs == 0) return FRW_OK;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
     CK(cudaSetDevice(ctx->device));
     std::vector<JobRun> runs(n_jobs);
     for (int i = 0; i < n_jobs; i++) {
@@ -1033,22 +1067,8 @@ extern "C" int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jo
         runs[i].desc = jobs[i];
     }
     std::vector<frw_stats> st(n_jobs);
-    const bool any_walks = [&] {
-        for (int i = 0; i < n_jobs; i++)
-            if (jobs[i].walk_budget) return true;
-        return false;
-    }();
-    if (any_walks) {
-        int rc = run_jobs(ctx, runs, st.data());
-        if (rc) return rc;
-    } else {
-        for (int i = 0; i < n_jobs; i++) {
-            runs[i].d.n_c = ctx->structs[jobs[i].structure_id].n_c;
-            runs[i].S1.assign(runs[i].d.n_c + 1, 0);
-            runs[i].S2.assign(runs[i].d.n_c + 1, 0);
-            memset(&st[i], 0, sizeof(frw_stats));
-        }
-    }
+    int rc = run_jobs(ctx, runs, st.data());
+    if (rc) return rc;
     bool notconv = false;
     size_t off = 0;
     for (int i = 0; i < n_jobs; i++) {
@@ -1076,20 +1096,14 @@ extern "C" int frw_extract(frw_ctx *ctx, int32_t sid, int32_t master, const frw_
     // shard / resume: walk ids start at walk_begin (batches and the stop rule count from there)
     int rc = check_job(ctx, j);
     if (rc) return rc;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
     CK(cudaSetDevice(ctx->device));
     std::vector<JobRun> runs(1);
     runs[0].desc = j;
     runs[0].walk_begin = p->walk_begin;
     frw_stats st;
-    if (j.walk_budget) {
-        rc = run_jobs(ctx, runs, &st);
-        if (rc) return rc;
-    } else {
-        runs[0].d.n_c = ctx->structs[sid].n_c;
-        runs[0].S1.assign(runs[0].d.n_c + 1, 0);
-        runs[0].S2.assign(runs[0].d.n_c + 1, 0);
-        memset(&st, 0, sizeof(st));
-    }
+    rc = run_jobs(ctx, runs, &st);
+    if (rc) return rc;
     row_from(runs[0], C_row, stderr_row);
     if (stats) *stats = st;
     return (j.sigma_target > 0.0 && !runs[0].converged) ? FRW_ENOTCONV : FRW_OK;
@@ -1110,6 +1124,7 @@ extern "C" int frw_walk_records(frw_ctx *ctx, int32_t sid, int32_t master, uint6
     int rc = check_job(ctx, j);
     if (rc) return rc;
     if (n_walks == 0) return FRW_OK;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
     CK(cudaSetDevice(ctx->device));
     std::vector<JobRun> runs(1);
     runs[0].desc = j;
@@ -1140,9 +1155,14 @@ extern "C" int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, con
     if (!ctx || (n_cubes > 0 && !d_cubes) || !eps_r || n_mat < 1 || n_mat > FRW_MAX_MATERIALS) return FRW_EINVAL;
     if (N != ctx->opt.N) return fail(ctx, FRW_EINVAL, "cube lattice edge must equal the context's N");
     if (n_cubes <= 0 || samples_per_cube == 0) return FRW_OK;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
     CK(cudaSetDevice(ctx->device));
     std::vector<uint8_t> map;
-    int rc = register_materials(ctx, eps_r, n_mat, map);
+    int rc;
+    {
+        std::lock_guard<std::mutex> ls(ctx->struct_mu);
+        rc = register_materials(ctx, eps_r, n_mat, map);
+    }
     if (rc) return rc;
     std::vector<void *> tmp;
     unsigned long long *d_head = nullptr;
@@ -1170,11 +1190,16 @@ extern "C" int frw_table(frw_ctx *ctx, int32_t kind, const int32_t *profile, con
     const int N = ctx->opt.N;
     const bool hom = (kind == TAB_SGF_HOM || kind == TAB_FLUX_HOM);
     uint32_t prof[4] = {0, 0, 0, 0};
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
     CK(cudaSetDevice(ctx->device));
     if (!hom) {
         if (!profile || !eps_r || n_mat < 1) return FRW_EINVAL;
         std::vector<uint8_t> map;
-        int rc = register_materials(ctx, eps_r, n_mat, map);
+        int rc;
+        {
+            std::lock_guard<std::mutex> ls(ctx->struct_mu);
+            rc = register_materials(ctx, eps_r, n_mat, map);
+        }
         if (rc) return rc;
         for (int i = 0; i < N; i++) {
             if (profile[i] < 0 || profile[i] >= n_mat) return fail(ctx, FRW_EINVAL, "profile material out of range");
@@ -1209,4 +1234,406 @@ extern "C" int frw_table(frw_ctx *ctx, int32_t kind, const int32_t *profile, con
     if (neg)
         for (size_t n = 0; n < P; n++) neg[n] = (hs[n >> 5] >> (n & 31)) & 1u;
     return FRW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving.  Requests submitted from any host thread queue in arrival order; a
+// scheduler thread admits them into an open run of the persistent walk kernel as
+// long as the run's job table and arenas have room (admission by memory).  Their
+// walks interleave on the device with the walks of earlier requests, and each
+// request completes as soon as its own stop rule holds (the host polls the job
+// states through copies on a second stream while the kernel runs).  A run closes
+// when a request needs more room than is left, or after a quiet spell; the next
+// request starts a new run.
+namespace {
+
+struct Ticket {
+    JobRun run;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    int state = 0;            // 0 queued, 1 on the device, 2 done
+    int rc = FRW_OK;
+};
+
+struct ServeRun {
+    bool active = false, closing = false;
+    Arena A;                  // arena ends (bump allocation)
+    uint32_t jcap = 0;
+    uint64_t wcap = 0, bcap = 0, acap = 0, scap = 0;
+    int max_nc = 1, n_mat = 0;
+    uint32_t pool = 0;
+    uint64_t slots = 0;
+    std::vector<uint64_t> ids;          // ticket of each published job
+    std::vector<char> finished;
+    uint32_t lo = 0;                    // every job below is finished
+    std::chrono::steady_clock::time_point t_start, t_quiet;
+    PublishStage P;
+};
+
+struct Server {
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool quit = false;
+    uint64_t next_ticket = 1;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, std::unique_ptr<Ticket>> tickets;
+    cudaStream_t st = nullptr;          // run set-up and the kernel
+    cudaStream_t poll = nullptr;        // publications, job-state copies and control words while it runs
+    cudaEvent_t ev_end = nullptr;
+    JobState *h_js = nullptr;           // pinned
+    unsigned long long *h_buf = nullptr;   // pinned: one job's sums + its issued count
+    size_t h_js_cap = 0, h_buf_cap = 0;
+    ServeRun R;
+};
+
+}  // namespace
+
+static double serve_quiet_s() { return 0.5; }   // an idle open run closes after this long
+
+// admission verdict for one request: 0 fits now, 1 fits a new run, 2 never fits
+static int serve_fits(frw_ctx *ctx, const ServeRun &R, const Ticket &t, int *why)
+{
+    const frw_job &j = t.run.desc;
+    if (j.structure_id < 0 || j.structure_id >= (int)ctx->structs.size() || !ctx->structs[j.structure_id].live) {
+        *why = FRW_ENOTFOUND;
+        return 2;
+    }
+    const HostStructure &H = ctx->structs[j.structure_id];
+    const uint64_t batch = j.batch ? j.batch : 16384;
+    const uint64_t nb = (j.walk_budget + batch - 1) / batch;
+    const uint64_t aw = nb * acc_stride_for(H.n_c), sw = sum_words(H.n_c);
+    if (j.walk_budget > R.wcap || nb > R.bcap || aw > R.acap || sw > R.scap) {
+        *why = FRW_ENOMEM;
+        return 2;
+    }
+    if (H.n_c > R.max_nc || H.mat_need > R.n_mat) return 1;   // the run's kernel was set up without it
+    if (R.A.jobs >= R.jcap || R.A.walks + j.walk_budget > R.wcap || R.A.batches + nb > R.bcap ||
+        R.A.acc + aw > R.acap || R.A.sums + sw > R.scap)
+        return 1;
+    return 0;
+}
+
+static int serve_start_run(frw_ctx *ctx, Server &S)
+{
+    ServeRun &R = S.R;
+    ctx->engine_mu.lock();
+    R = ServeRun();
+    {
+        std::lock_guard<std::mutex> lk(ctx->struct_mu);
+        for (const auto &H : ctx->structs)
+            if (H.live) R.max_nc = std::max(R.max_nc, H.n_c);
+        R.n_mat = (int)ctx->eps.size();
+    }
+    const int64_t mb = ctx->opt.serve_arena_mb > 0 ? ctx->opt.serve_arena_mb : 4096;
+    R.jcap = ctx->opt.serve_jobs > 0 ? (uint32_t)ctx->opt.serve_jobs : 4096u;
+    R.wcap = ((uint64_t)mb << 20) / 32;                 // 32 bytes of records per walk
+    R.bcap = R.wcap / 1024 + R.jcap;                    // batches of >= 1024 walks, one partial per job
+    R.acap = R.bcap * acc_stride_for(R.max_nc);
+    R.scap = (uint64_t)R.jcap * sum_words(R.max_nc);
+    int rc;
+    if ((rc = ensure_records(ctx, R.wcap)) || (rc = ensure_runbufs(ctx, R.jcap, R.bcap, R.acap, R.scap))) {
+        ctx->engine_mu.unlock();
+        return rc;
+    }
+    if (S.h_js_cap < R.jcap) {
+        if (S.h_js) cudaFreeHost(S.h_js);
+        S.h_js = nullptr;
+        if (cudaMallocHost(&S.h_js, sizeof(JobState) * R.jcap) != cudaSuccess) {
+            ctx->engine_mu.unlock();
+            return fail(ctx, FRW_ENOMEM, "pinned job-state buffer");
+        }
+        S.h_js_cap = R.jcap;
+    }
+    const size_t hb = sum_words(R.max_nc) + 1;
+    if (S.h_buf_cap < hb) {
+        if (S.h_buf) cudaFreeHost(S.h_buf);
+        S.h_buf = nullptr;
+        if (cudaMallocHost(&S.h_buf, sizeof(unsigned long long) * hb) != cudaSuccess) {
+            ctx->engine_mu.unlock();
+            return fail(ctx, FRW_ENOMEM, "pinned result buffer");
+        }
+        S.h_buf_cap = hb;
+    }
+    R.pool = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
+    R.slots = (uint64_t)R.pool * ctx->grid;
+    Arena full;
+    full.jobs = R.jcap;
+    full.walks = R.wcap;
+    full.batches = R.bcap;
+    full.acc = R.acap;
+    full.sums = R.scap;
+    static const uint32_t ctrl_open[CTRL_WORDS] = {1u, 0u, 0u, 0u};
+    cudaError_t e = zero_run(ctx, R.jcap, full, S.st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ctrl, ctrl_open, sizeof(ctrl_open), cudaMemcpyHostToDevice, S.st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, S.st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, S.st);
+    // the set-up is complete before the kernel starts and before any publication
+    // (publications and polls go through the second stream while the kernel runs)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
+    const EngineView E = run_view(ctx, R.jcap, R.max_nc, R.pool, R.bcap);
+    if (e == cudaSuccess) e = launch_walk(E, ctx->shape, S.st);
+    if (e == cudaSuccess) e = cudaEventRecord(S.ev_end, S.st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(S.st);
+        ctx->engine_mu.unlock();
+        return cuda_fail(ctx, e, "serving run start");
+    }
+    R.active = true;
+    R.t_start = R.t_quiet = std::chrono::steady_clock::now();
+    return FRW_OK;
+}
+
+static void serve_complete(Server &S, Ticket &t, int rc)
+{
+    t.rc = rc;
+    t.state = 2;
+    t.t_done = std::chrono::steady_clock::now();
+    S.cv_done.notify_all();
+}
+
+// copy the states of the run's unfinished jobs; finish every decided one
+static int serve_poll(frw_ctx *ctx, Server &S)
+{
+    ServeRun &R = S.R;
+    const uint32_t pub = (uint32_t)R.ids.size();
+    if (pub <= R.lo) return FRW_OK;
+    const uint32_t n = pub - R.lo;
+    CK(cudaMemcpyAsync(S.h_js + R.lo, ctx->rb.js + R.lo, sizeof(JobState) * n, cudaMemcpyDeviceToHost, S.poll));
+    CK(cudaStreamSynchronize(S.poll));
+    for (uint32_t i = R.lo; i < pub; i++) {
+        if (R.finished[i] || S.h_js[i].decided == 0u) continue;
+        // decided: the job's sums and state are final; read them again, in full
+        Ticket *tp;
+        {
+            std::lock_guard<std::mutex> lk(S.mu);
+            tp = S.tickets[R.ids[i]].get();
+        }
+        JobRun &j = tp->run;
+        const uint32_t words = acc_stride_for(j.d.n_c);
+        CK(cudaMemcpyAsync(S.h_js + i, ctx->rb.js + i, sizeof(JobState), cudaMemcpyDeviceToHost, S.poll));
+        CK(cudaMemcpyAsync(S.h_buf, ctx->rb.jsum + j.sum_off, sizeof(unsigned long long) * words,
+                           cudaMemcpyDeviceToHost, S.poll));
+        CK(cudaMemcpyAsync(S.h_buf + words, ctx->rb.next + i, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           S.poll));
+        CK(cudaStreamSynchronize(S.poll));
+        take_result(j, S.h_js[i], S.h_buf, S.h_buf[words]);
+        R.finished[i] = 1;
+        std::lock_guard<std::mutex> lk(S.mu);
+        serve_complete(S, *tp, j.desc.sigma_target > 0.0 && !j.converged ? FRW_ENOTCONV : FRW_OK);
+    }
+    while (R.lo < pub && R.finished[R.lo]) R.lo++;
+    return FRW_OK;
+}
+
+static void serve_end_run(frw_ctx *ctx, Server &S, int rc_run)
+{
+    ServeRun &R = S.R;
+    cudaStreamSynchronize(S.st);
+    int rc = rc_run ? rc_run : check_status(ctx, S.st);
+    if (!rc) rc = serve_poll(ctx, S);
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        for (size_t i = 0; i < R.ids.size(); i++)
+            if (!R.finished[i]) serve_complete(S, *S.tickets[R.ids[i]], rc ? rc : FRW_EDEVICE);
+    }
+    R.active = false;
+    R.closing = false;
+    ctx->engine_mu.unlock();
+}
+
+static void serve_loop(frw_ctx *ctx)
+{
+    Server &S = *ctx->srv;
+    cudaSetDevice(ctx->device);
+    static const uint32_t closed = 0u;
+    for (;;) {
+        ServeRun &R = S.R;
+        if (!R.active) {
+            {
+                std::unique_lock<std::mutex> lk(S.mu);
+                S.cv_work.wait(lk, [&] { return S.quit || !S.queue.empty(); });
+                if (S.queue.empty()) break;   // quit with nothing queued
+            }
+            const int rc = serve_start_run(ctx, S);
+            if (rc) {
+                std::lock_guard<std::mutex> lk(S.mu);
+                while (!S.queue.empty()) {
+                    serve_complete(S, *S.tickets[S.queue.front()], rc);
+                    S.queue.pop_front();
+                }
+                continue;
+            }
+        }
+        // admission, in arrival order
+        std::vector<JobRun *> adm;
+        bool want_close = false;
+        {
+            std::lock_guard<std::mutex> lk(S.mu);
+            std::lock_guard<std::mutex> ls(ctx->struct_mu);
+            while (!R.closing && !S.queue.empty()) {
+                Ticket &t = *S.tickets[S.queue.front()];
+                if (t.run.desc.walk_budget == 0) {   // nothing to run: an all-zero row
+                    const int nc = t.run.desc.structure_id >= 0 && t.run.desc.structure_id < (int)ctx->structs.size()
+                                       ? ctx->structs[t.run.desc.structure_id].n_c : 0;
+                    t.run.d.n_c = nc;
+                    t.run.S1.assign(nc + 1, 0);
+                    t.run.S2.assign(nc + 1, 0);
+                    serve_complete(S, t, FRW_OK);
+                    S.queue.pop_front();
+                    continue;
+                }
+                int why = FRW_OK;
+                const int v = serve_fits(ctx, R, t, &why);
+                if (v == 2) {
+                    serve_complete(S, t, why);
+                    S.queue.pop_front();
+                    continue;
+                }
+                if (v == 1) {
+                    want_close = true;
+                    break;
+                }
+                place_job(ctx, t.run, R.A);
+                t.state = 1;
+                adm.push_back(&t.run);
+                R.ids.push_back(S.queue.front());
+                R.finished.push_back(0);
+                S.queue.pop_front();
+            }
+        }
+        int rc = FRW_OK;
+        if (!adm.empty()) {
+            int n_sigma = 0;
+            for (size_t i = R.lo; i < R.ids.size(); i++) n_sigma += R.finished[i] ? 0 : 1;
+            for (JobRun *j : adm) j->first_limit = first_wave(*j, R.slots, n_sigma);
+            const uint32_t j0 = (uint32_t)(R.ids.size() - adm.size());
+            cudaError_t e = publish_jobs(ctx, adm.data(), j0, (uint32_t)adm.size(), R.P, S.poll);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(S.poll);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "serving publication");
+            R.t_quiet = std::chrono::steady_clock::now();
+        }
+        if (!rc) rc = serve_poll(ctx, S);
+        const auto now = std::chrono::steady_clock::now();
+        const bool all_done = R.lo == (uint32_t)R.ids.size();
+        if (!all_done) R.t_quiet = now;
+        bool quit_now;
+        {
+            std::lock_guard<std::mutex> lk(S.mu);
+            quit_now = S.quit && S.queue.empty();
+        }
+        const bool quiet = all_done && std::chrono::duration<double>(now - R.t_quiet).count() > serve_quiet_s();
+        const bool overdue = std::chrono::duration<double>(now - R.t_start).count() > run_timeout_s();
+        if (!R.closing && (rc || want_close || quiet || quit_now || overdue)) {
+            if (overdue) {
+                static const uint32_t abort1 = 1;
+                cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, S.poll);
+                if (!rc) rc = fail(ctx, FRW_ETIMEOUT, "serving run exceeded its wall-clock limit (FRW_RUN_TIMEOUT_S)");
+            }
+            cudaMemcpyAsync(ctx->ctrl + CTRL_OPEN, &closed, sizeof(uint32_t), cudaMemcpyHostToDevice, S.poll);
+            cudaStreamSynchronize(S.poll);
+            R.closing = true;
+        }
+        if (R.closing && cudaEventQuery(S.ev_end) != cudaErrorNotReady) {
+            serve_end_run(ctx, S, rc);
+            continue;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(30));
+    }
+}
+
+static int start_server(frw_ctx *ctx)
+{
+    if (ctx->srv) return FRW_OK;
+    std::unique_ptr<Server> S(new Server());
+    if (cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->poll, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->ev_end, cudaEventDisableTiming) != cudaSuccess)
+        return fail(ctx, FRW_EDEVICE, "serving streams");
+    ctx->srv = S.release();
+    ctx->srv->th = std::thread(serve_loop, ctx);
+    return FRW_OK;
+}
+
+static void stop_server(frw_ctx *ctx)
+{
+    Server *S = ctx->srv;
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->quit = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    if (S->h_js) cudaFreeHost(S->h_js);
+    if (S->h_buf) cudaFreeHost(S->h_buf);
+    if (S->ev_end) cudaEventDestroy(S->ev_end);
+    if (S->st) cudaStreamDestroy(S->st);
+    if (S->poll) cudaStreamDestroy(S->poll);
+    delete S;
+    ctx->srv = nullptr;
+}
+
+extern "C" int frw_submit(frw_ctx *ctx, const frw_job *job, uint64_t *ticket)
+{
+    if (!ctx || !job || !ticket) return FRW_EINVAL;
+    {
+        std::lock_guard<std::mutex> ls(ctx->struct_mu);
+        const int rc = check_job(ctx, *job);
+        if (rc) return rc;
+    }
+    if (!ctx->srv) {
+        const int rc = start_server(ctx);
+        if (rc) return rc;
+    }
+    Server &S = *ctx->srv;
+    std::unique_ptr<Ticket> t(new Ticket());
+    t->run.desc = *job;
+    t->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        const uint64_t id = S.next_ticket++;
+        S.tickets[id] = std::move(t);
+        S.queue.push_back(id);
+        *ticket = id;
+    }
+    S.cv_work.notify_all();
+    return FRW_OK;
+}
+
+extern "C" int frw_poll(frw_ctx *ctx, uint64_t ticket, int32_t *done)
+{
+    if (!ctx || !done) return FRW_EINVAL;
+    if (!ctx->srv) return FRW_ENOTFOUND;
+    Server &S = *ctx->srv;
+    std::lock_guard<std::mutex> lk(S.mu);
+    auto it = S.tickets.find(ticket);
+    if (it == S.tickets.end()) return FRW_ENOTFOUND;
+    *done = it->second->state == 2 ? 1 : 0;
+    return FRW_OK;
+}
+
+extern "C" int frw_wait(frw_ctx *ctx, uint64_t ticket, double timeout_s, double *C_row, double *stderr_row,
+                        frw_stats *stats)
+{
+    if (!ctx) return FRW_EINVAL;
+    if (!ctx->srv) return FRW_ENOTFOUND;
+    Server &S = *ctx->srv;
+    std::unique_lock<std::mutex> lk(S.mu);
+    auto it = S.tickets.find(ticket);
+    if (it == S.tickets.end()) return FRW_ENOTFOUND;
+    Ticket *t = it->second.get();
+    const auto pred = [&] { return t->state == 2; };
+    if (timeout_s < 0) S.cv_done.wait(lk, pred);
+    else if (!S.cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) return FRW_ETIMEOUT;
+    const int rc = t->rc;
+    if (rc == FRW_OK || rc == FRW_ENOTCONV) {
+        row_from(t->run, C_row, stderr_row);
+        if (stats) {
+            fill_stats(*stats, t->run);
+            stats->seconds = std::chrono::duration<double>(t->t_done - t->t_submit).count();
+            stats->launches = 0;
+        }
+    }
+    S.tickets.erase(it);
+    return rc;
 }
