@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2507_09730_gb300 import workloads as W  # noqa: E402
 
-METRIC = "FRW walks/s at 0.5% 1-sigma (interconnect, N=24)"
+METRIC = "FRW walks/s and MicroWalk transitions/s at 1% 1\u03c3; request p50/p99 latency"
 UNIT = "walks/s"
 INT_OPS_PER_MICRO_STEP = 45   # algorithmic integer ops of one MicroWalk step
 
@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="arrival window of the serving measurement at 200 req/s (0: skip it)")
     return ap.parse_args()
 
 
@@ -202,6 +204,62 @@ def traffic_per_launch(agg, n_launch):
     return DRAM_BYTES_PER_WALK * agg["issued"] / n_launch
 
 
+SERVE_BUDGET = 4_000_000     # walk budget (cap) of one served request
+
+
+def serving_measurement(N, precision, rate, duration, seed=0):
+    """Serving form: Poisson arrivals of extraction requests over a pool of 32
+    structures with 4-200 conductors, 1-sigma targets U[0.5 %, 2 %].  Served
+    through frw_submit (admitted into the running walk kernel as room frees up)
+    and, on the same arrival times, one request per launch in arrival order
+    (frw_extract).  Latency = completion - arrival."""
+    from paper_2507_09730_gb300 import binding as B
+    pool = W.serving_pool(32)
+    reqs = W.serving_requests(pool, rate=rate, duration=duration, seed=seed)
+    ctx = B.Context(0, N=N, precision=precision, seed=0, serve_arena_mb=16384, serve_jobs=4096)
+    sids = [ctx.load(st) for st in pool]
+    ctx.extract_batch([dict(structure_id=sid, master=m, walk_budget=20000, request_id=1 + m)
+                       for sid, st in zip(sids, pool) for m in range(0, st.n_cond, max(1, st.n_cond // 4))])
+
+    def job(i, r):
+        return dict(structure_id=sids[r.structure], master=r.master, walk_budget=SERVE_BUDGET, sigma_target=r.sigma,
+                    request_id=10_000 + i)
+
+    t0 = time.perf_counter()
+    tickets = []
+    for i, r in enumerate(reqs):
+        dt = r.t - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(ctx.submit(job(i, r)))
+    lat, walks, rows = [], 0, []
+    for t in tickets:
+        C, se, st, conv = ctx.wait(t)
+        lat.append(st["seconds"])
+        walks += st["walks"]
+        rows.append(C)
+    span = time.perf_counter() - t0
+    served = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+              "walks_per_s": walks / span, "makespan_s": span}
+    t0 = time.perf_counter()
+    lat_b, walks_b, same = [], 0, 0
+    for i, r in enumerate(reqs):
+        dt = r.t - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        C, se, st, conv = ctx.extract(sids[r.structure], r.master, SERVE_BUDGET, r.sigma, 10_000 + i)
+        lat_b.append(time.perf_counter() - t0 - r.t)
+        walks_b += st["walks"]
+        same += int(np.array_equal(C, rows[i]))
+    span_b = time.perf_counter() - t0
+    ctx.close()
+    return {"rate_per_s": rate, "arrival_window_s": duration, "requests": len(reqs),
+            "walks_per_request": walks / max(1, len(reqs)), "served": served,
+            "one_job_per_launch": {"p50_s": float(np.percentile(lat_b, 50)), "p99_s": float(np.percentile(lat_b, 99)),
+                                   "walks_per_s": walks_b / span_b, "makespan_s": span_b},
+            "identical_results": same}
+
+
 def structure_bytes(s):
     return (s.cond_lo.nbytes + s.cond_hi.nbytes + s.block_lo.nbytes + s.block_hi.nbytes + s.block_mat.nbytes +
             s.eps.nbytes + 48 + 40 * len(s.masters))
@@ -334,8 +392,9 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * t_all / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "interconnect 3-layer/24-wire + shells + 12 LDE, N=%d, masters %s, sigma %.3g, "
-                                   "budget %d/master" % (a.N, masters, a.sigma, a.budget),
+            "config": {"workload": "interconnect 3-layer/24-wire + shells + 12 LDE, N=%d, masters %s, sigma %.3g "
+                                   "(the interconnect configuration's target), budget %d/master"
+                                   % (a.N, masters, a.sigma, a.budget),
                        "geometry": a.precision, "accumulate": "exact int128 (fp64 in/out)",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"weak x{world}"},
             "micro_transitions_per_s": agg["micro"] * (walks_all / max(1, agg["walks"])) / t_all,
@@ -344,6 +403,13 @@ def main():
             "gpu_launches": agg["launches"], "roofline": roofline, "clocks": clocks}
     if e2e:
         line["e2e"] = e2e
+    if rank == 0 and world == 1 and a.serve_seconds > 0:
+        line["serving"] = {
+            "workload": "Poisson arrivals over 32 structures of 4-200 conductors, N=%d, sigma U[0.5%%, 2%%], "
+                        "budget %d per request; served = frw_submit into the running kernel, "
+                        "one_job_per_launch = frw_extract in arrival order, same GPU" % (a.N, SERVE_BUDGET),
+            "at_200_per_s": serving_measurement(a.N, prec, 200.0, a.serve_seconds),
+            "at_25_per_s": serving_measurement(a.N, prec, 25.0, 2.0 * a.serve_seconds)}
     if rank == 0 and world == 1 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(s, masters, a.N, a.cpu_seconds)
     if rank == 0:

@@ -885,13 +885,17 @@ static void fill_stats(frw_stats &s, const JobRun &j)
     s.walks_issued = j.issued;
 }
 
-// first issue limit of a sigma job: its share of the slot pool (the device then
-// steers the limit from the completed prefix), at least 4 batches
-static uint64_t first_wave(const JobRun &j, uint64_t slots, int n_sigma)
+// first issue limit of a sigma job: 1/div of its share of the slot pool, at least
+// 4 batches; the device then steers the limit to the need predicted from the
+// completed prefix.  Closed runs (throughput) take the whole share (div 1).  The
+// serving loop (latency) takes an eighth: the stop rule reads a prefix of walk
+// ids, and walks issued together finish together, so a request that needs few
+// walks would otherwise wait for a whole pool of them.
+static uint64_t first_wave(const JobRun &j, uint64_t slots, int n_sigma, uint64_t div)
 {
     if (!(j.desc.sigma_target > 0.0)) return j.d.walk_count;
     const uint64_t b = j.d.batch;
-    uint64_t first = std::max<uint64_t>(4 * b, slots / (uint64_t)std::max(1, n_sigma));
+    uint64_t first = std::max<uint64_t>(4 * b, slots / (div * (uint64_t)std::max(1, n_sigma)));
     first = (first + b - 1) / b * b;
     return std::min<uint64_t>(first, j.d.walk_count);
 }
@@ -968,7 +972,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     const uint64_t run_slots = (uint64_t)run_pool * ctx->grid;
     int n_sigma = 0;
     for (JobRun *j : live) n_sigma += j->desc.sigma_target > 0.0 ? 1 : 0;
-    for (JobRun *j : live) j->first_limit = first_wave(*j, run_slots, n_sigma);
+    for (JobRun *j : live) j->first_limit = first_wave(*j, run_slots, n_sigma, 1);
     cudaStream_t st = ctx->stream, ax = ctx->aux;
     PublishStage P;
     const uint32_t ctrl0[CTRL_WORDS] = {0u, 0u, 0u, 0u};
@@ -1505,7 +1509,7 @@ static void serve_loop(frw_ctx *ctx)
         if (!adm.empty()) {
             int n_sigma = 0;
             for (size_t i = R.lo; i < R.ids.size(); i++) n_sigma += R.finished[i] ? 0 : 1;
-            for (JobRun *j : adm) j->first_limit = first_wave(*j, R.slots, n_sigma);
+            for (JobRun *j : adm) j->first_limit = first_wave(*j, R.slots, n_sigma, 8);
             const uint32_t j0 = (uint32_t)(R.ids.size() - adm.size());
             cudaError_t e = publish_jobs(ctx, adm.data(), j0, (uint32_t)adm.size(), R.P, S.poll);
             if (e == cudaSuccess) e = cudaStreamSynchronize(S.poll);

@@ -227,6 +227,29 @@ def serving_pool(n_structures: int = 32, seed: int = 0):
     return batched_family(n_structures, seed=1000 + seed, n_min=4, n_max=200)
 
 
+@dataclass
+class Request:
+    t: float            # arrival time (s from the start)
+    structure: int      # index into the pool
+    master: int
+    sigma: float        # relative 1-sigma target
+
+
+def serving_requests(pool, rate: float = 200.0, duration: float = 60.0, seed: int = 0,
+                     sigma_lo: float = 0.005, sigma_hi: float = 0.02):
+    """Poisson arrivals of mean `rate` per second over `duration` seconds; each
+    request draws a structure of the pool, a master among its conductors and a
+    1-sigma target uniform in [sigma_lo, sigma_hi]."""
+    rng = np.random.default_rng(np.random.SeedSequence([4, seed]))
+    out, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return out
+        k = int(rng.integers(0, len(pool)))
+        out.append(Request(t, k, int(rng.integers(0, pool[k].n_cond)), float(rng.uniform(sigma_lo, sigma_hi))))
+
+
 # ---------------------------------------------------------------------------
 # Workload 1: random transition cubes given directly as integer voxel ranges
 # ---------------------------------------------------------------------------
