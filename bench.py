@@ -204,6 +204,64 @@ def traffic_per_launch(agg, n_launch):
     return DRAM_BYTES_PER_WALK * agg["issued"] / n_launch
 
 
+def microwalk_kernel(alu_peak, steps_timed=3):
+    """MicroWalk transition kernel alone (Algorithm 3): 2^24 samples from the
+    centres of 1024 random N = 16 cubes (16384 each), 2-6 blocks per cube with
+    permittivities from {2.5, 3.9, 7.0, 25.0}; CUDA events on the launch stream."""
+    import torch
+    from paper_2507_09730_gb300 import binding as B
+    N, n_cubes, spc = 16, 1024, 16384
+    cubes = W.random_cubes(n_cubes, N=N, seed=0)
+    rec = torch.from_numpy(B.pack_cubes(cubes)).cuda()
+    n = n_cubes * spc
+    ex = torch.empty(n, dtype=torch.int32, device="cuda")
+    stp = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx = B.Context(0, N=N, slots=1 << 12)
+    stream = torch.cuda.current_stream()
+    B.frw_set_stream(ctx.ctx, stream.cuda_stream)
+    run = lambda r: B.frw_microwalk_cubes(ctx.ctx, N, n_cubes, rec.data_ptr(), cubes.eps, spc, r, ex.data_ptr(),
+                                          stp.data_ptr())
+    for r in range(3):
+        run(r)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in range(steps_timed):
+        run(100 + r)
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3 / steps_timed
+    steps = int(stp.to(torch.int64).sum().item())
+    ctx.close()
+    ach = INT_OPS_PER_MICRO_STEP * steps / secs / 1e12
+    return {"workload": "2^24 samples, 1024 random N=16 cubes x 16384, eps {2.5,3.9,7.0,25.0}",
+            "samples_per_s": n / secs, "micro_transitions_per_s": steps / secs, "ms_per_launch": 1e3 * secs,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tint-op/s",
+                         "frac": ach / alu_peak}}
+
+
+def fp32_deviation(s, masters, N, sigma, budget):
+    """FP32 cube geometry against FP64 geometry on the same requests: the walks
+    differ only where a geometric decision differs, so the rows agree within
+    their combined standard errors; reported per master as (C32 - C64) / C64 for
+    C_ii and that difference in combined standard errors."""
+    from paper_2507_09730_gb300 import binding as B
+    out = []
+    rows = {}
+    for prec in (B.FRW_FP32_GEOM, B.FRW_FP64_GEOM):
+        ctx = B.Context(0, N=N, precision=prec, seed=0)
+        sid = ctx.load(s)
+        res, _ = ctx.extract_batch([dict(structure_id=sid, master=m, walk_budget=budget, sigma_target=sigma,
+                                         request_id=777 + i) for i, m in enumerate(masters)])
+        rows[prec] = res
+        ctx.close()
+    for m, (C32, se32, _), (C64, se64, _) in zip(masters, rows[B.FRW_FP32_GEOM], rows[B.FRW_FP64_GEOM]):
+        d = C32[m] - C64[m]
+        out.append({"master": m, "C_ii_fp64": C64[m], "rel_dev": d / C64[m],
+                    "dev_in_sigma": d / float(np.hypot(se32[m], se64[m]))})
+    return out
+
+
 SERVE_BUDGET = 4_000_000     # walk budget (cap) of one served request
 
 
@@ -403,6 +461,9 @@ def main():
             "gpu_launches": agg["launches"], "roofline": roofline, "clocks": clocks}
     if e2e:
         line["e2e"] = e2e
+    if rank == 0 and world == 1:
+        line["microwalk_kernel"] = microwalk_kernel(alu_peak)
+        line["fp32_vs_fp64"] = fp32_deviation(s, masters, a.N, a.sigma, a.budget)
     if rank == 0 and world == 1 and a.serve_seconds > 0:
         line["serving"] = {
             "workload": "Poisson arrivals over 32 structures of 4-200 conductors, N=%d, sigma U[0.5%%, 2%%], "
