@@ -176,6 +176,48 @@ typedef struct {
 int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs, double *C_rows,
                       double *stderr_rows, frw_stats *stats);
 
+/* Batching with a captured launch (the paper has no counterpart).  A plan lays a
+ * fixed set of jobs out once, in a job table, arenas and record pool of its own,
+ * and captures its whole launch sequence (arena reset, job publication from
+ * pinned host staging, the persistent walk kernel) in a CUDA graph.  Each
+ * frw_plan_run replays the graph with request ids shifted by request_offset
+ * (job i runs as request jobs[i].request_id + request_offset) and returns the
+ * rows as frw_extract_batch does (same layout, same results for the same ids).
+ * A plan keeps its device memory until frw_plan_destroy; destroy plans before
+ * their context. */
+typedef struct frw_plan frw_plan;
+int frw_plan_create(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs, frw_plan **out);
+int frw_plan_run(frw_plan *plan, uint64_t request_offset, double *C_rows, double *stderr_rows,
+                 frw_stats *stats);
+void frw_plan_destroy(frw_plan *plan);
+
+/* Launch settings of the walk kernel and of the stand-alone MicroWalk kernel.
+ * No setting changes any result (walks are keyed by their ids and accumulated
+ * exactly); they change only speed. */
+typedef struct {
+    int32_t pool_per_cta;      /* walk slots per CTA of the walk kernel (256 .. 4096, multiple of 256;
+                                  at most the context's pool) */
+    int32_t hops_per_epoch;    /* analytical hops one walk may take per epoch (1 .. 64) */
+    int32_t mw_warps_per_cta;  /* stand-alone MicroWalk kernel: warps per CTA (1 .. 16) */
+    int32_t mw_ctas_per_sm;    /* ... CTAs per SM (1 .. 32) */
+    double walks_per_s;        /* frw_autotune: measured with the chosen walk-kernel settings */
+    double mw_steps_per_s;     /* frw_autotune: measured with the chosen MicroWalk shape */
+} frw_tuning;
+
+int frw_get_tuning(frw_ctx *ctx, frw_tuning *out);
+int frw_set_tuning(frw_ctx *ctx, const frw_tuning *t);   /* FRW_EINVAL outside the ranges above */
+
+/* Autotuner: runs the sample jobs in budget mode (each capped at sample_walks
+ * walks) once per candidate walk-kernel setting (slots per CTA in {1024, 2048,
+ * 3072, 4096} x analytical hops per epoch in {4, 8, 16}) and keeps the fastest;
+ * then times the stand-alone MicroWalk kernel on 512 random cubes of the
+ * context's N (2-6 blocks of up to four of its registered materials, 4096
+ * samples each) for each shape (warps per CTA x
+ * CTAs per SM in {8x2, 8x4, 16x1, 16x2, 16x3}) and keeps the fastest.  The
+ * chosen settings apply to later calls; *out (may be NULL) receives them. */
+int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sample, uint64_t sample_walks,
+                 frw_tuning *out);
+
 /* Serving (the paper has no counterpart: a deployment form of Algorithm 1's
  * extraction).  frw_submit queues one extraction and returns at once with a
  * ticket; a scheduler thread of the context admits queued requests, in arrival

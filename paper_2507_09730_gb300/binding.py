@@ -21,7 +21,8 @@ FRW_TAB_SGF, FRW_TAB_FLUX_PAR, FRW_TAB_FLUX_PERP, FRW_TAB_SGF_HOM, FRW_TAB_FLUX_
 EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream", "frw_load_structure",
            "frw_unload_structure", "frw_extract", "frw_extract_batch", "frw_walk_records",
            "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
-           "frw_submit", "frw_poll", "frw_wait")
+           "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
+           "frw_get_tuning", "frw_set_tuning", "frw_autotune")
 
 
 class frw_box(ctypes.Structure):
@@ -48,6 +49,14 @@ class frw_extract_params(ctypes.Structure):
 class frw_job(ctypes.Structure):
     _fields_ = [("structure_id", c_int32), ("master", c_int32), ("walk_budget", c_uint64),
                 ("sigma_target", c_double), ("request_id", c_uint64), ("batch", c_uint64)]
+
+
+class frw_tuning(ctypes.Structure):
+    _fields_ = [("pool_per_cta", c_int32), ("hops_per_epoch", c_int32), ("mw_warps_per_cta", c_int32),
+                ("mw_ctas_per_sm", c_int32), ("walks_per_s", c_double), ("mw_steps_per_s", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class frw_stats(ctypes.Structure):
@@ -103,12 +112,19 @@ def lib():
     L.frw_submit.argtypes = [c_void_p, POINTER(frw_job), POINTER(c_uint64)]
     L.frw_poll.argtypes = [c_void_p, c_uint64, POINTER(c_int32)]
     L.frw_wait.argtypes = [c_void_p, c_uint64, c_double, P(c_double), P(c_double), POINTER(frw_stats)]
+    L.frw_plan_create.argtypes = [c_void_p, POINTER(frw_job), c_int32, POINTER(c_void_p)]
+    L.frw_plan_run.argtypes = [c_void_p, c_uint64, P(c_double), P(c_double), POINTER(frw_stats)]
+    L.frw_plan_destroy.argtypes = [c_void_p]
+    L.frw_plan_destroy.restype = None
+    L.frw_get_tuning.argtypes = [c_void_p, POINTER(frw_tuning)]
+    L.frw_set_tuning.argtypes = [c_void_p, POINTER(frw_tuning)]
+    L.frw_autotune.argtypes = [c_void_p, POINTER(frw_job), c_int32, c_uint64, POINTER(frw_tuning)]
     L.frw_strerror.argtypes = [c_int]
     L.frw_strerror.restype = ctypes.c_char_p
     L.frw_last_error.argtypes = [c_void_p]
     L.frw_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("frw_default_options", "frw_destroy", "frw_strerror", "frw_last_error"):
+        if name not in ("frw_default_options", "frw_destroy", "frw_strerror", "frw_last_error", "frw_plan_destroy"):
             getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -213,6 +229,65 @@ def frw_extract_batch(ctx, jobs, n_conds):
         out.append((C[off:off + nc + 1].copy(), se[off:off + nc + 1].copy(), st[i].as_dict()))
         off += nc + 1
     return out, rc == FRW_OK
+
+
+def _jobs_array(jobs):
+    arr = (frw_job * max(1, len(jobs)))()
+    for i, j in enumerate(jobs):
+        arr[i] = frw_job(int(j["structure_id"]), int(j["master"]), int(j["walk_budget"]),
+                         float(j.get("sigma_target", 0.0)), int(j.get("request_id", 0)), int(j.get("batch", 0)))
+    return arr
+
+
+class Plan:
+    """A fixed job set replayed through a captured CUDA graph (frw_plan_*)."""
+
+    def __init__(self, ctx, jobs, n_conds):
+        self.ctx = ctx
+        self.n_conds = list(n_conds)
+        h = c_void_p(0)
+        _check(ctx, lib().frw_plan_create(ctx, _jobs_array(jobs), len(jobs), ctypes.byref(h)))
+        self.h = h
+
+    def run(self, request_offset=0):
+        n = len(self.n_conds)
+        tot = sum(nc + 1 for nc in self.n_conds)
+        C = np.zeros(max(1, tot))
+        se = np.zeros(max(1, tot))
+        st = (frw_stats * max(1, n))()
+        rc = lib().frw_plan_run(self.h, int(request_offset), _ptr(C, c_double), _ptr(se, c_double), st)
+        _check(self.ctx, rc, (FRW_OK, FRW_ENOTCONV))
+        out, off = [], 0
+        for i, nc in enumerate(self.n_conds):
+            out.append((C[off:off + nc + 1].copy(), se[off:off + nc + 1].copy(), st[i].as_dict()))
+            off += nc + 1
+        return out, rc == FRW_OK
+
+    def close(self):
+        if self.h:
+            lib().frw_plan_destroy(self.h)
+            self.h = None
+
+
+def frw_get_tuning(ctx) -> dict:
+    t = frw_tuning()
+    _check(ctx, lib().frw_get_tuning(ctx, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def frw_set_tuning(ctx, **kw):
+    t = frw_tuning()
+    _check(ctx, lib().frw_get_tuning(ctx, ctypes.byref(t)))
+    for k, v in kw.items():
+        setattr(t, k, v)
+    _check(ctx, lib().frw_set_tuning(ctx, ctypes.byref(t)))
+
+
+def frw_autotune(ctx, sample_jobs, sample_walks) -> dict:
+    t = frw_tuning()
+    _check(ctx, lib().frw_autotune(ctx, _jobs_array(sample_jobs), len(sample_jobs), int(sample_walks),
+                                   ctypes.byref(t)))
+    return t.as_dict()
 
 
 def frw_submit(ctx, job) -> int:
@@ -349,6 +424,18 @@ class Context:
 
     def extract_batch(self, jobs):
         return frw_extract_batch(self.ctx, jobs, [self._n_cond.get(j["structure_id"], 0) for j in jobs])
+
+    def plan(self, jobs) -> Plan:
+        return Plan(self.ctx, jobs, [self._n_cond.get(j["structure_id"], 0) for j in jobs])
+
+    def tuning(self) -> dict:
+        return frw_get_tuning(self.ctx)
+
+    def set_tuning(self, **kw):
+        frw_set_tuning(self.ctx, **kw)
+
+    def autotune(self, sample_jobs, sample_walks=200_000) -> dict:
+        return frw_autotune(self.ctx, sample_jobs, sample_walks)
 
     def submit(self, job) -> int:
         t = frw_submit(self.ctx, job)

@@ -210,6 +210,7 @@ struct EngineView {
     uint32_t *ctrl;        // CTRL_WORDS (host -> device)
     unsigned long long *cycles;   // [5] CTA cycles: geometry busy, fill, reduce, MicroWalk busy, total
     double idle_timeout_s; // idle wait limit of the walk kernel
+    int hops_per_epoch;    // analytical hops one walk may take per epoch (tunable, >= 1)
 };
 
 // ---- launchers (frw_kernels.cu) ----
@@ -222,6 +223,9 @@ struct LaunchShape {
 };
 
 // the persistent walk kernel: runs every job of the view to completion
+// (prepare_walk sets its shared-memory limit; call it before launching, and
+// outside any stream capture)
+cudaError_t prepare_walk(const EngineView &E);
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 size_t walk_smem_bytes(int N, int max_nc);
 int walk_pool_slots();

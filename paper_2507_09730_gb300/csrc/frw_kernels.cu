@@ -736,7 +736,6 @@ __device__ FRW_OUTLINE bool issue_walk(const EngineView &E, IssueRanges &ir, Wal
     return true;
 }
 
-constexpr int HOPS_PER_EPOCH = 8;     // analytical hops one walk may take per epoch
 
 // Geometry-phase work of one slot: a new walk and its first transition if the
 // slot is free, then one step of the walk (Algorithm 1 inner loop): absorption
@@ -833,7 +832,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         panel_node(N, fr, m, node);
         node_point(pos, R, N, node, pos);
         w.hop++;
-        if (hops_here + 1 < HOPS_PER_EPOCH) continue;   // next hop of the same walk in this epoch
+        if (hops_here + 1 < E.hops_per_epoch) continue;   // next hop of the same walk in this epoch
     }
     if (wait || m >= 0) {
         E.s.pos[s] = (double)pos[0];
@@ -1878,20 +1877,20 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
     }
 }
 
+cudaError_t prepare_walk(const EngineView &E)
+{
+    const int smem = (int)walk_smem_bytes(E.N, E.max_nc);
+    return E.fp32 ? cudaFuncSetAttribute(k_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                  : cudaFuncSetAttribute(k_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st)
 {
     (void)L;
     const size_t smem = walk_smem_bytes(E.N, E.max_nc);
     const unsigned grid = E.NS / E.pool;
-    if (E.fp32) {
-        cudaError_t e = cudaFuncSetAttribute(k_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_walk<float><<<grid, WALK_THREADS, smem, st>>>(E);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_walk<double><<<grid, WALK_THREADS, smem, st>>>(E);
-    }
+    if (E.fp32) k_walk<float><<<grid, WALK_THREADS, smem, st>>>(E);
+    else k_walk<double><<<grid, WALK_THREADS, smem, st>>>(E);
     return cudaGetLastError();
 }
 

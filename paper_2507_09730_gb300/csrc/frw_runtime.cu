@@ -90,6 +90,7 @@ struct frw_ctx {
     std::mutex engine_mu;               // held for the whole of a run (closed or serving)
     std::mutex struct_mu;               // guards the host structure table against the serving thread
     Server *srv = nullptr;              // serving loop (started by the first frw_submit)
+    frw_tuning tune;                    // walk-kernel settings (defaults or frw_autotune)
 };
 
 static const char *kErr[] = {"ok",
@@ -198,6 +199,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.ctrl = ctx->ctrl;
     E.cycles = ctx->cycles;
     E.idle_timeout_s = 10.0;
+    E.hops_per_epoch = ctx->tune.hops_per_epoch;
     return E;
 }
 
@@ -315,6 +317,12 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         if (pool > (uint64_t)walk_pool_slots()) pool = walk_pool_slots();
         ctx->NS = (uint32_t)(pool * ctx->grid);
     }
+    ctx->tune.pool_per_cta = (int32_t)(ctx->NS / ctx->grid);
+    ctx->tune.hops_per_epoch = 8;
+    ctx->tune.mw_warps_per_cta = ctx->shape.mw_warps;
+    ctx->tune.mw_ctas_per_sm = ctx->shape.mw_ctas_per_sm;
+    ctx->tune.walks_per_s = 0.0;
+    ctx->tune.mw_steps_per_s = 0.0;
     uint32_t cap = opt.table_capacity > 0 ? (uint32_t)opt.table_capacity : (N <= 16 ? (1u << 16) : (1u << 14));
     uint32_t c2 = 1;
     while (c2 < cap) c2 <<= 1;
@@ -724,9 +732,8 @@ static int ensure_records(frw_ctx *ctx, uint64_t n)
 
 // job table and arenas, grown (never while a run is on the device) to at least the
 // given capacities
-static int ensure_runbufs(frw_ctx *ctx, uint32_t jcap, uint64_t bcap, uint64_t acap, uint64_t scap)
+static int grow_runbufs(frw_ctx *ctx, RunBufs &B, uint32_t jcap, uint64_t bcap, uint64_t acap, uint64_t scap)
 {
-    RunBufs &B = ctx->rb;
     if (jcap <= B.jcap && bcap <= B.bcap && acap <= B.acap && scap <= B.scap) return FRW_OK;
     jcap = std::max(jcap, B.jcap);
     bcap = std::max(bcap, B.bcap);
@@ -751,6 +758,11 @@ static int ensure_runbufs(frw_ctx *ctx, uint32_t jcap, uint64_t bcap, uint64_t a
     B.acap = acap;
     B.scap = scap;
     return FRW_OK;
+}
+
+static int ensure_runbufs(frw_ctx *ctx, uint32_t jcap, uint64_t bcap, uint64_t acap, uint64_t scap)
+{
+    return grow_runbufs(ctx, ctx->rb, jcap, bcap, acap, scap);
 }
 
 // Bump allocation of a run's arenas.
@@ -795,9 +807,8 @@ static void place_job(frw_ctx *ctx, JobRun &j, Arena &A)
 }
 
 // Zero a run's job table and arenas up to the given sizes (stream order).
-static cudaError_t zero_run(frw_ctx *ctx, uint32_t jobs, const Arena &A, cudaStream_t st)
+static cudaError_t zero_run(RunBufs &B, int32_t *rec_k, uint32_t jobs, const Arena &A, cudaStream_t st)
 {
-    RunBufs &B = ctx->rb;
     const uint64_t nb = std::max<uint64_t>(A.batches, 1);
     cudaError_t e;
     if ((e = cudaMemsetAsync(B.next, 0, sizeof(unsigned long long) * std::max<uint32_t>(jobs, 1), st)) ||
@@ -810,31 +821,27 @@ static cudaError_t zero_run(frw_ctx *ctx, uint32_t jobs, const Arena &A, cudaStr
         (e = cudaMemsetAsync(B.rq, 0xff, sizeof(uint32_t) * nb, st)) ||
         (e = cudaMemsetAsync(B.rqc, 0, sizeof(uint32_t) * 2, st)) ||
         (e = cudaMemsetAsync(B.jctl, 0, sizeof(uint32_t) * JC_WORDS, st)) ||
-        (e = cudaMemsetAsync(ctx->rec.k, 0x80, sizeof(int32_t) * std::max<uint64_t>(A.walks, 1), st)))
+        (e = cudaMemsetAsync(rec_k, 0x80, sizeof(int32_t) * std::max<uint64_t>(A.walks, 1), st)))
         return e;
     return cudaSuccess;
 }
 
-// Write jobs[j0 .. j0 + n) (table indices j0 ..) and then publish them: the kernel
-// sees a job only once the published count covers it (copies in stream order).
-// Host buffers must stay valid until the stream has run the copies.
+// Host image of jobs [j0, j0 + n) of a run's table.
 struct PublishStage {
     std::vector<DevJob> d;
     std::vector<unsigned long long> lim, off;
     std::vector<uint32_t> bjob;
+    uint64_t b0 = 0;
     uint32_t pub = 0;
 };
 
-static cudaError_t publish_jobs(frw_ctx *ctx, JobRun *const *jobs, uint32_t j0, uint32_t n, PublishStage &P,
-                                cudaStream_t st)
+static void stage_jobs(JobRun *const *jobs, uint32_t j0, uint32_t n, PublishStage &P)
 {
-    RunBufs &B = ctx->rb;
-    if (n == 0) return cudaSuccess;
     P.d.resize(n);
     P.lim.resize(n);
     P.off.resize(n);
     P.bjob.clear();
-    const uint64_t b0 = jobs[0]->d.batch_base;
+    P.b0 = n ? jobs[0]->d.batch_base : 0;
     for (uint32_t i = 0; i < n; i++) {
         const JobRun &j = *jobs[i];
         P.d[i] = j.d;
@@ -842,16 +849,32 @@ static cudaError_t publish_jobs(frw_ctx *ctx, JobRun *const *jobs, uint32_t j0, 
         P.off[i] = j.sum_off;
         for (uint64_t b = 0; b < j.n_batches; b++) P.bjob.push_back(j0 + i);
     }
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(B.jobs + j0, P.d.data(), sizeof(DevJob) * n, cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(B.limit + j0, P.lim.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(B.jsoff + j0, P.off.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st)))
-        return e;
-    if (!P.bjob.empty() &&
-        (e = cudaMemcpyAsync(B.bjob + b0, P.bjob.data(), sizeof(uint32_t) * P.bjob.size(), cudaMemcpyHostToDevice, st)))
-        return e;
     P.pub = j0 + n;
-    return cudaMemcpyAsync(B.jctl + JC_PUBLISHED, &P.pub, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+}
+
+// Write jobs [j0, j0 + n) into the table and then publish them: the kernel sees a
+// job only once the published count covers it (copies in stream order).  The
+// host buffers must stay valid until the stream has run the copies.
+static cudaError_t publish_copies(RunBufs &B, uint32_t j0, uint32_t n, const DevJob *d, const unsigned long long *lim,
+                                  const unsigned long long *off, uint64_t b0, const uint32_t *bjob, uint64_t nb,
+                                  const uint32_t *pub, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(B.jobs + j0, d, sizeof(DevJob) * n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(B.limit + j0, lim, sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(B.jsoff + j0, off, sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st)))
+        return e;
+    if (nb && (e = cudaMemcpyAsync(B.bjob + b0, bjob, sizeof(uint32_t) * nb, cudaMemcpyHostToDevice, st))) return e;
+    return cudaMemcpyAsync(B.jctl + JC_PUBLISHED, pub, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+}
+
+static cudaError_t publish_jobs(RunBufs &B, JobRun *const *jobs, uint32_t j0, uint32_t n, PublishStage &P,
+                                cudaStream_t st)
+{
+    stage_jobs(jobs, j0, n, P);
+    return publish_copies(B, j0, n, P.d.data(), P.lim.data(), P.off.data(), P.b0, P.bjob.data(), P.bjob.size(),
+                          &P.pub, st);
 }
 
 // Read a decided job's sums and counters back (stream order) and fill its result.
@@ -908,10 +931,10 @@ static double run_timeout_s()
     return t > 0.0 ? t : 3600.0;
 }
 
-static EngineView run_view(frw_ctx *ctx, uint32_t jcap, int max_nc, uint32_t pool, uint64_t batches)
+static EngineView run_view(frw_ctx *ctx, RunBufs &B, const RecArrays &rec, uint32_t jcap, int max_nc, uint32_t pool,
+                           uint64_t batches)
 {
     EngineView E = make_view(ctx);
-    RunBufs &B = ctx->rb;
     E.n_jobs = (int)jcap;
     E.max_nc = max_nc;
     E.jobs = B.jobs;
@@ -930,10 +953,19 @@ static EngineView run_view(frw_ctx *ctx, uint32_t jcap, int max_nc, uint32_t poo
     E.rq_count = B.rqc;
     E.rq_head = B.rqc + 1;
     E.rq_cap = (uint32_t)std::max<uint64_t>(batches, 1);
-    E.rec = ctx->rec;
+    E.rec = rec;
     E.pool = pool;
     E.NS = pool * (uint32_t)ctx->grid;
     return E;
+}
+
+// slots per CTA for a run of `walks` walks: the tuned pool, fewer for small runs
+static uint32_t run_pool_for(frw_ctx *ctx, uint64_t walks)
+{
+    const uint32_t pool0 = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
+    const uint32_t tuned = std::min<uint32_t>(pool0, (uint32_t)ctx->tune.pool_per_cta);
+    const uint64_t per = std::max<uint64_t>(256, ((walks / ctx->grid + 255) / 256) * 256);
+    return (uint32_t)std::min<uint64_t>(tuned, per);
 }
 
 // Run a set of jobs to completion: one launch of the persistent walk kernel with
@@ -965,10 +997,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     int rc = ensure_records(ctx, A.walks);
     if (rc) return rc;
     if ((rc = ensure_runbufs(ctx, nj, A.batches, A.acc, A.sums))) return rc;
-    // slots for this run (fewer for small runs)
-    const uint32_t pool0 = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
-    const uint64_t per = std::max<uint64_t>(256, ((A.walks / ctx->grid + 255) / 256) * 256);
-    const uint32_t run_pool = (uint32_t)std::min<uint64_t>(pool0, per);
+    const uint32_t run_pool = run_pool_for(ctx, A.walks);
     const uint64_t run_slots = (uint64_t)run_pool * ctx->grid;
     int n_sigma = 0;
     for (JobRun *j : live) n_sigma += j->desc.sigma_target > 0.0 ? 1 : 0;
@@ -976,12 +1005,13 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     cudaStream_t st = ctx->stream, ax = ctx->aux;
     PublishStage P;
     const uint32_t ctrl0[CTRL_WORDS] = {0u, 0u, 0u, 0u};
-    CK(zero_run(ctx, nj, A, st));
+    CK(zero_run(ctx->rb, ctx->rec.k, nj, A, st));
     CK(cudaMemcpyAsync(ctx->ctrl, ctrl0, sizeof(ctrl0), cudaMemcpyHostToDevice, st));
-    CK(publish_jobs(ctx, live.data(), 0, nj, P, st));
+    CK(publish_jobs(ctx->rb, live.data(), 0, nj, P, st));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
     CK(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, st));
-    const EngineView E = run_view(ctx, nj, max_nc, run_pool, A.batches);
+    const EngineView E = run_view(ctx, ctx->rb, ctx->rec, nj, max_nc, run_pool, A.batches);
+    CK(prepare_walk(E));
     CK(cudaEventRecord(ctx->ev[0], st));
     CK(launch_walk(E, ctx->shape, st));
     CK(cudaEventRecord(ctx->ev[1], st));
@@ -1358,7 +1388,7 @@ static int serve_start_run(frw_ctx *ctx, Server &S)
         }
         S.h_buf_cap = hb;
     }
-    R.pool = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
+    R.pool = run_pool_for(ctx, ~0ull >> 8);
     R.slots = (uint64_t)R.pool * ctx->grid;
     Arena full;
     full.jobs = R.jcap;
@@ -1367,14 +1397,15 @@ static int serve_start_run(frw_ctx *ctx, Server &S)
     full.acc = R.acap;
     full.sums = R.scap;
     static const uint32_t ctrl_open[CTRL_WORDS] = {1u, 0u, 0u, 0u};
-    cudaError_t e = zero_run(ctx, R.jcap, full, S.st);
+    cudaError_t e = zero_run(ctx->rb, ctx->rec.k, R.jcap, full, S.st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ctrl, ctrl_open, sizeof(ctrl_open), cudaMemcpyHostToDevice, S.st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, S.st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, S.st);
     // the set-up is complete before the kernel starts and before any publication
     // (publications and polls go through the second stream while the kernel runs)
     if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
-    const EngineView E = run_view(ctx, R.jcap, R.max_nc, R.pool, R.bcap);
+    const EngineView E = run_view(ctx, ctx->rb, ctx->rec, R.jcap, R.max_nc, R.pool, R.bcap);
+    if (e == cudaSuccess) e = prepare_walk(E);
     if (e == cudaSuccess) e = launch_walk(E, ctx->shape, S.st);
     if (e == cudaSuccess) e = cudaEventRecord(S.ev_end, S.st);
     if (e != cudaSuccess) {
@@ -1511,7 +1542,7 @@ static void serve_loop(frw_ctx *ctx)
             for (size_t i = R.lo; i < R.ids.size(); i++) n_sigma += R.finished[i] ? 0 : 1;
             for (JobRun *j : adm) j->first_limit = first_wave(*j, R.slots, n_sigma, 8);
             const uint32_t j0 = (uint32_t)(R.ids.size() - adm.size());
-            cudaError_t e = publish_jobs(ctx, adm.data(), j0, (uint32_t)adm.size(), R.P, S.poll);
+            cudaError_t e = publish_jobs(ctx->rb, adm.data(), j0, (uint32_t)adm.size(), R.P, S.poll);
             if (e == cudaSuccess) e = cudaStreamSynchronize(S.poll);
             if (e != cudaSuccess) rc = cuda_fail(ctx, e, "serving publication");
             R.t_quiet = std::chrono::steady_clock::now();
@@ -1640,4 +1671,397 @@ extern "C" int frw_wait(frw_ctx *ctx, uint64_t ticket, double timeout_s, double 
     }
     S.tickets.erase(it);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Launch settings and the autotuner.
+static int tuning_ok(frw_ctx *ctx, const frw_tuning &t)
+{
+    const int pool0 = (int)(ctx->NS / ctx->grid);
+    return t.pool_per_cta >= 256 && t.pool_per_cta <= pool0 && t.pool_per_cta % 256 == 0 && t.hops_per_epoch >= 1 &&
+           t.hops_per_epoch <= 64 && t.mw_warps_per_cta >= 1 && t.mw_warps_per_cta <= 16 && t.mw_ctas_per_sm >= 1 &&
+           t.mw_ctas_per_sm <= 32;
+}
+
+static int apply_tuning(frw_ctx *ctx, const frw_tuning &t)
+{
+    if (!tuning_ok(ctx, t)) return fail(ctx, FRW_EINVAL, "tuning outside its ranges");
+    const cudaError_t e = set_kernel_attributes(ctx->opt.N, t.mw_warps_per_cta, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    ctx->tune = t;
+    ctx->shape.mw_warps = t.mw_warps_per_cta;
+    ctx->shape.mw_ctas_per_sm = t.mw_ctas_per_sm;
+    return FRW_OK;
+}
+
+extern "C" int frw_get_tuning(frw_ctx *ctx, frw_tuning *out)
+{
+    if (!ctx || !out) return FRW_EINVAL;
+    *out = ctx->tune;
+    return FRW_OK;
+}
+
+extern "C" int frw_set_tuning(frw_ctx *ctx, const frw_tuning *t)
+{
+    if (!ctx || !t) return FRW_EINVAL;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
+    CK(cudaSetDevice(ctx->device));
+    return apply_tuning(ctx, *t);
+}
+
+// random cube records for timing the MicroWalk kernel (64 int32 words each, the
+// frw_microwalk_cubes layout): background and 2-6 blocks with voxel ranges
+// uniform in [0, N] and materials 0 .. n_mat-1 (a plain 64-bit LCG)
+static void tune_cubes(int N, int n_cubes, int n_mat, std::vector<int32_t> &rec)
+{
+    rec.assign((size_t)n_cubes * 64, 0);
+    uint64_t x = 0x9e3779b97f4a7c15ull;
+    auto next = [&](uint32_t m) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        return (uint32_t)((x >> 33) % m);
+    };
+    for (int c = 0; c < n_cubes; c++) {
+        int32_t *r = &rec[(size_t)c * 64];
+        r[0] = (int32_t)next((uint32_t)n_mat);
+        const int K = 2 + (int)next(5);
+        r[1] = K;
+        for (int b = 0; b < K; b++) {
+            for (int a = 0; a < 3; a++) {
+                int lo = (int)next((uint32_t)N), hi = (int)next((uint32_t)N);
+                if (lo > hi) std::swap(lo, hi);
+                r[2 + 7 * b + 2 * a] = lo;
+                r[3 + 7 * b + 2 * a] = hi + 1;
+            }
+            r[8 + 7 * b] = (int32_t)next((uint32_t)n_mat);
+        }
+    }
+}
+
+extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sample, uint64_t sample_walks,
+                            frw_tuning *out)
+{
+    if (!ctx || (n_sample > 0 && !sample) || n_sample < 0) return FRW_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    frw_tuning best = ctx->tune;
+    // walk kernel: slots per CTA x analytical hops per epoch on the sample jobs (budget mode)
+    if (n_sample > 0 && sample_walks > 0) {
+        std::vector<frw_job> jobs(sample, sample + n_sample);
+        for (auto &j : jobs) {
+            int rc = check_job(ctx, j);
+            if (rc) return rc;
+            j.sigma_target = 0.0;
+            j.walk_budget = std::min<uint64_t>(j.walk_budget ? j.walk_budget : sample_walks, sample_walks);
+        }
+        const int pool0 = (int)(ctx->NS / ctx->grid);
+        double best_rate = 0.0;
+        for (int rep = 0; rep < 2; rep++) {           // the first pass also warms the table cache
+            for (int pool : {1024, 2048, 3072, 4096}) {
+                if (pool > pool0) continue;
+                for (int hops : {4, 8, 16}) {
+                    frw_tuning t = ctx->tune;
+                    t.pool_per_cta = pool;
+                    t.hops_per_epoch = hops;
+                    std::vector<JobRun> runs(jobs.size());
+                    for (size_t i = 0; i < jobs.size(); i++) runs[i].desc = jobs[i];
+                    std::vector<frw_stats> st(jobs.size());
+                    std::lock_guard<std::mutex> engine(ctx->engine_mu);
+                    const frw_tuning keep = ctx->tune;
+                    ctx->tune = t;
+                    const int rc = run_jobs(ctx, runs, st.data());
+                    ctx->tune = keep;
+                    if (rc) return rc;
+                    uint64_t walks = 0;
+                    for (auto &r : runs) walks += r.walks;
+                    const double rate = st[0].kernel_ms > 0 ? walks / (st[0].kernel_ms * 1e-3) : 0.0;
+                    if (rep == 1 && rate > best_rate) {
+                        best_rate = rate;
+                        best.pool_per_cta = pool;
+                        best.hops_per_epoch = hops;
+                        best.walks_per_s = rate;
+                    }
+                }
+            }
+        }
+    }
+    // stand-alone MicroWalk kernel: warps per CTA x CTAs per SM on random cubes of the context's N
+    {
+        const int N = ctx->opt.N, n_cubes = 512;
+        const uint64_t spc = 4096;
+        std::vector<int32_t> rec;
+        std::vector<uint8_t> map;
+        int rc = FRW_OK, n_mat = 0;
+        {
+            // the context's own materials when it has some (registers nothing new)
+            std::lock_guard<std::mutex> ls(ctx->struct_mu);
+            n_mat = std::min<int>(4, (int)ctx->eps.size());
+            if (n_mat >= 2) {
+                map.assign(16, 0);
+                for (int i = 0; i < n_mat; i++) map[i] = (uint8_t)i;
+            } else {
+                const double eps4[4] = {2.5, 3.9, 7.0, 25.0};
+                n_mat = 4;
+                rc = register_materials(ctx, eps4, 4, map);
+            }
+        }
+        if (rc) return rc;
+        tune_cubes(N, n_cubes, n_mat, rec);
+        std::vector<void *> tmp;
+        int32_t *d_cubes = nullptr;
+        uint32_t *d_exit = nullptr, *d_steps = nullptr;
+        unsigned long long *d_head = nullptr;
+        auto cleanup = [&]() {
+            for (void *p : tmp) cudaFree(p);
+        };
+        if ((rc = dalloc(ctx, &d_cubes, rec.size(), tmp)) || (rc = dalloc(ctx, &d_exit, n_cubes * spc, tmp)) ||
+            (rc = dalloc(ctx, &d_steps, n_cubes * spc, tmp)) || (rc = dalloc(ctx, &d_head, 1, tmp))) {
+            cleanup();
+            return rc;
+        }
+        std::lock_guard<std::mutex> engine(ctx->engine_mu);
+        cudaStream_t st = ctx->stream;
+        cudaError_t e = cudaMemcpyAsync(d_cubes, rec.data(), sizeof(int32_t) * rec.size(), cudaMemcpyHostToDevice, st);
+        double best_mw = 0.0;
+        const int shapes[5][2] = {{8, 2}, {8, 4}, {16, 1}, {16, 2}, {16, 3}};
+        for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+            for (const auto &sh : shapes) {
+                LaunchShape L = ctx->shape;
+                L.mw_warps = sh[0];
+                L.mw_ctas_per_sm = sh[1];
+                if ((e = set_kernel_attributes(N, sh[0], 0)) != cudaSuccess) break;
+                if ((e = cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), st)) != cudaSuccess) break;
+                if ((e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st)) != cudaSuccess) break;
+                if ((e = cudaEventRecord(ctx->ev[2], st)) != cudaSuccess) break;
+                e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, spc, 1u, 2u, map.data(), ctx->d_W, d_exit, d_steps,
+                                    d_head, ctx->status + STAT_ERR, L, st);
+                if (e != cudaSuccess) break;
+                if ((e = cudaEventRecord(ctx->ev[3], st)) != cudaSuccess) break;
+                if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+                if (rep == 1 && ms > 0.f) {
+                    std::vector<uint32_t> steps(n_cubes * spc);
+                    if ((e = cudaMemcpy(steps.data(), d_steps, sizeof(uint32_t) * steps.size(),
+                                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+                        break;
+                    double tot = 0.0;
+                    for (uint32_t v : steps) tot += v;
+                    const double rate = tot / (ms * 1e-3);
+                    if (rate > best_mw) {
+                        best_mw = rate;
+                        best.mw_warps_per_cta = sh[0];
+                        best.mw_ctas_per_sm = sh[1];
+                        best.mw_steps_per_s = rate;
+                    }
+                }
+            }
+        }
+        cleanup();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "MicroWalk autotune");
+        if ((rc = check_status(ctx))) return rc;
+        if ((rc = apply_tuning(ctx, best))) return rc;
+    }
+    if (out) *out = ctx->tune;
+    return FRW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plans: a fixed job set with its launch sequence captured in a CUDA graph.
+struct frw_plan {
+    frw_ctx *ctx = nullptr;
+    std::vector<JobRun> jobs;
+    std::vector<JobRun *> live;
+    std::vector<uint64_t> base_request;   // request id of each job before the offset
+    Arena A;
+    int max_nc = 1;
+    uint32_t pool = 0;
+    RunBufs rb;
+    RecArrays rec;
+    std::vector<void *> allocs;
+    // pinned staging, read by the graph's copy nodes
+    DevJob *h_jobs = nullptr;
+    unsigned long long *h_lim = nullptr, *h_off = nullptr;
+    uint32_t *h_bjob = nullptr, *h_words = nullptr;   // h_words: [0] published count, [1..4] control words
+    uint64_t nbjob = 0;
+    JobState *h_js = nullptr;
+    unsigned long long *h_sum = nullptr, *h_next = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+extern "C" void frw_plan_destroy(frw_plan *P)
+{
+    if (!P) return;
+    cudaSetDevice(P->ctx->device);
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->ev0) cudaEventDestroy(P->ev0);
+    if (P->ev1) cudaEventDestroy(P->ev1);
+    for (void *p : P->allocs) cudaFree(p);
+    for (void *p : P->rb.allocs) cudaFree(p);
+    for (void *p : {(void *)P->h_jobs, (void *)P->h_lim, (void *)P->h_off, (void *)P->h_bjob, (void *)P->h_words,
+                    (void *)P->h_js, (void *)P->h_sum, (void *)P->h_next})
+        if (p) cudaFreeHost(p);
+    delete P;
+}
+
+template <typename T> static bool pinned(T **p, size_t n)
+{
+    return cudaMallocHost((void **)p, sizeof(T) * std::max<size_t>(n, 1)) == cudaSuccess;
+}
+
+extern "C" int frw_plan_create(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs, frw_plan **out)
+{
+    if (!ctx || !out || n_jobs < 1 || !jobs) return FRW_EINVAL;
+    *out = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    std::unique_ptr<frw_plan, void (*)(frw_plan *)> P(new frw_plan(), frw_plan_destroy);
+    P->ctx = ctx;
+    P->jobs.resize(n_jobs);
+    {
+        std::lock_guard<std::mutex> ls(ctx->struct_mu);
+        for (int i = 0; i < n_jobs; i++) {
+            int rc = check_job(ctx, jobs[i]);
+            if (rc) return rc;
+            P->jobs[i].desc = jobs[i];
+            P->base_request.push_back(jobs[i].request_id);
+            const HostStructure &H = ctx->structs[jobs[i].structure_id];
+            P->jobs[i].d.n_c = H.n_c;
+            P->jobs[i].S1.assign(H.n_c + 1, 0);
+            P->jobs[i].S2.assign(H.n_c + 1, 0);
+            if (jobs[i].walk_budget) {
+                place_job(ctx, P->jobs[i], P->A);
+                P->live.push_back(&P->jobs[i]);
+                P->max_nc = std::max(P->max_nc, H.n_c);
+            }
+        }
+    }
+    const uint32_t nj = (uint32_t)P->live.size();
+    if (nj == 0) {
+        *out = P.release();
+        return FRW_OK;
+    }
+    if (P->A.batches >= 0xffffffffull) return fail(ctx, FRW_EINVAL, "too many batches");
+    if (P->A.walks * 32ull > (64ull << 30)) return fail(ctx, FRW_ENOMEM, "plan's walk budget too large (64 GB of records)");
+    int rc;
+    RecArrays &R = P->rec;
+    const uint64_t nw = P->A.walks;
+    if ((rc = grow_runbufs(ctx, P->rb, nj, P->A.batches, P->A.acc, P->A.sums)) ||
+        (rc = dalloc(ctx, &R.omega, nw, P->allocs)) || (rc = dalloc(ctx, &R.k, nw, P->allocs)) ||
+        (rc = dalloc(ctx, &R.hops, nw, P->allocs)) || (rc = dalloc(ctx, &R.steps, nw, P->allocs)) ||
+        (rc = dalloc(ctx, &R.cnt_sh, nw, P->allocs)) || (rc = dalloc(ctx, &R.cnt_mw, nw, P->allocs)) ||
+        (rc = dalloc(ctx, &R.branch, nw, P->allocs)))
+        return rc;
+    P->pool = run_pool_for(ctx, P->A.walks);
+    int n_sigma = 0;
+    for (JobRun *j : P->live) n_sigma += j->desc.sigma_target > 0.0 ? 1 : 0;
+    for (JobRun *j : P->live) j->first_limit = first_wave(*j, (uint64_t)P->pool * ctx->grid, n_sigma, 1);
+    PublishStage S;
+    stage_jobs(P->live.data(), 0, nj, S);
+    P->nbjob = S.bjob.size();
+    if (!pinned(&P->h_jobs, nj) || !pinned(&P->h_lim, nj) || !pinned(&P->h_off, nj) || !pinned(&P->h_bjob, P->nbjob) ||
+        !pinned(&P->h_words, 1 + CTRL_WORDS) || !pinned(&P->h_js, nj) || !pinned(&P->h_sum, P->A.sums) ||
+        !pinned(&P->h_next, nj))
+        return fail(ctx, FRW_ENOMEM, "pinned plan staging");
+    memcpy(P->h_jobs, S.d.data(), sizeof(DevJob) * nj);
+    memcpy(P->h_lim, S.lim.data(), sizeof(unsigned long long) * nj);
+    memcpy(P->h_off, S.off.data(), sizeof(unsigned long long) * nj);
+    if (P->nbjob) memcpy(P->h_bjob, S.bjob.data(), sizeof(uint32_t) * P->nbjob);
+    P->h_words[0] = nj;
+    for (int w = 0; w < CTRL_WORDS; w++) P->h_words[1 + w] = 0u;
+    CK(cudaEventCreate(&P->ev0));
+    CK(cudaEventCreate(&P->ev1));
+    // capture: reset, publication, the walk kernel
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
+    const EngineView E = run_view(ctx, P->rb, P->rec, nj, P->max_nc, P->pool, P->A.batches);
+    CK(prepare_walk(E));
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = zero_run(P->rb, P->rec.k, nj, P->A, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->ctrl, P->h_words + 1, sizeof(uint32_t) * CTRL_WORDS, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = publish_copies(P->rb, 0, nj, P->h_jobs, P->h_lim, P->h_off, S.b0, P->h_bjob, P->nbjob, P->h_words, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, st);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev0, st);
+    if (e == cudaSuccess) e = launch_walk(E, ctx->shape, st);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev1, st);
+    const cudaError_t e2 = cudaStreamEndCapture(st, &P->graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plan capture");
+    *out = P.release();
+    return FRW_OK;
+}
+
+extern "C" int frw_plan_run(frw_plan *P, uint64_t request_offset, double *C_rows, double *stderr_rows,
+                            frw_stats *stats)
+{
+    if (!P) return FRW_EINVAL;
+    frw_ctx *ctx = P->ctx;
+    CK(cudaSetDevice(ctx->device));
+    const uint32_t nj = (uint32_t)P->live.size();
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (size_t i = 0; i < P->jobs.size(); i++) {
+        JobRun &j = P->jobs[i];
+        j.desc.request_id = P->base_request[i] + request_offset;
+        j.d.key1 = (uint32_t)(ctx->opt.seed >> 32) ^ (uint32_t)j.desc.request_id;
+        std::fill(j.S1.begin(), j.S1.end(), 0);
+        std::fill(j.S2.begin(), j.S2.end(), 0);
+        j.walks = j.issued = 0;
+        for (auto &x : j.ex) x = 0;
+        j.converged = false;
+    }
+    for (uint32_t i = 0; i < nj; i++) P->h_jobs[i].key1 = P->live[i]->d.key1;
+    cudaStream_t st = ctx->stream;
+    if (nj) {
+        CK(cudaGraphLaunch(P->exec, st));
+        const double limit_s = run_timeout_s();
+        bool timed_out = false;
+        while (cudaEventQuery(P->ev1) == cudaErrorNotReady) {
+            if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) {
+                static const uint32_t abort1 = 1;
+                CK(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->aux));
+                CK(cudaStreamSynchronize(ctx->aux));
+                timed_out = true;
+                break;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        CK(cudaStreamSynchronize(st));
+        int rc = check_status(ctx);
+        if (rc) return rc;
+        if (timed_out) return fail(ctx, FRW_ETIMEOUT, "run exceeded its wall-clock limit (FRW_RUN_TIMEOUT_S)");
+        CK(cudaMemcpyAsync(P->h_js, P->rb.js, sizeof(JobState) * nj, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(P->h_sum, P->rb.jsum, sizeof(unsigned long long) * P->A.sums, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(P->h_next, P->rb.next, sizeof(unsigned long long) * nj, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (uint32_t i = 0; i < nj; i++) {
+            if (P->h_js[i].decided == 0u) return fail(ctx, FRW_EDEVICE, "a job was not decided when the kernel ended");
+            take_result(*P->live[i], P->h_js[i], P->h_sum + P->live[i]->sum_off, P->h_next[i]);
+        }
+    }
+    float kms = 0.f;
+    if (nj) cudaEventElapsedTime(&kms, P->ev0, P->ev1);
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    bool notconv = false;
+    size_t off = 0;
+    for (size_t i = 0; i < P->jobs.size(); i++) {
+        const JobRun &j = P->jobs[i];
+        row_from(j, C_rows ? C_rows + off : nullptr, stderr_rows ? stderr_rows + off : nullptr);
+        off += j.d.n_c + 1;
+        if (stats) {
+            fill_stats(stats[i], j);
+            stats[i].seconds = secs;
+            stats[i].kernel_ms = kms;
+            stats[i].launches = nj ? 1 : 0;
+            stats[i].rounds = ctx->h_status[STAT_EPOCHS];
+            stats[i].tables_built = ctx->h_status[STAT_BUILT];
+        }
+        if (j.desc.sigma_target > 0.0 && !j.converged) notconv = true;
+    }
+    return notconv ? FRW_ENOTCONV : FRW_OK;
 }
