@@ -342,6 +342,9 @@ def main():
     sid = ctx.load(s)
     masters = list(s.masters)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    # launch settings from the project's autotuner, on this workload in budget mode (results do not depend on them)
+    tuning = ctx.autotune([dict(structure_id=sid, master=m, walk_budget=400_000, request_id=90 + i)
+                           for i, m in enumerate(masters)], sample_walks=400_000)
 
     def jobs_for(step):
         rq = 1_000_000 * (rank + 1) + step
@@ -454,7 +457,8 @@ def main():
                                    "(the interconnect configuration's target), budget %d/master"
                                    % (a.N, masters, a.sigma, a.budget),
                        "geometry": a.precision, "accumulate": "exact int128 (fp64 in/out)",
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"weak x{world}"},
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"weak x{world}",
+                       "tuning": {k: tuning[k] for k in ("pool_per_cta", "hops_per_epoch")}},
             "micro_transitions_per_s": agg["micro"] * (walks_all / max(1, agg["walks"])) / t_all,
             "hops_per_walk": agg["hops"] / max(1, agg["walks"]),
             "mw_hop_fraction": agg["mw_hops"] / max(1, agg["hops"] - agg["walks"]),
