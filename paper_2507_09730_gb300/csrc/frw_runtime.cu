@@ -2023,7 +2023,7 @@ extern "C" int frw_plan_run(frw_plan *P, uint64_t request_offset, double *C_rows
         CK(cudaEventRecord(ctx->ev[1], st));
         const double limit_s = run_timeout_s();
         bool timed_out = false;
-        while (cudaEventQuery(P->ev1) == cudaErrorNotReady) {
+        while (cudaEventQuery(ctx->ev[1]) == cudaErrorNotReady) {
             if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > limit_s) {
                 static const uint32_t abort1 = 1;
                 CK(cudaMemcpyAsync(ctx->ctrl + CTRL_ABORT, &abort1, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->aux));
