@@ -398,13 +398,9 @@ def main():
     t_all = elapsed
     walks_all = agg["walks"]
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_all = float(t.item())
-        wt = torch.tensor([agg["walks"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(wt)
-        walks_all = int(wt.item())
+        from paper_2507_09730_gb300 import sharding
+        t_all = sharding.reduce_max(elapsed)
+        walks_all = int(sharding.reduce_sum(agg["walks"]))
     value = walks_all / t_all
 
     # end to end through the C ABI with host buffers: load (H2D), extract, rows back (D2H), unload

@@ -160,6 +160,18 @@ int frw_extract(frw_ctx *ctx, int32_t structure_id, int32_t master,
                 const frw_extract_params *params, double *C_row, double *stderr_row,
                 frw_stats *stats);
 
+/* Like frw_extract, but returns the estimator's exact sums instead of the row, for
+ * combining shards of one extraction run on several GPUs (disjoint walk-id ranges
+ * through params->walk_begin; sigma_target must be 0).  sums (host, 4 (n_cond + 1)
+ * uint64): [2k, 2k+1] = S1_k = sum of omega over walks ending at k, as a two's
+ * complement int128 (low word first) in units of 2^-64 fF; [2(n_cond+1) + 2k, +1]
+ * = S2_k = sum of omega^2 in units of 2^-40 fF^2.  *n_walks = walks counted.
+ * Integer sums add exactly, so the combined shards give bit-for-bit the row of a
+ * single run over the union of the ranges: C_k = S1_k / n, and the standard error
+ * sqrt((S2_k - S1_k^2 / n) / (n (n - 1))), each sum converted to double first. */
+int frw_extract_sums(frw_ctx *ctx, int32_t structure_id, int32_t master, const frw_extract_params *params,
+                     uint64_t *sums, uint64_t *n_walks, frw_stats *stats);
+
 /* Several extractions (possibly different structures, masters, budgets and
  * targets) interleaved in one engine run.  C_rows / stderr_rows are host arrays
  * holding each job's n_cond + 1 entries back to back in job order; stats (may be

@@ -22,7 +22,7 @@ EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream",
            "frw_unload_structure", "frw_extract", "frw_extract_batch", "frw_walk_records",
            "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
            "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
-           "frw_get_tuning", "frw_set_tuning", "frw_autotune")
+           "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums")
 
 
 class frw_box(ctypes.Structure):
@@ -119,6 +119,8 @@ def lib():
     L.frw_get_tuning.argtypes = [c_void_p, POINTER(frw_tuning)]
     L.frw_set_tuning.argtypes = [c_void_p, POINTER(frw_tuning)]
     L.frw_autotune.argtypes = [c_void_p, POINTER(frw_job), c_int32, c_uint64, POINTER(frw_tuning)]
+    L.frw_extract_sums.argtypes = [c_void_p, c_int32, c_int32, POINTER(frw_extract_params), P(c_uint64),
+                                   POINTER(c_uint64), POINTER(frw_stats)]
     L.frw_strerror.argtypes = [c_int]
     L.frw_strerror.restype = ctypes.c_char_p
     L.frw_last_error.argtypes = [c_void_p]
@@ -208,6 +210,18 @@ def frw_extract(ctx, sid: int, master: int, n_cond: int, walk_budget: int, sigma
                            ctypes.byref(st))
     _check(ctx, rc, (FRW_OK, FRW_ENOTCONV))
     return C, se, st.as_dict(), rc == FRW_OK
+
+
+def frw_extract_sums(ctx, sid: int, master: int, n_cond: int, walk_budget: int, request_id: int = 0,
+                     batch: int = 0, walk_begin: int = 0):
+    """-> (exact sums as 4 (n_cond + 1) uint64 words, walks counted, stats); budget mode."""
+    p = frw_extract_params(int(walk_budget), 0.0, int(request_id), int(batch), int(walk_begin))
+    words = np.zeros(4 * (n_cond + 1), np.uint64)
+    n = c_uint64(0)
+    st = frw_stats()
+    _check(ctx, lib().frw_extract_sums(ctx, int(sid), int(master), ctypes.byref(p), _ptr(words, c_uint64),
+                                       ctypes.byref(n), ctypes.byref(st)))
+    return words, int(n.value), st.as_dict()
 
 
 def frw_extract_batch(ctx, jobs, n_conds):

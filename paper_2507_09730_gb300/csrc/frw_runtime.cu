@@ -1143,6 +1143,41 @@ extern "C" int frw_extract(frw_ctx *ctx, int32_t sid, int32_t master, const frw_
     return (j.sigma_target > 0.0 && !runs[0].converged) ? FRW_ENOTCONV : FRW_OK;
 }
 
+extern "C" int frw_extract_sums(frw_ctx *ctx, int32_t sid, int32_t master, const frw_extract_params *p,
+                                uint64_t *sums, uint64_t *n_walks, frw_stats *stats)
+{
+    if (!ctx || !p || !sums || !n_walks) return FRW_EINVAL;
+    if (p->sigma_target != 0.0) return fail(ctx, FRW_EINVAL, "shards run in budget mode (sigma_target = 0)");
+    frw_job j;
+    j.structure_id = sid;
+    j.master = master;
+    j.walk_budget = p->walk_budget;
+    j.sigma_target = 0.0;
+    j.request_id = p->request_id;
+    j.batch = p->batch;
+    int rc = check_job(ctx, j);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
+    CK(cudaSetDevice(ctx->device));
+    std::vector<JobRun> runs(1);
+    runs[0].desc = j;
+    runs[0].walk_begin = p->walk_begin;
+    frw_stats st;
+    rc = run_jobs(ctx, runs, &st);
+    if (rc) return rc;
+    const int nc1 = runs[0].d.n_c + 1;
+    for (int k = 0; k < nc1; k++) {
+        const unsigned __int128 a = (unsigned __int128)runs[0].S1[k], b = (unsigned __int128)runs[0].S2[k];
+        sums[2 * k] = (uint64_t)a;
+        sums[2 * k + 1] = (uint64_t)(a >> 64);
+        sums[2 * nc1 + 2 * k] = (uint64_t)b;
+        sums[2 * nc1 + 2 * k + 1] = (uint64_t)(b >> 64);
+    }
+    *n_walks = runs[0].walks;
+    if (stats) *stats = st;
+    return FRW_OK;
+}
+
 extern "C" int frw_walk_records(frw_ctx *ctx, int32_t sid, int32_t master, uint64_t request_id, uint64_t walk_begin,
                                 uint64_t n_walks, double *omega, int32_t *electrode, uint32_t *hops,
                                 uint64_t *micro_steps, int32_t *branch)

@@ -1,0 +1,129 @@
+"""Sharding one extraction over ranks (one process per GPU): shard ranges, the
+exact int128 exchange and the row formed from the combined sums.
+
+The host side runs here as two gloo ranks on the CPU, with a stand-in engine
+that returns exact integer sums for a walk-id range (signed 127-bit per-walk
+terms, so carries across the 64-bit halves and negative totals occur).  The
+device side (frw_extract_sums on shards of one GPU, combined) is checked
+bit-for-bit against one full run in the GPU test."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2507_09730_gb300 import sharding as S
+
+
+def _walk_terms(walk, k):
+    """stand-in per-walk exact sums (S1, S2 words of k electrodes) for walk id `walk`"""
+    rng = np.random.default_rng([walk, 17])
+    e = int(rng.integers(0, k))
+    s1 = [0] * k
+    s2 = [0] * k
+    mag = int(rng.integers(0, 1 << 62)) << 62 | int(rng.integers(0, 1 << 62))
+    s1[e] = -mag if rng.integers(0, 2) else mag
+    s2[e] = mag >> 3
+    return s1, s2
+
+
+def _range_sums(begin, count, k):
+    S1 = [0] * k
+    S2 = [0] * k
+    for w in range(begin, begin + count):
+        a, b = _walk_terms(w, k)
+        S1 = [x + y for x, y in zip(S1, a)]
+        S2 = [x + y for x, y in zip(S2, b)]
+    return np.concatenate([S.ints_to_words(S1), S.ints_to_words(S2)]), count
+
+
+def test_shard_ranges_partition():
+    for n in (0, 1, 7, 1000, 12345):
+        for world in (1, 2, 3, 8):
+            got = [S.shard_range(n, r, world) for r in range(world)]
+            assert got[0][0] == 0 and sum(c for _, c in got) == n
+            for (b0, c0), (b1, _) in zip(got, got[1:]):
+                assert b0 + c0 == b1
+            assert max(c for _, c in got) - min(c for _, c in got) <= 1
+    with pytest.raises(ValueError):
+        S.shard_range(10, 2, 2)
+
+
+def test_int128_words_roundtrip():
+    vals = [0, 1, -1, (1 << 64) - 1, 1 << 64, -(1 << 64), (1 << 127) - 1, -(1 << 127), 123456789012345678901234567]
+    assert S.words_to_ints(S.ints_to_words(vals)) == vals
+
+
+def test_row_from_sums_matches_definition():
+    # C = S1 / n and se = sqrt((S2 - S1^2/n) / (n (n - 1))) in fF units
+    s1 = [int(0.75 * 2 ** 64) * 8, -int(0.25 * 2 ** 64) * 8]
+    s2 = [int(0.75 * 2 ** 40) * 8, int(0.125 * 2 ** 40) * 8]
+    C, se = S.row_from_sums(s1, s2, 8)
+    assert C[0] == 0.75 and C[1] == -0.25
+    assert se[0] == np.sqrt((6.0 - 36.0 / 8) / 56) and se[1] == np.sqrt((1.0 - 4.0 / 8) / 56)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, n, k, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        begin, count = S.shard_range(n, rank, world)
+        words, cnt = _range_sums(begin, count, k)
+        parts = S.allgather_sums(words, cnt)
+        S1, S2, total = S.combine(parts)
+        t = S.reduce_max(float(rank + 1))
+        w = S.reduce_sum(float(cnt))
+        q.put((rank, [str(x) for x in S1], [str(x) for x in S2], total, t, w))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_combine_exactly():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    n, k, world = 301, 5, 2
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, n, k, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    full, _ = _range_sums(0, n, k)
+    F = S.words_to_ints(full)
+    for rank, s1, s2, total, t, w in got:
+        assert [int(x) for x in s1] == F[:k] and [int(x) for x in s2] == F[k:]
+        assert total == n and t == float(world) and w == float(n)
+
+
+@pytest.mark.gpu
+def test_gpu_shards_equal_one_run():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_09730_gb300 import binding as B
+    from paper_2507_09730_gb300 import workloads as W
+    s = W.interconnect(1)
+    with B.Context(0, N=16, precision=B.FRW_FP32_GEOM, seed=21, slots=1 << 16) as c:
+        sid = c.load(s)
+        n = 100_003
+        parts = []
+        for r in range(3):
+            begin, count = S.shard_range(n, r, 3)
+            words, cnt, _ = B.frw_extract_sums(c.ctx, sid, 11, s.n_cond, count, 5, 4096, begin)
+            parts.append((words, cnt))
+        C, se = S.row_from_sums(*S.combine(parts))
+        Cf, sef, st, _ = c.extract(sid, 11, n, 0.0, 5, 4096)
+        np.testing.assert_array_equal(C, Cf)
+        np.testing.assert_array_equal(se, sef)
+        assert st["walks"] == n
