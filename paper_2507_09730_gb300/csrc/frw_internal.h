@@ -211,6 +211,8 @@ struct EngineView {
     unsigned long long *cycles;   // [5] CTA cycles: geometry busy, fill, reduce, MicroWalk busy, total
     double idle_timeout_s; // idle wait limit of the walk kernel
     int hops_per_epoch;    // analytical hops one walk may take per epoch (tunable, >= 1)
+    int suspend_lanes;     // a MicroWalk warp with at most this many lanes left may suspend them
+    uint32_t suspend_min_steps;   // ... once each has made this many steps in the epoch
 };
 
 // ---- launchers (frw_kernels.cu) ----

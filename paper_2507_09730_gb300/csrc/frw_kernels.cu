@@ -1555,9 +1555,7 @@ constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int MW_WARPS = WALK_WARPS;
 constexpr int POOL_MAX = 4096;
 constexpr int FILL_MAX = 128;
-constexpr int SUSPEND_LANES = 8;
-constexpr uint32_t SUSPEND_MIN_STEPS = 64;    // progress a job makes in an epoch before it may be suspended
-constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // ... and only if this much geometry work is waiting
+constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // suspension only if this much geometry work is waiting
 
 struct WalkShared {
     uint32_t g_head, pad3[3];
@@ -1745,10 +1743,10 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
                 // them has made progress this epoch and the CTA has other work
                 // waiting (so every job advances every epoch: no livelock).
                 const bool qexh = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.q_head >= qn), 0) != 0u;
-                const bool progressed = __all_sync(FULL_MASK, !active || t - t_in >= SUSPEND_MIN_STEPS);
+                const bool progressed = __all_sync(FULL_MASK, !active || t - t_in >= E.suspend_min_steps);
                 const bool other_work = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.finished >=
                                                                            SUSPEND_MIN_FINISHED || sh.issuable), 0) != 0u;
-                if (qexh && progressed && other_work && __popc(ab) <= SUSPEND_LANES) {
+                if (qexh && progressed && other_work && __popc(ab) <= E.suspend_lanes) {
                     if (active) {
                         MWJob &b = E.mwq[base + my_o];
                         b.start = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16);

@@ -200,6 +200,8 @@ static EngineView make_view(frw_ctx *ctx)
     E.cycles = ctx->cycles;
     E.idle_timeout_s = 10.0;
     E.hops_per_epoch = ctx->tune.hops_per_epoch;
+    E.suspend_lanes = ctx->tune.suspend_lanes;
+    E.suspend_min_steps = 64;
     return E;
 }
 
@@ -319,6 +321,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     }
     ctx->tune.pool_per_cta = (int32_t)(ctx->NS / ctx->grid);
     ctx->tune.hops_per_epoch = 4;
+    ctx->tune.suspend_lanes = 8;
     ctx->tune.mw_warps_per_cta = ctx->shape.mw_warps;
     ctx->tune.mw_ctas_per_sm = ctx->shape.mw_ctas_per_sm;
     ctx->tune.walks_per_s = 0.0;
@@ -1714,8 +1717,8 @@ static int tuning_ok(frw_ctx *ctx, const frw_tuning &t)
 {
     const int pool0 = (int)(ctx->NS / ctx->grid);
     return t.pool_per_cta >= 256 && t.pool_per_cta <= pool0 && t.pool_per_cta % 256 == 0 && t.hops_per_epoch >= 1 &&
-           t.hops_per_epoch <= 64 && t.mw_warps_per_cta >= 1 && t.mw_warps_per_cta <= 16 && t.mw_ctas_per_sm >= 1 &&
-           t.mw_ctas_per_sm <= 32;
+           t.hops_per_epoch <= 64 && t.suspend_lanes >= 0 && t.suspend_lanes <= 32 && t.mw_warps_per_cta >= 1 &&
+           t.mw_warps_per_cta <= 16 && t.mw_ctas_per_sm >= 1 && t.mw_ctas_per_sm <= 32;
 }
 
 static int apply_tuning(frw_ctx *ctx, const frw_tuning &t)
@@ -1792,10 +1795,11 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
         for (int rep = 0; rep < 2; rep++) {           // the first pass also warms the table cache
             for (int pool : {1024, 2048, 3072, 4096}) {
                 if (pool > pool0) continue;
-                for (int hops : {4, 8, 16}) {
+                for (int hs : {0x204, 0x404, 0x804, 0x1004, 0x208, 0x408, 0x808, 0x1008, 0x410}) {
                     frw_tuning t = ctx->tune;
                     t.pool_per_cta = pool;
-                    t.hops_per_epoch = hops;
+                    t.hops_per_epoch = hs & 0xff;
+                    t.suspend_lanes = hs >> 8;
                     std::vector<JobRun> runs(jobs.size());
                     for (size_t i = 0; i < jobs.size(); i++) runs[i].desc = jobs[i];
                     std::vector<frw_stats> st(jobs.size());
@@ -1811,7 +1815,8 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
                     if (rep == 1 && rate > best_rate) {
                         best_rate = rate;
                         best.pool_per_cta = pool;
-                        best.hops_per_epoch = hops;
+                        best.hops_per_epoch = t.hops_per_epoch;
+                        best.suspend_lanes = t.suspend_lanes;
                         best.walks_per_s = rate;
                     }
                 }
