@@ -224,7 +224,8 @@ int frw_set_tuning(frw_ctx *ctx, const frw_tuning *t);   /* FRW_EINVAL outside t
 
 /* Autotuner: runs the sample jobs in budget mode (each capped at sample_walks
  * walks) once per candidate walk-kernel setting (slots per CTA in {1024, 2048,
- * 3072, 4096} x (analytical hops per epoch, suspension lanes) in {4, 8} x
+ * 3072, 4096, the context's pool} up to the context's pool x (analytical hops
+ * per epoch, suspension lanes) in {4, 8} x
  * {2, 4, 8, 16} and (16, 4)) and keeps the fastest;
  * then times the stand-alone MicroWalk kernel on 512 random cubes of the
  * context's N (2-6 blocks of up to four of its registered materials, 4096

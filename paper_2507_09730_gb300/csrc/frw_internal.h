@@ -231,6 +231,7 @@ cudaError_t prepare_walk(const EngineView &E);
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 size_t walk_smem_bytes(int N, int max_nc);
 int walk_pool_slots();
+int walk_ctas_per_sm(int N, int fp32);
 // fill one table with an explicit key into entry `entry` of the cache arrays
 cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4],
                             uint32_t entry, double *values_out, cudaStream_t st);

@@ -913,10 +913,12 @@ __device__ __forceinline__ void build_masks(uint16_t *Mw, int r, int N, int lane
     }
 }
 
-// One step of the lattice walk: weights W[mv][m_k] of Eq. 6 (quantised; one copy
-// of the 16 x 16 table per lane, so lookups never conflict), integer prefix sums,
-// neighbour chosen by (u * S) >> 32.  Returns true on reaching a boundary node.
-// M points at the lane's column (Mw + lane), Wl at the lane's table (Wrep + lane).
+// One step of the lattice walk: weights W[mv][m_k] of Eq. 6 (quantised), integer
+// prefix sums, neighbour chosen by (u * S) >> 32.  Returns true on reaching a
+// boundary node.  M points at the lane's column (Mw + lane).  The weight table is
+// either one copy per lane (WS = 32: Wl = Wrep + lane, lookups never conflict) or
+// a single shared copy (WS = 1: Wl = W).
+template <int WS>
 __device__ __forceinline__ bool mw_step(const uint16_t *__restrict__ M, const uint32_t *__restrict__ Wl, int N,
                                         int &x, int &y, int &z, uint64_t mm, uint32_t u)
 {
@@ -927,13 +929,13 @@ __device__ __forceinline__ bool mw_step(const uint16_t *__restrict__ M, const ui
     const uint32_t zm = Mz[0], z0 = Mz[32], zp = Mz[64];
     const uint32_t yz = y0 & z0, xz = x0 & z0, xy = x0 & y0;
     const int mv = mat_of(mm, xy & z0);
-    const uint32_t *Wr = Wl + mv * 16 * 32;
-    const uint32_t w0 = Wr[mat_of(mm, xm & yz) * 32];
-    const uint32_t w1 = Wr[mat_of(mm, xp & yz) * 32];
-    const uint32_t w2 = Wr[mat_of(mm, ym & xz) * 32];
-    const uint32_t w3 = Wr[mat_of(mm, yp & xz) * 32];
-    const uint32_t w4 = Wr[mat_of(mm, zm & xy) * 32];
-    const uint32_t w5 = Wr[mat_of(mm, zp & xy) * 32];
+    const uint32_t *Wr = Wl + mv * 16 * WS;
+    const uint32_t w0 = Wr[mat_of(mm, xm & yz) * WS];
+    const uint32_t w1 = Wr[mat_of(mm, xp & yz) * WS];
+    const uint32_t w2 = Wr[mat_of(mm, ym & xz) * WS];
+    const uint32_t w3 = Wr[mat_of(mm, yp & xz) * WS];
+    const uint32_t w4 = Wr[mat_of(mm, zm & xy) * WS];
+    const uint32_t w5 = Wr[mat_of(mm, zp & xy) * WS];
     const uint32_t p0 = w0, p1 = p0 + w1, p2 = p1 + w2, p3 = p2 + w3, p4 = p3 + w4, p5 = p4 + w5;
     const uint32_t r = __umulhi(u, p5);
     const int k = (int)(r >= p0) + (int)(r >= p1) + (int)(r >= p2) + (int)(r >= p3) + (int)(r >= p4);
@@ -1058,7 +1060,7 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 if (active) {
-                    if (mw_step(M, Wl, N, x, y, z, L.mm, words[k])) {
+                    if (mw_step<32>(M, Wl, N, x, y, z, L.mm, words[k])) {
                         src.finish(L, x, y, z, t + (uint32_t)k + 1u);
                         active = false;
                     }
@@ -1558,6 +1560,7 @@ constexpr int FILL_MAX = 128;
 constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // suspension only if this much geometry work is waiting
 
 struct WalkShared {
+    uint32_t W[256];                 // quantised weights of Eq. 6, [centre][neighbour material]
     uint32_t g_head, pad3[3];
     uint32_t q_count, q_head, s_count, g_count;
     uint32_t f_count, active, issuable, stop;
@@ -1581,8 +1584,8 @@ size_t mw_smem_bytes(int N, int warps)
     return sizeof(uint32_t) * 256 * 32 + sizeof(uint16_t) * (size_t)warps * 3 * (N + 2) * 32;
 }
 
-// dynamic shared memory of the walk kernel: the per-lane weight table, then one
-// region shared in turn by the MicroWalk masks, the table fill and the reduction
+// dynamic shared memory of the walk kernel: one region shared in turn by the
+// MicroWalk masks, the table fill and the reduction
 size_t walk_scratch_bytes(int N, int max_nc)
 {
     const size_t masks = sizeof(uint16_t) * (size_t)MW_WARPS * 3 * (N + 2) * 32;
@@ -1591,12 +1594,12 @@ size_t walk_scratch_bytes(int N, int max_nc)
     return std::max(masks, std::max(fill, red));
 }
 
-size_t walk_smem_bytes(int N, int max_nc) { return sizeof(uint32_t) * 256 * 32 + walk_scratch_bytes(N, max_nc); }
+size_t walk_smem_bytes(int N, int max_nc) { return walk_scratch_bytes(N, max_nc); }
 
 int walk_pool_slots() { return POOL_MAX; }
 
 template <typename T>
-__global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
+__global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
 {
     extern __shared__ __align__(16) unsigned char dsm_all[];
     __shared__ WalkShared sh;
@@ -1604,10 +1607,9 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
     const int N = E.N;
     const uint32_t P = E.pool;
     const uint32_t base = blockIdx.x * P;
-    uint32_t *Wrep = reinterpret_cast<uint32_t *>(dsm_all);
-    unsigned char *dsm = dsm_all + sizeof(uint32_t) * 256 * 32;
+    unsigned char *dsm = dsm_all;
     double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.tc.P;
-    replicate_w(Wrep, E.W);
+    for (int i = tid; i < 256; i += WALK_THREADS) sh.W[i] = E.W[i];
     for (uint32_t o = tid; o < P; o += WALK_THREADS) {
         const uint32_t s = base + o;
         E.s.state[s] = ST_FRESH;
@@ -1691,7 +1693,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
             const int mwarp = warp;
             uint16_t *Mw = reinterpret_cast<uint16_t *>(dsm) + (size_t)mwarp * mask_rows(N) * 32;
             const uint16_t *M = Mw + lane;
-            const uint32_t *Wl = Wrep + lane;
+            const uint32_t *Wl = sh.W;
             const uint32_t qn = sh.q_count;
             bool active = false, exhausted = false;
             int x = 0, y = 0, z = 0;
@@ -1763,7 +1765,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 2) k_walk(EngineView E)
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         if (active) {
-                            if (mw_step(M, Wl, N, x, y, z, L.mm, words[k])) {
+                            if (mw_step<1>(M, Wl, N, x, y, z, L.mm, words[k])) {
                                 const uint32_t sl2 = L.tag;
                                 E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
                                 E.s.steps[sl2] += t + (uint32_t)k + 1u;
@@ -2029,3 +2031,21 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
     if (cudaStreamSynchronize(st) != cudaSuccess) return FRW_EDEVICE;
     return err ? FRW_EDEVICE : FRW_OK;
 }
+
+namespace frw {
+// CTAs of the walk kernel resident per SM at this lattice edge (3 by design at
+// N = 24: at most 85 registers per thread and about 67 KB of shared memory each)
+int walk_ctas_per_sm(int N, int fp32)
+{
+    int n = 0;
+    const int smem = (int)walk_smem_bytes(N, 200);
+    if (fp32) {
+        cudaFuncSetAttribute(k_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<float>, WALK_THREADS, smem);
+    } else {
+        cudaFuncSetAttribute(k_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<double>, WALK_THREADS, smem);
+    }
+    return n > 0 ? n : 1;
+}
+}  // namespace frw

@@ -309,8 +309,8 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->shape.mw_ctas_per_sm = opt.mw_ctas_per_sm > 0 ? opt.mw_ctas_per_sm : 2;
     ctx->shape.fill_ctas = ctx->shape.sms;
     const int N = opt.N;
-    // walk kernel: CTAs resident at once (2 per SM), each with a pool of slots
-    ctx->grid = 2 * ctx->shape.sms;
+    // walk kernel: CTAs resident at once (as many per SM as fit), each with a pool of slots
+    ctx->grid = walk_ctas_per_sm(N, opt.precision == FRW_FP32_GEOM) * ctx->shape.sms;
     {
         uint64_t want = opt.slots > 0 ? (uint64_t)opt.slots : (1ull << 20);
         uint64_t pool = (want + ctx->grid - 1) / ctx->grid;
@@ -1793,8 +1793,8 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
         const int pool0 = (int)(ctx->NS / ctx->grid);
         double best_rate = 0.0;
         for (int rep = 0; rep < 2; rep++) {           // the first pass also warms the table cache
-            for (int pool : {1024, 2048, 3072, 4096}) {
-                if (pool > pool0) continue;
+            for (int pool : {1024, 2048, 3072, 4096, pool0}) {
+                if (pool > pool0 || (pool == pool0 && pool0 % 1024 == 0)) continue;   // pool0 itself: once
                 for (int hs : {0x204, 0x404, 0x804, 0x1004, 0x208, 0x408, 0x808, 0x1008, 0x410}) {
                     frw_tuning t = ctx->tune;
                     t.pool_per_cta = pool;
