@@ -364,7 +364,8 @@ def main():
     clk = ClockSampler(local)
     clk.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    agg = dict(walks=0, micro=0, mw_ms=0.0, geom_ms=0.0, fill_ms=0.0, kernel_ms=0.0, launches=0, hops=0, mw_hops=0,
+    agg = dict(walks=0, micro=0, mw_ms=0.0, geom_ms=0.0, fill_ms=0.0, reduce_ms=0.0, kernel_ms=0.0, launches=0,
+               hops=0, mw_hops=0,
                strat=0, hom=0, rounds=0, tables=0, mw_jobs=0, walk_launches=0, issued=0)
     rows = None
     ev0.record(stream)
@@ -382,6 +383,7 @@ def main():
         agg["mw_ms"] += st0["mw_ms"]
         agg["geom_ms"] += st0["geom_ms"]
         agg["fill_ms"] += st0["fill_ms"]
+        agg["reduce_ms"] += st0["reduce_ms"]
         agg["kernel_ms"] += st0["kernel_ms"]
         agg["walk_launches"] += st0["launches"]
         agg["launches"] += st0["launches"] + 1     # + the L2 flush
@@ -444,7 +446,8 @@ def main():
                 "micro_steps_per_launch": agg["micro"] / n_l,
                 "phase_share": {"mw": agg["mw_ms"] / max(1e-9, agg["kernel_ms"]),
                                 "geom": agg["geom_ms"] / max(1e-9, agg["kernel_ms"]),
-                                "fill": agg["fill_ms"] / max(1e-9, agg["kernel_ms"])},
+                                "fill": agg["fill_ms"] / max(1e-9, agg["kernel_ms"]),
+                                "reduce": agg["reduce_ms"] / max(1e-9, agg["kernel_ms"])},
                 "mw_phase": {"achieved": mw_ach, "frac": (mw_ach / alu_peak) if mw_ach else None}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * t_all / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -119,12 +119,13 @@ typedef struct {
     double seconds;            /* wall time of the call */
     double geom_ms;            /* walk-kernel time in its geometry phase: kernel_ms x that phase's
                                   share of the CTAs' busy cycles */
-    double fill_ms;            /* ... in its table-fill and batch-reduction phases */
+    double fill_ms;            /* ... in its table-fill phase */
     double mw_ms;              /* ... in its MicroWalk phase */
     uint64_t launches;         /* kernels launched by the call (memsets not counted) */
     uint64_t mw_jobs;          /* MicroWalk transitions */
     uint64_t walks_issued;     /* walk ids started (>= walks: a sigma-target run stops mid-flight) */
     double kernel_ms;          /* device time of the walk kernel (CUDA events on the launch stream) */
+    double reduce_ms;          /* walk-kernel time in its batch-reduction phase (as geom_ms) */
 } frw_stats;
 
 /* Fill *opt with defaults (N = 24, FP64 geometry, hybrid on, offset 0.5,

@@ -65,7 +65,8 @@ class frw_stats(ctypes.Structure):
                 ("branch", c_uint64 * 3), ("strat_hops", c_uint64), ("hom_hops", c_uint64),
                 ("mw_hops", c_uint64), ("tables_built", c_uint64), ("rounds", c_uint64), ("seconds", c_double),
                 ("geom_ms", c_double), ("fill_ms", c_double), ("mw_ms", c_double), ("launches", c_uint64),
-                ("mw_jobs", c_uint64), ("walks_issued", c_uint64), ("kernel_ms", c_double)]
+                ("mw_jobs", c_uint64), ("walks_issued", c_uint64), ("kernel_ms", c_double),
+                ("reduce_ms", c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "branch"}

@@ -1561,7 +1561,7 @@ constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // suspension only if this much ge
 
 struct WalkShared {
     uint32_t W[256];                 // quantised weights of Eq. 6, [centre][neighbour material]
-    uint32_t g_head, pad3[3];
+    uint32_t g_head, g_back, pad3[2];
     uint32_t q_count, q_head, s_count, g_count;
     uint32_t f_count, active, issuable, stop;
     uint32_t red, finished, n_free, j_lo;
@@ -1633,16 +1633,13 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
             scan_jobs(E, lo, pub, open);
             if (lane == 0) {
                 sh.g_count = 0; sh.f_count = 0; sh.active = 0; sh.finished = 0; sh.n_free = 0; sh.g_head = 0;
+                sh.g_back = 0;
                 sh.issuable = open;
                 sh.j_lo = lo;
                 sh.j_pub = pub;
             }
         }
         __syncthreads();
-        // Two warp groups run concurrently in every epoch.  Geometry warps step every
-        // slot that is not in MicroWalk (and queue new MicroWalk jobs for the next
-        // epoch); MicroWalk warps run the jobs queued by the previous epoch.  The
-        // groups touch disjoint slots; both append to the next epoch's queue.
         uint16_t *q_now = sh.qlist[cur];
         uint16_t *q_next = sh.qlist[cur ^ 1];
         {
@@ -1661,28 +1658,37 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
                 if (st != ST_FRESH && st != ST_IDLE && st != ST_MW) wj = E.s.job[s];
                 const bool free_slot =
                     st == ST_FRESH || (need && st != ST_FRESH && ((volatile int *)E.job_cancel)[wj]);
-                const uint32_t ba = __ballot_sync(FULL_MASK, act), bn = __ballot_sync(FULL_MASK, need);
+                // slots that start a walk (first transition) are listed from the front,
+                // the others from the back: warps then take work of one kind, the
+                // costliest first
+                const bool first = need && (free_slot || st == ST_FIRST);
+                const uint32_t ba = __ballot_sync(FULL_MASK, act);
+                const uint32_t b1 = __ballot_sync(FULL_MASK, first), b2 = __ballot_sync(FULL_MASK, need && !first);
                 const uint32_t bf = __ballot_sync(FULL_MASK, free_slot);
-                uint32_t gb = 0;
+                uint32_t g1 = 0, g2 = 0;
                 if (lane == 0) {
                     if (ba) atomicAdd(&sh.active, (uint32_t)__popc(ba));
-                    if (bn) gb = atomicAdd(&sh.g_count, (uint32_t)__popc(bn));
+                    if (b1) g1 = atomicAdd(&sh.g_count, (uint32_t)__popc(b1));
+                    if (b2) g2 = atomicAdd(&sh.g_back, (uint32_t)__popc(b2));
                     if (bf) atomicAdd(&sh.n_free, (uint32_t)__popc(bf));
                 }
-                gb = __shfl_sync(FULL_MASK, gb, 0);
-                if (need) sh.glist[gb + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)o;
+                g1 = __shfl_sync(FULL_MASK, g1, 0);
+                g2 = __shfl_sync(FULL_MASK, g2, 0);
+                const uint32_t below = (1u << lane) - 1u;
+                if (first) sh.glist[g1 + __popc(b1 & below)] = (uint16_t)o;
+                else if (need) sh.glist[P - 1u - (g2 + __popc(b2 & below))] = (uint16_t)o;
             }
             __syncthreads();
             if (warp == 0) claim_ids(E, sh.ir, sh.n_free, sh.j_lo, sh.j_pub);
             __syncthreads();
-            const uint32_t ng = sh.g_count;
+            const uint32_t n1 = sh.g_count, ng = n1 + sh.g_back;
             const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
             // dynamic distribution: slot steps differ a lot in cost (first transitions,
             // chains of analytical hops), so threads take the next slot when free
             for (;;) {
                 const uint32_t i = atomicAdd(&sh.g_head, 1u);
                 if (i >= ng) break;
-                const uint32_t o = sh.glist[i];
+                const uint32_t o = i < n1 ? sh.glist[i] : sh.glist[P - 1u - (i - n1)];
                 geo_slot<T>(E, base + o, o, fl, q_now, &sh.q_count, sh.ir);
             }
         }

@@ -1058,7 +1058,8 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             s.rounds = ctx->h_status[STAT_EPOCHS];
             s.seconds = secs;
             s.geom_ms = ctot > 0 ? kms * (double)cyc[0] / ctot : 0.0;
-            s.fill_ms = ctot > 0 ? kms * (double)(cyc[1] + cyc[2]) / ctot : 0.0;
+            s.fill_ms = ctot > 0 ? kms * (double)cyc[1] / ctot : 0.0;
+            s.reduce_ms = ctot > 0 ? kms * (double)cyc[2] / ctot : 0.0;
             s.mw_ms = ctot > 0 ? kms * (double)cyc[3] / ctot : 0.0;
             s.launches = 1;
             s.kernel_ms = kms;
