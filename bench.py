@@ -457,7 +457,8 @@ def main():
                                    % (a.N, masters, a.sigma, a.budget),
                        "geometry": a.precision, "accumulate": "exact int128 (fp64 in/out)",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"weak x{world}",
-                       "tuning": {k: tuning[k] for k in ("pool_per_cta", "hops_per_epoch", "suspend_lanes")}},
+                       "tuning": {k: tuning[k] for k in ("pool_per_cta", "hops_per_epoch", "suspend_lanes",
+                                                            "suspend_min_steps")}},
             "micro_transitions_per_s": agg["micro"] * (walks_all / max(1, agg["walks"])) / t_all,
             "hops_per_walk": agg["hops"] / max(1, agg["walks"]),
             "mw_hop_fraction": agg["mw_hops"] / max(1, agg["hops"] - agg["walks"]),

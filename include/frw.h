@@ -215,7 +215,7 @@ typedef struct {
                                   still walking may park them until the next epoch (0 .. 32) */
     int32_t mw_warps_per_cta;  /* stand-alone MicroWalk kernel: warps per CTA (1 .. 16) */
     int32_t mw_ctas_per_sm;    /* ... CTAs per SM (1 .. 32) */
-    int32_t reserved;
+    int32_t suspend_min_steps; /* ... once each of them has made this many steps in the epoch (4 .. 4096) */
     double walks_per_s;        /* frw_autotune: measured with the chosen walk-kernel settings */
     double mw_steps_per_s;     /* frw_autotune: measured with the chosen MicroWalk shape */
 } frw_tuning;
@@ -225,9 +225,9 @@ int frw_set_tuning(frw_ctx *ctx, const frw_tuning *t);   /* FRW_EINVAL outside t
 
 /* Autotuner: runs the sample jobs in budget mode (each capped at sample_walks
  * walks) once per candidate walk-kernel setting (slots per CTA in {1024, 2048,
- * 3072, 4096, the context's pool} up to the context's pool x (analytical hops
- * per epoch, suspension lanes) in {4, 8} x
- * {2, 4, 8, 16} and (16, 4)) and keeps the fastest;
+ * 3072, 4096, the context's pool} up to the context's pool x ten combinations of
+ * analytical hops per epoch {2, 4, 8}, suspension lanes {4, 8, 16, 32} and
+ * suspension progress guard {32, 64, 128}) and keeps the fastest;
  * then times the stand-alone MicroWalk kernel on 512 random cubes of the
  * context's N (2-6 blocks of up to four of its registered materials, 4096
  * samples each) for each shape (warps per CTA x

@@ -1559,6 +1559,16 @@ constexpr int POOL_MAX = 4096;
 constexpr int FILL_MAX = 128;
 constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // suspension only if this much geometry work is waiting
 
+// Clock read that cannot move above the preceding barrier: it is taken only after
+// a shared-memory word loaded after that barrier has been tested.
+__device__ __forceinline__ long long clock_after(const uint32_t *anchor)
+{
+    const uint32_t v = *(const volatile uint32_t *)anchor;
+    long long c = 0;
+    if (v != 0xfffffffeu) c = clock64();
+    return c;
+}
+
 struct WalkShared {
     uint32_t W[256];                 // quantised weights of Eq. 6, [centre][neighbour material]
     uint32_t g_head, g_back, pad3[2];
@@ -1693,7 +1703,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
             }
         }
         __syncthreads();
-        const long long cg1 = clock64();
+        const long long cg1 = clock_after(&sh.q_count);
         {
             // ---------------- MicroWalk ----------------
             const int mwarp = warp;
@@ -1797,7 +1807,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
             }
         }
         __syncthreads();
-        const long long c1 = clock64();
+        const long long c1 = clock_after(&sh.q_next);
         if (tid == 0) {
             cyc[0] += (unsigned long long)(cg1 - c0);
             cyc[3] += (unsigned long long)(c1 - cg1);
@@ -1827,7 +1837,8 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
             }
             __syncthreads();
         }
-        const long long c2 = clock64();
+        __syncthreads();
+        const long long c2 = clock_after(&sh.f_count);
         // ---------------- reduction phase ----------------
         for (;;) {
             if (tid == 0) sh.red = take_batch(E);
@@ -1838,7 +1849,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
             reduce_batch(E, g, reinterpret_cast<unsigned long long *>(dsm));
             if (tid == 0) advance_job(E, __ldcg(E.batch_job + g));
         }
-        const long long c3 = clock64();
+        const long long c3 = clock_after(&sh.red);
         epochs++;
         if (tid == 0) {
             cyc[1] += (unsigned long long)(c2 - c1);

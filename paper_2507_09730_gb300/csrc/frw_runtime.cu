@@ -201,7 +201,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.idle_timeout_s = 10.0;
     E.hops_per_epoch = ctx->tune.hops_per_epoch;
     E.suspend_lanes = ctx->tune.suspend_lanes;
-    E.suspend_min_steps = 64;
+    E.suspend_min_steps = (uint32_t)ctx->tune.suspend_min_steps;
     return E;
 }
 
@@ -322,6 +322,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->tune.pool_per_cta = (int32_t)(ctx->NS / ctx->grid);
     ctx->tune.hops_per_epoch = 4;
     ctx->tune.suspend_lanes = 8;
+    ctx->tune.suspend_min_steps = 64;
     ctx->tune.mw_warps_per_cta = ctx->shape.mw_warps;
     ctx->tune.mw_ctas_per_sm = ctx->shape.mw_ctas_per_sm;
     ctx->tune.walks_per_s = 0.0;
@@ -1718,7 +1719,8 @@ static int tuning_ok(frw_ctx *ctx, const frw_tuning &t)
 {
     const int pool0 = (int)(ctx->NS / ctx->grid);
     return t.pool_per_cta >= 256 && t.pool_per_cta <= pool0 && t.pool_per_cta % 256 == 0 && t.hops_per_epoch >= 1 &&
-           t.hops_per_epoch <= 64 && t.suspend_lanes >= 0 && t.suspend_lanes <= 32 && t.mw_warps_per_cta >= 1 &&
+           t.hops_per_epoch <= 64 && t.suspend_lanes >= 0 && t.suspend_lanes <= 32 && t.suspend_min_steps >= 4 &&
+           t.suspend_min_steps <= 4096 && t.mw_warps_per_cta >= 1 &&
            t.mw_warps_per_cta <= 16 && t.mw_ctas_per_sm >= 1 && t.mw_ctas_per_sm <= 32;
 }
 
@@ -1796,11 +1798,15 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
         for (int rep = 0; rep < 2; rep++) {           // the first pass also warms the table cache
             for (int pool : {1024, 2048, 3072, 4096, pool0}) {
                 if (pool > pool0 || (pool == pool0 && pool0 % 1024 == 0)) continue;   // pool0 itself: once
-                for (int hs : {0x204, 0x404, 0x804, 0x1004, 0x208, 0x408, 0x808, 0x1008, 0x410}) {
+                // (hops per epoch, suspension lanes, suspension progress guard)
+                static const int cand[][3] = {{4, 8, 64},  {4, 16, 64}, {4, 32, 64},  {4, 32, 32}, {4, 32, 128},
+                                              {4, 16, 32}, {8, 8, 64},  {8, 32, 64},  {2, 32, 64}, {4, 4, 64}};
+                for (const auto &c : cand) {
                     frw_tuning t = ctx->tune;
                     t.pool_per_cta = pool;
-                    t.hops_per_epoch = hs & 0xff;
-                    t.suspend_lanes = hs >> 8;
+                    t.hops_per_epoch = c[0];
+                    t.suspend_lanes = c[1];
+                    t.suspend_min_steps = c[2];
                     std::vector<JobRun> runs(jobs.size());
                     for (size_t i = 0; i < jobs.size(); i++) runs[i].desc = jobs[i];
                     std::vector<frw_stats> st(jobs.size());
@@ -1818,6 +1824,7 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
                         best.pool_per_cta = pool;
                         best.hops_per_epoch = t.hops_per_epoch;
                         best.suspend_lanes = t.suspend_lanes;
+                        best.suspend_min_steps = t.suspend_min_steps;
                         best.walks_per_s = rate;
                     }
                 }
