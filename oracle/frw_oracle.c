@@ -42,6 +42,20 @@
  *      B3 homogenise to the volume-mean permittivity.
  *   R7 Gaussian surface = master box grown by gauss_frac * (smallest L-infinity gap
  *      to another conductor or wall), point uniform by area.
+ *   R8 MicroWalk-E (Sec. III-B, Fig. 3b; optional, factor f > 1): a later cube
+ *      that is not stratified is expanded to half-size f * R (R = the half-size of
+ *      the conductor-free cube just classified).  A voxel whose centre lies
+ *      outside the domain is a node of the grounded walls; one whose centre lies in
+ *      conductor k (half-open test) is a node of k, whatever block covers it.
+ *      Such a neighbour has alpha = 1 (like a boundary panel, Scheme B); stepping
+ *      onto it absorbs the walk at that conductor.  The expanded cube lists its
+ *      dielectric blocks (rule of cube_classify) plus every conductor and every
+ *      exterior slab (x < lo or x >= hi on one axis) holding a voxel centre; if
+ *      that is more than ORC_KMAX objects, or its dielectric list overflows, f is
+ *      lowered by one, down to 2, and otherwise plain MicroWalk runs on the R
+ *      cube.  Structures of more than 254 conductors use plain MicroWalk.  An exit
+ *      panel that lies in a conductor or outside the domain is absorbed by the
+ *      next hop's distance test.
  */
 #include <math.h>
 #include <stdint.h>
@@ -117,6 +131,7 @@ typedef struct {
     int first_mode;        /* 0: branches B1-B3; 1: exact FD flux kernel per walk */
     double gauss_frac;     /* Gaussian-surface offset as a fraction of the smallest gap */
     int max_hops;
+    int mwe;               /* MicroWalk-E expansion factor (R8); 0 or 1: off */
 } orc_options;
 
 /* Quantised alpha of Eq. 6 (reading R4): W[v][i] for an interior neighbour i of v,
@@ -336,6 +351,126 @@ static void microwalk(int N, const uint8_t *lat, const uint32_t W[16][16], const
     }
     node[0] = x[0]; node[1] = x[1]; node[2] = x[2];
     *steps = t;
+}
+
+/* ------------------------------------------------------------------------- */
+/* MicroWalk-E (reading R8). */
+static int in_box(const double p[3], const double *lo, const double *hi)
+{
+    return lo[0] <= p[0] && p[0] < hi[0] && lo[1] <= p[1] && p[1] < hi[1] && lo[2] <= p[2] && p[2] < hi[2];
+}
+
+/* conductor absorbing at point p: n_c outside the domain, k inside conductor k,
+ * -1 in the dielectric */
+static int conductor_at(const orc_structure *S, const double p[3])
+{
+    if (!in_box(p, S->dom_lo, S->dom_hi)) return S->n_c;
+    for (int k = 0; k < S->n_c; k++)
+        if (in_box(p, S->c_lo + 3 * k, S->c_hi + 3 * k)) return k;
+    return -1;
+}
+
+/* explicit lattice of an expanded cube: material ids and conductor ids (-1: none) */
+static void cube_lattice_e(const orc_structure *S, const cube_t *q, uint8_t *lat, int16_t *cond)
+{
+    int N = q->N;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++) {
+                double p[3] = {vcentre(q->base[0], q->h, i), vcentre(q->base[1], q->h, j),
+                               vcentre(q->base[2], q->h, k)};
+                int v = (i * N + j) * N + k;
+                cond[v] = (int16_t)conductor_at(S, p);
+                lat[v] = (uint8_t)material_at(S, p);
+            }
+}
+
+/* conductors and exterior slabs holding a voxel centre of the cube */
+static int mwe_extra(const orc_structure *S, const cube_t *q)
+{
+    int N = q->N, n = 0;
+    for (int k = 0; k < S->n_c; k++) {
+        int hit = 1;
+        for (int a = 0; a < 3 && hit; a++) {
+            double lo = S->c_lo[3 * k + a], hi = S->c_hi[3 * k + a];
+            int any = 0;
+            for (int i = 0; i < N; i++) {
+                double x = vcentre(q->base[a], q->h, i);
+                if (lo <= x && x < hi) any = 1;
+            }
+            hit = any;
+        }
+        n += hit;
+    }
+    for (int a = 0; a < 3; a++) {
+        if (vcentre(q->base[a], q->h, 0) < S->dom_lo[a]) n++;
+        if (vcentre(q->base[a], q->h, N - 1) >= S->dom_hi[a]) n++;
+    }
+    return n;
+}
+
+/* MicroWalk on an expanded lattice: conductor neighbours have alpha = 1; the walk
+ * ends on leaving the lattice (returns -1, exit node) or on stepping onto a
+ * conductor node (returns that conductor). */
+static int microwalk_e(int N, const uint8_t *lat, const int16_t *cond, const uint32_t W[16][16],
+                       const uint32_t key[2], uint64_t walk, uint32_t hop, uint32_t start_word, int node[3],
+                       uint64_t *steps)
+{
+    uint32_t s = start_word >> 29;
+    int x[3] = {N / 2 - 1 + (int)(s & 1u), N / 2 - 1 + (int)((s >> 1) & 1u),
+                N / 2 - 1 + (int)((s >> 2) & 1u)};
+    uint32_t blk[4] = {0, 0, 0, 0};
+    uint64_t t = 0;
+    int absorbed = -1;
+    for (;;) {
+        if ((t & 3u) == 0) walk_block(key, walk, hop, (uint32_t)(1u + (uint32_t)(t >> 2)), blk);
+        uint32_t u = blk[t & 3u];
+        int mv = lat[(x[0] * N + x[1]) * N + x[2]];
+        uint32_t prefix[6], acc = 0;
+        for (int k = 0; k < 6; k++) {
+            int a = k >> 1, d = (k & 1) ? 1 : -1;
+            int y[3] = {x[0], x[1], x[2]};
+            y[a] += d;
+            int mk;
+            if (y[a] < 0 || y[a] >= N) mk = ORC_BOUNDARY;
+            else {
+                int v = (y[0] * N + y[1]) * N + y[2];
+                mk = cond[v] >= 0 ? ORC_BOUNDARY : lat[v];
+            }
+            acc += W[mv][mk];
+            prefix[k] = acc;
+        }
+        uint32_t r = (uint32_t)(((uint64_t)u * (uint64_t)acc) >> 32);
+        int k = 0;
+        while (k < 5 && !(r < prefix[k])) k++;
+        x[k >> 1] += (k & 1) ? 1 : -1;
+        t++;
+        if (x[k >> 1] < 0 || x[k >> 1] >= N) break;
+        int c = cond[(x[0] * N + x[1]) * N + x[2]];
+        if (c >= 0) {
+            absorbed = c;
+            break;
+        }
+    }
+    node[0] = x[0]; node[1] = x[1]; node[2] = x[2];
+    *steps = t;
+    return absorbed;
+}
+
+/* Stand-alone MicroWalk-E for tests: material ids and conductor ids per voxel.
+ * Returns the conductor reached, or -1 with node_out on the boundary. */
+int orc_microwalk_e(int N, const uint8_t *lat, const int16_t *cond, const double *eps, int n_mat, uint64_t seed,
+                    uint64_t request, uint64_t walk, uint32_t hop, int32_t *node_out, uint64_t *steps)
+{
+    uint32_t W[16][16];
+    make_w_table(eps, n_mat, W);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ (uint32_t)request};
+    uint32_t b0[4];
+    walk_block(key, walk, hop, 0, b0);
+    int node[3];
+    int c = microwalk_e(N, lat, cond, W, key, walk, hop, b0[0], node, steps);
+    node_out[0] = node[0]; node_out[1] = node[1]; node_out[2] = node[2];
+    return c;
 }
 
 /* Stand-alone MicroWalk for tests: lattice given as material ids. */
@@ -766,6 +901,7 @@ typedef struct {
     uint64_t steps;       /* MicroWalk steps */
     int32_t branch;       /* first-cube branch */
     uint32_t n_strat, n_hom, n_mw;
+    uint32_t n_mwe;       /* MicroWalk transitions on expanded cubes (R8) */
 } walk_rec;
 
 typedef struct {
@@ -827,6 +963,7 @@ typedef struct {
     double tau;
     tcache_t *tc;
     uint8_t *lat;
+    int16_t *cond;
 } walker_t;
 
 static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
@@ -964,10 +1101,33 @@ static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
             rec->n_strat++;
         } else {
             uint64_t st;
-            cube_lattice(S, &q, wk->lat);
-            microwalk(N, wk->lat, wk->W, wk->key, walk, hop, hb[0], node, &st);
-            rec->steps += st;
-            rec->n_mw++;
+            int done = 0;
+            if (o->mwe > 1 && S->n_c <= 254) {
+                for (int f = o->mwe; f >= 2 && !done; f--) {
+                    cube_t qe;
+                    cube_setup(&qe, r, q.R * (double)f, N);
+                    cube_classify(S, &qe);
+                    if (qe.kind == CUBE_OVERFLOW || qe.nlist + mwe_extra(S, &qe) > ORC_KMAX) continue;
+                    cube_lattice_e(S, &qe, wk->lat, wk->cond);
+                    int kabs = microwalk_e(N, wk->lat, wk->cond, wk->W, wk->key, walk, hop, hb[0], node, &st);
+                    rec->steps += st;
+                    rec->n_mw++;
+                    rec->n_mwe++;
+                    if (kabs >= 0) {
+                        rec->k = kabs;
+                        rec->hops = hop + 1;
+                        return;
+                    }
+                    q = qe;
+                    done = 1;
+                }
+            }
+            if (!done) {
+                cube_lattice(S, &q, wk->lat);
+                microwalk(N, wk->lat, wk->W, wk->key, walk, hop, hb[0], node, &st);
+                rec->steps += st;
+                rec->n_mw++;
+            }
         }
         node_point(&q, node, r);
         hop++;
@@ -985,16 +1145,16 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
                 const double *c_hi, int n_b, const double *b_lo, const double *b_hi,
                 const int32_t *b_mat, int n_mat, const double *eps, int bg,
                 int N, uint64_t seed, uint64_t request, int hybrid, int first_mode,
-                double gauss_frac, int max_hops, int master, uint64_t walk_begin, uint64_t n_walks,
+                double gauss_frac, int max_hops, int mwe, int master, uint64_t walk_begin, uint64_t n_walks,
                 double sigma_target, uint64_t batch,
                 double *S1, double *S2, uint64_t *n_used,
                 double *rec_omega, int32_t *rec_k, uint32_t *rec_hops, uint64_t *rec_steps,
                 int32_t *rec_branch,
-                uint64_t *stats /* 10: hops, steps, strat, hom, mw, branch 0..2, truncated, - */)
+                uint64_t *stats /* 10: hops, steps, strat, hom, mw, branch 0..2, truncated, mwe */)
 {
     orc_structure S = {{dom_lo[0], dom_lo[1], dom_lo[2]}, {dom_hi[0], dom_hi[1], dom_hi[2]},
                        n_c, c_lo, c_hi, n_b, b_lo, b_hi, b_mat, n_mat, eps, bg};
-    orc_options o = {N, seed, request, hybrid, first_mode, gauss_frac, max_hops};
+    orc_options o = {N, seed, request, hybrid, first_mode, gauss_frac, max_hops, mwe};
     walker_t wk;
     wk.S = &S;
     wk.o = &o;
@@ -1008,6 +1168,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
     wk.tau = 1e-9 * edge;
     wk.tc = calloc(1, sizeof(tcache_t));
     wk.lat = malloc((size_t)N * N * N);
+    wk.cond = malloc(sizeof(int16_t) * (size_t)N * N * N);
     for (int k = 0; k <= n_c; k++) { S1[k] = 0.0; S2[k] = 0.0; }
     for (int s = 0; s < 10; s++) stats[s] = 0;
     uint64_t used = 0;
@@ -1030,6 +1191,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
         stats[2] += rec.n_strat;
         stats[3] += rec.n_hom;
         stats[4] += rec.n_mw;
+        stats[9] += rec.n_mwe;
         if (rec.branch >= 0 && rec.branch <= 2) stats[5 + rec.branch]++;
         used = w + 1;
         if (sigma_target > 0.0 && batch > 0 && used % batch == 0 && used >= 2) {
@@ -1058,6 +1220,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
     tcache_free(wk.tc);
     free(wk.tc);
     free(wk.lat);
+    free(wk.cond);
     return ntab;
 }
 
@@ -1099,4 +1262,15 @@ void orc_microwalk_many(int N, const uint8_t *lat, const double *eps, int n_mat,
         microwalk(N, lat, W, key, walk0 + w, 0, b0[0], node, &steps[w]);
         nodes[3 * w] = node[0]; nodes[3 * w + 1] = node[1]; nodes[3 * w + 2] = node[2];
     }
+}
+
+/* n MicroWalk-E walks (walk ids walk0 .. walk0+n-1, the given hop) for tests:
+ * conductor reached (or -1) and exit node of each. */
+void orc_microwalk_e_many(int N, const uint8_t *lat, const int16_t *cond, const double *eps, int n_mat, uint64_t seed,
+                          uint64_t request, uint64_t walk0, uint64_t n, uint32_t hop, int32_t *cond_out,
+                          int32_t *nodes_out, uint64_t *steps_out)
+{
+    for (uint64_t w = 0; w < n; w++)
+        cond_out[w] = orc_microwalk_e(N, lat, cond, eps, n_mat, seed, request, walk0 + w, hop, nodes_out + 3 * w,
+                                      steps_out + w);
 }

@@ -68,8 +68,13 @@ def lib():
         L.orc_expected_steps.restype = d
         L.orc_table.argtypes = [i, i, i, i, P(u8), P(d), P(u32), P(u8), P(d)]
         L.orc_panel_node.argtypes = [i, i, i, i, i, P(ctypes.c_int32)]
+        L.orc_microwalk_e.argtypes = [i, P(u8), P(ctypes.c_int16), P(d), i, u64, u64, u64, u32,
+                                      P(ctypes.c_int32), P(u64)]
+        L.orc_microwalk_e.restype = i
+        L.orc_microwalk_e_many.argtypes = [i, P(u8), P(ctypes.c_int16), P(d), i, u64, u64, u64, u64, u32,
+                                           P(ctypes.c_int32), P(ctypes.c_int32), P(u64)]
         L.orc_frw_run.argtypes = ([P(d), P(d), i, P(d), P(d), i, P(d), P(d), P(ctypes.c_int32), i,
-                                   P(d), i, i, u64, u64, i, i, d, i, i, u64, u64, d, u64,
+                                   P(d), i, i, u64, u64, i, i, d, i, i, i, u64, u64, d, u64,
                                    P(d), P(d), P(u64), P(d), P(ctypes.c_int32), P(u32), P(u64),
                                    P(ctypes.c_int32), P(u64)])
         L.orc_frw_run.restype = i
@@ -224,7 +229,7 @@ class RunResult:
 
 
 def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, gauss_frac=0.5,
-            max_hops=100000, walk_begin=0, sigma_target=0.0, batch=16384, records=True):
+            max_hops=100000, walk_begin=0, sigma_target=0.0, batch=16384, records=True, mwe=0):
     """Run walks ``walk_begin .. walk_begin + n_walks - 1`` of Algorithm 1 for
     ``master`` on structure ``s`` (a :class:`workloads.Structure`)."""
     L = lib()
@@ -248,13 +253,42 @@ def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, 
         _p(s.block_lo, ctypes.c_double), _p(s.block_hi, ctypes.c_double),
         _p(s.block_mat, ctypes.c_int32), s.n_mat, _p(s.eps, ctypes.c_double), int(s.background),
         int(N), int(seed), int(request), int(hybrid), int(first_mode), float(gauss_frac),
-        int(max_hops), int(master), int(walk_begin), n, float(sigma_target), int(batch),
+        int(max_hops), int(mwe), int(master), int(walk_begin), n, float(sigma_target), int(batch),
         _p(S1, ctypes.c_double), _p(S2, ctypes.c_double), _p(used, ctypes.c_uint64), *rp,
         _p(stats, ctypes.c_uint64))
     u = int(used[0])
     if records:
         om, kk, hp, st, br = om[:u], kk[:u], hp[:u], st[:u], br[:u]
     return RunResult(S1, S2, u, om, kk, hp, st, br, stats, ntab)
+
+
+def microwalk_e(N, lat, cond, eps, seed, request, walk, hop=1):
+    """One MicroWalk-E walk (reading R8 of frw_oracle.c) on an explicit lattice with
+    conductor nodes (cond >= 0).  -> (conductor reached or -1, exit node, steps)."""
+    lat = np.ascontiguousarray(lat, np.uint8).ravel()
+    cond = np.ascontiguousarray(cond, np.int16).ravel()
+    e = np.ascontiguousarray(eps, np.float64)
+    node = np.zeros(3, np.int32)
+    st = np.zeros(1, np.uint64)
+    c = lib().orc_microwalk_e(int(N), _p(lat, ctypes.c_uint8), _p(cond, ctypes.c_int16), _p(e, ctypes.c_double),
+                              len(e), int(seed), int(request), int(walk), int(hop), _p(node, ctypes.c_int32),
+                              _p(st, ctypes.c_uint64))
+    return int(c), node, int(st[0])
+
+
+def microwalk_e_many(N, lat, cond, eps, seed, request, walk0, n, hop=0):
+    """n MicroWalk-E walks (walk ids walk0.., the given hop) -> (conductor reached or
+    -1, exit nodes (n, 3), steps)."""
+    lat = np.ascontiguousarray(lat, np.uint8).ravel()
+    cond = np.ascontiguousarray(cond, np.int16).ravel()
+    e = np.ascontiguousarray(eps, np.float64)
+    co = np.zeros(n, np.int32)
+    nodes = np.zeros((n, 3), np.int32)
+    st = np.zeros(n, np.uint64)
+    lib().orc_microwalk_e_many(int(N), _p(lat, ctypes.c_uint8), _p(cond, ctypes.c_int16), _p(e, ctypes.c_double),
+                               len(e), int(seed), int(request), int(walk0), int(n), int(hop), _p(co, ctypes.c_int32),
+                               _p(nodes, ctypes.c_int32), _p(st, ctypes.c_uint64))
+    return co, nodes, st
 
 
 # ---------------------------------------------------------------------------
@@ -335,3 +369,83 @@ def absorption_exact(N, lat, eps, quantised=True):
     P = B.T @ y
     Etau = float(y.sum())
     return P.reshape(6, N, N), Etau
+
+
+def absorption_exact_e(N, lat, cond, eps):
+    """MicroWalk-E's exact absorbing chain (reading R8): dielectric voxels are the
+    transient states; a step leaves the lattice (boundary panel) or lands on a
+    conductor voxel (absorbed there), both with weight alpha = 1; the quantised
+    32-bit law as in :func:`absorption_exact`.
+
+    Returns (P[6, N, N] exit probabilities per boundary panel, Q[c] absorption
+    probability per conductor id, E(tau))."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+
+    lat = np.asarray(lat).reshape(N, N, N)
+    cond = np.asarray(cond).reshape(N, N, N)
+    W = w_table(np.asarray(eps, np.float64)).astype(np.int64)
+    diel = cond < 0
+    ids = -np.ones((N, N, N), np.int64)
+    ids[diel] = np.arange(int(diel.sum()))
+    n = int(diel.sum())
+    nc = int(cond.max()) + 1 if (cond >= 0).any() else 0
+
+    def panel(a, side, x):
+        o = [b for b in range(3) if b != a]
+        return ((2 * a + side) * N + x[o[0]]) * N + x[o[1]]
+
+    rows, cols, vals = [], [], []
+    brow, bcol, bval = [], [], []
+    crow, ccol, cval = [], [], []
+    for i in range(N):
+        for j in range(N):
+            for k in range(N):
+                if not diel[i, j, k]:
+                    continue
+                v = int(ids[i, j, k])
+                mv = int(lat[i, j, k])
+                wts, dests = [], []
+                for kk in range(6):
+                    a, d = kk >> 1, (1 if kk & 1 else -1)
+                    x = [i, j, k]
+                    x[a] += d
+                    if x[a] < 0 or x[a] >= N:
+                        wts.append(W[mv, BOUNDARY])
+                        dests.append(("b", panel(a, 0 if x[a] < 0 else 1, x)))
+                    elif cond[x[0], x[1], x[2]] >= 0:
+                        wts.append(W[mv, BOUNDARY])
+                        dests.append(("c", int(cond[x[0], x[1], x[2]])))
+                    else:
+                        wts.append(W[mv, int(lat[x[0], x[1], x[2]])])
+                        dests.append(("i", int(ids[x[0], x[1], x[2]])))
+                S = int(sum(wts))
+                pre = np.cumsum(np.asarray(wts, np.int64))
+                ce = [-(-int(p) * 2 ** 32 // S) for p in pre]
+                prob = np.diff(np.concatenate([[0], ce])) / 2.0 ** 32
+                rows.append(v)
+                cols.append(v)
+                vals.append(1.0)
+                for (kind, dst), pr in zip(dests, prob):
+                    if kind == "i":
+                        rows.append(v)
+                        cols.append(dst)
+                        vals.append(-pr)
+                    elif kind == "b":
+                        brow.append(v)
+                        bcol.append(dst)
+                        bval.append(pr)
+                    else:
+                        crow.append(v)
+                        ccol.append(dst)
+                        cval.append(pr)
+    A = sp.csc_matrix((vals, (rows, cols)), shape=(n, n))
+    B = sp.csr_matrix((bval, (brow, bcol)), shape=(n, 6 * N * N))
+    Cm = sp.csr_matrix((cval, (crow, ccol)), shape=(n, max(nc, 1)))
+    ec = np.zeros(n)
+    for i in (N // 2 - 1, N // 2):
+        for j in (N // 2 - 1, N // 2):
+            for k in (N // 2 - 1, N // 2):
+                ec[ids[i, j, k]] += 0.125
+    y = spl.splu(A.T.tocsc()).solve(ec)
+    return (B.T @ y).reshape(6, N, N), np.asarray(Cm.T @ y).ravel()[:nc], float(y.sum())

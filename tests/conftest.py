@@ -14,3 +14,15 @@ def pytest_configure(config):
 
 
 GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def two_plate_fdm():
+    """Whole-structure finite-difference rows of the two-plate structure (master 0)
+    at h = 0.05 um (with its discrete energy) and h = 0.025 um (about 45 s)."""
+    from paper_2507_09730_gb300 import workloads as W
+    from tests import fdm_reference as F
+    s = W.tiny_two_plate()
+    c1, u1 = F.capacitance_row(s, 0, 0.05, energy=True)
+    c2 = F.capacitance_row(s, 0, 0.025, rtol=1e-8)
+    return s, (c1, u1), c2

@@ -17,11 +17,8 @@ H = 0.05     # every face of the two-plate structure lies on the planes of h and
 
 
 @pytest.fixture(scope="module")
-def fdm_rows():
-    s = W.tiny_two_plate()
-    c1, u1 = F.capacitance_row(s, 0, H, energy=True)
-    c2 = F.capacitance_row(s, 0, H / 2, rtol=1e-8)     # 4 M cells, about 45 s
-    return s, (c1, u1), c2
+def fdm_rows(two_plate_fdm):
+    return two_plate_fdm
 
 
 def test_fdm_reference_is_consistent(fdm_rows):
