@@ -262,6 +262,40 @@ def fp32_deviation(s, masters, N, sigma, budget):
     return out
 
 
+def mwe_measurement(s, masters, N, precision, sigma, budget, tuning, rows_mw, steps=2):
+    """FRW-MWE: the same extraction with MicroWalk-E (non-stratified later cubes
+    expanded 5x, conductors inside them absorbing), timed like the main steps; its
+    rows compared with the FRW-MW rows of the main measurement."""
+    import torch
+    from paper_2507_09730_gb300 import binding as B
+    ctx = B.Context(0, N=N, precision=precision, seed=0, mwe_factor=5)
+    ctx.set_tuning(**{k: tuning[k] for k in ("pool_per_cta", "hops_per_epoch", "suspend_lanes", "suspend_min_steps")})
+    stream = torch.cuda.current_stream()
+    B.frw_set_stream(ctx.ctx, stream.cuda_stream)
+    sid = ctx.load(s)
+    jobs = lambda r: [dict(structure_id=sid, master=m, walk_budget=budget, sigma_target=sigma,
+                           request_id=r * 4 + i) for i, m in enumerate(masters)]
+    ctx.extract_batch(jobs(70_000))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    walks = hops = 0
+    e0.record(stream)
+    for k in range(steps):
+        res, _ = ctx.extract_batch(jobs(80_000 + k))
+        walks += sum(r[2]["walks"] for r in res)
+        hops += sum(r[2]["hops"] for r in res)
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    ctx.close()
+    dev = []
+    for m, (C, se, _), (Cw, sew, _) in zip(masters, res, rows_mw):
+        dev.append({"master": m, "C_ii_mwe": C[m], "C_ii_mw": Cw[m], "diff_in_sigma": (C[m] - Cw[m]) / float(np.hypot(se[m], sew[m]))})
+    return {"workload": "as the main line, MicroWalk-E (expansion 5) on non-stratified later cubes",
+            "walks_per_s": walks / secs, "ms_per_step": 1e3 * secs / steps, "hops_per_walk": hops / max(1, walks),
+            "vs_frw_mw": dev}
+
+
 SERVE_BUDGET = 4_000_000     # walk budget (cap) of one served request
 
 
@@ -466,6 +500,7 @@ def main():
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and world == 1:
+        line["frw_mwe"] = mwe_measurement(s, masters, a.N, prec, a.sigma, a.budget, tuning, rows)
         line["microwalk_kernel"] = microwalk_kernel(alu_peak)
         line["fp32_vs_fp64"] = fp32_deviation(s, masters, a.N, a.sigma, a.budget)
     if rank == 0 and world == 1 and a.serve_seconds > 0:

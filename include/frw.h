@@ -92,7 +92,13 @@ typedef struct {
     int32_t serve_jobs;        /* serving: job-table entries of one run (0: 4096) */
     int32_t serve_arena_mb;    /* serving: MB of per-walk records of one run, 32 B per walk of
                                   budget; also sizes its batch arenas (0: 4096) */
-    int32_t reserved[4];
+    int32_t mwe_factor;        /* MicroWalk-E (Sec. III-B, Fig. 3b): a later transition cube that is
+                                  not stratified is expanded this many times (the paper: 5) and may
+                                  hold conductors, whose voxels absorb the walk; lowered while the
+                                  cube lists more than 14 blocks, conductors and exterior slabs,
+                                  plain MicroWalk below 2 or above 254 conductors (0 .. 16; 0 or 1:
+                                  off, plain FRW-MW) */
+    int32_t reserved[3];
 } frw_options;
 
 /* One extraction: a row of the capacitance matrix for one master conductor. */

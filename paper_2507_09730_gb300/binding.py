@@ -38,7 +38,7 @@ class frw_options(ctypes.Structure):
                 ("hybrid", c_int32), ("gauss_offset_frac", c_double), ("max_hops", c_int32),
                 ("slots", c_int32), ("table_capacity", c_int32), ("mw_warps_per_cta", c_int32),
                 ("mw_ctas_per_sm", c_int32), ("geom_threads", c_int32), ("serve_jobs", c_int32),
-                ("serve_arena_mb", c_int32), ("reserved", c_int32 * 4)]
+                ("serve_arena_mb", c_int32), ("mwe_factor", c_int32), ("reserved", c_int32 * 3)]
 
 
 class frw_extract_params(ctypes.Structure):

@@ -211,6 +211,7 @@ struct EngineView {
     unsigned long long *cycles;   // [5] CTA cycles: geometry busy, fill, reduce, MicroWalk busy, total
     double idle_timeout_s; // idle wait limit of the walk kernel
     int hops_per_epoch;    // analytical hops one walk may take per epoch (tunable, >= 1)
+    int mwe;               // MicroWalk-E expansion factor (0 or 1: plain MicroWalk)
     int suspend_lanes;     // a MicroWalk warp with at most this many lanes left may suspend them
     uint32_t suspend_min_steps;   // ... once each has made this many steps in the epoch
 };
@@ -231,7 +232,7 @@ cudaError_t prepare_walk(const EngineView &E);
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 size_t walk_smem_bytes(int N, int max_nc);
 int walk_pool_slots();
-int walk_ctas_per_sm(int N, int fp32);
+int walk_ctas_per_sm(int N, int fp32, int mwe);
 // fill one table with an explicit key into entry `entry` of the cache arrays
 cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4],
                             uint32_t entry, double *values_out, cudaStream_t st);

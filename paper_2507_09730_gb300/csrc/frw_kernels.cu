@@ -303,6 +303,73 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
     q.prof[0] = pf[0]; q.prof[1] = pf[1]; q.prof[2] = pf[2]; q.prof[3] = pf[3];
 }
 
+// MicroWalk-E cube of half-size R (expanded, may hold conductors): the dielectric
+// blocks as classify_cube lists them, then every conductor and every exterior
+// slab of the domain (centres with x < lo or x >= hi on one axis) that holds a
+// voxel centre, listed after the blocks so that they win, as objects of material
+// BOUNDARY (alpha = 1) with their conductor id (n_c: the walls) in the top byte of
+// rng.y.  False when the dielectric list overflows or more than KMAX objects.
+template <typename T>
+__device__ FRW_OUTLINE bool classify_cube_e(const SView<T> &S, const T c[3], T R, int N, CubeInfo &q)
+{
+    typedef Ar<T> A;
+    classify_cube(S, c, R, N, q);
+    if (q.kind == CUBE_OVERFLOW) return false;
+    const T h = A::div(A::mul(T(2), R), T(N));
+    const T invh = T(1) / h;
+    T base[3], xmax[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        base[a] = A::sub(c[a], R);
+        xmax[a] = vcentre(base[a], h, N - 1);
+    }
+    int count = q.K;
+    const int n = S.n_c;
+    const uint32_t cmat = (uint32_t)BOUNDARY << 16;
+    for (int k = 0; k < n; k++) {
+        T lo[3], hi[3];
+        bool rej = false;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            lo[a] = __ldg(&S.clo[a * n + k]);
+            hi[a] = __ldg(&S.chi[a * n + k]);
+            rej |= !(hi[a] > base[a]) || (lo[a] > xmax[a]);
+        }
+        if (rej) continue;
+        int r0[3], r1[3];
+        bool empty = false;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            r0[a] = first_ge(base[a], h, invh, N, lo[a]);
+            r1[a] = first_ge(base[a], h, invh, N, hi[a]);
+            empty |= r0[a] >= r1[a];
+        }
+        if (empty) continue;
+        if (count >= KMAX) return false;
+        q.rng[count++] = make_uint2((uint32_t)r0[0] | ((uint32_t)r1[0] << 8) | ((uint32_t)r0[1] << 16) |
+                                        ((uint32_t)r1[1] << 24),
+                                    (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | cmat | ((uint32_t)k << 24));
+    }
+    for (int a = 0; a < 3; a++) {
+        const int i1 = first_ge(base[a], h, invh, N, S.dlo[a]);   // centres below the domain: [0, i1)
+        const int i0 = first_ge(base[a], h, invh, N, S.dhi[a]);   // centres at or above its top: [i0, N)
+        for (int side = 0; side < 2; side++) {
+            const int lo_a = side ? i0 : 0, hi_a = side ? N : i1;
+            if (lo_a >= hi_a) continue;
+            if (count >= KMAX) return false;
+            int r0[3] = {0, 0, 0}, r1[3] = {N, N, N};
+            r0[a] = lo_a;
+            r1[a] = hi_a;
+            q.rng[count++] = make_uint2((uint32_t)r0[0] | ((uint32_t)r1[0] << 8) | ((uint32_t)r0[1] << 16) |
+                                            ((uint32_t)r1[1] << 24),
+                                        (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | cmat | ((uint32_t)n << 24));
+        }
+    }
+    q.K = count;
+    q.kind = CUBE_NONSTRAT;
+    return true;
+}
+
 // Volume-mean permittivity of the cube's lattice: constant-mask runs per axis,
 // material of each run triple by the last listed block containing it.
 __device__ FRW_OUTLINE double mean_eps(const CubeInfo &q, int N, const double *eps)
@@ -741,7 +808,7 @@ __device__ FRW_OUTLINE bool issue_walk(const EngineView &E, IssueRanges &ir, Wal
 // slot is free, then one step of the walk (Algorithm 1 inner loop): absorption
 // test, cube sizing, classification, then the analytical route in place or a
 // MicroWalk job queued for this CTA.
-template <typename T>
+template <typename T, bool MWE>
 __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const FillList &fl, uint16_t *qlist,
                          uint32_t *q_count, IssueRanges &ir)
 {
@@ -774,6 +841,13 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         w.hop = 1;
     } else if (st == ST_MWDONE) {
         const uint32_t en = E.s.exitnode[s];
+        if (MWE && (en & 0x80000000u)) {   // MicroWalk-E: absorbed by a conductor inside its expanded cube
+            w.hop++;
+            finish_walk(E, J, w, (int)(en & 0xffu));
+            E.s.state[s] = ST_FRESH;
+            E.s.job[s] = w.job;
+            return;
+        }
         const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
         const T c[3] = {(T)E.s.cube[s], (T)E.s.cube[NS + s], (T)E.s.cube[2 * NS + s]};
         const T R = (T)E.s.cube[3 * NS + s];
@@ -844,6 +918,19 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
     }
     break;
   }
+    // MicroWalk-E: expand the cube f-fold (f = mwe .. 2, the first that lists at
+    // most KMAX objects) so that it may reach conductors
+    if (MWE && S.n_c <= 254) {
+        CubeInfo qe;
+        for (int f = E.mwe; f >= 2; f--) {
+            const T Re = A::mul(R, T(f));
+            if (classify_cube_e<T>(S, pos, Re, N, qe)) {
+                q = qe;
+                R = Re;
+                break;
+            }
+        }
+    }
     // MicroWalk job (Algorithm 3) for this cube, recorded with the slot
     MWJob *jb = E.mwq + s;
     const uint32_t s3 = hb.x >> 29;
@@ -914,13 +1001,15 @@ __device__ __forceinline__ void build_masks(uint16_t *Mw, int r, int N, int lane
 }
 
 // One step of the lattice walk: weights W[mv][m_k] of Eq. 6 (quantised), integer
-// prefix sums, neighbour chosen by (u * S) >> 32.  Returns true on reaching a
-// boundary node.  M points at the lane's column (Mw + lane).  The weight table is
-// either one copy per lane (WS = 32: Wl = Wrep + lane, lookups never conflict) or
-// a single shared copy (WS = 1: Wl = W).
-template <int WS>
-__device__ __forceinline__ bool mw_step(const uint16_t *__restrict__ M, const uint32_t *__restrict__ Wl, int N,
-                                        int &x, int &y, int &z, uint64_t mm, uint32_t u)
+// prefix sums, neighbour chosen by (u * S) >> 32.  Returns 1 on reaching a
+// boundary node, 2 (MWE only) on stepping onto a node of material BOUNDARY inside
+// the lattice (a conductor of a MicroWalk-E cube; slot = its mask slot), else 0.
+// M points at the lane's column (Mw + lane).  The weight table is either one copy
+// per lane (WS = 32: Wl = Wrep + lane, lookups never conflict) or a single shared
+// copy (WS = 1: Wl = W).
+template <int WS, bool MWE>
+__device__ __forceinline__ int mw_step(const uint16_t *__restrict__ M, const uint32_t *__restrict__ Wl, int N,
+                                       int &x, int &y, int &z, uint64_t mm, uint32_t u, int &slot)
 {
     const int AR = (N + 2) * 32;
     const uint16_t *Mx = M + x * 32, *My = M + AR + y * 32, *Mz = M + 2 * AR + z * 32;
@@ -930,12 +1019,15 @@ __device__ __forceinline__ bool mw_step(const uint16_t *__restrict__ M, const ui
     const uint32_t yz = y0 & z0, xz = x0 & z0, xy = x0 & y0;
     const int mv = mat_of(mm, xy & z0);
     const uint32_t *Wr = Wl + mv * 16 * WS;
-    const uint32_t w0 = Wr[mat_of(mm, xm & yz) * WS];
-    const uint32_t w1 = Wr[mat_of(mm, xp & yz) * WS];
-    const uint32_t w2 = Wr[mat_of(mm, ym & xz) * WS];
-    const uint32_t w3 = Wr[mat_of(mm, yp & xz) * WS];
-    const uint32_t w4 = Wr[mat_of(mm, zm & xy) * WS];
-    const uint32_t w5 = Wr[mat_of(mm, zp & xy) * WS];
+    const uint32_t n0 = xm & yz, n1 = xp & yz, n2 = ym & xz, n3 = yp & xz, n4 = zm & xy, n5 = zp & xy;
+    const int m0 = mat_of(mm, n0), m1 = mat_of(mm, n1), m2 = mat_of(mm, n2);
+    const int m3 = mat_of(mm, n3), m4 = mat_of(mm, n4), m5 = mat_of(mm, n5);
+    const uint32_t w0 = Wr[m0 * WS];
+    const uint32_t w1 = Wr[m1 * WS];
+    const uint32_t w2 = Wr[m2 * WS];
+    const uint32_t w3 = Wr[m3 * WS];
+    const uint32_t w4 = Wr[m4 * WS];
+    const uint32_t w5 = Wr[m5 * WS];
     const uint32_t p0 = w0, p1 = p0 + w1, p2 = p1 + w2, p3 = p2 + w3, p4 = p3 + w4, p5 = p4 + w5;
     const uint32_t r = __umulhi(u, p5);
     const int k = (int)(r >= p0) + (int)(r >= p1) + (int)(r >= p2) + (int)(r >= p3) + (int)(r >= p4);
@@ -944,7 +1036,16 @@ __device__ __forceinline__ bool mw_step(const uint16_t *__restrict__ M, const ui
     x += (ax == 0) ? d : 0;
     y += (ax == 1) ? d : 0;
     z += (ax == 2) ? d : 0;
-    return ((unsigned)x >= (unsigned)N) | ((unsigned)y >= (unsigned)N) | ((unsigned)z >= (unsigned)N);
+    if (((unsigned)x >= (unsigned)N) | ((unsigned)y >= (unsigned)N) | ((unsigned)z >= (unsigned)N)) return 1;
+    if (MWE) {
+        const int mk = k == 0 ? m0 : k == 1 ? m1 : k == 2 ? m2 : k == 3 ? m3 : k == 4 ? m4 : m5;
+        if (mk == BOUNDARY) {
+            const uint32_t nk = k == 0 ? n0 : k == 1 ? n1 : k == 2 ? n2 : k == 3 ? n3 : k == 4 ? n4 : n5;
+            slot = 32 - __clz((int)nk);
+            return 2;
+        }
+    }
+    return 0;
 }
 
 // replicate the 16 x 16 weight table once per lane: Wrep[entry * 32 + lane]
@@ -1060,7 +1161,8 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 if (active) {
-                    if (mw_step<32>(M, Wl, N, x, y, z, L.mm, words[k])) {
+                    int slot_unused = 0;
+                    if (mw_step<32, false>(M, Wl, N, x, y, z, L.mm, words[k], slot_unused)) {
                         src.finish(L, x, y, z, t + (uint32_t)k + 1u);
                         active = false;
                     }
@@ -1608,7 +1710,7 @@ size_t walk_smem_bytes(int N, int max_nc) { return walk_scratch_bytes(N, max_nc)
 
 int walk_pool_slots() { return POOL_MAX; }
 
-template <typename T>
+template <typename T, bool MWE>
 __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
 {
     extern __shared__ __align__(16) unsigned char dsm_all[];
@@ -1699,7 +1801,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
                 const uint32_t i = atomicAdd(&sh.g_head, 1u);
                 if (i >= ng) break;
                 const uint32_t o = i < n1 ? sh.glist[i] : sh.glist[P - 1u - (i - n1)];
-                geo_slot<T>(E, base + o, o, fl, q_now, &sh.q_count, sh.ir);
+                geo_slot<T, MWE>(E, base + o, o, fl, q_now, &sh.q_count, sh.ir);
             }
         }
         __syncthreads();
@@ -1781,9 +1883,14 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         if (active) {
-                            if (mw_step<1>(M, Wl, N, x, y, z, L.mm, words[k])) {
+                            int slot = 0;
+                            const int code = mw_step<1, MWE>(M, Wl, N, x, y, z, L.mm, words[k], slot);
+                            if (code) {
                                 const uint32_t sl2 = L.tag;
-                                E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+                                // exit node, or (MicroWalk-E) the conductor reached, flagged by bit 31
+                                E.s.exitnode[sl2] =
+                                    code == 2 ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                                              : ((uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16));
                                 E.s.steps[sl2] += t + (uint32_t)k + 1u;
                                 __threadfence_block();      // exit data before the state (read by geometry warps)
                                 E.s.state[sl2] = ST_MWDONE;
@@ -1897,8 +2004,12 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
 cudaError_t prepare_walk(const EngineView &E)
 {
     const int smem = (int)walk_smem_bytes(E.N, E.max_nc);
-    return E.fp32 ? cudaFuncSetAttribute(k_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                  : cudaFuncSetAttribute(k_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (E.mwe > 1)
+        return E.fp32 ? cudaFuncSetAttribute(k_walk<float, true>, at, smem)
+                      : cudaFuncSetAttribute(k_walk<double, true>, at, smem);
+    return E.fp32 ? cudaFuncSetAttribute(k_walk<float, false>, at, smem)
+                  : cudaFuncSetAttribute(k_walk<double, false>, at, smem);
 }
 
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st)
@@ -1906,8 +2017,13 @@ cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t 
     (void)L;
     const size_t smem = walk_smem_bytes(E.N, E.max_nc);
     const unsigned grid = E.NS / E.pool;
-    if (E.fp32) k_walk<float><<<grid, WALK_THREADS, smem, st>>>(E);
-    else k_walk<double><<<grid, WALK_THREADS, smem, st>>>(E);
+    if (E.mwe > 1) {
+        if (E.fp32) k_walk<float, true><<<grid, WALK_THREADS, smem, st>>>(E);
+        else k_walk<double, true><<<grid, WALK_THREADS, smem, st>>>(E);
+    } else {
+        if (E.fp32) k_walk<float, false><<<grid, WALK_THREADS, smem, st>>>(E);
+        else k_walk<double, false><<<grid, WALK_THREADS, smem, st>>>(E);
+    }
     return cudaGetLastError();
 }
 
@@ -2052,17 +2168,19 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
 namespace frw {
 // CTAs of the walk kernel resident per SM at this lattice edge (3 by design at
 // N = 24: at most 85 registers per thread and about 67 KB of shared memory each)
-int walk_ctas_per_sm(int N, int fp32)
+template <typename T, bool MWE> static int walk_occupancy(int smem)
 {
     int n = 0;
+    cudaFuncSetAttribute(k_walk<T, MWE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<T, MWE>, WALK_THREADS, smem);
+    return n;
+}
+
+int walk_ctas_per_sm(int N, int fp32, int mwe)
+{
     const int smem = (int)walk_smem_bytes(N, 200);
-    if (fp32) {
-        cudaFuncSetAttribute(k_walk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<float>, WALK_THREADS, smem);
-    } else {
-        cudaFuncSetAttribute(k_walk<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<double>, WALK_THREADS, smem);
-    }
+    const int n = mwe > 1 ? (fp32 ? walk_occupancy<float, true>(smem) : walk_occupancy<double, true>(smem))
+                          : (fp32 ? walk_occupancy<float, false>(smem) : walk_occupancy<double, false>(smem));
     return n > 0 ? n : 1;
 }
 }  // namespace frw

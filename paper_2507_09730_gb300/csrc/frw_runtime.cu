@@ -200,6 +200,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.cycles = ctx->cycles;
     E.idle_timeout_s = 10.0;
     E.hops_per_epoch = ctx->tune.hops_per_epoch;
+    E.mwe = ctx->opt.mwe_factor;
     E.suspend_lanes = ctx->tune.suspend_lanes;
     E.suspend_min_steps = (uint32_t)ctx->tune.suspend_min_steps;
     return E;
@@ -284,6 +285,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     if (opt.max_hops <= 0) return FRW_EINVAL;
     if (opt.mw_warps_per_cta < 0 || opt.mw_warps_per_cta > 16 || opt.mw_ctas_per_sm < 0 || opt.mw_ctas_per_sm > 32)
         return FRW_EINVAL;
+    if (opt.mwe_factor < 0 || opt.mwe_factor > 16) return FRW_EINVAL;
     frw_ctx *ctx = new frw_ctx();
     ctx->opt = opt;
     ctx->device = device;
@@ -310,7 +312,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->shape.fill_ctas = ctx->shape.sms;
     const int N = opt.N;
     // walk kernel: CTAs resident at once (as many per SM as fit), each with a pool of slots
-    ctx->grid = walk_ctas_per_sm(N, opt.precision == FRW_FP32_GEOM) * ctx->shape.sms;
+    ctx->grid = walk_ctas_per_sm(N, opt.precision == FRW_FP32_GEOM, opt.mwe_factor) * ctx->shape.sms;
     {
         uint64_t want = opt.slots > 0 ? (uint64_t)opt.slots : (1ull << 20);
         uint64_t pool = (want + ctx->grid - 1) / ctx->grid;
