@@ -195,6 +195,16 @@ typedef struct {
 int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs, double *C_rows,
                       double *stderr_rows, frw_stats *stats);
 
+/* Full capacitance matrix of a structure (every conductor as master, in one run;
+ * master i runs as request params->request_id + i with the other parameters of
+ * params, walk_begin ignored).  C and stderr (host, n_cond x (n_cond + 1), row i
+ * = frw_extract's row of master i, last column = grounded walls); C_sym (host,
+ * n_cond x n_cond, may be NULL) = the symmetrised matrix, (C_ij + C_ji) / 2 off
+ * the diagonal, C_ii on it (the reciprocity C_ij = C_ji holds in expectation).
+ * stats: n_cond entries or NULL.  FRW_ENOTCONV if some row missed its target. */
+int frw_extract_matrix(frw_ctx *ctx, int32_t structure_id, const frw_extract_params *params, double *C,
+                       double *stderr_rows, double *C_sym, frw_stats *stats);
+
 /* Batching with a captured launch (the paper has no counterpart).  A plan lays a
  * fixed set of jobs out once, in a job table, arenas and record pool of its own,
  * and captures its whole launch sequence (arena reset, job publication from

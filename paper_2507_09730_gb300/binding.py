@@ -22,7 +22,7 @@ EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream",
            "frw_unload_structure", "frw_extract", "frw_extract_batch", "frw_walk_records",
            "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
            "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
-           "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums")
+           "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums", "frw_extract_matrix")
 
 
 class frw_box(ctypes.Structure):
@@ -123,6 +123,8 @@ def lib():
     L.frw_autotune.argtypes = [c_void_p, POINTER(frw_job), c_int32, c_uint64, POINTER(frw_tuning)]
     L.frw_extract_sums.argtypes = [c_void_p, c_int32, c_int32, POINTER(frw_extract_params), P(c_uint64),
                                    POINTER(c_uint64), POINTER(frw_stats)]
+    L.frw_extract_matrix.argtypes = [c_void_p, c_int32, POINTER(frw_extract_params), P(c_double), P(c_double),
+                                     P(c_double), POINTER(frw_stats)]
     L.frw_strerror.argtypes = [c_int]
     L.frw_strerror.restype = ctypes.c_char_p
     L.frw_last_error.argtypes = [c_void_p]
@@ -224,6 +226,20 @@ def frw_extract_sums(ctx, sid: int, master: int, n_cond: int, walk_budget: int, 
     _check(ctx, lib().frw_extract_sums(ctx, int(sid), int(master), ctypes.byref(p), _ptr(words, c_uint64),
                                        ctypes.byref(n), ctypes.byref(st)))
     return words, int(n.value), st.as_dict()
+
+
+def frw_extract_matrix(ctx, sid: int, n_cond: int, walk_budget: int, sigma_target: float = 0.0,
+                       request_id: int = 0, batch: int = 0):
+    """-> (C (n, n+1), stderr (n, n+1), C_sym (n, n), stats list, all converged)."""
+    p = frw_extract_params(int(walk_budget), float(sigma_target), int(request_id), int(batch), 0)
+    C = np.zeros((n_cond, n_cond + 1))
+    se = np.zeros((n_cond, n_cond + 1))
+    Cs = np.zeros((n_cond, n_cond))
+    st = (frw_stats * n_cond)()
+    rc = lib().frw_extract_matrix(ctx, int(sid), ctypes.byref(p), _ptr(C, c_double), _ptr(se, c_double),
+                                  _ptr(Cs, c_double), st)
+    _check(ctx, rc, (FRW_OK, FRW_ENOTCONV))
+    return C, se, Cs, [x.as_dict() for x in st], rc == FRW_OK
 
 
 def frw_extract_batch(ctx, jobs, n_conds):
@@ -440,6 +456,9 @@ class Context:
 
     def extract_batch(self, jobs):
         return frw_extract_batch(self.ctx, jobs, [self._n_cond.get(j["structure_id"], 0) for j in jobs])
+
+    def matrix(self, sid, walk_budget, sigma_target=0.0, request_id=0, batch=0):
+        return frw_extract_matrix(self.ctx, sid, self._n_cond[sid], walk_budget, sigma_target, request_id, batch)
 
     def plan(self, jobs) -> Plan:
         return Plan(self.ctx, jobs, [self._n_cond.get(j["structure_id"], 0) for j in jobs])

@@ -1122,6 +1122,41 @@ extern "C" int frw_extract_batch(frw_ctx *ctx, const frw_job *jobs, int32_t n_jo
     return notconv ? FRW_ENOTCONV : FRW_OK;
 }
 
+extern "C" int frw_extract_matrix(frw_ctx *ctx, int32_t sid, const frw_extract_params *p, double *C, double *se,
+                                  double *C_sym, frw_stats *stats)
+{
+    if (!ctx || !p || !C) return FRW_EINVAL;
+    int n = 0;
+    {
+        std::lock_guard<std::mutex> ls(ctx->struct_mu);
+        if (sid < 0 || sid >= (int)ctx->structs.size() || !ctx->structs[sid].live) return FRW_ENOTFOUND;
+        n = ctx->structs[sid].n_c;
+    }
+    std::vector<frw_job> jobs(n);
+    for (int i = 0; i < n; i++) {
+        jobs[i].structure_id = sid;
+        jobs[i].master = i;
+        jobs[i].walk_budget = p->walk_budget;
+        jobs[i].sigma_target = p->sigma_target;
+        jobs[i].request_id = p->request_id + (uint64_t)i;
+        jobs[i].batch = p->batch;
+    }
+    std::vector<double> se_local;
+    if (!se) {
+        se_local.resize((size_t)n * (n + 1));
+        se = se_local.data();
+    }
+    const int rc = frw_extract_batch(ctx, jobs.data(), n, C, se, stats);
+    if (rc != FRW_OK && rc != FRW_ENOTCONV) return rc;
+    if (C_sym)
+        for (int i = 0; i < n; i++)
+            for (int j = 0; j < n; j++)
+                C_sym[(size_t)i * n + j] =
+                    i == j ? C[(size_t)i * (n + 1) + i]
+                           : 0.5 * (C[(size_t)i * (n + 1) + j] + C[(size_t)j * (n + 1) + i]);
+    return rc;
+}
+
 extern "C" int frw_extract(frw_ctx *ctx, int32_t sid, int32_t master, const frw_extract_params *p, double *C_row,
                            double *stderr_row, frw_stats *stats)
 {

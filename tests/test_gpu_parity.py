@@ -218,3 +218,24 @@ def test_edge_cases(torch_cuda):
     o = O.frw_run(s, 0, 500, N=2)
     _records_match(g, o)
     c2.unload(sid)
+
+
+def test_capacitance_matrix_and_symmetrisation(torch_cuda):
+    """Full matrix (every master in one run): rows as frw_extract gives them,
+    reciprocity C_ij = C_ji within the errors, symmetrised matrix = the average."""
+    s = W.interconnect(2)
+    c = ctx_for(8)
+    sid = c.load(s)
+    C, se, Cs, st, _ = c.matrix(sid, 20000, request_id=40)
+    n = s.n_cond
+    assert C.shape == (n, n + 1) and Cs.shape == (n, n)
+    for i in (0, 7, n - 1):
+        Ci, sei, _, _ = c.extract(sid, i, 20000, request_id=40 + i)
+        np.testing.assert_array_equal(C[i], Ci)
+        np.testing.assert_array_equal(se[i], sei)
+    assert (np.diag(C[:, :n]) > 0).all()
+    off = ~np.eye(n, dtype=bool)
+    z = (C[:, :n] - C[:, :n].T)[off] / np.hypot(se[:, :n], se[:, :n].T)[off]
+    assert np.mean(np.abs(z) > 4.0) < 0.01
+    np.testing.assert_allclose(Cs, 0.5 * (C[:, :n] + C[:, :n].T) * off + np.diag(np.diag(C[:, :n])), rtol=0, atol=0)
+    c.unload(sid)
