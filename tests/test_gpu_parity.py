@@ -239,3 +239,27 @@ def test_capacitance_matrix_and_symmetrisation(torch_cuda):
     assert np.mean(np.abs(z) > 4.0) < 0.01
     np.testing.assert_allclose(Cs, 0.5 * (C[:, :n] + C[:, :n].T) * off + np.diag(np.diag(C[:, :n])), rtol=0, atol=0)
     c.unload(sid)
+
+
+def test_expected_steps_study_cubes_match_eq11(torch_cuda):
+    """The E(tau) study's random cubes (permittivities ~ Exp, mean 10): the mean
+    walk length the MicroWalk kernel measures equals Eq. 11 solved by the oracle."""
+    from paper_2507_09730_gb300 import studies
+    N, samples = 8, 40000
+    rng = np.random.default_rng([6, 99, N])
+    for g in range(3):
+        recs, eps = studies._cube_pair(rng, N, 2)
+        d = torch_cuda.from_numpy(recs).cuda()
+        st = torch_cuda.empty(2 * samples, dtype=torch_cuda.int32, device="cuda")
+        ex = torch_cuda.empty(2 * samples, dtype=torch_cuda.int32, device="cuda")
+        rc = B.frw_microwalk_cubes_noalloc(N, 2, d.data_ptr(), eps, 0, samples, 70 + g, ex.data_ptr(), st.data_ptr(),
+                                           torch_cuda.cuda.current_stream().cuda_stream)
+        assert rc == B.FRW_OK
+        steps = st.view(2, samples).to(torch_cuda.float64).cpu().numpy()
+        for c in range(2):
+            K = recs[c, 1]
+            ranges = recs[c, 2:2 + 7 * K].reshape(K, 7)
+            lat = O.lattice_from_ranges(N, recs[c, 0], ranges[:, :6], ranges[:, 6])
+            Et = O.expected_steps(N, eps[lat])
+            m, se = steps[c].mean(), steps[c].std() / np.sqrt(samples)
+            assert abs(m - Et) < 4.0 * se + 1e-3 * Et, (g, c, m, Et, se)
