@@ -399,7 +399,7 @@ def main():
     clk.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     agg = dict(walks=0, micro=0, mw_ms=0.0, geom_ms=0.0, fill_ms=0.0, reduce_ms=0.0, kernel_ms=0.0, launches=0,
-               hops=0, mw_hops=0,
+               hops=0, mw_hops=0, branch=[0, 0, 0], truncated=0,
                strat=0, hom=0, rounds=0, tables=0, mw_jobs=0, walk_launches=0, issued=0)
     rows = None
     ev0.record(stream)
@@ -413,6 +413,9 @@ def main():
             agg["mw_hops"] += st["mw_hops"]
             agg["strat"] += st["strat_hops"]
             agg["hom"] += st["hom_hops"]
+            agg["truncated"] += st["truncated"]
+            for b in range(3):
+                agg["branch"][b] += st["branch"][b]
         st0 = res[0][2]
         agg["mw_ms"] += st0["mw_ms"]
         agg["geom_ms"] += st0["geom_ms"]
@@ -496,6 +499,11 @@ def main():
             "micro_transitions_per_s": agg["micro"] * (walks_all / max(1, agg["walks"])) / t_all,
             "hops_per_walk": agg["hops"] / max(1, agg["walks"]),
             "mw_hop_fraction": agg["mw_hops"] / max(1, agg["hops"] - agg["walks"]),
+            "analytical_hop_fraction": (agg["strat"] + agg["hom"]) / max(1, agg["hops"] - agg["walks"]),
+            "first_cube_branches": {"stratified": agg["branch"][0] / max(1, agg["walks"]),
+                                    "shrunk": agg["branch"][1] / max(1, agg["walks"]),
+                                    "homogenised": agg["branch"][2] / max(1, agg["walks"])},
+            "truncated_walks": agg["truncated"],
             "gpu_launches": agg["launches"], "roofline": roofline, "clocks": clocks}
     if e2e:
         line["e2e"] = e2e

@@ -43,6 +43,7 @@ extern "C" {
 #define FRW_ENOTCONV 5    /* walk budget exhausted before the sigma target (results valid) */
 #define FRW_ECAPACITY 6   /* a fixed-size table (materials, cache, jobs) is full */
 #define FRW_ENOTFOUND 7   /* unknown structure id / ticket */
+#define FRW_ECANCELED 8   /* the request was cancelled (frw_cancel) */
 
 /* ---- option values ---- */
 #define FRW_FP64_GEOM 0   /* cube sizing, voxel ranges and points in FP64 */
@@ -98,7 +99,9 @@ typedef struct {
                                   cube lists more than 14 blocks, conductors and exterior slabs,
                                   plain MicroWalk below 2 or above 254 conductors (0 .. 16; 0 or 1:
                                   off, plain FRW-MW) */
-    int32_t reserved[3];
+    int32_t idle_timeout_ms;   /* a walk-kernel CTA with nothing to do gives up waiting after this
+                                  long and ends the run with an error status (0: 10000) */
+    int32_t reserved[2];
 } frw_options;
 
 /* One extraction: a row of the capacitance matrix for one master conductor. */
@@ -276,6 +279,23 @@ int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sample, uint64_t
  *               the ticket.  Returns the request's status (FRW_OK, FRW_ENOTCONV with
  *               results filled, or an error). */
 int frw_submit(frw_ctx *ctx, const frw_job *job, uint64_t *ticket);
+/* Cancel a submitted request: a queued one is never admitted; a running one has
+ * its walks dropped and its job closed by the kernel at its next epoch.  The
+ * ticket then completes with FRW_ECANCELED (frw_wait still collects it).
+ * FRW_ENOTFOUND for an unknown or collected ticket; a request that has already
+ * completed keeps its result (FRW_OK returned, nothing changed). */
+int frw_cancel(frw_ctx *ctx, uint64_t ticket);
+
+/* Counters of the serving loop since the context was created. */
+typedef struct {
+    uint64_t submitted, completed, cancelled, refused;   /* refused: could never fit (FRW_ENOMEM) */
+    uint64_t runs;                /* open runs of the walk kernel started */
+    uint64_t runs_failed;         /* runs that ended with a device error status (e.g. the idle limit
+                                     of idle_timeout_ms ran out); the next request starts a new run */
+    uint32_t last_status;         /* device status flags of the last failed run (0: none) */
+    uint32_t reserved;
+} frw_serve_info;
+int frw_get_serve_info(frw_ctx *ctx, frw_serve_info *out);
 int frw_poll(frw_ctx *ctx, uint64_t ticket, int32_t *done);
 int frw_wait(frw_ctx *ctx, uint64_t ticket, double timeout_s, double *C_row, double *stderr_row,
              frw_stats *stats);

@@ -7,6 +7,7 @@ library cannot be built or loaded, :func:`lib` raises.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from ctypes import POINTER, c_double, c_int, c_int32, c_uint8, c_uint32, c_uint64, c_void_p
 
@@ -14,7 +15,8 @@ import numpy as np
 
 from . import build as _build
 
-FRW_OK, FRW_EINVAL, FRW_ENOMEM, FRW_ETIMEOUT, FRW_EDEVICE, FRW_ENOTCONV, FRW_ECAPACITY, FRW_ENOTFOUND = range(8)
+(FRW_OK, FRW_EINVAL, FRW_ENOMEM, FRW_ETIMEOUT, FRW_EDEVICE, FRW_ENOTCONV, FRW_ECAPACITY, FRW_ENOTFOUND,
+ FRW_ECANCELED) = range(9)
 FRW_FP64_GEOM, FRW_FP32_GEOM = 0, 1
 FRW_TAB_SGF, FRW_TAB_FLUX_PAR, FRW_TAB_FLUX_PERP, FRW_TAB_SGF_HOM, FRW_TAB_FLUX_HOM = range(5)
 
@@ -22,7 +24,8 @@ EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream",
            "frw_unload_structure", "frw_extract", "frw_extract_batch", "frw_walk_records",
            "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
            "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
-           "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums", "frw_extract_matrix")
+           "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums", "frw_extract_matrix",
+           "frw_cancel", "frw_get_serve_info")
 
 
 class frw_box(ctypes.Structure):
@@ -38,7 +41,8 @@ class frw_options(ctypes.Structure):
                 ("hybrid", c_int32), ("gauss_offset_frac", c_double), ("max_hops", c_int32),
                 ("slots", c_int32), ("table_capacity", c_int32), ("mw_warps_per_cta", c_int32),
                 ("mw_ctas_per_sm", c_int32), ("geom_threads", c_int32), ("serve_jobs", c_int32),
-                ("serve_arena_mb", c_int32), ("mwe_factor", c_int32), ("reserved", c_int32 * 3)]
+                ("serve_arena_mb", c_int32), ("mwe_factor", c_int32), ("idle_timeout_ms", c_int32),
+                ("reserved", c_int32 * 2)]
 
 
 class frw_extract_params(ctypes.Structure):
@@ -58,6 +62,14 @@ class frw_tuning(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class frw_serve_info(ctypes.Structure):
+    _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("cancelled", c_uint64), ("refused", c_uint64),
+                ("runs", c_uint64), ("runs_failed", c_uint64), ("last_status", c_uint32), ("reserved", c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class frw_stats(ctypes.Structure):
@@ -113,6 +125,8 @@ def lib():
                             P(c_double), P(c_double)]
     L.frw_submit.argtypes = [c_void_p, POINTER(frw_job), POINTER(c_uint64)]
     L.frw_poll.argtypes = [c_void_p, c_uint64, POINTER(c_int32)]
+    L.frw_cancel.argtypes = [c_void_p, c_uint64]
+    L.frw_get_serve_info.argtypes = [c_void_p, POINTER(frw_serve_info)]
     L.frw_wait.argtypes = [c_void_p, c_uint64, c_double, P(c_double), P(c_double), POINTER(frw_stats)]
     L.frw_plan_create.argtypes = [c_void_p, POINTER(frw_job), c_int32, POINTER(c_void_p)]
     L.frw_plan_run.argtypes = [c_void_p, c_uint64, P(c_double), P(c_double), POINTER(frw_stats)]
@@ -331,6 +345,10 @@ def frw_submit(ctx, job) -> int:
     return int(t.value)
 
 
+def frw_cancel(ctx, ticket: int):
+    _check(ctx, lib().frw_cancel(ctx, int(ticket)))
+
+
 def frw_poll(ctx, ticket: int) -> bool:
     d = c_int32(0)
     _check(ctx, lib().frw_poll(ctx, int(ticket), ctypes.byref(d)))
@@ -414,12 +432,17 @@ def decode_exit(packed: np.ndarray) -> np.ndarray:
     return np.stack([(p & 255) - 1, ((p >> 8) & 255) - 1, ((p >> 16) & 255) - 1], axis=1)
 
 
+_TUNE_KEYS = ("pool_per_cta", "hops_per_epoch", "suspend_lanes", "suspend_min_steps", "mw_warps_per_cta",
+              "mw_ctas_per_sm")
+
+
 class Context:
     """Convenience owner of a context (destroyed on close / garbage collection)."""
 
     def __init__(self, device: int = 0, **opts):
         self.options = frw_default_options(**opts)
         self.N = self.options.N
+        self.device = device
         self.ctx = frw_create(device, self.options)
         self._n_cond = {}
         self._tickets = {}
@@ -469,8 +492,35 @@ class Context:
     def set_tuning(self, **kw):
         frw_set_tuning(self.ctx, **kw)
 
-    def autotune(self, sample_jobs, sample_walks=200_000) -> dict:
-        return frw_autotune(self.ctx, sample_jobs, sample_walks)
+    def autotune(self, sample_jobs, sample_walks=200_000, cache=None) -> dict:
+        """frw_autotune on the sample jobs.  With `cache` (a JSON file path), settings
+        are kept per (device name, N, geometry precision, MicroWalk-E factor): a
+        cached entry is applied without tuning, a new one is written after tuning."""
+        key = None
+        if cache:
+            try:
+                import torch
+                dev = torch.cuda.get_device_name(self.device)
+            except Exception:
+                dev = f"cuda:{self.device}"
+            key = f"{dev}|N={self.N}|precision={self.options.precision}|mwe={self.options.mwe_factor}"
+            try:
+                with open(cache) as f:
+                    data = json.load(f)
+            except (OSError, ValueError):
+                data = {}
+            if key in data:
+                t = data[key]
+                self.set_tuning(**{k: t[k] for k in _TUNE_KEYS})
+                return self.tuning()
+        t = frw_autotune(self.ctx, sample_jobs, sample_walks)
+        if key:
+            data[key] = t
+            tmp = f"{cache}.{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return t
 
     def submit(self, job) -> int:
         t = frw_submit(self.ctx, job)
@@ -479,6 +529,14 @@ class Context:
 
     def poll(self, ticket) -> bool:
         return frw_poll(self.ctx, ticket)
+
+    def cancel(self, ticket):
+        frw_cancel(self.ctx, ticket)
+
+    def serve_info(self) -> dict:
+        i = frw_serve_info()
+        _check(self.ctx, lib().frw_get_serve_info(self.ctx, ctypes.byref(i)))
+        return i.as_dict()
 
     def wait(self, ticket, timeout_s=-1.0):
         r = frw_wait(self.ctx, ticket, self._tickets[ticket], timeout_s)

@@ -101,7 +101,7 @@ struct alignas(256) DevJob {
 struct JobState {
     unsigned long long prefix;     // complete batches folded so far
     unsigned long long used;       // walks in the estimate once decided
-    uint32_t decided;              // 1: converged, 2: budget exhausted
+    uint32_t decided;              // 1: converged, 2: budget exhausted, 3: cancelled
     uint32_t lock;                 // held by the thread folding batches
     uint32_t pending;              // set by a thread that found the lock held
     uint32_t pad;
@@ -188,7 +188,7 @@ struct EngineView {
     const DevJob *jobs;
     unsigned long long *job_next;    // next walk offset per job (claimed by compare-and-swap)
     unsigned long long *job_limit;   // issue limit per job (<= walk_count), written by the host
-    int *job_cancel;                 // set when the stop rule holds (or by the host)
+    int *job_cancel;                 // 1: the stop rule holds; 2: cancelled by the host (walks dropped)
     JobState *jstate;                // per job
     uint32_t *jctl;                  // JC_WORDS job-table control words
     uint32_t *batch_job;             // job of each batch

@@ -776,6 +776,13 @@ __device__ FRW_OUTLINE void scan_jobs(const EngineView &E, uint32_t &lo_out, uin
         if (lead < 32u) break;
     }
     if (lane == 0 && lo > lo0) atomicMax(&E.jctl[JC_LOW], lo);
+    // a job the host cancelled (job_cancel = 2) is closed here: decided = 3, counted once
+    for (uint32_t c = 0; lo + c < pub && c < JOB_WINDOW; c += 32) {
+        const uint32_t j = lo + c + (uint32_t)lane;
+        if (j < pub && ((volatile int *)E.job_cancel)[j] == 2 && *(volatile uint32_t *)&E.jstate[j].decided == 0u &&
+            atomicCAS(&E.jstate[j].decided, 0u, 3u) == 0u)
+            atomicAdd(&E.jctl[JC_DECIDED], 1u);
+    }
     uint32_t open = 0;
     const uint32_t span = pub > lo ? min(pub - lo, JOB_WINDOW) : 0u;
     for (uint32_t c = 0; c < span && !open; c += 32) {
@@ -1596,8 +1603,7 @@ __device__ void advance_locked(const EngineView &E, uint32_t j, JobState &S)
     }
     if (decided) {
         __threadfence();
-        atomicExch(&S.decided, decided);
-        atomicAdd(&E.jctl[JC_DECIDED], 1u);
+        if (atomicCAS(&S.decided, 0u, decided) == 0u) atomicAdd(&E.jctl[JC_DECIDED], 1u);
     }
 }
 

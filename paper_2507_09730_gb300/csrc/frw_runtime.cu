@@ -100,7 +100,8 @@ static const char *kErr[] = {"ok",
                              "device error",
                              "walk budget exhausted before the sigma target",
                              "capacity exceeded",
-                             "not found"};
+                             "not found",
+                             "cancelled"};
 
 static int fail(frw_ctx *c, int code, const std::string &msg)
 {
@@ -198,7 +199,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.fill_scratch = ctx->fill_scratch;
     E.ctrl = ctx->ctrl;
     E.cycles = ctx->cycles;
-    E.idle_timeout_s = 10.0;
+    E.idle_timeout_s = ctx->opt.idle_timeout_ms > 0 ? 1e-3 * ctx->opt.idle_timeout_ms : 10.0;
     E.hops_per_epoch = ctx->tune.hops_per_epoch;
     E.mwe = ctx->opt.mwe_factor;
     E.suspend_lanes = ctx->tune.suspend_lanes;
@@ -221,7 +222,7 @@ extern "C" void frw_default_options(frw_options *o)
 
 extern "C" const char *frw_strerror(int code)
 {
-    if (code < 0 || code > 7) return "unknown status";
+    if (code < 0 || code > 8) return "unknown status";
     return kErr[code];
 }
 
@@ -285,7 +286,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     if (opt.max_hops <= 0) return FRW_EINVAL;
     if (opt.mw_warps_per_cta < 0 || opt.mw_warps_per_cta > 16 || opt.mw_ctas_per_sm < 0 || opt.mw_ctas_per_sm > 32)
         return FRW_EINVAL;
-    if (opt.mwe_factor < 0 || opt.mwe_factor > 16) return FRW_EINVAL;
+    if (opt.mwe_factor < 0 || opt.mwe_factor > 16 || opt.idle_timeout_ms < 0) return FRW_EINVAL;
     frw_ctx *ctx = new frw_ctx();
     ctx->opt = opt;
     ctx->device = device;
@@ -1363,6 +1364,7 @@ struct Ticket {
     std::chrono::steady_clock::time_point t_submit, t_done;
     int state = 0;            // 0 queued, 1 on the device, 2 done
     int rc = FRW_OK;
+    uint32_t index = 0;       // job-table index in its run (state 1)
 };
 
 struct ServeRun {
@@ -1395,6 +1397,7 @@ struct Server {
     unsigned long long *h_buf = nullptr;   // pinned: one job's sums + its issued count
     size_t h_js_cap = 0, h_buf_cap = 0;
     ServeRun R;
+    frw_serve_info info = {};       // counters (under mu)
 };
 
 }  // namespace
@@ -1492,6 +1495,10 @@ static int serve_start_run(frw_ctx *ctx, Server &S)
     }
     R.active = true;
     R.t_start = R.t_quiet = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.info.runs++;
+    }
     return FRW_OK;
 }
 
@@ -1499,6 +1506,9 @@ static void serve_complete(Server &S, Ticket &t, int rc)
 {
     t.rc = rc;
     t.state = 2;
+    if (rc == FRW_ECANCELED) S.info.cancelled++;
+    else if (rc == FRW_ENOMEM) S.info.refused++;
+    else S.info.completed++;
     t.t_done = std::chrono::steady_clock::now();
     S.cv_done.notify_all();
 }
@@ -1521,6 +1531,12 @@ static int serve_poll(frw_ctx *ctx, Server &S)
             tp = S.tickets[R.ids[i]].get();
         }
         JobRun &j = tp->run;
+        if (S.h_js[i].decided == 3u) {   // cancelled: no result
+            R.finished[i] = 1;
+            std::lock_guard<std::mutex> lk(S.mu);
+            serve_complete(S, *tp, FRW_ECANCELED);
+            continue;
+        }
         const uint32_t words = acc_stride_for(j.d.n_c);
         CK(cudaMemcpyAsync(S.h_js + i, ctx->rb.js + i, sizeof(JobState), cudaMemcpyDeviceToHost, S.poll));
         CK(cudaMemcpyAsync(S.h_buf, ctx->rb.jsum + j.sum_off, sizeof(unsigned long long) * words,
@@ -1542,6 +1558,11 @@ static void serve_end_run(frw_ctx *ctx, Server &S, int rc_run)
     ServeRun &R = S.R;
     cudaStreamSynchronize(S.st);
     int rc = rc_run ? rc_run : check_status(ctx, S.st);
+    if (rc) {
+        std::lock_guard<std::mutex> lk(S.mu);
+        S.info.runs_failed++;
+        S.info.last_status = ctx->h_status[STAT_ERR];
+    }
     if (!rc) rc = serve_poll(ctx, S);
     {
         std::lock_guard<std::mutex> lk(S.mu);
@@ -1607,6 +1628,7 @@ static void serve_loop(frw_ctx *ctx)
                 }
                 place_job(ctx, t.run, R.A);
                 t.state = 1;
+                t.index = (uint32_t)R.ids.size();
                 adm.push_back(&t.run);
                 R.ids.push_back(S.queue.front());
                 R.finished.push_back(0);
@@ -1645,7 +1667,9 @@ static void serve_loop(frw_ctx *ctx)
             cudaStreamSynchronize(S.poll);
             R.closing = true;
         }
-        if (R.closing && cudaEventQuery(S.ev_end) != cudaErrorNotReady) {
+        // the run ends once closed and drained, or when its kernel ended on its own
+        // (a device error, e.g. the idle limit): the next request starts a new run
+        if (cudaEventQuery(S.ev_end) != cudaErrorNotReady) {
             serve_end_run(ctx, S, rc);
             continue;
         }
@@ -1706,9 +1730,46 @@ extern "C" int frw_submit(frw_ctx *ctx, const frw_job *job, uint64_t *ticket)
         const uint64_t id = S.next_ticket++;
         S.tickets[id] = std::move(t);
         S.queue.push_back(id);
+        S.info.submitted++;
         *ticket = id;
     }
     S.cv_work.notify_all();
+    return FRW_OK;
+}
+
+extern "C" int frw_get_serve_info(frw_ctx *ctx, frw_serve_info *out)
+{
+    if (!ctx || !out) return FRW_EINVAL;
+    memset(out, 0, sizeof(*out));
+    if (!ctx->srv) return FRW_OK;
+    std::lock_guard<std::mutex> lk(ctx->srv->mu);
+    *out = ctx->srv->info;
+    return FRW_OK;
+}
+
+extern "C" int frw_cancel(frw_ctx *ctx, uint64_t ticket)
+{
+    if (!ctx) return FRW_EINVAL;
+    if (!ctx->srv) return FRW_ENOTFOUND;
+    Server &S = *ctx->srv;
+    std::lock_guard<std::mutex> lk(S.mu);
+    auto it = S.tickets.find(ticket);
+    if (it == S.tickets.end()) return FRW_ENOTFOUND;
+    Ticket &t = *it->second;
+    if (t.state == 0) {
+        for (auto q = S.queue.begin(); q != S.queue.end(); ++q)
+            if (*q == ticket) {
+                S.queue.erase(q);
+                break;
+            }
+        serve_complete(S, t, FRW_ECANCELED);
+    } else if (t.state == 1) {
+        // the kernel drops the job's walks and closes the job at its next epoch; the
+        // copy completes before the lock is released, hence before the run can end
+        static const int two = 2;
+        CK(cudaMemcpyAsync(ctx->rb.cancel + t.index, &two, sizeof(int), cudaMemcpyHostToDevice, S.poll));
+        CK(cudaStreamSynchronize(S.poll));
+    }
     return FRW_OK;
 }
 

@@ -63,3 +63,17 @@ def test_autotune_changes_speed_only(torch_cuda):
         _rows_equal(before, c.extract_batch(jobs)[0])
         with pytest.raises(B.FRWError):
             c.set_tuning(pool_per_cta=300)
+
+
+def test_autotune_cache(torch_cuda, tmp_path):
+    cache = str(tmp_path / "tune.json")
+    with B.Context(0, N=16, precision=B.FRW_FP32_GEOM, seed=12, slots=1 << 18) as c:
+        sids = (c.load(W.tiny_two_plate()), c.load(W.interconnect(3)))
+        t1 = c.autotune(_jobs(sids), sample_walks=40000, cache=cache)
+        c.set_tuning(pool_per_cta=256, hops_per_epoch=1)
+        t2 = c.autotune(_jobs(sids), sample_walks=40000, cache=cache)   # from the cache, no tuning
+        for k in ("pool_per_cta", "hops_per_epoch", "suspend_lanes", "suspend_min_steps"):
+            assert t2[k] == t1[k]
+    import json
+    data = json.load(open(cache))
+    assert len(data) == 1 and list(data)[0].endswith("|N=16|precision=1|mwe=0")

@@ -127,3 +127,35 @@ def test_gpu_shards_equal_one_run():
         np.testing.assert_array_equal(C, Cf)
         np.testing.assert_array_equal(se, sef)
         assert st["walks"] == n
+
+
+def _dying_rank_main(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=15))
+    if rank == 1:
+        os._exit(0)          # this rank leaves between steps, before the exchange
+    try:
+        S.allgather_sums(np.zeros(8, np.uint64), 5)
+        q.put((rank, "no error"))
+    except Exception as e:   # the collective ends with an error instead of waiting forever
+        q.put((rank, type(e).__name__))
+
+
+def test_lost_rank_ends_the_exchange_with_an_error():
+    import multiprocessing as mp
+    import time
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    rank, what = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and what != "no error"
+    assert time.time() - t0 < 100
