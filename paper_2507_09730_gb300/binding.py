@@ -100,7 +100,7 @@ def lib():
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build()
+    path = _build.build(checked=os.environ.get("FRW_CHECKED") == "1")
     L = ctypes.CDLL(path)
     P = POINTER
     L.frw_default_options.argtypes = [P(frw_options)]

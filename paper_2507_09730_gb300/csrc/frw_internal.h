@@ -22,7 +22,8 @@ enum : uint32_t { ST_IDLE = 0, ST_FRESH = 1, ST_FIRST = 2, ST_HOP = 3, ST_MW = 4
 // device error flags (status word 1)
 enum : uint32_t {
     ERR_MWQ_OVERFLOW = 1u, ERR_CACHE_FULL = 2u, ERR_FILL = 4u, ERR_SHRINK = 8u, ERR_ACC_RANGE = 16u,
-    ERR_MW_STEPS = 32u, ERR_IDLE_TIMEOUT = 64u, ERR_REDUCE_QUEUE = 128u
+    ERR_MW_STEPS = 32u, ERR_IDLE_TIMEOUT = 64u, ERR_REDUCE_QUEUE = 128u,
+    ERR_CHECK = 256u              // a bounds check of the debug build (-DFRW_CHECKS) failed
 };
 // status words
 enum { STAT_ACTIVE = 0, STAT_ERR = 1, STAT_BUILT = 2, STAT_MWJOBS = 3, STAT_EPOCHS = 4, STAT_SUSPENDED = 5,
@@ -200,6 +201,7 @@ struct EngineView {
     uint32_t *rq, *rq_count, *rq_head;   // queue of completed batches awaiting reduction
     uint32_t rq_cap;
     RecArrays rec;
+    uint64_t rec_cap, acc_cap, jsum_cap;   // record, accumulator and running-sum capacities (bounds checks)
     MWJob *mwq;                      // one MicroWalk job record per slot
     TableCache tc;
     const uint32_t *W;     // [16][16]

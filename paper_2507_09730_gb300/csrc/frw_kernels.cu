@@ -30,6 +30,14 @@ namespace cg = cooperative_groups;
 // loops then fit the instruction cache.
 #define FRW_OUTLINE __noinline__
 
+// Bounds checks of the debug build (-DFRW_CHECKS): a failed check sets ERR_CHECK
+// (the run then ends with an error status) and the guarded access is skipped.
+#ifdef FRW_CHECKS
+#define FRW_CHECKED(E, cond) ((cond) ? true : (atomicOr(&(E).status[STAT_ERR], ERR_CHECK), false))
+#else
+#define FRW_CHECKED(E, cond) true
+#endif
+
 __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                           uint32_t k0, uint32_t k1)
 {
@@ -546,6 +554,7 @@ __device__ FRW_OUTLINE void finish_walk(const EngineView &E, const DevJob &J, co
 {
     const uint64_t rel = w.walk - J.walk_begin;
     const uint64_t r = J.rec_base + rel;
+    if (!FRW_CHECKED(E, rel < J.walk_count && r < E.rec_cap && J.batch_base + rel / J.batch < E.rq_cap)) return;
     E.rec.omega[r] = w.omega;
     E.rec.hops[r] = w.hop;
     E.rec.steps[r] = (uint32_t)w.steps;
@@ -962,7 +971,8 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         cg::coalesced_group g = cg::coalesced_threads();
         uint32_t base = 0;
         if (g.thread_rank() == 0) base = atomicAdd(q_count, (uint32_t)g.size());
-        qlist[g.shfl(base, 0) + g.thread_rank()] = (uint16_t)o;
+        const uint32_t qi = g.shfl(base, 0) + g.thread_rank();
+        if (FRW_CHECKED(E, qi < E.pool)) qlist[qi] = (uint16_t)o;
     }
 }
 
@@ -1473,7 +1483,8 @@ __device__ FRW_OUTLINE void reduce_batch(const EngineView &E, uint32_t g, unsign
     }
     __syncthreads();
     unsigned long long *out = E.acc + J.acc_base + b * words;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) out[i] = acc_sm[i];
+    const bool in_range = FRW_CHECKED(E, J.acc_base + (b + 1) * words <= E.acc_cap);
+    for (uint32_t i = threadIdx.x; i < words && in_range; i += blockDim.x) out[i] = acc_sm[i];
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -1546,6 +1557,7 @@ __device__ void advance_locked(const EngineView &E, uint32_t j, JobState &S)
 {
     const DevJob &J = E.jobs[j];
     unsigned long long *sum = E.jsum + __ldcg(E.jsum_off + j);
+    if (!FRW_CHECKED(E, __ldcg(E.jsum_off + j) + J.acc_stride <= E.jsum_cap)) return;
     const int nc1 = J.n_c + 1;
     const uint64_t nb = (J.walk_count + J.batch - 1) / J.batch;
     unsigned long long prefix = *(volatile unsigned long long *)&S.prefix;
@@ -1793,8 +1805,13 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
                 g1 = __shfl_sync(FULL_MASK, g1, 0);
                 g2 = __shfl_sync(FULL_MASK, g2, 0);
                 const uint32_t below = (1u << lane) - 1u;
-                if (first) sh.glist[g1 + __popc(b1 & below)] = (uint16_t)o;
-                else if (need) sh.glist[P - 1u - (g2 + __popc(b2 & below))] = (uint16_t)o;
+                if (first) {
+                    const uint32_t gi = g1 + __popc(b1 & below);
+                    if (FRW_CHECKED(E, gi < P)) sh.glist[gi] = (uint16_t)o;
+                } else if (need) {
+                    const uint32_t gi = g2 + __popc(b2 & below);
+                    if (FRW_CHECKED(E, gi < P)) sh.glist[P - 1u - gi] = (uint16_t)o;
+                }
             }
             __syncthreads();
             if (warp == 0) claim_ids(E, sh.ir, sh.n_free, sh.j_lo, sh.j_pub);
@@ -1877,12 +1894,16 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
                         MWJob &b = E.mwq[base + my_o];
                         b.start = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16);
                         b.pad0 = t;
-                        q_next[atomicAdd(&sh.q_next, 1u)] = (uint16_t)my_o;
+                        const uint32_t qi = atomicAdd(&sh.q_next, 1u);
+                        if (FRW_CHECKED(E, qi < P)) q_next[qi] = (uint16_t)my_o;
                         atomicAdd(&sh.s_count, 1u);
                         active = false;
                     }
                     break;
                 }
+                if (active && !FRW_CHECKED(E, (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N &&
+                                                   (unsigned)z < (unsigned)N))
+                    active = false;
                 if (active) {
                     const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
                     const uint32_t words[4] = {blk.x, blk.y, blk.z, blk.w};
@@ -1895,7 +1916,9 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
                                 const uint32_t sl2 = L.tag;
                                 // exit node, or (MicroWalk-E) the conductor reached, flagged by bit 31
                                 E.s.exitnode[sl2] =
-                                    code == 2 ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                                    code == 2 ? (FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
+                                                     ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                                                     : 0x80000000u)
                                               : ((uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16));
                                 E.s.steps[sl2] += t + (uint32_t)k + 1u;
                                 __threadfence_block();      // exit data before the state (read by geometry warps)

@@ -264,10 +264,12 @@ static int check_status(frw_ctx *ctx, cudaStream_t st = nullptr)
     const uint32_t e = ctx->h_status[STAT_ERR];
     if (e) {
         char buf[160];
-        snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s)", e,
+        snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s%s%s%s)", e,
                  (e & ERR_MWQ_OVERFLOW) ? "queue overflow " : "", (e & ERR_CACHE_FULL) ? "table cache full " : "",
                  (e & ERR_FILL) ? "table fill check " : "", (e & ERR_SHRINK) ? "cube shrink limit " : "",
-                 (e & ERR_ACC_RANGE) ? "accumulator range " : "", (e & ERR_MW_STEPS) ? "MicroWalk step cap" : "");
+                 (e & ERR_ACC_RANGE) ? "accumulator range " : "", (e & ERR_MW_STEPS) ? "MicroWalk step cap " : "",
+                 (e & ERR_IDLE_TIMEOUT) ? "idle limit " : "", (e & ERR_REDUCE_QUEUE) ? "reduction queue " : "",
+                 (e & ERR_CHECK) ? "bounds check" : "");
         return fail(ctx, (e & ERR_CACHE_FULL) ? FRW_ECAPACITY : FRW_EDEVICE, buf);
     }
     return FRW_OK;
@@ -938,8 +940,8 @@ static double run_timeout_s()
     return t > 0.0 ? t : 3600.0;
 }
 
-static EngineView run_view(frw_ctx *ctx, RunBufs &B, const RecArrays &rec, uint32_t jcap, int max_nc, uint32_t pool,
-                           uint64_t batches)
+static EngineView run_view(frw_ctx *ctx, RunBufs &B, const RecArrays &rec, uint64_t rec_cap, uint32_t jcap,
+                           int max_nc, uint32_t pool, uint64_t batches)
 {
     EngineView E = make_view(ctx);
     E.n_jobs = (int)jcap;
@@ -961,6 +963,9 @@ static EngineView run_view(frw_ctx *ctx, RunBufs &B, const RecArrays &rec, uint3
     E.rq_head = B.rqc + 1;
     E.rq_cap = (uint32_t)std::max<uint64_t>(batches, 1);
     E.rec = rec;
+    E.rec_cap = rec_cap;
+    E.acc_cap = B.acap;
+    E.jsum_cap = B.scap;
     E.pool = pool;
     E.NS = pool * (uint32_t)ctx->grid;
     return E;
@@ -1017,7 +1022,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     CK(publish_jobs(ctx->rb, live.data(), 0, nj, P, st));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
     CK(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, st));
-    const EngineView E = run_view(ctx, ctx->rb, ctx->rec, nj, max_nc, run_pool, A.batches);
+    const EngineView E = run_view(ctx, ctx->rb, ctx->rec, ctx->rec_cap, nj, max_nc, run_pool, A.batches);
     CK(prepare_walk(E));
     CK(cudaEventRecord(ctx->ev[0], st));
     CK(launch_walk(E, ctx->shape, st));
@@ -1484,7 +1489,7 @@ static int serve_start_run(frw_ctx *ctx, Server &S)
     // the set-up is complete before the kernel starts and before any publication
     // (publications and polls go through the second stream while the kernel runs)
     if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
-    const EngineView E = run_view(ctx, ctx->rb, ctx->rec, R.jcap, R.max_nc, R.pool, R.bcap);
+    const EngineView E = run_view(ctx, ctx->rb, ctx->rec, ctx->rec_cap, R.jcap, R.max_nc, R.pool, R.bcap);
     if (e == cudaSuccess) e = prepare_walk(E);
     if (e == cudaSuccess) e = launch_walk(E, ctx->shape, S.st);
     if (e == cudaSuccess) e = cudaEventRecord(S.ev_end, S.st);
@@ -2119,7 +2124,7 @@ extern "C" int frw_plan_create(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs
     CK(cudaEventCreate(&P->ev1));
     // capture: reset, publication, the walk kernel
     std::lock_guard<std::mutex> engine(ctx->engine_mu);
-    const EngineView E = run_view(ctx, P->rb, P->rec, nj, P->max_nc, P->pool, P->A.batches);
+    const EngineView E = run_view(ctx, P->rb, P->rec, P->A.walks, nj, P->max_nc, P->pool, P->A.batches);
     CK(prepare_walk(E));
     cudaStream_t st = ctx->stream;
     CK(cudaStreamSynchronize(st));

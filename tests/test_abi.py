@@ -23,6 +23,13 @@ def test_library_exports_every_declared_symbol():
     assert set(B.EXPORTS) == set(names)
 
 
+def test_checked_library_exports_the_same_symbols():
+    from paper_2507_09730_gb300 import build as bld
+    L = ctypes.CDLL(bld.build(checked=True))
+    for n in declared_functions():
+        assert hasattr(L, n), n
+
+
 def test_options_layout_and_defaults():
     assert ctypes.sizeof(B.frw_options) == 80
     assert ctypes.sizeof(B.frw_block) == 56
