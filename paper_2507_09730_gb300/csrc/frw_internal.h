@@ -73,6 +73,56 @@ struct DevStructure {
     const uint32_t *sl_H;      // [3][S][words]
 };
 
+// The structure as the geometry code reads it, in one precision: the fields of
+// DevStructure for that precision.  Built on the host at load time and kept in
+// device memory per structure, so that walk threads reference one shared copy
+// (read through L1, the same line for every thread of a structure) instead of
+// each holding its own.
+template <typename T> struct SView {
+    int n_c, n_b, bg;
+    T dlo[3], dhi[3];
+    T tau, margin;
+    const T *clo, *chi, *blo, *bhi;
+    const uint8_t *bmat;
+    int gdim[3], sl_S, sl_words;
+    T g_org[3], g_inv[3], sl_org[3], sl_inv[3];
+    const uint32_t *g_off;
+    const uint16_t *g_ids;
+    const uint32_t *sl_L, *sl_H;
+};
+
+template <typename T> __host__ __device__ inline SView<T> sview(const DevStructure &S);
+template <> __host__ __device__ inline SView<double> sview<double>(const DevStructure &S)
+{
+    SView<double> v;
+    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
+    for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo[a]; v.dhi[a] = S.dom_hi[a]; }
+    v.tau = S.tau; v.margin = 0.0;
+    v.clo = S.c_lo; v.chi = S.c_hi; v.blo = S.b_lo; v.bhi = S.b_hi; v.bmat = S.b_mat;
+    for (int a = 0; a < 3; a++) {
+        v.gdim[a] = S.gdim[a]; v.g_org[a] = S.g_org[a]; v.g_inv[a] = S.g_inv[a];
+        v.sl_org[a] = S.sl_org[a]; v.sl_inv[a] = S.sl_inv[a];
+    }
+    v.sl_S = S.sl_S; v.sl_words = S.sl_words;
+    v.g_off = S.g_off; v.g_ids = S.g_ids; v.sl_L = S.sl_L; v.sl_H = S.sl_H;
+    return v;
+}
+template <> __host__ __device__ inline SView<float> sview<float>(const DevStructure &S)
+{
+    SView<float> v;
+    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
+    for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo_f[a]; v.dhi[a] = S.dom_hi_f[a]; }
+    v.tau = S.tau_f; v.margin = S.margin_f;
+    v.clo = S.c_lo_f; v.chi = S.c_hi_f; v.blo = S.b_lo_f; v.bhi = S.b_hi_f; v.bmat = S.b_mat;
+    for (int a = 0; a < 3; a++) {
+        v.gdim[a] = S.gdim[a]; v.g_org[a] = S.g_org_f[a]; v.g_inv[a] = S.g_inv_f[a];
+        v.sl_org[a] = S.sl_org_f[a]; v.sl_inv[a] = S.sl_inv_f[a];
+    }
+    v.sl_S = S.sl_S; v.sl_words = S.sl_words;
+    v.g_off = S.g_off; v.g_ids = S.g_ids; v.sl_L = S.sl_L; v.sl_H = S.sl_H;
+    return v;
+}
+
 // One extraction job (request x master).
 // 256-byte aligned: the host publishes jobs into a running kernel, and no cache
 // line of a job may be shared with another job's.
@@ -186,6 +236,7 @@ struct EngineView {
     int max_nc;            // largest conductor count a job of this run may have (reduction scratch)
     SlotArrays s;
     const DevStructure *structs;
+    const void *view_f, *view_d;     // per structure: SView<float>[] and SView<double>[]
     const DevJob *jobs;
     unsigned long long *job_next;    // next walk offset per job (claimed by compare-and-swap)
     unsigned long long *job_limit;   // issue limit per job (<= walk_count), written by the host

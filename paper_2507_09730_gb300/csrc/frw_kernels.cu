@@ -84,49 +84,14 @@ template <> struct Ar<float> {
     static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 };
 
-template <typename T> struct SView {
-    int n_c, n_b, bg;
-    T dlo[3], dhi[3];
-    T tau, margin;
-    const T *clo, *chi, *blo, *bhi;
-    const uint8_t *bmat;
-    int gdim[3], sl_S, sl_words;
-    T g_org[3], g_inv[3], sl_org[3], sl_inv[3];
-    const uint32_t *g_off;
-    const uint16_t *g_ids;
-    const uint32_t *sl_L, *sl_H;
-};
-
-template <typename T> __device__ __forceinline__ SView<T> sview(const DevStructure &S);
-template <> __device__ __forceinline__ SView<double> sview<double>(const DevStructure &S)
+template <typename T> __device__ __forceinline__ const SView<T> &structure_view(const EngineView &E, int sid);
+template <> __device__ __forceinline__ const SView<float> &structure_view<float>(const EngineView &E, int sid)
 {
-    SView<double> v;
-    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
-    for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo[a]; v.dhi[a] = S.dom_hi[a]; }
-    v.tau = S.tau; v.margin = 0.0;
-    v.clo = S.c_lo; v.chi = S.c_hi; v.blo = S.b_lo; v.bhi = S.b_hi; v.bmat = S.b_mat;
-    for (int a = 0; a < 3; a++) {
-        v.gdim[a] = S.gdim[a]; v.g_org[a] = S.g_org[a]; v.g_inv[a] = S.g_inv[a];
-        v.sl_org[a] = S.sl_org[a]; v.sl_inv[a] = S.sl_inv[a];
-    }
-    v.sl_S = S.sl_S; v.sl_words = S.sl_words;
-    v.g_off = S.g_off; v.g_ids = S.g_ids; v.sl_L = S.sl_L; v.sl_H = S.sl_H;
-    return v;
+    return static_cast<const SView<float> *>(E.view_f)[sid];
 }
-template <> __device__ __forceinline__ SView<float> sview<float>(const DevStructure &S)
+template <> __device__ __forceinline__ const SView<double> &structure_view<double>(const EngineView &E, int sid)
 {
-    SView<float> v;
-    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
-    for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo_f[a]; v.dhi[a] = S.dom_hi_f[a]; }
-    v.tau = S.tau_f; v.margin = S.margin_f;
-    v.clo = S.c_lo_f; v.chi = S.c_hi_f; v.blo = S.b_lo_f; v.bhi = S.b_hi_f; v.bmat = S.b_mat;
-    for (int a = 0; a < 3; a++) {
-        v.gdim[a] = S.gdim[a]; v.g_org[a] = S.g_org_f[a]; v.g_inv[a] = S.g_inv_f[a];
-        v.sl_org[a] = S.sl_org_f[a]; v.sl_inv[a] = S.sl_inv_f[a];
-    }
-    v.sl_S = S.sl_S; v.sl_words = S.sl_words;
-    v.g_off = S.g_off; v.g_ids = S.g_ids; v.sl_L = S.sl_L; v.sl_H = S.sl_H;
-    return v;
+    return static_cast<const SView<double> *>(E.view_d)[sid];
 }
 
 // cell / slab index of a coordinate (clamped; the host built the index with
@@ -227,6 +192,8 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
     int bg = S.bg;
     const int nb = S.n_b;
     const int SS = S.sl_S, nw = S.sl_words;
+    const T *__restrict__ blo = S.blo, *__restrict__ bhi = S.bhi;
+    const uint8_t *__restrict__ bmat = S.bmat;
     const uint32_t *Lx = S.sl_L + (size_t)(0 * SS + cell_of(A::add(c[0], R), S.sl_org[0], S.sl_inv[0], SS)) * nw;
     const uint32_t *Hx = S.sl_H + (size_t)(0 * SS + cell_of(A::sub(c[0], R), S.sl_org[0], S.sl_inv[0], SS)) * nw;
     const uint32_t *Ly = S.sl_L + (size_t)(1 * SS + cell_of(A::add(c[1], R), S.sl_org[1], S.sl_inv[1], SS)) * nw;
@@ -243,8 +210,8 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
         bool rej = false;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            lo[a] = __ldg(&S.blo[a * nb + b]);
-            hi[a] = __ldg(&S.bhi[a * nb + b]);
+            lo[a] = __ldg(&blo[a * nb + b]);
+            hi[a] = __ldg(&bhi[a * nb + b]);
             rej |= !(hi[a] > base[a]) || (lo[a] > xmax[a]);
         }
         if (rej) continue;
@@ -258,7 +225,7 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
             full &= (r0[a] == 0) && (r1[a] == N);
         }
         if (empty) continue;
-        const int m = __ldg(&S.bmat[b]);
+        const int m = __ldg(&bmat[b]);
         if (full) { count = 0; bg = m; continue; }
         if (count < KMAX)
             q.rng[count] = make_uint2((uint32_t)r0[0] | ((uint32_t)r1[0] << 8) | ((uint32_t)r0[1] << 16) |
@@ -846,7 +813,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         st = ST_FIRST;
     }
     const DevJob &J = E.jobs[w.job];
-    const SView<T> S = sview<T>(E.structs[J.sid]);
+    const SView<T> &S = structure_view<T>(E, J.sid);
     T pos[3];
     if (st == ST_FIRST) {
         if (!first_transition<T>(E, J, S, w, pos, fl)) {   // table not ready: retry next epoch
@@ -1673,6 +1640,10 @@ __device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 // The kernel exits when its pool is empty, no walk can be issued and every stop
 // rule is decided; an idle wait is bounded by E.idle_timeout_s.
 constexpr int WALK_THREADS = 256;
+#ifndef FRW_WALK_CTAS
+#define FRW_WALK_CTAS 3
+#endif
+constexpr int WALK_CTAS = FRW_WALK_CTAS;   // CTAs per SM the walk kernel is compiled for
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int MW_WARPS = WALK_WARPS;
 constexpr int POOL_MAX = 4096;
@@ -1729,7 +1700,7 @@ size_t walk_smem_bytes(int N, int max_nc) { return walk_scratch_bytes(N, max_nc)
 int walk_pool_slots() { return POOL_MAX; }
 
 template <typename T, bool MWE>
-__global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
+__global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk(EngineView E)
 {
     extern __shared__ __align__(16) unsigned char dsm_all[];
     __shared__ WalkShared sh;
@@ -2030,15 +2001,25 @@ __global__ void __launch_bounds__(WALK_THREADS, 3) k_walk(EngineView E)
     }
 }
 
+// Shared-memory carve-out for WALK_CTAS resident CTAs of the walk kernel: no more
+// than they need, so that the rest of the SM's on-chip memory serves as L1 (the
+// geometry phase's structure data and stack live there).
+template <typename T, bool MWE> static cudaError_t set_walk_attributes(int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_walk<T, MWE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k_walk<T, MWE>)) != cudaSuccess) return e;
+    const size_t need = (size_t)WALK_CTAS * ((size_t)smem + fa.sharedSizeBytes + 1024);
+    const int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+    return cudaFuncSetAttribute(k_walk<T, MWE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 cudaError_t prepare_walk(const EngineView &E)
 {
     const int smem = (int)walk_smem_bytes(E.N, E.max_nc);
-    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (E.mwe > 1)
-        return E.fp32 ? cudaFuncSetAttribute(k_walk<float, true>, at, smem)
-                      : cudaFuncSetAttribute(k_walk<double, true>, at, smem);
-    return E.fp32 ? cudaFuncSetAttribute(k_walk<float, false>, at, smem)
-                  : cudaFuncSetAttribute(k_walk<double, false>, at, smem);
+    if (E.mwe > 1) return E.fp32 ? set_walk_attributes<float, true>(smem) : set_walk_attributes<double, true>(smem);
+    return E.fp32 ? set_walk_attributes<float, false>(smem) : set_walk_attributes<double, false>(smem);
 }
 
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st)
@@ -2200,7 +2181,7 @@ namespace frw {
 template <typename T, bool MWE> static int walk_occupancy(int smem)
 {
     int n = 0;
-    cudaFuncSetAttribute(k_walk<T, MWE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    set_walk_attributes<T, MWE>(smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<T, MWE>, WALK_THREADS, smem);
     return n;
 }

@@ -74,6 +74,8 @@ struct frw_ctx {
     FillConsts fc;
     double *fc_buf = nullptr;
     DevStructure *d_structs = nullptr;
+    SView<float> *d_view_f = nullptr;    // per structure, built at load
+    SView<double> *d_view_d = nullptr;
     int struct_cap = 0;
     std::vector<HostStructure> structs;
     uint32_t *h_status = nullptr;       // pinned
@@ -190,6 +192,8 @@ static EngineView make_view(frw_ctx *ctx)
     E.pool = ctx->grid ? ctx->NS / ctx->grid : ctx->NS;
     E.s = ctx->slots;
     E.structs = ctx->d_structs;
+    E.view_f = ctx->d_view_f;
+    E.view_d = ctx->d_view_d;
     E.mwq = ctx->mwq;
     E.tc = ctx->tc;
     E.W = ctx->d_W;
@@ -387,7 +391,9 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         ctx->fc.d = ctx->fc_buf + (size_t)N * N + 2 * N;
     }
     ctx->struct_cap = 256;
-    if ((rc = dalloc(ctx, &ctx->d_structs, ctx->struct_cap, A))) return bail(rc);
+    if ((rc = dalloc(ctx, &ctx->d_structs, ctx->struct_cap, A)) || (rc = dalloc(ctx, &ctx->d_view_f, ctx->struct_cap, A)) ||
+        (rc = dalloc(ctx, &ctx->d_view_d, ctx->struct_cap, A)))
+        return bail(rc);
     if (cudaMallocHost(&ctx->h_status, sizeof(uint32_t) * STAT_WORDS) != cudaSuccess) return bail(FRW_ENOMEM);
     for (auto &e : ctx->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(FRW_EDEVICE);
@@ -647,7 +653,11 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
         H.dev.clear();
         return rc;
     }
+    const SView<float> vf = sview<float>(D);
+    const SView<double> vd = sview<double>(D);
     CK(cudaMemcpyAsync(ctx->d_structs + sid, &D, sizeof(DevStructure), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_view_f + sid, &vf, sizeof(vf), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_view_d + sid, &vd, sizeof(vd), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     H.live = true;
     *structure_id = sid;
