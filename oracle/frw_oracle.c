@@ -56,9 +56,16 @@
  *      cube.  Structures of more than 254 conductors use plain MicroWalk.  An exit
  *      panel that lies in a conductor or outside the domain is absorbed by the
  *      next hop's distance test.
+ *   R9 FRW-FDM (Algorithm 2; optional): a later cube that is not stratified
+ *      takes the FD-based transition instead of MicroWalk: P of Eq. 8 with the
+ *      unquantised alpha of Eq. 6, thresholds as in R5 over the panels in natural
+ *      face order (face 2a + side, then the other two axes in increasing order),
+ *      one panel sampled with the hop's first word (the word MicroWalk uses for
+ *      its start node).
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -132,6 +139,7 @@ typedef struct {
     double gauss_frac;     /* Gaussian-surface offset as a fraction of the smallest gap */
     int max_hops;
     int mwe;               /* MicroWalk-E expansion factor (R8); 0 or 1: off */
+    int transition;        /* non-stratified cubes: 0 MicroWalk (Algorithm 3), 1 FD solve (Algorithm 2) */
 } orc_options;
 
 /* Quantised alpha of Eq. 6 (reading R4): W[v][i] for an interior neighbour i of v,
@@ -964,7 +972,58 @@ typedef struct {
     tcache_t *tc;
     uint8_t *lat;
     int16_t *cond;
+    double *fe, *fp;       /* FD transitions: voxel eps, panel probabilities */
+    uint32_t *fthr;        /* FD transitions: cumulative thresholds */
 } walker_t;
+
+/* FD-based transition of Algorithm 2 on a voxel lattice: the discrete SGF P of
+ * Eq. 8 for the voxel permittivities e (direct CG solve of the symmetric FD
+ * system, e_c averaging the 8 central nodes as for MicroWalk), thresholds over the
+ * panels in natural face order (face 2a + side, then the other two axes in
+ * increasing order), then one boundary node per word u.  fp (6N^2 doubles) and
+ * thr (6N^2 words) are work space. */
+static void fdm_sample(int N, const double *e, double *fp, uint32_t *thr, int n, const uint32_t *u,
+                       int32_t *nodes)
+{
+    int P = 6 * N * N;
+    if (orc_sgf(N, e, fp) < 0) {
+        fprintf(stderr, "oracle: FD transition solve did not converge\n");
+        abort();
+    }
+    double tot = 0.0;
+    for (int m = 0; m < P; m++) tot += fp[m];
+    build_thresholds(N, fp, tot, thr);
+    const int natural[3] = {0, 1, 2};
+    for (int i = 0; i < n; i++) {
+        int q[3];
+        panel_node(N, natural, sample_panel(N, thr, u[i]), q);
+        for (int a = 0; a < 3; a++) nodes[3 * i + a] = q[a];
+    }
+}
+
+/* FD transition of the walk (FRW-FDM) on the cube q with the hop's first word u. */
+static void fdm_transition(walker_t *wk, const cube_t *q, uint32_t u, int node[3])
+{
+    const orc_structure *S = wk->S;
+    int N = wk->o->N, n3 = N * N * N;
+    cube_lattice(S, q, wk->lat);
+    for (int v = 0; v < n3; v++) wk->fe[v] = S->eps[wk->lat[v]];
+    int32_t nd[3];
+    fdm_sample(N, wk->fe, wk->fp, wk->fthr, 1, &u, nd);
+    for (int a = 0; a < 3; a++) node[a] = nd[a];
+}
+
+/* For tests: n FD transitions of one lattice (material ids, eps per id), one per
+ * word of u; boundary nodes (one coordinate -1 or N) into nodes[3n]. */
+void orc_fdm_transitions(int N, const uint8_t *lat, const double *eps, int n, const uint32_t *u, int32_t *nodes)
+{
+    int n3 = N * N * N, P = 6 * N * N;
+    double *e = malloc(sizeof(double) * n3), *fp = malloc(sizeof(double) * P);
+    uint32_t *thr = malloc(sizeof(uint32_t) * P);
+    for (int v = 0; v < n3; v++) e[v] = eps[lat[v]];
+    fdm_sample(N, e, fp, thr, n, u, nodes);
+    free(e); free(fp); free(thr);
+}
 
 static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
 {
@@ -1122,6 +1181,11 @@ static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
                     done = 1;
                 }
             }
+            if (!done && o->transition == 1) {
+                fdm_transition(wk, &q, hb[0], node);
+                rec->n_mw++;
+                done = 1;
+            }
             if (!done) {
                 cube_lattice(S, &q, wk->lat);
                 microwalk(N, wk->lat, wk->W, wk->key, walk, hop, hb[0], node, &st);
@@ -1145,7 +1209,8 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
                 const double *c_hi, int n_b, const double *b_lo, const double *b_hi,
                 const int32_t *b_mat, int n_mat, const double *eps, int bg,
                 int N, uint64_t seed, uint64_t request, int hybrid, int first_mode,
-                double gauss_frac, int max_hops, int mwe, int master, uint64_t walk_begin, uint64_t n_walks,
+                double gauss_frac, int max_hops, int mwe, int transition, int master, uint64_t walk_begin,
+                uint64_t n_walks,
                 double sigma_target, uint64_t batch,
                 double *S1, double *S2, uint64_t *n_used,
                 double *rec_omega, int32_t *rec_k, uint32_t *rec_hops, uint64_t *rec_steps,
@@ -1154,7 +1219,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
 {
     orc_structure S = {{dom_lo[0], dom_lo[1], dom_lo[2]}, {dom_hi[0], dom_hi[1], dom_hi[2]},
                        n_c, c_lo, c_hi, n_b, b_lo, b_hi, b_mat, n_mat, eps, bg};
-    orc_options o = {N, seed, request, hybrid, first_mode, gauss_frac, max_hops, mwe};
+    orc_options o = {N, seed, request, hybrid, first_mode, gauss_frac, max_hops, mwe, transition};
     walker_t wk;
     wk.S = &S;
     wk.o = &o;
@@ -1169,6 +1234,9 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
     wk.tc = calloc(1, sizeof(tcache_t));
     wk.lat = malloc((size_t)N * N * N);
     wk.cond = malloc(sizeof(int16_t) * (size_t)N * N * N);
+    wk.fe = malloc(sizeof(double) * (size_t)N * N * N);
+    wk.fp = malloc(sizeof(double) * 6 * (size_t)N * N);
+    wk.fthr = malloc(sizeof(uint32_t) * 6 * (size_t)N * N);
     for (int k = 0; k <= n_c; k++) { S1[k] = 0.0; S2[k] = 0.0; }
     for (int s = 0; s < 10; s++) stats[s] = 0;
     uint64_t used = 0;
@@ -1221,6 +1289,9 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
     free(wk.tc);
     free(wk.lat);
     free(wk.cond);
+    free(wk.fe);
+    free(wk.fp);
+    free(wk.fthr);
     return ntab;
 }
 

@@ -74,10 +74,11 @@ def lib():
         L.orc_microwalk_e_many.argtypes = [i, P(u8), P(ctypes.c_int16), P(d), i, u64, u64, u64, u64, u32,
                                            P(ctypes.c_int32), P(ctypes.c_int32), P(u64)]
         L.orc_frw_run.argtypes = ([P(d), P(d), i, P(d), P(d), i, P(d), P(d), P(ctypes.c_int32), i,
-                                   P(d), i, i, u64, u64, i, i, d, i, i, i, u64, u64, d, u64,
+                                   P(d), i, i, u64, u64, i, i, d, i, i, i, i, u64, u64, d, u64,
                                    P(d), P(d), P(u64), P(d), P(ctypes.c_int32), P(u32), P(u64),
                                    P(ctypes.c_int32), P(u64)])
         L.orc_frw_run.restype = i
+        L.orc_fdm_transitions.argtypes = [i, P(u8), P(d), i, P(u32), P(ctypes.c_int32)]
         _lib = L
     return _lib
 
@@ -229,9 +230,11 @@ class RunResult:
 
 
 def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, gauss_frac=0.5,
-            max_hops=100000, walk_begin=0, sigma_target=0.0, batch=16384, records=True, mwe=0):
+            max_hops=100000, walk_begin=0, sigma_target=0.0, batch=16384, records=True, mwe=0, fdm=False):
     """Run walks ``walk_begin .. walk_begin + n_walks - 1`` of Algorithm 1 for
-    ``master`` on structure ``s`` (a :class:`workloads.Structure`)."""
+    ``master`` on structure ``s`` (a :class:`workloads.Structure`).  ``fdm``: the
+    non-stratified transitions solve the cube's FD system (Algorithm 2, FRW-FDM)
+    instead of running MicroWalk; they are counted in ``stats[4]``."""
     L = lib()
     nc = s.n_cond
     S1 = np.zeros(nc + 1)
@@ -253,13 +256,25 @@ def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, 
         _p(s.block_lo, ctypes.c_double), _p(s.block_hi, ctypes.c_double),
         _p(s.block_mat, ctypes.c_int32), s.n_mat, _p(s.eps, ctypes.c_double), int(s.background),
         int(N), int(seed), int(request), int(hybrid), int(first_mode), float(gauss_frac),
-        int(max_hops), int(mwe), int(master), int(walk_begin), n, float(sigma_target), int(batch),
+        int(max_hops), int(mwe), int(bool(fdm)), int(master), int(walk_begin), n, float(sigma_target), int(batch),
         _p(S1, ctypes.c_double), _p(S2, ctypes.c_double), _p(used, ctypes.c_uint64), *rp,
         _p(stats, ctypes.c_uint64))
     u = int(used[0])
     if records:
         om, kk, hp, st, br = om[:u], kk[:u], hp[:u], st[:u], br[:u]
     return RunResult(S1, S2, u, om, kk, hp, st, br, stats, ntab)
+
+
+def fdm_transitions(N, lat, eps, u):
+    """FD-based transitions (Algorithm 2) of one lattice of material ids: the
+    boundary node sampled from the SGF of Eq. 8 for each 32-bit word of ``u``."""
+    lat = np.ascontiguousarray(lat, np.uint8).reshape(-1)
+    e = np.ascontiguousarray(eps, np.float64)
+    u = np.ascontiguousarray(u, np.uint32)
+    nodes = np.zeros((u.size, 3), np.int32)
+    lib().orc_fdm_transitions(int(N), _p(lat, ctypes.c_uint8), _p(e, ctypes.c_double), int(u.size),
+                              _p(u, ctypes.c_uint32), _p(nodes, ctypes.c_int32))
+    return nodes
 
 
 def microwalk_e(N, lat, cond, eps, seed, request, walk, hop=1):
