@@ -296,6 +296,71 @@ def mwe_measurement(s, masters, N, precision, sigma, budget, tuning, rows_mw, st
             "vs_frw_mw": dev}
 
 
+FDM_BUDGET = 1000            # walks per master of the FRW-FDM comparison run
+FDM_CUBES = 1216             # random non-stratified cubes of the per-transition comparison
+
+
+def fdm_measurement(s, masters, N, precision, walks_per_s_mw):
+    """FRW-FDM, the paper's comparator (Algorithm 2: each later non-stratified
+    transition solves the cube's FD system and samples its SGF), on the same
+    structure and masters at a fixed budget of FDM_BUDGET walks per master, timed
+    with CUDA events around one batched extraction; and the cost of one transition
+    both ways on FDM_CUBES random cubes of the same N (2-6 blocks, permittivities
+    {2.5, 3.9, 7.0, 25.0}): FD solves per second against MicroWalk samples per
+    second (64 per cube)."""
+    import torch
+    from paper_2507_09730_gb300 import binding as B
+    from paper_2507_09730_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    ctx = B.Context(0, N=N, precision=precision, seed=0, transition=B.FRW_TRANSITION_FDM)
+    B.frw_set_stream(ctx.ctx, stream.cuda_stream)
+    sid = ctx.load(s)
+    jobs = lambda r, b: [dict(structure_id=sid, master=m, walk_budget=b, request_id=r * 4 + i)
+                         for i, m in enumerate(masters)]
+    ctx.extract_batch(jobs(90_000, 100))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res, _ = ctx.extract_batch(jobs(90_001, FDM_BUDGET))
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    walks = sum(r[2]["walks"] for r in res)
+    fd = sum(r[2]["mw_hops"] for r in res)
+    ctx.close()
+    cubes = W.random_cubes(FDM_CUBES, N=N, seed=5)
+    c = B.Context(0, N=N, slots=1 << 12)
+    B.frw_set_stream(c.ctx, stream.cuda_stream)
+    rec = torch.from_numpy(B.pack_cubes(cubes)).cuda()
+    it = torch.zeros(FDM_CUBES, dtype=torch.int32, device="cuda")
+    spc = 64
+    ex = torch.zeros(FDM_CUBES * spc, dtype=torch.int32, device="cuda")
+    times = {}
+    for name, run in (("fd", lambda: B.frw_fdm_cubes(c.ctx, N, FDM_CUBES, rec.data_ptr(), cubes.eps, 0, 0, 0,
+                                                     it.data_ptr())),
+                      ("mw", lambda: B.frw_microwalk_cubes(c.ctx, N, FDM_CUBES, rec.data_ptr(), cubes.eps, spc, 5,
+                                                           ex.data_ptr(), 0))):
+        run()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        e1.synchronize()
+        times[name] = e0.elapsed_time(e1) / 1e3
+    iv = it.cpu().numpy().view(np.uint32)
+    c.close()
+    fd_rate = FDM_CUBES / times["fd"]
+    mw_rate = FDM_CUBES * spc / times["mw"]
+    return {"workload": f"as the main line, FD-based later non-stratified transitions, {FDM_BUDGET} walks per master",
+            "walks_per_s": walks / secs, "seconds": secs, "walks": walks, "fd_transitions_per_walk": fd / max(1, walks),
+            "frw_mw_over_frw_fdm": walks_per_s_mw / (walks / secs),
+            "per_transition": {"cubes": f"{FDM_CUBES} random cubes, N = {N}, 2-6 blocks",
+                               "fd_solves_per_s": fd_rate, "microwalk_samples_per_s": mw_rate,
+                               "microwalk_over_fd": mw_rate / fd_rate,
+                               "cg_iterations_mean": float((iv & 0xFFFFFF).mean()),
+                               "refinement_passes_mean": float((iv >> 24).mean())}}
+
+
 SERVE_BUDGET = 4_000_000     # walk budget (cap) of one served request
 
 
@@ -509,6 +574,7 @@ def main():
         line["e2e"] = e2e
     if rank == 0 and world == 1:
         line["frw_mwe"] = mwe_measurement(s, masters, a.N, prec, a.sigma, a.budget, tuning, rows)
+        line["frw_fdm"] = fdm_measurement(s, masters, a.N, prec, value)
         line["microwalk_kernel"] = microwalk_kernel(alu_peak)
         line["fp32_vs_fp64"] = fp32_deviation(s, masters, a.N, a.sigma, a.budget)
     if rank == 0 and world == 1 and a.serve_seconds > 0:

@@ -60,6 +60,10 @@ extern "C" {
 #define FRW_MAX_N 32         /* lattice edge N: even, 2 <= N <= 32 */
 #define FRW_MAX_MATERIALS 15 /* distinct permittivities per context */
 #define FRW_MAX_CUBE_BLOCKS 14
+#define FRW_FDM_MAX_N 24     /* FD transitions: the solve's vectors of N^3 floats in shared memory */
+
+#define FRW_TRANSITION_MICROWALK 0
+#define FRW_TRANSITION_FDM 1
 
 typedef struct frw_ctx frw_ctx;
 
@@ -101,7 +105,11 @@ typedef struct {
                                   off, plain FRW-MW) */
     int32_t idle_timeout_ms;   /* a walk-kernel CTA with nothing to do gives up waiting after this
                                   long and ends the run with an error status (0: 10000) */
-    int32_t reserved[2];
+    int32_t transition;        /* later non-stratified cubes: FRW_TRANSITION_MICROWALK (Algorithm 3,
+                                  FRW-MW) or FRW_TRANSITION_FDM (Algorithm 2, FRW-FDM: the cube's
+                                  FD system is solved and its SGF sampled; the paper's comparator;
+                                  N <= FRW_FDM_MAX_N, no MicroWalk-E) */
+    int32_t reserved;
 } frw_options;
 
 /* One extraction: a row of the capacitance matrix for one master conductor. */
@@ -343,6 +351,24 @@ int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t 
 int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int32_t *d_cubes, const double *eps_r,
                                 int32_t n_mat, uint64_t seed, uint64_t samples_per_cube, uint64_t request_id,
                                 uint32_t *d_exit, uint32_t *d_steps, void *cuda_stream);
+
+/* FD-based transition (Algorithm 2) on n_cubes lattice cubes given as for
+ * frw_microwalk_cubes (records of 64 int32, at most 8 blocks; N = the context's N,
+ * N <= FRW_FDM_MAX_N): per cube, the discrete SGF P = e_c^T A_II^{-1} A_IB of Eq. 8
+ * with the unquantised alpha of Eq. 6 and e_c averaging the 8 central nodes, from a
+ * mixed-precision solve of the symmetric FD system (FP32 conjugate gradients
+ * refined in FP64 until the FP64 residual is at most 1e-12 of ||e_c||_2), then one
+ * boundary node sampled with the word d_u[c]: the first panel, in natural face
+ * order (face 2a + side, then the other two axes in increasing order), whose
+ * threshold min(floor(2^32 cum / total), 2^32 - 1) exceeds the word.
+ * Device inputs: d_cubes; d_u (n_cubes words; NULL: 0xffffffff for every cube).
+ * Device outputs, each may be NULL: d_P[c * 6N^2 + m] = P of panel m (not
+ * normalised: the sum is 1 up to the solve's residual); d_exit[c] = the sampled
+ * boundary node, packed as by frw_microwalk_cubes; d_iters[c] = inner conjugate-
+ * gradient iterations | (refinement passes << 24).  FRW_EDEVICE if a solve did not
+ * reach its tolerance.  Blocks the calling thread until done. */
+int frw_fdm_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t *d_cubes, const double *eps_r,
+                  int32_t n_mat, const uint32_t *d_u, double *d_P, uint32_t *d_exit, uint32_t *d_iters);
 
 /* One analytical table computed on the device (Eq. 8 for SGF kinds; the
  * first-cube flux kernel for FLUX kinds) for the context's N: profile[N] = material

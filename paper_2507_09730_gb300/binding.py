@@ -18,6 +18,8 @@ from . import build as _build
 (FRW_OK, FRW_EINVAL, FRW_ENOMEM, FRW_ETIMEOUT, FRW_EDEVICE, FRW_ENOTCONV, FRW_ECAPACITY, FRW_ENOTFOUND,
  FRW_ECANCELED) = range(9)
 FRW_FP64_GEOM, FRW_FP32_GEOM = 0, 1
+FRW_TRANSITION_MICROWALK, FRW_TRANSITION_FDM = 0, 1
+FRW_FDM_MAX_N = 24
 FRW_TAB_SGF, FRW_TAB_FLUX_PAR, FRW_TAB_FLUX_PERP, FRW_TAB_SGF_HOM, FRW_TAB_FLUX_HOM = range(5)
 
 EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream", "frw_load_structure",
@@ -25,7 +27,7 @@ EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream",
            "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
            "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
            "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums", "frw_extract_matrix",
-           "frw_cancel", "frw_get_serve_info")
+           "frw_cancel", "frw_get_serve_info", "frw_fdm_cubes")
 
 
 class frw_box(ctypes.Structure):
@@ -42,7 +44,7 @@ class frw_options(ctypes.Structure):
                 ("slots", c_int32), ("table_capacity", c_int32), ("mw_warps_per_cta", c_int32),
                 ("mw_ctas_per_sm", c_int32), ("geom_threads", c_int32), ("serve_jobs", c_int32),
                 ("serve_arena_mb", c_int32), ("mwe_factor", c_int32), ("idle_timeout_ms", c_int32),
-                ("reserved", c_int32 * 2)]
+                ("transition", c_int32), ("reserved", c_int32)]
 
 
 class frw_extract_params(ctypes.Structure):
@@ -121,6 +123,8 @@ def lib():
                                       c_uint64, c_void_p, c_void_p]
     L.frw_microwalk_cubes_noalloc.argtypes = [c_int32, c_int32, c_void_p, P(c_double), c_int32, c_uint64, c_uint64,
                                               c_uint64, c_void_p, c_void_p, c_void_p]
+    L.frw_fdm_cubes.argtypes = [c_void_p, c_int32, c_int32, c_void_p, P(c_double), c_int32, c_void_p, c_void_p,
+                                c_void_p, c_void_p]
     L.frw_table.argtypes = [c_void_p, c_int32, P(c_int32), P(c_double), c_int32, P(c_uint32), P(c_uint8),
                             P(c_double), P(c_double)]
     L.frw_submit.argtypes = [c_void_p, POINTER(frw_job), POINTER(c_uint64)]
@@ -409,6 +413,16 @@ def frw_microwalk_cubes_noalloc(N: int, n_cubes: int, d_cubes_ptr: int, eps, see
                                              int(seed), int(samples_per_cube), int(request_id),
                                              c_void_p(d_exit_ptr or 0), c_void_p(d_steps_ptr or 0),
                                              c_void_p(stream_handle or 0))
+
+
+def frw_fdm_cubes(ctx, N: int, n_cubes: int, d_cubes_ptr: int, eps, d_u_ptr: int = 0, d_P_ptr: int = 0,
+                  d_exit_ptr: int = 0, d_iters_ptr: int = 0) -> None:
+    """FD-based transitions (Algorithm 2) of stand-alone cubes; device pointers."""
+    e = np.ascontiguousarray(eps, np.float64)
+    rc = lib().frw_fdm_cubes(ctx, int(N), int(n_cubes), c_void_p(d_cubes_ptr), _ptr(e, c_double), len(e),
+                             c_void_p(d_u_ptr or 0), c_void_p(d_P_ptr or 0), c_void_p(d_exit_ptr or 0),
+                             c_void_p(d_iters_ptr or 0))
+    _check(ctx, rc)
 
 
 def frw_table(ctx, N: int, kind: int, profile=None, eps=None):

@@ -11,6 +11,7 @@ constexpr int KMAX = 14;                 // blocks per transition cube (mask bit
 constexpr int BOUNDARY = 15;             // material id of absorbing boundary nodes
 constexpr int NMAT = 16;                 // material slots (15 real + boundary)
 constexpr double EPS0 = 8.8541878128e-3; // fF / um
+constexpr int FDM_MAX_N = 24;            // FD transitions: p and r of N^3 floats in shared memory
 constexpr int GUIDE = 2048;              // guide-table buckets of the inverse-CDF sampler (2^11)
 
 // analytical table kinds (same numbering as the ABI's FRW_TAB_*)
@@ -23,10 +24,12 @@ enum : uint32_t { ST_IDLE = 0, ST_FRESH = 1, ST_FIRST = 2, ST_HOP = 3, ST_MW = 4
 enum : uint32_t {
     ERR_MWQ_OVERFLOW = 1u, ERR_CACHE_FULL = 2u, ERR_FILL = 4u, ERR_SHRINK = 8u, ERR_ACC_RANGE = 16u,
     ERR_MW_STEPS = 32u, ERR_IDLE_TIMEOUT = 64u, ERR_REDUCE_QUEUE = 128u,
-    ERR_CHECK = 256u              // a bounds check of the debug build (-DFRW_CHECKS) failed
+    ERR_CHECK = 256u,             // a bounds check of the debug build (-DFRW_CHECKS) failed
+    ERR_FDM = 512u                // an FD transition solve did not reach its tolerance
 };
 // status words
 enum { STAT_ACTIVE = 0, STAT_ERR = 1, STAT_BUILT = 2, STAT_MWJOBS = 3, STAT_EPOCHS = 4, STAT_SUSPENDED = 5,
+       STAT_PROGRESS = 6,   // epochs in which some walk-kernel CTA had work (its idle CTAs wait while it moves)
        STAT_WORDS = 8 };
 // host control words read by the running walk kernel
 enum { CTRL_OPEN = 0, CTRL_ABORT = 1, CTRL_WORDS = 4 };
@@ -265,6 +268,8 @@ struct EngineView {
     double idle_timeout_s; // idle wait limit of the walk kernel
     int hops_per_epoch;    // analytical hops one walk may take per epoch (tunable, >= 1)
     int mwe;               // MicroWalk-E expansion factor (0 or 1: plain MicroWalk)
+    int transition;        // non-stratified transitions: 0 MicroWalk, 1 FD solve (FRW-FDM)
+    unsigned char *fdm_scratch;   // FRW-FDM: per walk-kernel CTA, fdm_cube_scratch_bytes(N)
     int suspend_lanes;     // a MicroWalk warp with at most this many lanes left may suspend them
     uint32_t suspend_min_steps;   // ... once each has made this many steps in the epoch
 };
@@ -283,9 +288,15 @@ struct LaunchShape {
 // outside any stream capture)
 cudaError_t prepare_walk(const EngineView &E);
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st);
-size_t walk_smem_bytes(int N, int max_nc);
+size_t walk_smem_bytes(int N, int max_nc, int transition);
 int walk_pool_slots();
-int walk_ctas_per_sm(int N, int fp32, int mwe);
+int walk_ctas_per_sm(int N, int fp32, int mwe, int transition);
+// FD transitions (Algorithm 2) of stand-alone cubes, one CTA per cube at a time;
+// scratch = grid x fdm_cube_scratch_bytes(N)
+size_t fdm_cube_scratch_bytes(int N);
+cudaError_t launch_fdm_cubes(int N, const int32_t *d_cubes, uint32_t n_cubes, const uint8_t *map, const double *eps,
+                             const uint32_t *d_u, double *d_P, uint32_t *d_exit, uint32_t *d_iters,
+                             unsigned char *scratch, int grid, uint32_t *d_err, cudaStream_t st);
 // fill one table with an explicit key into entry `entry` of the cache arrays
 cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t prof[4],
                             uint32_t entry, double *values_out, cudaStream_t st);

@@ -1660,6 +1660,9 @@ __device__ __forceinline__ long long clock_after(const uint32_t *anchor)
     return c;
 }
 
+#include "fdm_transition.cuh"
+constexpr uint32_t FDM_CLAIM_CAP = 32;   // FRW-FDM: walk ids a CTA claims per epoch
+
 struct WalkShared {
     uint32_t W[256];                 // quantised weights of Eq. 6, [centre][neighbour material]
     uint32_t g_head, g_back, pad3[2];
@@ -1667,7 +1670,8 @@ struct WalkShared {
     uint32_t f_count, active, issuable, stop;
     uint32_t red, finished, n_free, j_lo;
     uint32_t j_pub, pad4[3];
-    uint32_t q_next, pad2[3];
+    uint32_t q_next, fdm_sel, progress_seen, pad2;
+    unsigned long long idle_t0;      // start of this CTA's idle wait (thread 0)
     IssueRanges ir;
     uint32_t fill[FILL_MAX];
     uint16_t qlist[2][POOL_MAX];
@@ -1695,12 +1699,19 @@ size_t walk_scratch_bytes(int N, int max_nc)
     return std::max(masks, std::max(fill, red));
 }
 
-size_t walk_smem_bytes(int N, int max_nc) { return walk_scratch_bytes(N, max_nc); }
+size_t walk_smem_bytes(int N, int max_nc, int transition)
+{
+    const size_t base = walk_scratch_bytes(N, max_nc);
+    return transition == 1 ? std::max(base, fdm_smem_bytes(N)) : base;
+}
 
 int walk_pool_slots() { return POOL_MAX; }
 
-template <typename T, bool MWE>
-__global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk(EngineView E)
+// FDM = true: the FRW-FDM comparator, whose non-stratified transitions solve the
+// cube's FD system (Algorithm 2) one cube at a time with the whole CTA, in place
+// of the MicroWalk phase (one CTA per SM: the solve's vectors fill shared memory).
+template <typename T, bool MWE, bool FDM>
+__global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(EngineView E)
 {
     extern __shared__ __align__(16) unsigned char dsm_all[];
     __shared__ WalkShared sh;
@@ -1722,10 +1733,12 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk(EngineView E)
         sh.issuable = 0;
         sh.j_lo = 0;
         sh.j_pub = 0;
+        sh.idle_t0 = 0;
+        sh.progress_seen = 0;
     }
     __syncthreads();
     int cur = 0;
-    unsigned long long idle_t0 = 0, cyc[5] = {0, 0, 0, 0, 0};
+    unsigned long long cyc[5] = {0, 0, 0, 0, 0};
     uint32_t epochs = 0;
     for (;;) {
         const long long c0 = clock64();
@@ -1785,7 +1798,9 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk(EngineView E)
                 }
             }
             __syncthreads();
-            if (warp == 0) claim_ids(E, sh.ir, sh.n_free, sh.j_lo, sh.j_pub);
+            // FRW-FDM: few new walks per CTA and epoch, so that the long FD solves
+            // spread over every CTA instead of the first ones to claim
+            if (warp == 0) claim_ids(E, sh.ir, FDM ? min(sh.n_free, FDM_CLAIM_CAP) : sh.n_free, sh.j_lo, sh.j_pub);
             __syncthreads();
             const uint32_t n1 = sh.g_count, ng = n1 + sh.g_back;
             const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
@@ -1800,7 +1815,45 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk(EngineView E)
         }
         __syncthreads();
         const long long cg1 = clock_after(&sh.q_count);
-        {
+        if constexpr (FDM) {
+            // ---------------- FD transitions (Algorithm 2) ----------------
+            const uint32_t qn = sh.q_count;
+            const FdmSmem S = fdm_smem(dsm, N);
+            const FdmScratch X = fdm_scratch(E.fdm_scratch + (size_t)blockIdx.x * fdm_scratch_bytes(N), N);
+            const FdmGrid G = fdm_grid(N);
+            if (qn) fdm_couplings(S, E.eps);
+            for (uint32_t qi = 0; qi < qn; qi++) {
+                const uint32_t o = q_now[qi];
+                if (!FRW_CHECKED(E, o < P)) continue;
+                const MWJob &b = E.mwq[base + o];
+                const int K = min((int)b.K, KMAX);
+                const uint64_t mm = (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32);
+                // voxel materials: background (slot 1), then the listed blocks in order
+                fdm_nodes(G, [&](int v, int i, int j, int k) {
+                    int slot = 1;
+                    for (int t = 0; t < K; t++) {
+                        const uint2 r = b.rng[t];
+                        if (i >= rng_lo(r, 0) && i < rng_hi(r, 0) && j >= rng_lo(r, 1) && j < rng_hi(r, 1) &&
+                            k >= rng_lo(r, 2) && k < rng_hi(r, 2))
+                            slot = 2 + t;
+                    }
+                    S.lat[v] = (uint8_t)((mm >> (4 * slot)) & 15ull);
+                });
+                __syncthreads();
+                // the hop's first word, as MicroWalk's start draw
+                const uint32_t u = philox10(b.walk_lo, b.walk_hi, b.hop, 0u, b.key0, b.key1).x;
+                const FdmResult r = fdm_solve(N, S, X, u, nullptr, &sh.fdm_sel);
+                if (tid == 0) {
+                    if (!r.converged) atomicOr(&E.status[STAT_ERR], ERR_FDM);
+                    const uint32_t sl = b.slot;
+                    E.s.exitnode[sl] = r.exitnode;
+                    __threadfence_block();
+                    E.s.state[sl] = ST_MWDONE;
+                    atomicAdd(&sh.finished, 1u);
+                }
+                __syncthreads();
+            }
+        } else {
             // ---------------- MicroWalk ----------------
             const int mwarp = warp;
             uint16_t *Mw = reinterpret_cast<uint16_t *>(dsm) + (size_t)mwarp * mask_rows(N) * 32;
@@ -1977,17 +2030,23 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk(EngineView E)
                 if (!undecided && *(volatile uint32_t *)&E.ctrl[CTRL_OPEN] == 0u) {
                     stop = 1;
                 } else {
+                    // the wait is limited only while no CTA of the run makes progress
+                    // (others may still be busy with walks this CTA cannot take over)
                     unsigned long long now;
                     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-                    if (idle_t0 == 0) idle_t0 = now;
-                    else if ((double)(now - idle_t0) * 1e-9 > E.idle_timeout_s) {
+                    const uint32_t prog = *(volatile uint32_t *)&E.status[STAT_PROGRESS];
+                    if (sh.idle_t0 == 0 || prog != sh.progress_seen) {
+                        sh.idle_t0 = now;
+                        sh.progress_seen = prog;
+                    } else if ((double)(now - sh.idle_t0) * 1e-9 > E.idle_timeout_s) {
                         atomicOr(&E.status[STAT_ERR], ERR_IDLE_TIMEOUT);
                         stop = 1;
                     }
                     __nanosleep(20000);
                 }
             } else {
-                idle_t0 = 0;
+                sh.idle_t0 = 0;
+                atomicAdd(&E.status[STAT_PROGRESS], 1u);
             }
             sh.stop = stop;
         }
@@ -2001,39 +2060,103 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk(EngineView E)
     }
 }
 
-// Shared-memory carve-out for WALK_CTAS resident CTAs of the walk kernel: no more
-// than they need, so that the rest of the SM's on-chip memory serves as L1 (the
-// geometry phase's structure data and stack live there).
-template <typename T, bool MWE> static cudaError_t set_walk_attributes(int smem)
+// Shared-memory carve-out for the resident CTAs of the walk kernel (WALK_CTAS;
+// one for the FDM comparator): no more than they need, so that the rest of the
+// SM's on-chip memory serves as L1 (the geometry phase's structure data and stack
+// live there).
+template <typename T, bool MWE, bool FDM> static cudaError_t set_walk_attributes(int smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_walk<T, MWE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_walk<T, MWE, FDM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, k_walk<T, MWE>)) != cudaSuccess) return e;
-    const size_t need = (size_t)WALK_CTAS * ((size_t)smem + fa.sharedSizeBytes + 1024);
+    if ((e = cudaFuncGetAttributes(&fa, k_walk<T, MWE, FDM>)) != cudaSuccess) return e;
+    const size_t need = (size_t)(FDM ? 1 : WALK_CTAS) * ((size_t)smem + fa.sharedSizeBytes + 1024);
     const int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
-    return cudaFuncSetAttribute(k_walk<T, MWE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    return cudaFuncSetAttribute(k_walk<T, MWE, FDM>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
-cudaError_t prepare_walk(const EngineView &E)
+static cudaError_t walk_attributes(int N, int max_nc, int fp32, int mwe, int transition)
 {
-    const int smem = (int)walk_smem_bytes(E.N, E.max_nc);
-    if (E.mwe > 1) return E.fp32 ? set_walk_attributes<float, true>(smem) : set_walk_attributes<double, true>(smem);
-    return E.fp32 ? set_walk_attributes<float, false>(smem) : set_walk_attributes<double, false>(smem);
+    const int smem = (int)walk_smem_bytes(N, max_nc, transition);
+    if (transition == 1)
+        return fp32 ? set_walk_attributes<float, false, true>(smem) : set_walk_attributes<double, false, true>(smem);
+    if (mwe > 1)
+        return fp32 ? set_walk_attributes<float, true, false>(smem) : set_walk_attributes<double, true, false>(smem);
+    return fp32 ? set_walk_attributes<float, false, false>(smem) : set_walk_attributes<double, false, false>(smem);
 }
+
+cudaError_t prepare_walk(const EngineView &E) { return walk_attributes(E.N, E.max_nc, E.fp32, E.mwe, E.transition); }
 
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st)
 {
     (void)L;
-    const size_t smem = walk_smem_bytes(E.N, E.max_nc);
+    const size_t smem = walk_smem_bytes(E.N, E.max_nc, E.transition);
     const unsigned grid = E.NS / E.pool;
-    if (E.mwe > 1) {
-        if (E.fp32) k_walk<float, true><<<grid, WALK_THREADS, smem, st>>>(E);
-        else k_walk<double, true><<<grid, WALK_THREADS, smem, st>>>(E);
+    if (E.transition == 1) {
+        if (E.fp32) k_walk<float, false, true><<<grid, WALK_THREADS, smem, st>>>(E);
+        else k_walk<double, false, true><<<grid, WALK_THREADS, smem, st>>>(E);
+    } else if (E.mwe > 1) {
+        if (E.fp32) k_walk<float, true, false><<<grid, WALK_THREADS, smem, st>>>(E);
+        else k_walk<double, true, false><<<grid, WALK_THREADS, smem, st>>>(E);
     } else {
-        if (E.fp32) k_walk<float, false><<<grid, WALK_THREADS, smem, st>>>(E);
-        else k_walk<double, false><<<grid, WALK_THREADS, smem, st>>>(E);
+        if (E.fp32) k_walk<float, false, false><<<grid, WALK_THREADS, smem, st>>>(E);
+        else k_walk<double, false, false><<<grid, WALK_THREADS, smem, st>>>(E);
     }
+    return cudaGetLastError();
+}
+
+// FD transitions of stand-alone cubes (records as for the MicroWalk kernel: 64
+// int32, [0] background, [1] K <= 8, then (i0, i1, j0, j1, k0, k1, mat) per block;
+// local material ids mapped to the context's ids through the nibble map mmap)
+__global__ void __launch_bounds__(FDM_THREADS, 1)
+    k_fdm_cubes(int N, const int32_t *__restrict__ cubes, uint32_t n_cubes, uint64_t mmap,
+                const double *__restrict__ eps, const uint32_t *__restrict__ u, double *P, uint32_t *exit_out,
+                uint32_t *iters, unsigned char *scratch, uint32_t *err)
+{
+    extern __shared__ __align__(16) unsigned char dsm_fdm[];
+    __shared__ uint32_t sel;
+    const FdmSmem S = fdm_smem(dsm_fdm, N);
+    const FdmScratch X = fdm_scratch(scratch + (size_t)blockIdx.x * fdm_scratch_bytes(N), N);
+    const FdmGrid G = fdm_grid(N);
+    fdm_couplings(S, eps);
+    for (uint32_t c = blockIdx.x; c < n_cubes; c += gridDim.x) {
+        const int32_t *rec = cubes + (size_t)c * 64;
+        const int K = min(max(rec[1], 0), 8);
+        const int bgm = (int)((mmap >> (4 * (rec[0] & 15))) & 15ull);
+        fdm_nodes(G, [&](int v, int i, int j, int k) {
+            int m = bgm;
+            for (int t = 0; t < K; t++) {
+                const int32_t *bk = rec + 2 + 7 * t;
+                if (i >= bk[0] && i < bk[1] && j >= bk[2] && j < bk[3] && k >= bk[4] && k < bk[5])
+                    m = (int)((mmap >> (4 * (bk[6] & 15))) & 15ull);
+            }
+            S.lat[v] = (uint8_t)m;
+        });
+        __syncthreads();
+        const FdmResult r =
+            fdm_solve(N, S, X, u ? u[c] : 0xffffffffu, P ? P + (size_t)c * 6 * N * N : nullptr, &sel);
+        if (threadIdx.x == 0) {
+            if (exit_out) exit_out[c] = r.exitnode;
+            if (iters) iters[c] = r.inner | (r.outer << 24);
+            if (!r.converged) atomicOr(err, ERR_FDM);
+        }
+        __syncthreads();
+    }
+}
+
+size_t fdm_cube_scratch_bytes(int N) { return fdm_scratch_bytes(N); }
+
+cudaError_t launch_fdm_cubes(int N, const int32_t *d_cubes, uint32_t n_cubes, const uint8_t *map, const double *eps,
+                             const uint32_t *d_u, double *d_P, uint32_t *d_exit, uint32_t *d_iters,
+                             unsigned char *scratch, int grid, uint32_t *d_err, cudaStream_t st)
+{
+    const int smem = (int)fdm_smem_bytes(N);
+    cudaError_t e = cudaFuncSetAttribute(k_fdm_cubes, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    uint64_t mm = 0;
+    for (int i = 0; i < 16; i++) mm |= (uint64_t)(map[i] & 15u) << (4 * i);
+    k_fdm_cubes<<<grid, FDM_THREADS, smem, st>>>(N, d_cubes, n_cubes, mm, eps, d_u, d_P, d_exit, d_iters, scratch,
+                                                  d_err);
     return cudaGetLastError();
 }
 
@@ -2177,20 +2300,26 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
 
 namespace frw {
 // CTAs of the walk kernel resident per SM at this lattice edge (3 by design at
-// N = 24: at most 85 registers per thread and about 67 KB of shared memory each)
-template <typename T, bool MWE> static int walk_occupancy(int smem)
+// N = 24: at most 85 registers per thread and about 67 KB of shared memory each;
+// one for the FDM comparator)
+template <typename T, bool MWE, bool FDM> static int walk_occupancy(int smem)
 {
     int n = 0;
-    set_walk_attributes<T, MWE>(smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<T, MWE>, WALK_THREADS, smem);
+    set_walk_attributes<T, MWE, FDM>(smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<T, MWE, FDM>, WALK_THREADS, smem);
     return n;
 }
 
-int walk_ctas_per_sm(int N, int fp32, int mwe)
+int walk_ctas_per_sm(int N, int fp32, int mwe, int transition)
 {
-    const int smem = (int)walk_smem_bytes(N, 200);
-    const int n = mwe > 1 ? (fp32 ? walk_occupancy<float, true>(smem) : walk_occupancy<double, true>(smem))
-                          : (fp32 ? walk_occupancy<float, false>(smem) : walk_occupancy<double, false>(smem));
+    const int smem = (int)walk_smem_bytes(N, 200, transition);
+    int n;
+    if (transition == 1)
+        n = fp32 ? walk_occupancy<float, false, true>(smem) : walk_occupancy<double, false, true>(smem);
+    else if (mwe > 1)
+        n = fp32 ? walk_occupancy<float, true, false>(smem) : walk_occupancy<double, true, false>(smem);
+    else
+        n = fp32 ? walk_occupancy<float, false, false>(smem) : walk_occupancy<double, false, false>(smem);
     return n > 0 ? n : 1;
 }
 }  // namespace frw

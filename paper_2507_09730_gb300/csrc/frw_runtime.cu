@@ -85,6 +85,7 @@ struct frw_ctx {
     unsigned long long *cycles = nullptr;      // phase cycle counters
     int grid = 0;                              // walk-kernel CTAs
     double *fill_scratch = nullptr;            // per CTA table-fill scratch
+    unsigned char *fdm_scratch = nullptr;      // FRW-FDM: per CTA FD-solve scratch
     RecArrays rec;                      // per-walk records (grown on demand)
     uint64_t rec_cap = 0;
     std::vector<void *> rec_allocs;
@@ -206,6 +207,8 @@ static EngineView make_view(frw_ctx *ctx)
     E.idle_timeout_s = ctx->opt.idle_timeout_ms > 0 ? 1e-3 * ctx->opt.idle_timeout_ms : 10.0;
     E.hops_per_epoch = ctx->tune.hops_per_epoch;
     E.mwe = ctx->opt.mwe_factor;
+    E.transition = ctx->opt.transition;
+    E.fdm_scratch = ctx->fdm_scratch;
     E.suspend_lanes = ctx->tune.suspend_lanes;
     E.suspend_min_steps = (uint32_t)ctx->tune.suspend_min_steps;
     return E;
@@ -268,12 +271,12 @@ static int check_status(frw_ctx *ctx, cudaStream_t st = nullptr)
     const uint32_t e = ctx->h_status[STAT_ERR];
     if (e) {
         char buf[160];
-        snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s%s%s%s)", e,
+        snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s%s%s%s%s)", e,
                  (e & ERR_MWQ_OVERFLOW) ? "queue overflow " : "", (e & ERR_CACHE_FULL) ? "table cache full " : "",
                  (e & ERR_FILL) ? "table fill check " : "", (e & ERR_SHRINK) ? "cube shrink limit " : "",
                  (e & ERR_ACC_RANGE) ? "accumulator range " : "", (e & ERR_MW_STEPS) ? "MicroWalk step cap " : "",
                  (e & ERR_IDLE_TIMEOUT) ? "idle limit " : "", (e & ERR_REDUCE_QUEUE) ? "reduction queue " : "",
-                 (e & ERR_CHECK) ? "bounds check" : "");
+                 (e & ERR_CHECK) ? "bounds check " : "", (e & ERR_FDM) ? "FD solve tolerance" : "");
         return fail(ctx, (e & ERR_CACHE_FULL) ? FRW_ECAPACITY : FRW_EDEVICE, buf);
     }
     return FRW_OK;
@@ -293,6 +296,8 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     if (opt.mw_warps_per_cta < 0 || opt.mw_warps_per_cta > 16 || opt.mw_ctas_per_sm < 0 || opt.mw_ctas_per_sm > 32)
         return FRW_EINVAL;
     if (opt.mwe_factor < 0 || opt.mwe_factor > 16 || opt.idle_timeout_ms < 0) return FRW_EINVAL;
+    if (opt.transition != FRW_TRANSITION_MICROWALK && opt.transition != FRW_TRANSITION_FDM) return FRW_EINVAL;
+    if (opt.transition == FRW_TRANSITION_FDM && (opt.N > FDM_MAX_N || opt.mwe_factor > 1)) return FRW_EINVAL;
     frw_ctx *ctx = new frw_ctx();
     ctx->opt = opt;
     ctx->device = device;
@@ -319,9 +324,11 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->shape.fill_ctas = ctx->shape.sms;
     const int N = opt.N;
     // walk kernel: CTAs resident at once (as many per SM as fit), each with a pool of slots
-    ctx->grid = walk_ctas_per_sm(N, opt.precision == FRW_FP32_GEOM, opt.mwe_factor) * ctx->shape.sms;
+    ctx->grid = walk_ctas_per_sm(N, opt.precision == FRW_FP32_GEOM, opt.mwe_factor, opt.transition) * ctx->shape.sms;
     {
-        uint64_t want = opt.slots > 0 ? (uint64_t)opt.slots : (1ull << 20);
+        // FRW-FDM: one slot per thread by default (a CTA solves its cubes one at a time)
+        const uint64_t dflt = opt.transition == FRW_TRANSITION_FDM ? 256ull * ctx->grid : (1ull << 20);
+        uint64_t want = opt.slots > 0 ? (uint64_t)opt.slots : dflt;
         uint64_t pool = (want + ctx->grid - 1) / ctx->grid;
         pool = ((pool + 255) / 256) * 256;
         if (pool < 256) pool = 256;
@@ -353,6 +360,9 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)) ||
         (rc = dalloc(ctx, &ctx->ctrl, CTRL_WORDS, A)) || (rc = dalloc(ctx, &ctx->cycles, 8, A)) ||
         (rc = dalloc(ctx, &ctx->fill_scratch, (size_t)ctx->grid * 6 * N * N, A)))
+        return bail(rc);
+    if (opt.transition == FRW_TRANSITION_FDM &&
+        (rc = dalloc(ctx, &ctx->fdm_scratch, (size_t)ctx->grid * fdm_cube_scratch_bytes(N), A)))
         return bail(rc);
     TableCache &T = ctx->tc;
     T.cap = cap;
@@ -1304,6 +1314,40 @@ extern "C" int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, con
     if (e != cudaSuccess) {
         for (void *p : tmp) cudaFree(p);
         return cuda_fail(ctx, e, "MicroWalk cube launch");
+    }
+    rc = check_status(ctx);
+    for (void *p : tmp) cudaFree(p);
+    return rc;
+}
+
+extern "C" int frw_fdm_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t *d_cubes, const double *eps_r,
+                             int32_t n_mat, const uint32_t *d_u, double *d_P, uint32_t *d_exit, uint32_t *d_iters)
+{
+    if (!ctx || (n_cubes > 0 && !d_cubes) || !eps_r || n_mat < 1 || n_mat > FRW_MAX_MATERIALS) return FRW_EINVAL;
+    if (N != ctx->opt.N) return fail(ctx, FRW_EINVAL, "cube lattice edge must equal the context's N");
+    if (N > FDM_MAX_N) return fail(ctx, FRW_EINVAL, "FD transitions need N <= FRW_FDM_MAX_N");
+    if (n_cubes <= 0) return FRW_OK;
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
+    CK(cudaSetDevice(ctx->device));
+    std::vector<uint8_t> map;
+    int rc;
+    {
+        std::lock_guard<std::mutex> ls(ctx->struct_mu);
+        rc = register_materials(ctx, eps_r, n_mat, map);
+    }
+    if (rc) return rc;
+    const int grid = std::min(n_cubes, ctx->shape.sms);
+    std::vector<void *> tmp;
+    unsigned char *scratch = nullptr;
+    if ((rc = dalloc(ctx, &scratch, (size_t)grid * fdm_cube_scratch_bytes(N), tmp))) return rc;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st);
+    if (e == cudaSuccess)
+        e = launch_fdm_cubes(N, d_cubes, (uint32_t)n_cubes, map.data(), ctx->d_eps, d_u, d_P, d_exit, d_iters, scratch,
+                             grid, ctx->status + STAT_ERR, st);
+    if (e != cudaSuccess) {
+        for (void *p : tmp) cudaFree(p);
+        return cuda_fail(ctx, e, "FD transition launch");
     }
     rc = check_status(ctx);
     for (void *p : tmp) cudaFree(p);
