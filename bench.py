@@ -195,7 +195,7 @@ def run_reference(a):
 # DRAM bytes (read + write) per walk of the walk kernel, from one ncu capture of
 # this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
 # launch started.  None once the kernel has changed since the capture.
-DRAM_BYTES_PER_WALK = 5507.0
+DRAM_BYTES_PER_WALK = 4607.0
 
 
 def traffic_per_launch(agg, n_launch):
@@ -296,7 +296,7 @@ def mwe_measurement(s, masters, N, precision, sigma, budget, tuning, rows_mw, st
             "vs_frw_mw": dev}
 
 
-FDM_BUDGET = 1000            # walks per master of the FRW-FDM comparison run
+FDM_BUDGET = 400             # walks per master of the FRW-FDM comparison run
 FDM_CUBES = 1216             # random non-stratified cubes of the per-transition comparison
 
 
@@ -317,7 +317,7 @@ def fdm_measurement(s, masters, N, precision, walks_per_s_mw):
     sid = ctx.load(s)
     jobs = lambda r, b: [dict(structure_id=sid, master=m, walk_budget=b, request_id=r * 4 + i)
                          for i, m in enumerate(masters)]
-    ctx.extract_batch(jobs(90_000, 100))
+    ctx.extract_batch(jobs(90_000, 20))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)

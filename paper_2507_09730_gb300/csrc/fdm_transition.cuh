@@ -23,17 +23,18 @@
 // min(floor(2^32 cum / total), 2^32 - 1) exceeds u, the last panel otherwise.
 #pragma once
 
-constexpr int FDM_THREADS = 256;          // one CTA per cube
+constexpr int FDM_THREADS = 256;          // block of the stand-alone kernel (the solve works for any
+                                          // multiple of 32 up to 1024: the walk kernel's block)
 constexpr int FDM_MAX_OUTER = 12;
 constexpr int FDM_MAX_INNER = 3000;
 constexpr double FDM_TOL = 1e-12;         // outer stop, FP64 residual relative to ||e_c||_2
 constexpr double FDM_INNER_TOL2 = 1e-10;  // inner stop, squared FP32 residual reduction
 
-// dynamic shared memory: [sig64 256][sig32 256][red 32 doubles][lat N^3 (16-aligned)][p N^3][z N^3][d N^3]
+// dynamic shared memory: [sig64 256][sig32 256][red 64 doubles][lat N^3 (16-aligned)][p N^3][z N^3][d N^3]
 __host__ __device__ inline size_t fdm_lat_bytes(int N) { return ((size_t)N * N * N + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t fdm_smem_bytes(int N)
 {
-    return 256 * sizeof(double) + 256 * sizeof(float) + 32 * sizeof(double) + fdm_lat_bytes(N) +
+    return 256 * sizeof(double) + 256 * sizeof(float) + 64 * sizeof(double) + fdm_lat_bytes(N) +
            3 * sizeof(float) * (size_t)N * N * N;
 }
 // global scratch per CTA: y (FP64)
@@ -56,7 +57,7 @@ __device__ __forceinline__ FdmSmem fdm_smem(unsigned char *base, int N)
     S.sig64 = reinterpret_cast<double *>(base);
     S.sig32 = reinterpret_cast<float *>(base + 256 * sizeof(double));
     S.red = reinterpret_cast<double *>(base + 256 * sizeof(double) + 256 * sizeof(float));
-    S.lat = base + 256 * sizeof(double) + 256 * sizeof(float) + 32 * sizeof(double);
+    S.lat = base + 256 * sizeof(double) + 256 * sizeof(float) + 64 * sizeof(double);
     S.p = reinterpret_cast<float *>(S.lat + fdm_lat_bytes(N));
     S.z = S.p + (size_t)N * N * N;
     S.d = S.z + (size_t)N * N * N;
@@ -89,10 +90,11 @@ __device__ __forceinline__ void fdm_couplings(const FdmSmem &S, const double *__
     }
 }
 
-// Nodes of this thread: v = tid + 256 t with coordinates (i, j, k) kept by carries
+// Nodes of this thread: v = tid + nt t (nt = the block size) with coordinates
+// (i, j, k) kept by carries
 struct FdmGrid {
-    int N, NN, n3;
-    int di, dj, dk;    // 256 written in base N
+    int N, NN, n3, nt;
+    int di, dj, dk;    // nt written in base N
 };
 
 __device__ __forceinline__ FdmGrid fdm_grid(int N)
@@ -101,9 +103,10 @@ __device__ __forceinline__ FdmGrid fdm_grid(int N)
     G.N = N;
     G.NN = N * N;
     G.n3 = N * N * N;
-    G.dk = FDM_THREADS % N;
-    G.dj = (FDM_THREADS / N) % N;
-    G.di = FDM_THREADS / G.NN;
+    G.nt = (int)blockDim.x;
+    G.dk = G.nt % N;
+    G.dj = (G.nt / N) % N;
+    G.di = G.nt / G.NN;
     return G;
 }
 
@@ -111,7 +114,7 @@ template <class F> __device__ __forceinline__ void fdm_nodes(const FdmGrid &G, F
 {
     int v = threadIdx.x;
     int i = v / G.NN, j = (v / G.N) % G.N, k = v % G.N;
-    for (; v < G.n3; v += FDM_THREADS) {
+    for (; v < G.n3; v += G.nt) {
         f(v, i, j, k);
         k += G.dk;
         if (k >= G.N) { k -= G.N; j++; }
@@ -180,7 +183,7 @@ __device__ __forceinline__ float fdm_apply_diag(const FdmGrid &G, const uint8_t 
     return acc;
 }
 
-// CTA-wide sums in a fixed order (warp butterflies, then the 8 warp totals in
+// CTA-wide sums in a fixed order (warp butterflies, then the warp totals in
 // order): every thread gets the same value
 __device__ __forceinline__ double fdm_warp_sum(double a)
 {
@@ -197,13 +200,14 @@ __device__ __forceinline__ double2 fdm_block_sum2(double a, double b, double *re
     __syncthreads();   // earlier readers of red are done
     if (lane == 0) {
         red[warp] = a;
-        red[16 + warp] = b;
+        red[32 + warp] = b;
     }
     __syncthreads();
     double sa = 0.0, sb = 0.0;
-    for (int w = 0; w < FDM_THREADS / 32; w++) {
+    const int nw = (int)(blockDim.x >> 5);
+    for (int w = 0; w < nw; w++) {
         sa += red[w];
-        sb += red[16 + w];
+        sb += red[32 + w];
     }
     return make_double2(sa, sb);
 }
@@ -305,7 +309,8 @@ __device__ FRW_OUTLINE FdmResult fdm_solve(int N, const FdmSmem &S, const FdmScr
     }
     // panel values eps_v y_v, prefix sums over contiguous chunks of panels
     const int P = 6 * N * N;
-    const int chunk = (P + FDM_THREADS - 1) / FDM_THREADS;
+    const int nt = (int)blockDim.x;
+    const int chunk = (P + nt - 1) / nt;
     const int m0 = min(tid * chunk, P), m1 = min(m0 + chunk, P);
     double loc = 0.0;
     for (int m = m0; m < m1; m++) {
@@ -328,7 +333,7 @@ __device__ FRW_OUTLINE FdmResult fdm_solve(int N, const FdmSmem &S, const FdmScr
     if (tid == 0) *sel = (uint32_t)(P - 1);
     __syncthreads();
     double off = 0.0, total = 0.0;
-    for (int w = 0; w < FDM_THREADS / 32; w++) {
+    for (int w = 0; w < nt / 32; w++) {
         if (w < warp) off += S.red[w];
         total += S.red[w];
     }

@@ -261,7 +261,8 @@ struct EngineView {
     const uint32_t *W;     // [16][16]
     const double *eps;     // [16]
     FillConsts fc;
-    double *fill_scratch;  // per walk-kernel CTA: 6N^2 doubles of table-fill scratch
+    double *fill_scratch;  // per walk-kernel CTA: fill_stride doubles of table-fill scratch
+    size_t fill_stride;
     uint32_t *status;      // STAT_WORDS
     uint32_t *ctrl;        // CTRL_WORDS (host -> device)
     unsigned long long *cycles;   // [5] CTA cycles: geometry busy, fill, reduce, MicroWalk busy, total
@@ -289,6 +290,7 @@ struct LaunchShape {
 cudaError_t prepare_walk(const EngineView &E);
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st);
 size_t walk_smem_bytes(int N, int max_nc, int transition);
+size_t walk_fill_scratch_doubles(int N);
 int walk_pool_slots();
 int walk_ctas_per_sm(int N, int fp32, int mwe, int transition);
 // FD transitions (Algorithm 2) of stand-alone cubes, one CTA per cube at a time;

@@ -1639,14 +1639,29 @@ __device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 //             the Philox stream continues unchanged) and they resume next epoch.
 // The kernel exits when its pool is empty, no walk can be issued and every stop
 // rule is decided; an idle wait is bounded by E.idle_timeout_s.
-constexpr int WALK_THREADS = 256;
+// Block of the walk kernel and CTAs per SM it is compiled for: 2 x 448 threads
+// (28 warps per SM at up to 72 registers) measured faster than 3 x 256, 3 x 320,
+// 2 x 384, 2 x 512, 4 x 256, 6 x 128 and 1 x 768 on the interconnect workload
+#ifndef FRW_WALK_THREADS
+#define FRW_WALK_THREADS 448
+#endif
+#ifndef FRW_POOL_MAX
+#define FRW_POOL_MAX 4096
+#endif
+#ifndef FRW_FILL_GLOBAL
+#define FRW_FILL_GLOBAL 0
+#endif
+constexpr int WALK_THREADS = FRW_WALK_THREADS;
+// 1: the walk kernel's table fill works in global scratch (per CTA) instead of
+// shared memory, so that the shared region holds only the MicroWalk masks
+constexpr bool FILL_GLOBAL = FRW_FILL_GLOBAL != 0;
 #ifndef FRW_WALK_CTAS
-#define FRW_WALK_CTAS 3
+#define FRW_WALK_CTAS 2
 #endif
 constexpr int WALK_CTAS = FRW_WALK_CTAS;   // CTAs per SM the walk kernel is compiled for
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int MW_WARPS = WALK_WARPS;
-constexpr int POOL_MAX = 4096;
+constexpr int POOL_MAX = FRW_POOL_MAX;
 constexpr int FILL_MAX = 128;
 constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // suspension only if this much geometry work is waiting
 
@@ -1661,7 +1676,7 @@ __device__ __forceinline__ long long clock_after(const uint32_t *anchor)
 }
 
 #include "fdm_transition.cuh"
-constexpr uint32_t FDM_CLAIM_CAP = 32;   // FRW-FDM: walk ids a CTA claims per epoch
+constexpr uint32_t FDM_CLAIM_CAP = 8;    // FRW-FDM: walk ids a CTA claims per epoch
 
 struct WalkShared {
     uint32_t W[256];                 // quantised weights of Eq. 6, [centre][neighbour material]
@@ -1678,10 +1693,12 @@ struct WalkShared {
     uint16_t glist[POOL_MAX];
 };
 
+// table-fill work space: ek[MAXN], yh[(N/2)^2 N], Z[MAXN^2], red[threads + 1] for
+// the larger of the fill kernel's 256 threads and the walk kernel's block
 size_t fill_smem_bytes(int N)
 {
     const int H = N / 2;
-    return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + 256 + 1);
+    return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + std::max(256, WALK_THREADS) + 1);
 }
 
 size_t mw_smem_bytes(int N, int warps)
@@ -1694,9 +1711,16 @@ size_t mw_smem_bytes(int N, int warps)
 size_t walk_scratch_bytes(int N, int max_nc)
 {
     const size_t masks = sizeof(uint16_t) * (size_t)MW_WARPS * 3 * (N + 2) * 32;
-    const size_t fill = fill_smem_bytes(N);
+    const size_t fill = FILL_GLOBAL ? 0 : fill_smem_bytes(N);
     const size_t red = sizeof(unsigned long long) * acc_stride_for(max_nc);
     return std::max(masks, std::max(fill, red));
+}
+
+// per walk-kernel CTA: doubles of global table-fill scratch (the 6N^2 panel
+// values, plus the fill's work arrays when they do not live in shared memory)
+size_t walk_fill_scratch_doubles(int N)
+{
+    return 6 * (size_t)N * N + (FILL_GLOBAL ? (fill_smem_bytes(N) + sizeof(double) - 1) / sizeof(double) : 0);
 }
 
 size_t walk_smem_bytes(int N, int max_nc, int transition)
@@ -1720,7 +1744,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
     const uint32_t P = E.pool;
     const uint32_t base = blockIdx.x * P;
     unsigned char *dsm = dsm_all;
-    double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.tc.P;
+    double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.fill_stride;
     for (int i = tid; i < 256; i += WALK_THREADS) sh.W[i] = E.W[i];
     for (uint32_t o = tid; o < P; o += WALK_THREADS) {
         const uint32_t s = base + o;
@@ -1759,7 +1783,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
         {
             // ---------------- geometry ----------------
             const bool iss = sh.issuable != 0;
-            for (uint32_t o = tid; o < P; o += WALK_THREADS) {   // P is a multiple of WALK_THREADS
+            for (uint32_t o = tid; o < P; o += WALK_THREADS) {   // P is a multiple of 32: whole warps
                 const uint32_t s = base + o;
                 uint32_t st = E.s.state[s];
                 if (st == ST_IDLE && iss) {
@@ -1988,7 +2012,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
             F.values = nullptr;
             F.err = &E.status[STAT_ERR];
             F.V = fill_v;
-            fill_table(F, N, E.eps, E.fc, reinterpret_cast<double *>(dsm));
+            fill_table(F, N, E.eps, E.fc, FILL_GLOBAL ? fill_v + 6 * N * N : reinterpret_cast<double *>(dsm));
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
@@ -2299,8 +2323,8 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
 }
 
 namespace frw {
-// CTAs of the walk kernel resident per SM at this lattice edge (3 by design at
-// N = 24: at most 85 registers per thread and about 67 KB of shared memory each;
+// CTAs of the walk kernel resident per SM at this lattice edge (2 by design at
+// N = 24: at most 72 registers per thread and about 97 KB of shared memory each;
 // one for the FDM comparator)
 template <typename T, bool MWE, bool FDM> static int walk_occupancy(int smem)
 {

@@ -202,6 +202,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.fc = ctx->fc;
     E.status = ctx->status;
     E.fill_scratch = ctx->fill_scratch;
+    E.fill_stride = walk_fill_scratch_doubles(ctx->opt.N);
     E.ctrl = ctx->ctrl;
     E.cycles = ctx->cycles;
     E.idle_timeout_s = ctx->opt.idle_timeout_ms > 0 ? 1e-3 * ctx->opt.idle_timeout_ms : 10.0;
@@ -359,7 +360,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         (rc = dalloc(ctx, &ctx->status, STAT_WORDS, A)) ||
         (rc = dalloc(ctx, &ctx->d_W, 256, A)) || (rc = dalloc(ctx, &ctx->d_eps, 16, A)) ||
         (rc = dalloc(ctx, &ctx->ctrl, CTRL_WORDS, A)) || (rc = dalloc(ctx, &ctx->cycles, 8, A)) ||
-        (rc = dalloc(ctx, &ctx->fill_scratch, (size_t)ctx->grid * 6 * N * N, A)))
+        (rc = dalloc(ctx, &ctx->fill_scratch, (size_t)ctx->grid * walk_fill_scratch_doubles(N), A)))
         return bail(rc);
     if (opt.transition == FRW_TRANSITION_FDM &&
         (rc = dalloc(ctx, &ctx->fdm_scratch, (size_t)ctx->grid * fdm_cube_scratch_bytes(N), A)))
@@ -1951,10 +1952,14 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
             j.walk_budget = std::min<uint64_t>(j.walk_budget ? j.walk_budget : sample_walks, sample_walks);
         }
         const int pool0 = (int)(ctx->NS / ctx->grid);
+        // candidate pools: 1024 .. 4096 up to the context's own, and the context's own, once each
+        std::vector<int> pools;
+        for (int pool : {1024, 2048, 3072, 4096})
+            if (pool < pool0) pools.push_back(pool);
+        pools.push_back(pool0);
         double best_rate = 0.0;
         for (int rep = 0; rep < 2; rep++) {           // the first pass also warms the table cache
-            for (int pool : {1024, 2048, 3072, 4096, pool0}) {
-                if (pool > pool0 || (pool == pool0 && pool0 % 1024 == 0)) continue;   // pool0 itself: once
+            for (int pool : pools) {
                 // (hops per epoch, suspension lanes, suspension progress guard)
                 static const int cand[][3] = {{4, 8, 64},  {4, 16, 64}, {4, 32, 64},  {4, 32, 32}, {4, 32, 128},
                                               {4, 16, 32}, {8, 8, 64},  {8, 32, 64},  {2, 32, 64}, {4, 4, 64}};

@@ -2,7 +2,7 @@
 
 walk       the persistent walk kernel on the interconnect structure (N = 24, FP32
            geometry, masters 3, 11, 19), budget mode, 2^20 walks per master, with
-           the launch settings the autotuner picks for this workload (2304 slots
+           the launch settings the autotuner picks for this workload (2048 slots
            per CTA, 2 analytical hops per epoch, MicroWalk lanes parked once the
            queue is empty and each has made 64 steps): one warm-up launch (fills
            the analytical-table cache), then the profiled launch.
@@ -22,7 +22,7 @@ from . import workloads as W
 def walk():
     s = W.interconnect(0)
     c = B.Context(0, N=24, precision=B.FRW_FP32_GEOM, seed=0)
-    c.set_tuning(pool_per_cta=2304, hops_per_epoch=2, suspend_lanes=32, suspend_min_steps=64)
+    c.set_tuning(pool_per_cta=2048, hops_per_epoch=2, suspend_lanes=32, suspend_min_steps=64)
     sid = c.load(s)
     jobs = lambda r: [dict(structure_id=sid, master=m, walk_budget=1 << 20, request_id=r + i)
                       for i, m in enumerate(s.masters)]
