@@ -9,6 +9,10 @@ walk       the persistent walk kernel on the interconnect structure (N = 24, FP3
 microwalk  the MicroWalk kernel alone: 2^24 samples from 1024 random N = 16 cubes
            (16384 each, 2-6 blocks, permittivities {2.5, 3.9, 7.0, 25.0}): one
            warm-up launch, then the profiled launch.
+fdm        the FD-transition kernel of the FRW-FDM comparator alone: 1216 random
+           N = 24 cubes (2-6 blocks, permittivities as above), one mixed-precision
+           FD solve and one sampled panel each: one warm-up launch on 8 cubes,
+           then the profiled launch.
 Prints what the launch processed (walks / samples and MicroWalk steps).
 """
 from __future__ import annotations
@@ -49,5 +53,22 @@ def microwalk():
     c.close()
 
 
+def fdm():
+    import numpy as np
+    import torch
+    N, n = 24, 1216
+    cubes = W.random_cubes(n, N=N, seed=5)
+    rec = torch.from_numpy(B.pack_cubes(cubes)).cuda()
+    it = torch.zeros(n, dtype=torch.int32, device="cuda")
+    c = B.Context(0, N=N, slots=1 << 12)
+    B.frw_fdm_cubes(c.ctx, N, 8, rec.data_ptr(), cubes.eps, 0, 0, 0, it.data_ptr())
+    B.frw_fdm_cubes(c.ctx, N, n, rec.data_ptr(), cubes.eps, 0, 0, 0, it.data_ptr())
+    torch.cuda.synchronize()
+    iv = it.cpu().numpy().view(np.uint32)
+    print(f"FD transitions: {n} cubes, {int((iv & 0xFFFFFF).sum())} CG iterations, "
+          f"{int((iv >> 24).sum())} refinement passes")
+    c.close()
+
+
 if __name__ == "__main__":
-    {"walk": walk, "microwalk": microwalk}[sys.argv[1]]()
+    {"walk": walk, "microwalk": microwalk, "fdm": fdm}[sys.argv[1]]()
