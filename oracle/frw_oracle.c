@@ -121,8 +121,10 @@ static double u53(uint32_t a, uint32_t b)
 /* ------------------------------------------------------------------------- */
 typedef struct {
     double dom_lo[3], dom_hi[3];
-    int n_c;
+    int n_c;                     /* conductor boxes */
     const double *c_lo, *c_hi;   /* n_c x 3 */
+    const int32_t *c_id;         /* conductor of each box (NULL: box k is conductor k) */
+    int n_cond;                  /* conductors; the grounded walls are conductor n_cond */
     int n_b;
     const double *b_lo, *b_hi;   /* n_b x 3 */
     const int32_t *b_mat;
@@ -178,15 +180,18 @@ static double linf_to_box(const double p[3], const double *lo, const double *hi)
     return d;
 }
 
-/* Distance to the nearest electrode; *who = conductor index, or n_c for the walls
- * (ties go to the conductor with the lowest index, then to the walls). */
+static int cond_of(const orc_structure *S, int k) { return S->c_id ? S->c_id[k] : k; }
+
+/* Distance to the nearest electrode (a conductor is the union of its boxes);
+ * *who = conductor index, or n_cond for the walls (ties go to the conductor with
+ * the lowest index, then to the walls). */
 static double nearest_electrode(const orc_structure *S, const double p[3], int *who)
 {
     double best = INFINITY;
     int kb = -1;
     for (int k = 0; k < S->n_c; k++) {
         double d = linf_to_box(p, S->c_lo + 3 * k, S->c_hi + 3 * k);
-        if (d < best) { best = d; kb = k; }
+        if (d < best || (d == best && kb >= 0 && cond_of(S, k) < cond_of(S, kb))) { best = d; kb = k; }
     }
     double dw = INFINITY;
     for (int a = 0; a < 3; a++) {
@@ -195,8 +200,8 @@ static double nearest_electrode(const orc_structure *S, const double p[3], int *
         t = S->dom_hi[a] - p[a];
         if (t < dw) dw = t;
     }
-    if (best <= dw) { *who = kb; return best; }
-    *who = S->n_c;
+    if (best <= dw) { *who = cond_of(S, kb); return best; }
+    *who = S->n_cond;
     return dw;
 }
 
@@ -368,13 +373,13 @@ static int in_box(const double p[3], const double *lo, const double *hi)
     return lo[0] <= p[0] && p[0] < hi[0] && lo[1] <= p[1] && p[1] < hi[1] && lo[2] <= p[2] && p[2] < hi[2];
 }
 
-/* conductor absorbing at point p: n_c outside the domain, k inside conductor k,
- * -1 in the dielectric */
+/* conductor absorbing at point p: n_cond outside the domain, k inside a box of
+ * conductor k, -1 in the dielectric */
 static int conductor_at(const orc_structure *S, const double p[3])
 {
-    if (!in_box(p, S->dom_lo, S->dom_hi)) return S->n_c;
+    if (!in_box(p, S->dom_lo, S->dom_hi)) return S->n_cond;
     for (int k = 0; k < S->n_c; k++)
-        if (in_box(p, S->c_lo + 3 * k, S->c_hi + 3 * k)) return k;
+        if (in_box(p, S->c_lo + 3 * k, S->c_hi + 3 * k)) return cond_of(S, k);
     return -1;
 }
 
@@ -393,7 +398,7 @@ static void cube_lattice_e(const orc_structure *S, const cube_t *q, uint8_t *lat
             }
 }
 
-/* conductors and exterior slabs holding a voxel centre of the cube */
+/* conductor boxes and exterior slabs holding a voxel centre of the cube */
 static int mwe_extra(const orc_structure *S, const cube_t *q)
 {
     int N = q->N, n = 0;
@@ -919,10 +924,12 @@ typedef struct {
 /* Gaussian surface of master i (reading R7). */
 static void gauss_setup(const orc_structure *S, int master, double frac, gauss_t *g)
 {
-    const double *lo = S->c_lo + 3 * master, *hi = S->c_hi + 3 * master;
+    int mb = 0;                       /* the master's (single) box */
+    while (mb < S->n_c && cond_of(S, mb) != master) mb++;
+    const double *lo = S->c_lo + 3 * mb, *hi = S->c_hi + 3 * mb;
     double gap = INFINITY;
     for (int k = 0; k < S->n_c; k++) {
-        if (k == master) continue;
+        if (cond_of(S, k) == master) continue;
         const double *l2 = S->c_lo + 3 * k, *h2 = S->c_hi + 3 * k;
         double d = 0.0;
         for (int a = 0; a < 3; a++) {
@@ -1161,7 +1168,7 @@ static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
         } else {
             uint64_t st;
             int done = 0;
-            if (o->mwe > 1 && S->n_c <= 254) {
+            if (o->mwe > 1 && S->n_cond <= 254) {
                 for (int f = o->mwe; f >= 2 && !done; f--) {
                     cube_t qe;
                     cube_setup(&qe, r, q.R * (double)f, N);
@@ -1203,10 +1210,12 @@ static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
  * If sigma_target > 0, after every `batch` walks the relative standard error of
  * C_ii and of the largest |C_ij| (j != i, ground excluded) is checked and the run
  * stops at the first batch boundary where both are <= sigma_target.
- * Outputs: S1, S2 (n_c + 1 each, last = ground), per-walk records (optional),
+ * Conductor k is the union of the boxes with c_id == k (c_id NULL: box k is
+ * conductor k); the master must be a single box (its Gaussian surface, R7).
+ * Outputs: S1, S2 (n_cond + 1 each, last = ground), per-walk records (optional),
  * the number of walks used.  Returns the number of distinct tables built. */
 int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const double *c_lo,
-                const double *c_hi, int n_b, const double *b_lo, const double *b_hi,
+                const double *c_hi, const int32_t *c_id, int n_cond, int n_b, const double *b_lo, const double *b_hi,
                 const int32_t *b_mat, int n_mat, const double *eps, int bg,
                 int N, uint64_t seed, uint64_t request, int hybrid, int first_mode,
                 double gauss_frac, int max_hops, int mwe, int transition, int master, uint64_t walk_begin,
@@ -1218,7 +1227,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
                 uint64_t *stats /* 10: hops, steps, strat, hom, mw, branch 0..2, truncated, mwe */)
 {
     orc_structure S = {{dom_lo[0], dom_lo[1], dom_lo[2]}, {dom_hi[0], dom_hi[1], dom_hi[2]},
-                       n_c, c_lo, c_hi, n_b, b_lo, b_hi, b_mat, n_mat, eps, bg};
+                       n_c, c_lo, c_hi, c_id, c_id ? n_cond : n_c, n_b, b_lo, b_hi, b_mat, n_mat, eps, bg};
     orc_options o = {N, seed, request, hybrid, first_mode, gauss_frac, max_hops, mwe, transition};
     walker_t wk;
     wk.S = &S;
@@ -1237,7 +1246,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
     wk.fe = malloc(sizeof(double) * (size_t)N * N * N);
     wk.fp = malloc(sizeof(double) * 6 * (size_t)N * N);
     wk.fthr = malloc(sizeof(uint32_t) * 6 * (size_t)N * N);
-    for (int k = 0; k <= n_c; k++) { S1[k] = 0.0; S2[k] = 0.0; }
+    for (int k = 0; k <= S.n_cond; k++) { S1[k] = 0.0; S2[k] = 0.0; }
     for (int s = 0; s < 10; s++) stats[s] = 0;
     uint64_t used = 0;
     for (uint64_t w = 0; w < n_walks; w++) {
@@ -1270,7 +1279,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
             if (!(ci != 0.0 && sqrt(vi > 0 ? vi : 0) <= sigma_target * fabs(ci))) ok = 0;
             int jb = -1;
             double cb = 0.0;
-            for (int j = 0; j < n_c; j++) {
+            for (int j = 0; j < S.n_cond; j++) {
                 if (j == master) continue;
                 double cj = fabs(S1[j] / n);
                 if (jb < 0 || cj > cb) { jb = j; cb = cj; }

@@ -73,7 +73,7 @@ def lib():
         L.orc_microwalk_e.restype = i
         L.orc_microwalk_e_many.argtypes = [i, P(u8), P(ctypes.c_int16), P(d), i, u64, u64, u64, u64, u32,
                                            P(ctypes.c_int32), P(ctypes.c_int32), P(u64)]
-        L.orc_frw_run.argtypes = ([P(d), P(d), i, P(d), P(d), i, P(d), P(d), P(ctypes.c_int32), i,
+        L.orc_frw_run.argtypes = ([P(d), P(d), i, P(d), P(d), P(ctypes.c_int32), i, i, P(d), P(d), P(ctypes.c_int32), i,
                                    P(d), i, i, u64, u64, i, i, d, i, i, i, i, u64, u64, d, u64,
                                    P(d), P(d), P(u64), P(d), P(ctypes.c_int32), P(u32), P(u64),
                                    P(ctypes.c_int32), P(u64)])
@@ -237,6 +237,9 @@ def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, 
     instead of running MicroWalk; they are counted in ``stats[4]``."""
     L = lib()
     nc = s.n_cond
+    cid = None if s.cond_id is None else np.ascontiguousarray(s.cond_id, np.int32)
+    if cid is not None and int((cid == master).sum()) != 1:
+        raise ValueError("the master must be a single box (its Gaussian surface)")
     S1 = np.zeros(nc + 1)
     S2 = np.zeros(nc + 1)
     used = np.zeros(1, np.uint64)
@@ -251,8 +254,9 @@ def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, 
         om = kk = hp = st = br = None
         rp = (None,) * 5
     ntab = L.orc_frw_run(
-        _p(s.domain_lo, ctypes.c_double), _p(s.domain_hi, ctypes.c_double), nc,
-        _p(s.cond_lo, ctypes.c_double), _p(s.cond_hi, ctypes.c_double), s.n_blocks,
+        _p(s.domain_lo, ctypes.c_double), _p(s.domain_hi, ctypes.c_double), s.n_boxes,
+        _p(s.cond_lo, ctypes.c_double), _p(s.cond_hi, ctypes.c_double), None if cid is None else _p(cid, ctypes.c_int32), nc,
+        s.n_blocks,
         _p(s.block_lo, ctypes.c_double), _p(s.block_hi, ctypes.c_double),
         _p(s.block_mat, ctypes.c_int32), s.n_mat, _p(s.eps, ctypes.c_double), int(s.background),
         int(N), int(seed), int(request), int(hybrid), int(first_mode), float(gauss_frac),

@@ -29,6 +29,8 @@ __all__ = [
     "Structure",
     "CubeSet",
     "tiny_two_plate",
+    "l_shape_pair",
+    "split_conductor",
     "interconnect",
     "batched_family",
     "serving_pool",
@@ -39,19 +41,22 @@ __all__ = [
 
 @dataclass
 class Structure:
-    """Conductor boxes + background + ordered dielectric blocks (see module doc)."""
+    """Conductor boxes + background + ordered dielectric blocks (see module doc).
+    A conductor is one box, or (``cond_id`` given: the conductor of each box) the
+    union of several boxes; only single-box conductors can be masters."""
 
     name: str
     domain_lo: np.ndarray            # (3,) float64
     domain_hi: np.ndarray            # (3,) float64
-    cond_lo: np.ndarray              # (n_cond, 3) float64
-    cond_hi: np.ndarray              # (n_cond, 3) float64
+    cond_lo: np.ndarray              # (n_boxes, 3) float64
+    cond_hi: np.ndarray              # (n_boxes, 3) float64
     eps: np.ndarray                  # (n_mat,) float64, relative permittivity per material
     background: int                  # material id of the background dielectric
     block_lo: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
     block_hi: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
     block_mat: np.ndarray = field(default_factory=lambda: np.zeros((0,), np.int32))
     masters: tuple = (0,)            # conductors the workload extracts rows for
+    cond_id: np.ndarray | None = None   # (n_boxes,) int32 conductor of each box; None: box k = conductor k
 
     def __post_init__(self):
         self.domain_lo = np.ascontiguousarray(self.domain_lo, np.float64).reshape(3)
@@ -62,10 +67,20 @@ class Structure:
         self.block_lo = np.ascontiguousarray(self.block_lo, np.float64).reshape(-1, 3)
         self.block_hi = np.ascontiguousarray(self.block_hi, np.float64).reshape(-1, 3)
         self.block_mat = np.ascontiguousarray(self.block_mat, np.int32).reshape(-1)
+        if self.cond_id is not None:
+            self.cond_id = np.ascontiguousarray(self.cond_id, np.int32).reshape(-1)
+
+    @property
+    def n_boxes(self) -> int:
+        return int(self.cond_lo.shape[0])
 
     @property
     def n_cond(self) -> int:
-        return int(self.cond_lo.shape[0])
+        return self.n_boxes if self.cond_id is None else int(self.cond_id.max()) + 1
+
+    def boxes_of(self, k: int) -> np.ndarray:
+        """Indices of conductor k's boxes."""
+        return np.array([k]) if self.cond_id is None else np.flatnonzero(self.cond_id == k)
 
     @property
     def n_blocks(self) -> int:
@@ -79,7 +94,7 @@ class Structure:
         """Same geometry with every permittivity multiplied by ``factor``."""
         return Structure(self.name + f"*eps{factor:g}", self.domain_lo, self.domain_hi,
                          self.cond_lo, self.cond_hi, self.eps * factor, self.background,
-                         self.block_lo, self.block_hi, self.block_mat, self.masters)
+                         self.block_lo, self.block_hi, self.block_mat, self.masters, self.cond_id)
 
 
 # ---------------------------------------------------------------------------
@@ -98,6 +113,40 @@ def tiny_two_plate() -> Structure:
         block_lo=[[1.8, 1.8, 1.8]], block_hi=[[2.2, 2.2, 2.2]], block_mat=[1],
         masters=(0, 1),
     )
+
+
+def l_shape_pair() -> Structure:
+    """The two-plate structure with the second conductor an L: its plate plus a
+    0.2 um leg along +y at the high-x end, touching the plate (two boxes, one
+    conductor).  Every face lies on the 0.05 um grid."""
+    s = tiny_two_plate()
+    return Structure(
+        name="l_shape_pair", domain_lo=s.domain_lo, domain_hi=s.domain_hi,
+        cond_lo=[[1.5, 1.65, 1.5], [1.5, 2.15, 1.5], [2.3, 2.35, 1.5]],
+        cond_hi=[[2.5, 1.85, 2.5], [2.5, 2.35, 2.5], [2.5, 2.95, 2.5]],
+        eps=s.eps, background=s.background, block_lo=s.block_lo, block_hi=s.block_hi, block_mat=s.block_mat,
+        masters=(0,), cond_id=[0, 1, 1],
+    )
+
+
+def split_conductor(s: Structure, k: int, pieces: int, axis: int = 0) -> Structure:
+    """The same structure with single-box conductor k cut into `pieces` touching
+    boxes along `axis` (the same conductor, the same union)."""
+    (kb,) = s.boxes_of(k)
+    ids = np.arange(s.n_boxes) if s.cond_id is None else s.cond_id
+    lo, hi = s.cond_lo[kb], s.cond_hi[kb]
+    cuts = np.linspace(lo[axis], hi[axis], pieces + 1)
+    blo, bhi, cid = [], [], []
+    for b in range(s.n_boxes):
+        if b != kb:
+            blo.append(s.cond_lo[b]); bhi.append(s.cond_hi[b]); cid.append(int(ids[b]))
+            continue
+        for p in range(pieces):
+            l, h = lo.copy(), hi.copy()
+            l[axis], h[axis] = cuts[p], cuts[p + 1]
+            blo.append(l); bhi.append(h); cid.append(k)
+    return Structure(s.name + f"+split{k}x{pieces}", s.domain_lo, s.domain_hi, np.array(blo), np.array(bhi),
+                     s.eps, s.background, s.block_lo, s.block_hi, s.block_mat, s.masters, np.array(cid))
 
 
 # ---------------------------------------------------------------------------

@@ -53,8 +53,9 @@ def capacitance_row(s, master: int, h: float, rtol: float = 1e-11, energy: bool 
     for b in range(s.n_blocks):                     # later blocks win
         eps[inside(s.block_lo[b], s.block_hi[b])] = s.eps[s.block_mat[b]]
     cond = np.full(P[0].shape, -1)
-    for k in range(s.n_cond):
-        cond[inside(s.cond_lo[k], s.cond_hi[k])] = k
+    cid = np.arange(s.n_boxes) if s.cond_id is None else s.cond_id
+    for b in range(s.n_boxes):                  # a conductor is the union of its boxes
+        cond[inside(s.cond_lo[b], s.cond_hi[b])] = cid[b]
     free = cond < 0
     idx = np.full(P[0].shape, -1)
     idx[free] = np.arange(int(free.sum()))
