@@ -168,6 +168,21 @@ int frw_set_stream(frw_ctx *ctx, void *cuda_stream);
 int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *conductors,
                        int32_t n_cond, const double *eps_r, int32_t n_mat, int32_t background_mat,
                        const frw_block *blocks, int32_t n_blocks, int32_t *structure_id);
+/* A structure whose conductors are unions of boxes (Sec. "next" of this library:
+ * the paper's conductors are single boxes).  Box i (host array boxes[n_boxes])
+ * belongs to conductor box_conductor[i], 0 <= id < n_cond, and every conductor has
+ * at least one box.  Boxes of one conductor may touch or overlap; boxes of
+ * different conductors must be apart (positive L-infinity gap); every box lies
+ * strictly inside the domain.  The distance to a conductor is the smallest over
+ * its boxes; a walk that reaches any box is absorbed by its conductor.  Only
+ * conductors of exactly one box can be masters (extraction of another returns
+ * FRW_EINVAL: the Gaussian surface of Algorithm 1 is the master's box grown by a
+ * margin), and the full matrix needs every conductor to be one.  At most 65535
+ * boxes.  Otherwise as frw_load_structure. */
+int frw_load_structure_boxes(frw_ctx *ctx, const frw_box *domain, const frw_box *boxes,
+                             const int32_t *box_conductor, int32_t n_boxes, int32_t n_cond,
+                             const double *eps_r, int32_t n_mat, int32_t background_mat,
+                             const frw_block *blocks, int32_t n_blocks, int32_t *structure_id);
 int frw_unload_structure(frw_ctx *ctx, int32_t structure_id);
 
 /* Capacitance row of `master` (Algorithm 1 output).  C_row and stderr_row are host

@@ -27,7 +27,7 @@ EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream",
            "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
            "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
            "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums", "frw_extract_matrix",
-           "frw_cancel", "frw_get_serve_info", "frw_fdm_cubes")
+           "frw_cancel", "frw_get_serve_info", "frw_fdm_cubes", "frw_load_structure_boxes")
 
 
 class frw_box(ctypes.Structure):
@@ -113,6 +113,8 @@ def lib():
     L.frw_set_stream.argtypes = [c_void_p, c_void_p]
     L.frw_load_structure.argtypes = [c_void_p, P(frw_box), P(frw_box), c_int32, P(c_double), c_int32, c_int32,
                                      P(frw_block), c_int32, P(c_int32)]
+    L.frw_load_structure_boxes.argtypes = [c_void_p, P(frw_box), P(frw_box), P(c_int32), c_int32, c_int32,
+                                           P(c_double), c_int32, c_int32, P(frw_block), c_int32, P(c_int32)]
     L.frw_unload_structure.argtypes = [c_void_p, c_int32]
     L.frw_extract.argtypes = [c_void_p, c_int32, c_int32, P(frw_extract_params), P(c_double), P(c_double),
                               P(frw_stats)]
@@ -198,10 +200,11 @@ def frw_set_stream(ctx, stream_handle: int | None) -> None:
 
 
 def frw_load_structure(ctx, s) -> int:
-    """Load a :class:`workloads.Structure` (host arrays are copied)."""
+    """Load a :class:`workloads.Structure` (host arrays are copied); structures
+    with multi-box conductors go through frw_load_structure_boxes."""
     dom = frw_box((c_double * 3)(*s.domain_lo), (c_double * 3)(*s.domain_hi))
-    cond = (frw_box * s.n_cond)()
-    for k in range(s.n_cond):
+    cond = (frw_box * s.n_boxes)()
+    for k in range(s.n_boxes):
         cond[k].lo = (c_double * 3)(*s.cond_lo[k])
         cond[k].hi = (c_double * 3)(*s.cond_hi[k])
     blk = (frw_block * max(1, s.n_blocks))()
@@ -211,8 +214,14 @@ def frw_load_structure(ctx, s) -> int:
         blk[b].mat = int(s.block_mat[b])
     eps = np.ascontiguousarray(s.eps, np.float64)
     sid = c_int32(-1)
-    rc = lib().frw_load_structure(ctx, ctypes.byref(dom), cond, s.n_cond, _ptr(eps, c_double), len(eps),
-                                  int(s.background), blk, s.n_blocks, ctypes.byref(sid))
+    if s.cond_id is None:
+        rc = lib().frw_load_structure(ctx, ctypes.byref(dom), cond, s.n_cond, _ptr(eps, c_double), len(eps),
+                                      int(s.background), blk, s.n_blocks, ctypes.byref(sid))
+    else:
+        cid = np.ascontiguousarray(s.cond_id, np.int32)
+        rc = lib().frw_load_structure_boxes(ctx, ctypes.byref(dom), cond, _ptr(cid, c_int32), s.n_boxes, s.n_cond,
+                                            _ptr(eps, c_double), len(eps), int(s.background), blk, s.n_blocks,
+                                            ctypes.byref(sid))
     _check(ctx, rc)
     return sid.value
 

@@ -44,8 +44,8 @@ constexpr double ACC_S2_SCALE = 1099511627776.0;          // 2^40
 // One loaded structure.  Coordinates SoA: x[a * n + i].  Material ids are the
 // context's global ids.
 struct DevStructure {
-    int n_c, n_b, bg;
-    int pad;
+    int n_c, n_b, bg;      // conductor boxes, dielectric blocks, background material
+    int n_cond;            // conductors (a conductor is the union of its boxes); the walls are n_cond
     double dom_lo[3], dom_hi[3];
     float dom_lo_f[3], dom_hi_f[3];
     double tau;            // absorption distance, FP64 mode
@@ -56,6 +56,7 @@ struct DevStructure {
     const double *b_lo, *b_hi;
     const float *b_lo_f, *b_hi_f;
     const uint8_t *b_mat;
+    const int32_t *box_cond;   // conductor of each box (boxes sorted by conductor)
     // index built at load time:
     //  - uniform grid; each cell lists (ascending) every conductor that can be the
     //    nearest electrode of some point of the cell (exact nearest query);
@@ -82,7 +83,8 @@ struct DevStructure {
 // (read through L1, the same line for every thread of a structure) instead of
 // each holding its own.
 template <typename T> struct SView {
-    int n_c, n_b, bg;
+    int n_c, n_b, bg, n_cond;   // boxes, blocks, background, conductors
+    const int32_t *bcond;       // conductor of each box
     T dlo[3], dhi[3];
     T tau, margin;
     const T *clo, *chi, *blo, *bhi;
@@ -98,7 +100,7 @@ template <typename T> __host__ __device__ inline SView<T> sview(const DevStructu
 template <> __host__ __device__ inline SView<double> sview<double>(const DevStructure &S)
 {
     SView<double> v;
-    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
+    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg; v.n_cond = S.n_cond; v.bcond = S.box_cond;
     for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo[a]; v.dhi[a] = S.dom_hi[a]; }
     v.tau = S.tau; v.margin = 0.0;
     v.clo = S.c_lo; v.chi = S.c_hi; v.blo = S.b_lo; v.bhi = S.b_hi; v.bmat = S.b_mat;
@@ -113,7 +115,7 @@ template <> __host__ __device__ inline SView<double> sview<double>(const DevStru
 template <> __host__ __device__ inline SView<float> sview<float>(const DevStructure &S)
 {
     SView<float> v;
-    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg;
+    v.n_c = S.n_c; v.n_b = S.n_b; v.bg = S.bg; v.n_cond = S.n_cond; v.bcond = S.box_cond;
     for (int a = 0; a < 3; a++) { v.dlo[a] = S.dom_lo_f[a]; v.dhi[a] = S.dom_hi_f[a]; }
     v.tau = S.tau_f; v.margin = S.margin_f;
     v.clo = S.c_lo_f; v.chi = S.c_hi_f; v.blo = S.b_lo_f; v.bhi = S.b_hi_f; v.bmat = S.b_mat;

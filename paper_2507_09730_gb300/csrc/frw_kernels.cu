@@ -104,9 +104,10 @@ template <typename T> __device__ __forceinline__ int cell_of(T x, T org, T inv, 
 }
 
 // L-infinity distance to the nearest electrode (conductor box or grounded wall);
-// who = conductor index (lowest index on ties) or n_c for the walls.  The grid
-// cell of p lists, in ascending order, every conductor that can be nearest (or
-// tie) anywhere in the cell, so the result equals the scan over all conductors.
+// who = conductor of the nearest box (lowest index on ties: boxes are sorted by
+// conductor) or n_cond for the walls.  The grid cell of p lists, in ascending
+// order, every box that can be nearest (or tie) anywhere in the cell, so the
+// result equals the scan over all boxes.
 template <typename T>
 __device__ FRW_OUTLINE T nearest_electrode(const SView<T> &S, const T p[3], int &who)
 {
@@ -139,8 +140,8 @@ __device__ FRW_OUTLINE T nearest_electrode(const SView<T> &S, const T p[3], int 
         t = A::sub(S.dhi[a], p[a]);
         if (t < dw) dw = t;
     }
-    if (best <= dw) { who = kb; return best; }
-    who = n;
+    if (best <= dw) { who = __ldg(&S.bcond[kb]); return best; }
+    who = S.n_cond;
     return dw;
 }
 
@@ -282,8 +283,9 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
 // blocks as classify_cube lists them, then every conductor and every exterior
 // slab of the domain (centres with x < lo or x >= hi on one axis) that holds a
 // voxel centre, listed after the blocks so that they win, as objects of material
-// BOUNDARY (alpha = 1) with their conductor id (n_c: the walls) in the top byte of
-// rng.y.  False when the dielectric list overflows or more than KMAX objects.
+// BOUNDARY (alpha = 1) with their conductor id (n_cond: the walls) in the top byte
+// of rng.y (one object per conductor box).  False when the dielectric list
+// overflows or more than KMAX objects.
 template <typename T>
 __device__ FRW_OUTLINE bool classify_cube_e(const SView<T> &S, const T c[3], T R, int N, CubeInfo &q)
 {
@@ -323,7 +325,8 @@ __device__ FRW_OUTLINE bool classify_cube_e(const SView<T> &S, const T c[3], T R
         if (count >= KMAX) return false;
         q.rng[count++] = make_uint2((uint32_t)r0[0] | ((uint32_t)r1[0] << 8) | ((uint32_t)r0[1] << 16) |
                                         ((uint32_t)r1[1] << 24),
-                                    (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | cmat | ((uint32_t)k << 24));
+                                    (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | cmat |
+                                        ((uint32_t)__ldg(&S.bcond[k]) << 24));
     }
     for (int a = 0; a < 3; a++) {
         const int i1 = first_ge(base[a], h, invh, N, S.dlo[a]);   // centres below the domain: [0, i1)
@@ -337,7 +340,8 @@ __device__ FRW_OUTLINE bool classify_cube_e(const SView<T> &S, const T c[3], T R
             r1[a] = hi_a;
             q.rng[count++] = make_uint2((uint32_t)r0[0] | ((uint32_t)r1[0] << 8) | ((uint32_t)r0[1] << 16) |
                                             ((uint32_t)r1[1] << 24),
-                                        (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | cmat | ((uint32_t)n << 24));
+                                        (uint32_t)r0[2] | ((uint32_t)r1[2] << 8) | cmat |
+                                            ((uint32_t)S.n_cond << 24));
         }
     }
     q.K = count;
@@ -903,7 +907,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
   }
     // MicroWalk-E: expand the cube f-fold (f = mwe .. 2, the first that lists at
     // most KMAX objects) so that it may reach conductors
-    if (MWE && S.n_c <= 254) {
+    if (MWE && S.n_cond <= 254) {
         CubeInfo qe;
         for (int f = E.mwe; f >= 2; f--) {
             const T Re = A::mul(R, T(f));

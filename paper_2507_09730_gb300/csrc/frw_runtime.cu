@@ -26,9 +26,12 @@ using namespace frw;
 namespace {
 
 struct HostStructure {
-    int n_c = 0, n_b = 0;
+    int n_c = 0, n_b = 0;             // conductors, dielectric blocks
+    int n_box = 0;                    // conductor boxes (sorted by conductor)
     int mat_need = 0;                 // 1 + the largest global material id it uses
-    std::vector<double> c_lo, c_hi;   // n_c x 3 (AoS, host copy for Gaussian set-up)
+    std::vector<double> c_lo, c_hi;   // n_box x 3 (AoS, host copy for Gaussian set-up)
+    std::vector<int32_t> box_cond;    // conductor of each box
+    std::vector<int32_t> master_box;  // per conductor: its box if it has exactly one, else -1
     double dom_lo[3], dom_hi[3];
     std::vector<void *> dev;          // device allocations of this structure
     DevStructure d;
@@ -535,24 +538,47 @@ static void build_index(const frw_box &dom, const frw_box *cond, int nc, const f
     }
 }
 
-extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *conductors, int32_t n_cond,
-                                  const double *eps_r, int32_t n_mat, int32_t background_mat,
-                                  const frw_block *blocks, int32_t n_blocks, int32_t *structure_id)
+// Load a structure whose conductors are unions of boxes: box i of `in_boxes`
+// belongs to conductor in_cond[i] (in_cond null: box i is conductor i).  The
+// boxes are stored sorted by conductor, so that the nearest-electrode scan's
+// lowest box index on ties is the lowest conductor index.
+static int load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *in_boxes, const int32_t *in_cond,
+                          int32_t n_box, int32_t n_cond, const double *eps_r, int32_t n_mat, int32_t background_mat,
+                          const frw_block *blocks, int32_t n_blocks, int32_t *structure_id)
 {
-    if (!ctx || !domain || !conductors || !eps_r || !structure_id) return FRW_EINVAL;
-    if (n_cond < 1 || n_mat < 1 || n_blocks < 0 || (n_blocks > 0 && !blocks))
-        return fail(ctx, FRW_EINVAL, "need at least one conductor and one material");
+    if (!ctx || !domain || !in_boxes || !eps_r || !structure_id) return FRW_EINVAL;
+    if (n_cond < 1 || n_box < n_cond || n_box > 65535 || n_mat < 1 || n_blocks < 0 || (n_blocks > 0 && !blocks))
+        return fail(ctx, FRW_EINVAL, "need at least one conductor, a box per conductor and one material");
     if (background_mat < 0 || background_mat >= n_mat) return fail(ctx, FRW_EINVAL, "background material out of range");
     if (!box_ok(*domain)) return fail(ctx, FRW_EINVAL, "degenerate domain");
-    for (int k = 0; k < n_cond; k++) {
+    std::vector<int32_t> perm(n_box), bc(n_box), per_cond(n_cond, 0);
+    for (int i = 0; i < n_box; i++) {
+        perm[i] = i;
+        bc[i] = in_cond ? in_cond[i] : i;
+        if (bc[i] < 0 || bc[i] >= n_cond) return fail(ctx, FRW_EINVAL, "box conductor index out of range");
+        per_cond[bc[i]]++;
+    }
+    for (int k = 0; k < n_cond; k++)
+        if (per_cond[k] == 0) return fail(ctx, FRW_EINVAL, "a conductor has no box");
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return bc[a] < bc[b]; });
+    std::vector<frw_box> boxv(n_box);
+    std::vector<int32_t> box_cond(n_box);
+    for (int i = 0; i < n_box; i++) {
+        boxv[i] = in_boxes[perm[i]];
+        box_cond[i] = bc[perm[i]];
+    }
+    const frw_box *conductors = boxv.data();
+    for (int k = 0; k < n_box; k++) {
         if (!box_ok(conductors[k])) return fail(ctx, FRW_EINVAL, "degenerate conductor box");
         for (int a = 0; a < 3; a++)
             if (!(conductors[k].lo[a] > domain->lo[a] && conductors[k].hi[a] < domain->hi[a]))
                 return fail(ctx, FRW_EINVAL, "conductor not strictly inside the domain");
     }
-    for (int k = 0; k < n_cond; k++)
-        for (int l = k + 1; l < n_cond; l++)
-            if (!(box_gap(conductors[k].lo, conductors[k].hi, conductors[l].lo, conductors[l].hi) > 0.0))
+    // boxes of one conductor may touch or overlap; those of different conductors may not
+    for (int k = 0; k < n_box; k++)
+        for (int l = k + 1; l < n_box; l++)
+            if (box_cond[k] != box_cond[l] &&
+                !(box_gap(conductors[k].lo, conductors[k].hi, conductors[l].lo, conductors[l].hi) > 0.0))
                 return fail(ctx, FRW_EINVAL, "conductors touch or overlap");
     for (int b = 0; b < n_blocks; b++) {
         if (!box_ok({{blocks[b].lo[0], blocks[b].lo[1], blocks[b].lo[2]}, {blocks[b].hi[0], blocks[b].hi[1], blocks[b].hi[2]}}))
@@ -577,18 +603,24 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
     HostStructure &H = ctx->structs[sid];
     H = HostStructure();
     H.n_c = n_cond;
+    H.n_box = n_box;
     H.mat_need = mat_need;
     H.n_b = n_blocks;
-    H.c_lo.resize(3 * (size_t)n_cond);
-    H.c_hi.resize(3 * (size_t)n_cond);
-    for (int k = 0; k < n_cond; k++)
+    H.box_cond = box_cond;
+    H.master_box.assign(n_cond, -1);
+    for (int k = 0; k < n_box; k++)
+        if (per_cond[box_cond[k]] == 1) H.master_box[box_cond[k]] = k;
+    H.c_lo.resize(3 * (size_t)n_box);
+    H.c_hi.resize(3 * (size_t)n_box);
+    for (int k = 0; k < n_box; k++)
         for (int a = 0; a < 3; a++) {
             H.c_lo[3 * k + a] = conductors[k].lo[a];
             H.c_hi[3 * k + a] = conductors[k].hi[a];
         }
     DevStructure &D = H.d;
     memset(&D, 0, sizeof(D));
-    D.n_c = n_cond;
+    D.n_c = n_box;
+    D.n_cond = n_cond;
     D.n_b = n_blocks;
     D.bg = map[background_mat];
     double edge = 0.0, maxabs = 0.0;
@@ -605,14 +637,14 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
     D.margin_f = m;
     D.tau_f = std::max((float)(1e-9 * edge), 2.0f * m);
     // SoA device copies
-    std::vector<double> clo(3 * (size_t)n_cond), chi(3 * (size_t)n_cond);
-    std::vector<float> clof(3 * (size_t)n_cond), chif(3 * (size_t)n_cond);
-    for (int k = 0; k < n_cond; k++)
+    std::vector<double> clo(3 * (size_t)n_box), chi(3 * (size_t)n_box);
+    std::vector<float> clof(3 * (size_t)n_box), chif(3 * (size_t)n_box);
+    for (int k = 0; k < n_box; k++)
         for (int a = 0; a < 3; a++) {
-            clo[(size_t)a * n_cond + k] = conductors[k].lo[a];
-            chi[(size_t)a * n_cond + k] = conductors[k].hi[a];
-            clof[(size_t)a * n_cond + k] = (float)conductors[k].lo[a];
-            chif[(size_t)a * n_cond + k] = (float)conductors[k].hi[a];
+            clo[(size_t)a * n_box + k] = conductors[k].lo[a];
+            chi[(size_t)a * n_box + k] = conductors[k].hi[a];
+            clof[(size_t)a * n_box + k] = (float)conductors[k].lo[a];
+            chif[(size_t)a * n_box + k] = (float)conductors[k].hi[a];
         }
     std::vector<double> blo(3 * (size_t)n_blocks), bhi(3 * (size_t)n_blocks);
     std::vector<float> blof(3 * (size_t)n_blocks), bhif(3 * (size_t)n_blocks);
@@ -639,7 +671,7 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
         return FRW_OK;
     };
     IndexHost X;
-    build_index(*domain, conductors, n_cond, blocks, n_blocks, X);
+    build_index(*domain, conductors, n_box, blocks, n_blocks, X);
     for (int a = 0; a < 3; a++) {
         D.gdim[a] = X.gdim[a];
         D.g_org[a] = X.g_org[a];
@@ -659,7 +691,7 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
         (rc = up((float **)&D.c_lo_f, clof)) || (rc = up((float **)&D.c_hi_f, chif)) ||
         (rc = up((double **)&D.b_lo, blo)) || (rc = up((double **)&D.b_hi, bhi)) ||
         (rc = up((float **)&D.b_lo_f, blof)) || (rc = up((float **)&D.b_hi_f, bhif)) ||
-        (rc = up((uint8_t **)&D.b_mat, bm))) {
+        (rc = up((uint8_t **)&D.b_mat, bm)) || (rc = up((int32_t **)&D.box_cond, box_cond))) {
         for (void *p : H.dev) cudaFree(p);
         H.dev.clear();
         return rc;
@@ -673,6 +705,24 @@ extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw
     H.live = true;
     *structure_id = sid;
     return FRW_OK;
+}
+
+extern "C" int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *conductors, int32_t n_cond,
+                                  const double *eps_r, int32_t n_mat, int32_t background_mat,
+                                  const frw_block *blocks, int32_t n_blocks, int32_t *structure_id)
+{
+    return load_structure(ctx, domain, conductors, nullptr, n_cond, n_cond, eps_r, n_mat, background_mat, blocks,
+                          n_blocks, structure_id);
+}
+
+extern "C" int frw_load_structure_boxes(frw_ctx *ctx, const frw_box *domain, const frw_box *boxes,
+                                        const int32_t *box_conductor, int32_t n_boxes, int32_t n_cond,
+                                        const double *eps_r, int32_t n_mat, int32_t background_mat,
+                                        const frw_block *blocks, int32_t n_blocks, int32_t *structure_id)
+{
+    if (!box_conductor) return FRW_EINVAL;
+    return load_structure(ctx, domain, boxes, box_conductor, n_boxes, n_cond, eps_r, n_mat, background_mat, blocks,
+                          n_blocks, structure_id);
 }
 
 extern "C" int frw_unload_structure(frw_ctx *ctx, int32_t sid)
@@ -692,10 +742,11 @@ extern "C" int frw_unload_structure(frw_ctx *ctx, int32_t sid)
 // L-infinity gap to another conductor or a wall; point uniform by area).
 static void gauss_setup(const HostStructure &H, int master, double frac, DevJob &J)
 {
-    const double *lo = &H.c_lo[3 * (size_t)master], *hi = &H.c_hi[3 * (size_t)master];
+    const int mb = H.master_box[master];   // single box (checked when the job was accepted)
+    const double *lo = &H.c_lo[3 * (size_t)mb], *hi = &H.c_hi[3 * (size_t)mb];
     double gap = INFINITY;
-    for (int k = 0; k < H.n_c; k++) {
-        if (k == master) continue;
+    for (int k = 0; k < H.n_box; k++) {
+        if (H.box_cond[k] == master) continue;
         const double d = box_gap(lo, hi, &H.c_lo[3 * (size_t)k], &H.c_hi[3 * (size_t)k]);
         if (d < gap) gap = d;
     }
@@ -1117,6 +1168,8 @@ static int check_job(frw_ctx *ctx, const frw_job &j)
     if (j.structure_id < 0 || j.structure_id >= (int)ctx->structs.size() || !ctx->structs[j.structure_id].live)
         return fail(ctx, FRW_ENOTFOUND, "unknown structure id");
     if (j.master < 0 || j.master >= ctx->structs[j.structure_id].n_c) return fail(ctx, FRW_EINVAL, "master out of range");
+    if (ctx->structs[j.structure_id].master_box[j.master] < 0)
+        return fail(ctx, FRW_EINVAL, "the master has several boxes (its Gaussian surface is defined for one box)");
     if (!(j.sigma_target >= 0.0)) return fail(ctx, FRW_EINVAL, "negative sigma target");
     return FRW_OK;
 }
