@@ -488,34 +488,62 @@ static void build_index(const frw_box &dom, const frw_box *cond, int nc, const f
     const size_t cells = (size_t)X.gdim[0] * X.gdim[1] * X.gdim[2];
     X.g_off.assign(cells + 1, 0);
     X.g_ids.clear();
-    std::vector<double> dmin(nc);
-    for (int i = 0; i < X.gdim[0]; i++)
-        for (int j = 0; j < X.gdim[1]; j++)
-            for (int k = 0; k < X.gdim[2]; k++) {
-                const int ii[3] = {i, j, k};
-                double lo[3], hi[3];
-                for (int a = 0; a < 3; a++) {
-                    const double w = ext[a] / X.gdim[a];
-                    lo[a] = dom.lo[a] + ii[a] * w - 0.02 * w;
-                    hi[a] = dom.lo[a] + (ii[a] + 1) * w + 0.02 * w;
-                }
-                // upper bound on the nearest-electrode distance over the cell
-                double U = INFINITY;
-                for (int a = 0; a < 3; a++) U = std::min(U, std::min(hi[a] - dom.lo[a], dom.hi[a] - lo[a]));
-                for (int c = 0; c < nc; c++) {
-                    double dmax = 0.0, dm = 0.0;
+    // candidate lists of the x-slabs [i0, i1) of cells (independent), in cell order
+    auto slab = [&](int i0, int i1, std::vector<uint32_t> &count, std::vector<uint16_t> &ids) {
+        std::vector<double> dmin(nc);
+        for (int i = i0; i < i1; i++)
+            for (int j = 0; j < X.gdim[1]; j++)
+                for (int k = 0; k < X.gdim[2]; k++) {
+                    const int ii[3] = {i, j, k};
+                    double lo[3], hi[3];
                     for (int a = 0; a < 3; a++) {
-                        dmax = std::max(dmax, std::max(cond[c].lo[a] - lo[a], hi[a] - cond[c].hi[a]));
-                        dm = std::max(dm, std::max(cond[c].lo[a] - hi[a], lo[a] - cond[c].hi[a]));
+                        const double w = ext[a] / X.gdim[a];
+                        lo[a] = dom.lo[a] + ii[a] * w - 0.02 * w;
+                        hi[a] = dom.lo[a] + (ii[a] + 1) * w + 0.02 * w;
                     }
-                    dmin[c] = dm;
-                    U = std::min(U, dmax);
+                    // upper bound on the nearest-electrode distance over the cell
+                    double U = INFINITY;
+                    for (int a = 0; a < 3; a++) U = std::min(U, std::min(hi[a] - dom.lo[a], dom.hi[a] - lo[a]));
+                    for (int c = 0; c < nc; c++) {
+                        double dmax = 0.0, dm = 0.0;
+                        for (int a = 0; a < 3; a++) {
+                            dmax = std::max(dmax, std::max(cond[c].lo[a] - lo[a], hi[a] - cond[c].hi[a]));
+                            dm = std::max(dm, std::max(cond[c].lo[a] - hi[a], lo[a] - cond[c].hi[a]));
+                        }
+                        dmin[c] = dm;
+                        U = std::min(U, dmax);
+                    }
+                    const double tol = 1e-6 * edge;   // covers FP32 rounding of device distances
+                    uint32_t n = 0;
+                    for (int c = 0; c < nc; c++)
+                        if (dmin[c] <= U + tol) {
+                            ids.push_back((uint16_t)c);
+                            n++;
+                        }
+                    count.push_back(n);
                 }
-                const double tol = 1e-6 * edge;   // covers FP32 rounding of device distances
-                for (int c = 0; c < nc; c++)
-                    if (dmin[c] <= U + tol) X.g_ids.push_back((uint16_t)c);
-                X.g_off[((size_t)i * X.gdim[1] + j) * X.gdim[2] + k + 1] = (uint32_t)X.g_ids.size();
-            }
+    };
+    // the slabs run on the host's cores (the index is the same for any split)
+    const int nth = (int)std::max(1u, std::min(32u, std::min((unsigned)X.gdim[0], std::thread::hardware_concurrency())));
+    std::vector<std::vector<uint32_t>> counts(nth);
+    std::vector<std::vector<uint16_t>> idl(nth);
+    {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; t++) {
+            const int i0 = (int)((int64_t)X.gdim[0] * t / nth), i1 = (int)((int64_t)X.gdim[0] * (t + 1) / nth);
+            th.emplace_back([&, t, i0, i1]() { slab(i0, i1, counts[t], idl[t]); });
+        }
+        for (auto &x : th) x.join();
+    }
+    size_t cell = 0;
+    for (int t = 0; t < nth; t++) {
+        size_t p = 0;
+        for (uint32_t n : counts[t]) {
+            X.g_ids.insert(X.g_ids.end(), idl[t].begin() + p, idl[t].begin() + p + n);
+            p += n;
+            X.g_off[++cell] = (uint32_t)X.g_ids.size();
+        }
+    }
     // slabs
     X.S = 256;
     X.words = std::max(1, (nb + 31) / 32);
