@@ -125,3 +125,32 @@ def test_fdm_option_validation(torch_cuda):
         B.Context(0, N=16, transition=B.FRW_TRANSITION_FDM, mwe_factor=5)
     with pytest.raises(B.FRWError):
         B.Context(0, N=16, transition=2)
+
+
+def test_fdm_cubes_edge_cases(torch_cuda):
+    """N = 2 (every node a centre node) against the oracle; no cubes is a no-op;
+    a context with N above the FD solve's limit refuses FD transitions."""
+    torch = torch_cuda
+    N = 2
+    rec = np.zeros((3, 64), np.int32)
+    rec[1, 1] = 1
+    rec[1, 2:9] = [0, 1, 0, 2, 0, 2, 1]        # one block on the low-x half, material 1
+    rec[2, 0] = 1                              # background material 1
+    eps = np.array([3.9, 25.0])
+    c = B.Context(0, N=N, slots=1 << 12)
+    d = torch.from_numpy(rec).cuda()
+    P = torch.zeros(3 * 6 * N * N, dtype=torch.float64, device="cuda")
+    B.frw_fdm_cubes(c.ctx, N, 3, d.data_ptr(), eps, 0, P.data_ptr())
+    Pg = P.cpu().numpy().reshape(3, 6, N, N)
+    lats = [np.zeros((N, N, N), np.uint8), np.zeros((N, N, N), np.uint8), np.ones((N, N, N), np.uint8)]
+    lats[1][0:1, 0:2, 0:2] = 1
+    for i, lat in enumerate(lats):
+        Po = O.sgf(N, eps[lat])
+        assert np.abs(Pg[i] - Po).max() <= 1e-10, i
+    B.frw_fdm_cubes(c.ctx, N, 0, d.data_ptr(), eps)           # nothing to do
+    c.close()
+    big = B.Context(0, N=26, slots=1 << 12)
+    with pytest.raises(B.FRWError) as e:
+        B.frw_fdm_cubes(big.ctx, 26, 1, d.data_ptr(), eps)
+    assert e.value.code == B.FRW_EINVAL
+    big.close()
