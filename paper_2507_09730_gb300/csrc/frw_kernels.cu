@@ -1193,6 +1193,8 @@ struct FillJob {
     uint32_t *err;
 };
 
+constexpr int FILL_CHUNKS = 256;   // chunks of the table fill's final sums (any block size)
+
 __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__restrict__ eps, const FillConsts &C,
                            double *sm)
 {
@@ -1201,7 +1203,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
     double *ek = sm;                 // N
     double *yh = ek + MAXN;          // M * N
     double *Z = yh + M * N;          // N * N
-    double *red = Z + MAXN * MAXN;   // nt + 1
+    double *red = Z + MAXN * MAXN;   // FILL_CHUNKS + 1
     double *V = F.V;                 // P, global scratch
     const uint32_t kind = F.kind;
     const bool hom = (kind == TAB_SGF_HOM || kind == TAB_FLUX_HOM);
@@ -1311,32 +1313,39 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
         }
         __syncthreads();
     }
-    // totals and thresholds in canonical order (chunked sequential scan)
-    const int chunk = (P + nt - 1) / nt;
-    const int b0 = tid * chunk, b1 = min(P, b0 + chunk);
-    double part = 0.0;
-    for (int n = b0; n < b1; n++) part += flux ? fabs(V[n]) : V[n];
-    red[tid] = part;
+    // totals and thresholds in canonical order: a sequential scan over FILL_CHUNKS
+    // fixed chunks, so that the sums round the same way whatever the block size
+    // (a table filled by the walk kernel equals the fill kernel's bit for bit)
+    const int chunk = (P + FILL_CHUNKS - 1) / FILL_CHUNKS;
+    for (int c = tid; c < FILL_CHUNKS; c += nt) {
+        const int b0 = min(P, c * chunk), b1 = min(P, b0 + chunk);
+        double part = 0.0;
+        for (int n = b0; n < b1; n++) part += flux ? fabs(V[n]) : V[n];
+        red[c] = part;
+    }
     __syncthreads();
     if (tid == 0) {
         double run = 0.0;
-        for (int i = 0; i < nt; i++) {
+        for (int i = 0; i < FILL_CHUNKS; i++) {
             const double v = red[i];
             red[i] = run;
             run += v;
         }
-        red[nt] = run;
+        red[FILL_CHUNKS] = run;
     }
     __syncthreads();
-    const double total = red[nt];
-    double cum = red[tid];
-    for (int n = b0; n < b1; n++) {
-        cum += flux ? fabs(V[n]) : V[n];
-        double tv = floor((cum / total) * 4294967296.0);
-        if (tv > 4294967295.0) tv = 4294967295.0;
-        if (tv < 0.0) tv = 0.0;
-        F.thr[n] = (uint32_t)tv;
-        if (F.values) F.values[n] = V[n];
+    const double total = red[FILL_CHUNKS];
+    for (int c = tid; c < FILL_CHUNKS; c += nt) {
+        const int b0 = min(P, c * chunk), b1 = min(P, b0 + chunk);
+        double cum = red[c];
+        for (int n = b0; n < b1; n++) {
+            cum += flux ? fabs(V[n]) : V[n];
+            double tv = floor((cum / total) * 4294967296.0);
+            if (tv > 4294967295.0) tv = 4294967295.0;
+            if (tv < 0.0) tv = 0.0;
+            F.thr[n] = (uint32_t)tv;
+            if (F.values) F.values[n] = V[n];
+        }
     }
     const int P32 = (P + 31) / 32;
     for (int wd = tid; wd < P32; wd += nt) {
@@ -1650,7 +1659,7 @@ __device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 #define FRW_WALK_THREADS 448
 #endif
 #ifndef FRW_POOL_MAX
-#define FRW_POOL_MAX 4096
+#define FRW_POOL_MAX 2048   // slot lists of 2048 entries: 12 KB less shared memory than 4096, more L1
 #endif
 #ifndef FRW_FILL_GLOBAL
 #define FRW_FILL_GLOBAL 0
@@ -1697,12 +1706,11 @@ struct WalkShared {
     uint16_t glist[POOL_MAX];
 };
 
-// table-fill work space: ek[MAXN], yh[(N/2)^2 N], Z[MAXN^2], red[threads + 1] for
-// the larger of the fill kernel's 256 threads and the walk kernel's block
+// table-fill work space: ek[MAXN], yh[(N/2)^2 N], Z[MAXN^2], red[FILL_CHUNKS + 1]
 size_t fill_smem_bytes(int N)
 {
     const int H = N / 2;
-    return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + std::max(256, WALK_THREADS) + 1);
+    return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + FILL_CHUNKS + 1);
 }
 
 size_t mw_smem_bytes(int N, int warps)
