@@ -2043,7 +2043,7 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
             for (int pool : pools) {
                 // (hops per epoch, suspension lanes, suspension progress guard)
                 static const int cand[][3] = {{4, 8, 64},  {4, 16, 64}, {4, 32, 64},  {4, 32, 32}, {4, 32, 128},
-                                              {4, 16, 32}, {8, 8, 64},  {8, 32, 64},  {2, 32, 64}, {4, 4, 64}};
+                                              {2, 32, 32}, {3, 32, 64}, {8, 32, 64},  {2, 32, 64}, {2, 32, 128}};
                 for (const auto &c : cand) {
                     frw_tuning t = ctx->tune;
                     t.pool_per_cta = pool;

@@ -54,7 +54,7 @@ def test_autotune_changes_speed_only(torch_cuda):
         jobs = _jobs(sids)
         before, _ = c.extract_batch(jobs)
         t = c.autotune(jobs, sample_walks=60000)
-        assert t["pool_per_cta"] % 256 == 0 and 256 <= t["pool_per_cta"] <= 4096 and t["hops_per_epoch"] in (2, 4, 8, 16)
+        assert t["pool_per_cta"] % 256 == 0 and 256 <= t["pool_per_cta"] <= 4096 and 1 <= t["hops_per_epoch"] <= 16
         assert t["walks_per_s"] > 0 and t["mw_steps_per_s"] > 0
         assert c.tuning() == t
         after, _ = c.extract_batch(jobs)
