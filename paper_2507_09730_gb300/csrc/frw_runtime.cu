@@ -2042,8 +2042,8 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
         for (int rep = 0; rep < 2; rep++) {           // the first pass also warms the table cache
             for (int pool : pools) {
                 // (hops per epoch, suspension lanes, suspension progress guard)
-                static const int cand[][3] = {{4, 8, 64},  {4, 16, 64}, {4, 32, 64},  {4, 32, 32}, {4, 32, 128},
-                                              {2, 32, 32}, {3, 32, 64}, {8, 32, 64},  {2, 32, 64}, {2, 32, 128}};
+                static const int cand[][3] = {{2, 32, 256}, {3, 32, 128}, {4, 32, 64},  {4, 32, 32}, {4, 32, 128},
+                                              {2, 32, 32},  {3, 32, 64},  {8, 32, 64},  {2, 32, 64}, {2, 32, 128}};
                 for (const auto &c : cand) {
                     frw_tuning t = ctx->tune;
                     t.pool_per_cta = pool;
