@@ -529,10 +529,17 @@ static void build_index(const frw_box &dom, const frw_box *cond, int nc, const f
     std::vector<std::vector<uint16_t>> idl(nth);
     {
         std::vector<std::thread> th;
-        for (int t = 0; t < nth; t++) {
-            const int i0 = (int)((int64_t)X.gdim[0] * t / nth), i1 = (int)((int64_t)X.gdim[0] * (t + 1) / nth);
-            th.emplace_back([&, t, i0, i1]() { slab(i0, i1, counts[t], idl[t]); });
+        int started = 0;
+        try {
+            for (; started < nth; started++) {
+                const int t = started;
+                const int i0 = (int)((int64_t)X.gdim[0] * t / nth), i1 = (int)((int64_t)X.gdim[0] * (t + 1) / nth);
+                th.emplace_back([&, t, i0, i1]() { slab(i0, i1, counts[t], idl[t]); });
+            }
+        } catch (...) {   // no thread to be had: the remaining slabs on this thread
         }
+        for (int t = started; t < nth; t++)
+            slab((int)((int64_t)X.gdim[0] * t / nth), (int)((int64_t)X.gdim[0] * (t + 1) / nth), counts[t], idl[t]);
         for (auto &x : th) x.join();
     }
     size_t cell = 0;
