@@ -1665,6 +1665,14 @@ __device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 #define FRW_FILL_GLOBAL 0
 #endif
 constexpr int WALK_THREADS = FRW_WALK_THREADS;
+// 1: the walk kernel's MicroWalk loop keeps one copy of the lattice step (the four
+// steps of a Philox block in a loop that is not unrolled): less code competes with
+// the geometry phase's for the instruction cache (+19 % walks/s in budget mode on
+// the interconnect workload; the stand-alone MicroWalk kernel, alone on its SMs,
+// keeps the unrolled form)
+#ifndef FRW_MW_COMPACT
+#define FRW_MW_COMPACT 1
+#endif
 // 1: the walk kernel's table fill works in global scratch (per CTA) instead of
 // shared memory, so that the shared region holds only the MicroWalk masks
 constexpr bool FILL_GLOBAL = FRW_FILL_GLOBAL != 0;
@@ -1966,6 +1974,30 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     active = false;
                 if (active) {
                     const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
+#if FRW_MW_COMPACT
+                    // one copy of the step in the loop body (smaller code next to the geometry phase's)
+                    int k = 0, code = 0, slot = 0;
+#pragma unroll 1
+                    for (; k < 4; k++) {
+                        const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
+                        code = mw_step<1, MWE>(M, Wl, N, x, y, z, L.mm, u, slot);
+                        if (code) break;
+                    }
+                    if (code) {
+                        const uint32_t sl2 = L.tag;
+                        // exit node, or (MicroWalk-E) the conductor reached, flagged by bit 31
+                        E.s.exitnode[sl2] =
+                            code == 2 ? (FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
+                                             ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                                             : 0x80000000u)
+                                      : ((uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16));
+                        E.s.steps[sl2] += t + (uint32_t)k + 1u;
+                        __threadfence_block();      // exit data before the state (read by geometry warps)
+                        E.s.state[sl2] = ST_MWDONE;
+                        active = false;
+                        atomicAdd(&sh.finished, 1u);
+                    }
+#else
                     const uint32_t words[4] = {blk.x, blk.y, blk.z, blk.w};
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
@@ -1988,6 +2020,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                             }
                         }
                     }
+#endif
                     t += 4;
                     if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
                         atomicOr(&E.status[STAT_ERR], ERR_MW_STEPS);
