@@ -195,7 +195,7 @@ def run_reference(a):
 # DRAM bytes (read + write) per walk of the walk kernel, from one ncu capture of
 # this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
 # launch started.  None once the kernel has changed since the capture.
-DRAM_BYTES_PER_WALK = 4609.0
+DRAM_BYTES_PER_WALK = 4701.0
 
 
 def traffic_per_launch(agg, n_launch):
