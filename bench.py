@@ -32,7 +32,11 @@ from paper_2507_09730_gb300 import workloads as W  # noqa: E402
 
 METRIC = "FRW walks/s and MicroWalk transitions/s at 1% 1\u03c3; request p50/p99 latency"
 UNIT = "walks/s"
-INT_OPS_PER_MICRO_STEP = 45   # algorithmic integer ops of one MicroWalk step
+# algorithmic integer ops of one MicroWalk step: a quarter of a Philox4x32-10 block
+# (15: ten rounds of two wide products and two xor-adds, over four words), the
+# seven material queries, six weight reads, five prefix adds, the mul-high and five
+# compares with four adds, and the move with its boundary test
+INT_OPS_PER_MICRO_STEP = 45
 
 
 def parse():
