@@ -200,6 +200,10 @@ def run_reference(a):
 # this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
 # launch started.  None once the kernel has changed since the capture.
 DRAM_BYTES_PER_WALK = 4701.0
+# issue-slot utilisation (smsp__issue_active) and instruction-cache hit rate of the
+# walk kernel in the same capture; None once the kernel has changed since
+ISSUE_ACTIVE_NCU = 0.482
+ICACHE_HIT_NCU = 0.836
 
 
 def traffic_per_launch(agg, n_launch):
@@ -601,7 +605,9 @@ def main():
                                 "geom": agg["geom_ms"] / max(1e-9, agg["kernel_ms"]),
                                 "fill": agg["fill_ms"] / max(1e-9, agg["kernel_ms"]),
                                 "reduce": agg["reduce_ms"] / max(1e-9, agg["kernel_ms"])},
-                "mw_phase": {"achieved": mw_ach, "frac": (mw_ach / alu_peak) if mw_ach else None}}
+                "mw_phase": {"achieved": mw_ach, "frac": (mw_ach / alu_peak) if mw_ach else None},
+                "ncu_capture": {"issue_active": ISSUE_ACTIVE_NCU, "icache_hit": ICACHE_HIT_NCU,
+                                "workload": "3 x 2^20 walks, budget mode, same structure and settings"}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * t_all / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic",
