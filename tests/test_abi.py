@@ -45,3 +45,51 @@ def test_strerror_and_bad_create():
     o = B.frw_default_options(N=7)
     ctx = ctypes.c_void_p()
     assert B.lib().frw_create(ctypes.byref(ctx), 0, ctypes.byref(o)) == B.FRW_EINVAL
+
+
+def _prototypes():
+    """name -> parameter count of every function prototype in include/frw.h"""
+    src = open(os.path.join(ROOT, "include", "frw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(frw_[a-z_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    protos = _prototypes()
+    L = B.lib()
+    assert set(protos) == set(B.EXPORTS)
+    for name, n in protos.items():
+        at = getattr(L, name).argtypes
+        assert at is not None and len(at) == n, (name, n, at)
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof and field offsets of the public structs as gcc lays them out against
+    the ctypes declarations of the binding."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        import pytest
+        pytest.skip("no C compiler")
+    structs = [n for n in ("frw_box", "frw_block", "frw_options", "frw_extract_params", "frw_stats", "frw_job",
+                           "frw_tuning", "frw_serve_info")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "frw.h"', "int main(void) {"]
+    for n in structs:
+        lines.append(f'    printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in getattr(B, n)._fields_:
+            lines.append(f'    printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["    return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for n in structs:
+        cls = getattr(B, n)
+        assert int(got[n]) == ctypes.sizeof(cls), n
+        for f, _ in cls._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(cls, f).offset, (n, f)
