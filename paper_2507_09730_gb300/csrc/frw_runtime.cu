@@ -274,7 +274,7 @@ static int check_status(frw_ctx *ctx, cudaStream_t st = nullptr)
     CK(cudaStreamSynchronize(st));
     const uint32_t e = ctx->h_status[STAT_ERR];
     if (e) {
-        char buf[160];
+        char buf[256];
         snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s%s%s%s%s)", e,
                  (e & ERR_MWQ_OVERFLOW) ? "queue overflow " : "", (e & ERR_CACHE_FULL) ? "table cache full " : "",
                  (e & ERR_FILL) ? "table fill check " : "", (e & ERR_SHRINK) ? "cube shrink limit " : "",
