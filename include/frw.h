@@ -333,11 +333,14 @@ int frw_walk_records(frw_ctx *ctx, int32_t structure_id, int32_t master, uint64_
 /* MicroWalk alone (Algorithm 3) on n_cubes lattice cubes of edge N given as
  * integer voxel ranges; samples_per_cube walks from the centre of each.
  * d_cubes (device): n_cubes records of 64 int32: [0] background material,
- * [1] block count K <= 6, [2 + 7b .. 8 + 7b] block b = (i0, i1, j0, j1, k0, k1, mat)
- * with 0 <= lo < hi <= N; later blocks win.  Material ids index eps_r (host).
- * Sample s of cube c is walk id c * samples_per_cube + s.  Outputs (device):
- * d_exit[walk] = (x+1) | (y+1) << 8 | (z+1) << 16 of the exit node (one coordinate
- * is -1 or N), d_steps[walk] = number of steps.  Either output may be NULL. */
+ * [1] block count 0 <= K <= 8, [2 + 7b .. 8 + 7b] block b = (i0, i1, j0, j1, k0, k1,
+ * mat) with 0 <= lo < hi <= N; later blocks win.  Material ids index eps_r (host)
+ * and must be below n_mat.  Sample s of cube c is walk id c * samples_per_cube + s.
+ * Outputs (device): d_exit[walk] = (x+1) | (y+1) << 8 | (z+1) << 16 of the exit node
+ * (one coordinate is -1 or N), d_steps[walk] = number of steps.  Either output may
+ * be NULL.  The records are checked on the device: a malformed one (K, a range or
+ * a material id out of bounds) makes the call return FRW_EINVAL, its samples are
+ * written as exit 0 and 0 steps, and the other cubes' samples are still valid. */
 int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t *d_cubes,
                         const double *eps_r, int32_t n_mat, uint64_t samples_per_cube,
                         uint64_t request_id, uint32_t *d_exit, uint32_t *d_steps);
@@ -355,14 +358,20 @@ int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, const int32_t 
  * file-scope device array of 2 KB that every GPU loading the library holds until
  * the process exits.
  *   - The first call on a device looks up that array's device address (once per
- *     device); make this first call before any stream capture.
+ *     device) and keeps it for the life of the process; after cudaDeviceReset the
+ *     kept address is stale, so do not use this entry point on a device that has
+ *     been reset in the same process.
  *   - Every call shares the array: it zeroes the counter and error word and writes
  *     the weight table before its launch, so calls in sequence are independent, but
  *     calls that overlap on the GPU (other streams, other host threads) race.
  *   - Limits: 2 <= N <= 32 even, at most 15 materials (n_mat > 15 returns
- *     FRW_ECAPACITY: the weight table has 15 rows), at most 8 blocks per cube record.
- *   - Blocks the calling thread until the launch has finished; FRW_EDEVICE if the
- *     kernel's step cap was hit or a CUDA call failed. */
+ *     FRW_ECAPACITY: the weight table has 15 rows), permittivities positive and
+ *     finite, records as for frw_microwalk_cubes (at most 8 blocks, material ids
+ *     below n_mat; a malformed record returns FRW_EINVAL).
+ *   - Every call copies its error word back and synchronises `cuda_stream`, so it
+ *     blocks the calling thread until the launch has finished and cannot be
+ *     recorded into a CUDA graph.  FRW_EDEVICE if the kernel's step cap was hit or
+ *     a CUDA call failed. */
 int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int32_t *d_cubes, const double *eps_r,
                                 int32_t n_mat, uint64_t seed, uint64_t samples_per_cube, uint64_t request_id,
                                 uint32_t *d_exit, uint32_t *d_steps, void *cuda_stream);

@@ -29,7 +29,14 @@
  *      lo <= x < hi, later blocks win; centre x_i = (c - R) + (i + 0.5) * h with
  *      h = (2 R) / N.
  *   R3 transition cube = largest conductor-free cube (L-infinity distance to the
- *      nearest conductor box or grounded wall).
+ *      nearest conductor box or grounded wall).  A cube that lists more than
+ *      ORC_KMAX = 14 dielectric blocks (after the rules of cube_classify) is
+ *      halved, R -> R / 2, until it lists at most 14.  Any conductor-free cube
+ *      centred at the walk's point is a valid transition domain (Sec. II-A: the
+ *      potential at the centre is the surface integral over any such cube), so
+ *      the estimator stays unbiased; only the walk's path changes.  The limit is
+ *      the lattice encoding of the GPU path (a 4-bit slot per listed block), not
+ *      a rule of the paper.
  *   R4 jump law: alpha of Eq. 6 quantised to W = floor(alpha * 2^24 + 0.5); a step
  *      draws one 32-bit word u and takes the first k with (u * S) >> 32 < prefix_k
  *      (S = sum of the six W, order -x,+x,-y,+y,-z,+z).
@@ -915,6 +922,7 @@ typedef struct {
     int32_t branch;       /* first-cube branch */
     uint32_t n_strat, n_hom, n_mw;
     uint32_t n_mwe;       /* MicroWalk transitions on expanded cubes (R8) */
+    uint32_t n_halved;    /* cube halvings of the R3 overflow rule */
 } walk_rec;
 
 typedef struct {
@@ -1062,6 +1070,7 @@ static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
     while (q.kind == CUBE_OVERFLOW) {
         cube_setup(&q, r, q.R * 0.5, N);
         cube_classify(S, &q);
+        rec->n_halved++;
     }
     table_t *tab = NULL;
     double keff;
@@ -1150,6 +1159,7 @@ static void do_walk(walker_t *wk, uint64_t walk, walk_rec *rec)
         while (q.kind == CUBE_OVERFLOW) {
             cube_setup(&q, r, q.R * 0.5, N);
             cube_classify(S, &q);
+            rec->n_halved++;
         }
         uint32_t hb[4];
         walk_block(wk->key, walk, hop, 0, hb);
@@ -1224,7 +1234,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
                 double *S1, double *S2, uint64_t *n_used,
                 double *rec_omega, int32_t *rec_k, uint32_t *rec_hops, uint64_t *rec_steps,
                 int32_t *rec_branch,
-                uint64_t *stats /* 10: hops, steps, strat, hom, mw, branch 0..2, truncated, mwe */)
+                uint64_t *stats /* 11: hops, steps, strat, hom, mw, branch 0..2, truncated, mwe, halvings */)
 {
     orc_structure S = {{dom_lo[0], dom_lo[1], dom_lo[2]}, {dom_hi[0], dom_hi[1], dom_hi[2]},
                        n_c, c_lo, c_hi, c_id, c_id ? n_cond : n_c, n_b, b_lo, b_hi, b_mat, n_mat, eps, bg};
@@ -1247,7 +1257,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
     wk.fp = malloc(sizeof(double) * 6 * (size_t)N * N);
     wk.fthr = malloc(sizeof(uint32_t) * 6 * (size_t)N * N);
     for (int k = 0; k <= S.n_cond; k++) { S1[k] = 0.0; S2[k] = 0.0; }
-    for (int s = 0; s < 10; s++) stats[s] = 0;
+    for (int s = 0; s < 11; s++) stats[s] = 0;
     uint64_t used = 0;
     for (uint64_t w = 0; w < n_walks; w++) {
         walk_rec rec;
@@ -1269,6 +1279,7 @@ int orc_frw_run(const double *dom_lo, const double *dom_hi, int n_c, const doubl
         stats[3] += rec.n_hom;
         stats[4] += rec.n_mw;
         stats[9] += rec.n_mwe;
+        stats[10] += rec.n_halved;
         if (rec.branch >= 0 && rec.branch <= 2) stats[5 + rec.branch]++;
         used = w + 1;
         if (sigma_target > 0.0 && batch > 0 && used % batch == 0 && used >= 2) {

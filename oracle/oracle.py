@@ -243,7 +243,7 @@ def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, 
     S1 = np.zeros(nc + 1)
     S2 = np.zeros(nc + 1)
     used = np.zeros(1, np.uint64)
-    stats = np.zeros(10, np.uint64)
+    stats = np.zeros(11, np.uint64)
     n = int(n_walks)
     if records:
         om, kk, hp, st, br = (np.zeros(n), np.zeros(n, np.int32), np.zeros(n, np.uint32),

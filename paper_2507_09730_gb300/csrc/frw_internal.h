@@ -25,7 +25,8 @@ enum : uint32_t {
     ERR_MWQ_OVERFLOW = 1u, ERR_CACHE_FULL = 2u, ERR_FILL = 4u, ERR_SHRINK = 8u, ERR_ACC_RANGE = 16u,
     ERR_MW_STEPS = 32u, ERR_IDLE_TIMEOUT = 64u, ERR_REDUCE_QUEUE = 128u,
     ERR_CHECK = 256u,             // a bounds check of the debug build (-DFRW_CHECKS) failed
-    ERR_FDM = 512u                // an FD transition solve did not reach its tolerance
+    ERR_FDM = 512u,               // an FD transition solve did not reach its tolerance
+    ERR_INPUT = 1024u             // a caller-given cube record is malformed (block count, range, material id)
 };
 // status words
 enum { STAT_ACTIVE = 0, STAT_ERR = 1, STAT_BUILT = 2, STAT_MWJOBS = 3, STAT_EPOCHS = 4, STAT_SUSPENDED = 5,
@@ -307,7 +308,7 @@ cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t p
 size_t fill_smem_bytes(int N);
 size_t mw_smem_bytes(int N, int warps);
 cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uint64_t spc,
-                            uint32_t key0, uint32_t key1, const uint8_t *matmap_local_to_global,
+                            uint32_t key0, uint32_t key1, int n_mat, const uint8_t *matmap_local_to_global,
                             const uint32_t *W, uint32_t *d_exit, uint32_t *d_steps,
                             unsigned long long *d_head, uint32_t *d_err, const LaunchShape &L,
                             cudaStream_t st);

@@ -1057,10 +1057,27 @@ struct CubeSource {
     uint32_t *d_exit, *d_steps;
     uint32_t *err;
     int N;
+    int n_mat;               // material ids of the records index 0 .. n_mat - 1
     __device__ uint64_t grab(uint32_t n) const { return atomicAdd(head, (unsigned long long)n); }
     __device__ void overrun() const { atomicOr(err, ERR_MW_STEPS); }
     __device__ bool valid(uint64_t j) const { return j < total; }
     __device__ int gmat(int local) const { return (int)((mmap_lo >> (4 * (local & 15))) & 15ull); }
+    // A record is usable when 0 <= K <= 8 (what 64 words hold), every material id
+    // is below n_mat and every block range satisfies 0 <= lo < hi <= N.
+    __device__ bool record_ok(const int32_t *c) const
+    {
+        const int K = c[1];
+        if (K < 0 || K > 8 || c[0] < 0 || c[0] >= n_mat) return false;
+        for (int t = 0; t < K; t++) {
+            const int m = c[8 + 7 * t];
+            if (m < 0 || m >= n_mat) return false;
+            for (int a = 0; a < 3; a++) {
+                const int lo = c[2 + 7 * t + 2 * a], hi = c[3 + 7 * t + 2 * a];
+                if (!(0 <= lo && lo < hi && hi <= N)) return false;
+            }
+        }
+        return true;
+    }
     __device__ void build(uint64_t j, uint16_t *Mw, int r, int N_, int lane) const
     {
         const int32_t *c = cubes + (j / spc) * 64;
@@ -1070,10 +1087,18 @@ struct CubeSource {
             hi = c[3 + 7 * q + 2 * a];
         });
     }
-    __device__ void load(uint64_t j, MWLane &L, int &x, int &y, int &z) const
+    // false (and the error flag set) for a malformed record: the sample is then
+    // written as exit 0, 0 steps and not walked
+    __device__ bool load(uint64_t j, MWLane &L, int &x, int &y, int &z) const
     {
         const int32_t *c = cubes + (j / spc) * 64;
-        const int K = min(max(c[1], 0), 8);
+        if (!record_ok(c)) {
+            atomicOr(err, ERR_INPUT);
+            if (d_exit) d_exit[j] = 0u;
+            if (d_steps) d_steps[j] = 0u;
+            return false;
+        }
+        const int K = c[1];
         uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)gmat(c[0]) << 4);
         for (int t = 0; t < K; t++) mm |= (uint64_t)gmat(c[2 + 7 * t + 6]) << (4 * (t + 2));
         L.mm = mm;
@@ -1089,6 +1114,7 @@ struct CubeSource {
         x = c0 + (int)(s3 & 1u);
         y = c0 + (int)((s3 >> 1) & 1u);
         z = c0 + (int)((s3 >> 2) & 1u);
+        return true;
     }
     __device__ void finish(const MWLane &L, int x, int y, int z, uint32_t steps) const
     {
@@ -1137,9 +1163,8 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
             }
             __syncwarp();
             if (got) {
-                src.load(myj, L, x, y, z);
                 t = 0;
-                active = true;
+                active = src.load(myj, L, x, y, z);
             }
         }
         if (__ballot_sync(FULL_MASK, active) == 0u) break;
@@ -2248,7 +2273,7 @@ cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t p
 }
 
 cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uint64_t spc, uint32_t key0,
-                            uint32_t key1, const uint8_t *map, const uint32_t *W, uint32_t *d_exit,
+                            uint32_t key1, int n_mat, const uint8_t *map, const uint32_t *W, uint32_t *d_exit,
                             uint32_t *d_steps, unsigned long long *d_head, uint32_t *d_err,
                             const LaunchShape &L, cudaStream_t st)
 {
@@ -2267,6 +2292,7 @@ cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uin
     src.d_exit = d_exit;
     src.d_steps = d_steps;
     src.N = N;
+    src.n_mat = n_mat;
     const int threads = 32 * L.mw_warps;
     k_mw<CubeSource><<<L.sms * L.mw_ctas_per_sm, threads, mw_smem_bytes(N, L.mw_warps), st>>>(src, W, N);
     return cudaGetLastError();
@@ -2320,7 +2346,7 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
     if (N < 2 || N > FRW_MAX_N || (N & 1) || n_cubes < 0 || !eps_r || n_mat < 1) return FRW_EINVAL;
     if (n_mat > FRW_MAX_MATERIALS) return FRW_ECAPACITY;
     for (int i = 0; i < n_mat; i++)
-        if (!(eps_r[i] > 0.0)) return FRW_EINVAL;
+        if (!(eps_r[i] > 0.0) || !std::isfinite(eps_r[i])) return FRW_EINVAL;
     if (n_cubes == 0 || samples_per_cube == 0) return FRW_OK;
     if (!d_cubes) return FRW_EINVAL;
     if (samples_per_cube > UINT64_MAX / (uint64_t)n_cubes) return FRW_EINVAL;
@@ -2357,13 +2383,14 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
     if (cudaMemcpyAsync(scr + NOALLOC_W_OFFSET, W, sizeof(W), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FRW_EDEVICE;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32) ^ (uint32_t)request_id;
-    if (launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, map, scr + NOALLOC_W_OFFSET,
+    if (launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, n_mat, map, scr + NOALLOC_W_OFFSET,
                         d_exit, d_steps, reinterpret_cast<unsigned long long *>(scr), scr + 2, L,
                         st) != cudaSuccess)
         return FRW_EDEVICE;
     uint32_t err = 0;
     if (cudaMemcpyAsync(&err, scr + 2, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FRW_EDEVICE;
     if (cudaStreamSynchronize(st) != cudaSuccess) return FRW_EDEVICE;
+    if (err & ERR_INPUT) return FRW_EINVAL;
     return err ? FRW_EDEVICE : FRW_OK;
 }
 

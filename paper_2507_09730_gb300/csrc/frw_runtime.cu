@@ -275,13 +275,14 @@ static int check_status(frw_ctx *ctx, cudaStream_t st = nullptr)
     const uint32_t e = ctx->h_status[STAT_ERR];
     if (e) {
         char buf[256];
-        snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s%s%s%s%s)", e,
+        snprintf(buf, sizeof buf, "device check failed (flags 0x%x: %s%s%s%s%s%s%s%s%s%s%s)", e,
                  (e & ERR_MWQ_OVERFLOW) ? "queue overflow " : "", (e & ERR_CACHE_FULL) ? "table cache full " : "",
                  (e & ERR_FILL) ? "table fill check " : "", (e & ERR_SHRINK) ? "cube shrink limit " : "",
                  (e & ERR_ACC_RANGE) ? "accumulator range " : "", (e & ERR_MW_STEPS) ? "MicroWalk step cap " : "",
                  (e & ERR_IDLE_TIMEOUT) ? "idle limit " : "", (e & ERR_REDUCE_QUEUE) ? "reduction queue " : "",
-                 (e & ERR_CHECK) ? "bounds check " : "", (e & ERR_FDM) ? "FD solve tolerance" : "");
-        return fail(ctx, (e & ERR_CACHE_FULL) ? FRW_ECAPACITY : FRW_EDEVICE, buf);
+                 (e & ERR_CHECK) ? "bounds check " : "", (e & ERR_FDM) ? "FD solve tolerance " : "",
+                 (e & ERR_INPUT) ? "malformed cube record" : "");
+        return fail(ctx, (e & ERR_INPUT) ? FRW_EINVAL : (e & ERR_CACHE_FULL) ? FRW_ECAPACITY : FRW_EDEVICE, buf);
     }
     return FRW_OK;
 }
@@ -1398,7 +1399,7 @@ extern "C" int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, con
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st);
     const uint32_t key0 = (uint32_t)ctx->opt.seed, key1 = (uint32_t)(ctx->opt.seed >> 32) ^ (uint32_t)request_id;
     if (e == cudaSuccess)
-        e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, map.data(), ctx->d_W, d_exit,
+        e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, n_mat, map.data(), ctx->d_W, d_exit,
                             d_steps, d_head, ctx->status + STAT_ERR, ctx->shape, st);
     if (e != cudaSuccess) {
         for (void *p : tmp) cudaFree(p);
@@ -2129,7 +2130,7 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
                 if ((e = cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), st)) != cudaSuccess) break;
                 if ((e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st)) != cudaSuccess) break;
                 if ((e = cudaEventRecord(ctx->ev[2], st)) != cudaSuccess) break;
-                e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, spc, 1u, 2u, map.data(), ctx->d_W, d_exit, d_steps,
+                e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, spc, 1u, 2u, 4, map.data(), ctx->d_W, d_exit, d_steps,
                                     d_head, ctx->status + STAT_ERR, L, st);
                 if (e != cudaSuccess) break;
                 if ((e = cudaEventRecord(ctx->ev[3], st)) != cudaSuccess) break;

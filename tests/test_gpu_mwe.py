@@ -67,4 +67,4 @@ def test_mwe_fp32_within_statistics(torch_cuda):
             rows[prec] = c.extract(sid, 11, 200_000, request_id=9 + prec)
     (C32, se32, _, _), (C64, se64, _, _) = rows[B.FRW_FP32_GEOM], rows[B.FRW_FP64_GEOM]
     for k in (11, 3, 19):
-        assert abs(C32[k] - C64[k]) <= 4.0 * np.hypot(se32[k], se64[k])
+        assert abs(C32[k] - C64[k]) <= 3.0 * np.hypot(se32[k], se64[k]), (k, C32[k], C64[k])

@@ -137,6 +137,20 @@ def test_walk_records_interconnect_fp64(torch_cuda):
     c.unload(sid)
 
 
+@pytest.mark.parametrize("N,n", [(8, 3000), (16, 600), (24, 200)])
+def test_walk_records_overflow_cubes_fp64(torch_cuda, N, n):
+    """Cubes that list more than 14 blocks are halved on both sides (reading R3):
+    the two-plate structure with its high-k cube cut into 32 blocks."""
+    s = W.split_blocks(W.tiny_two_plate(), (4, 4, 2))
+    c = ctx_for(N)
+    sid = c.load(s)
+    g = c.walk_records(sid, 0, n, request_id=23)
+    o = O.frw_run(s, 0, n, N=N, seed=0, request=23)
+    assert o.stats[10] > 0                     # the overflow rule was taken
+    _records_match(g, o)
+    c.unload(sid)
+
+
 def test_extract_matches_oracle_fp64(torch_cuda):
     s = W.tiny_two_plate()
     c = ctx_for(8)
@@ -235,7 +249,15 @@ def test_capacitance_matrix_and_symmetrisation(torch_cuda):
         np.testing.assert_array_equal(se[i], sei)
     assert (np.diag(C[:, :n]) > 0).all()
     off = ~np.eye(n, dtype=bool)
-    z = (C[:, :n] - C[:, :n].T)[off] / np.hypot(se[:, :n], se[:, :n].T)[off]
+    sd = np.hypot(se[:, :n], se[:, :n].T)[off]
+    dC = (C[:, :n] - C[:, :n].T)[off]
+    # a pair that no walk of either row reached has both entries exactly 0
+    # (no hits, zero standard error): check that, then test the others by z-score
+    none = sd == 0.0
+    assert (dC[none] == 0.0).all() and (C[:, :n][off][none] == 0.0).all()
+    assert (~none).sum() >= n              # most rows reach several neighbours
+    z = dC[~none] / sd[~none]
+    assert np.isfinite(z).all()
     assert np.mean(np.abs(z) > 4.0) < 0.01
     np.testing.assert_allclose(Cs, 0.5 * (C[:, :n] + C[:, :n].T) * off + np.diag(np.diag(C[:, :n])), rtol=0, atol=0)
     c.unload(sid)

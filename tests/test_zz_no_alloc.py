@@ -60,3 +60,51 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     assert B.frw_microwalk_cubes_noalloc(8, 1, rec.data_ptr(), eps16, 0, 4, 0, out.data_ptr(), 0) == B.FRW_ECAPACITY
     assert B.frw_microwalk_cubes_noalloc(7, 1, rec.data_ptr(), [1.0], 0, 4, 0, out.data_ptr(), 0) == B.FRW_EINVAL
     assert B.frw_microwalk_cubes_noalloc(34, 1, rec.data_ptr(), [1.0], 0, 4, 0, out.data_ptr(), 0) == B.FRW_EINVAL
+
+
+def test_noalloc_and_context_reject_malformed_records():
+    """A record with a material id >= n_mat, more than 8 blocks or an empty range is
+    refused by both entry points (FRW_EINVAL) instead of being walked with zero
+    weights; the well-formed cubes of the same call keep their samples."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    N, spc = 8, 64
+    cubes = W.random_cubes(4, N=N, seed=9)
+    good = B.pack_cubes(cubes)
+    n_mat = len(cubes.eps)
+    bad_mat = good[0].copy()
+    bad_mat[8] = n_mat                      # block 0's material id: one past the table
+    bad_bg = good[0].copy()
+    bad_bg[0] = 15                          # background id aliasing the boundary slot
+    bad_k = good[0].copy()
+    bad_k[1] = 9                            # more blocks than a 64-word record holds
+    bad_rng = good[0].copy()
+    bad_rng[2], bad_rng[3] = 5, 5           # empty range on axis 0
+    stream = torch.cuda.current_stream().cuda_stream
+    for bad in (bad_mat, bad_bg, bad_k, bad_rng):
+        recs = np.concatenate([good[1:2], bad[None, :]])
+        d = torch.from_numpy(recs).cuda()
+        ex = torch.full((2 * spc,), -1, dtype=torch.int32, device="cuda")
+        st = torch.full((2 * spc,), -1, dtype=torch.int32, device="cuda")
+        rc = B.frw_microwalk_cubes_noalloc(N, 2, d.data_ptr(), cubes.eps, 0, spc, 3, ex.data_ptr(), st.data_ptr(),
+                                           stream)
+        assert rc == B.FRW_EINVAL
+        torch.cuda.synchronize()
+        assert (ex[spc:] == 0).all() and (st[spc:] == 0).all()
+        ex_ok = torch.zeros(spc, dtype=torch.int32, device="cuda")
+        st_ok = torch.zeros(spc, dtype=torch.int32, device="cuda")
+        d1 = torch.from_numpy(np.ascontiguousarray(good[1:2])).cuda()
+        assert B.frw_microwalk_cubes_noalloc(N, 1, d1.data_ptr(), cubes.eps, 0, spc, 3, ex_ok.data_ptr(),
+                                             st_ok.data_ptr(), stream) == B.FRW_OK
+        torch.cuda.synchronize()
+        assert torch.equal(ex[:spc], ex_ok) and torch.equal(st[:spc], st_ok)
+        with B.Context(0, N=N, slots=1 << 12) as c:
+            with pytest.raises(B.FRWError) as ei:
+                B.frw_microwalk_cubes(c.ctx, N, 2, d.data_ptr(), cubes.eps, spc, 3, ex.data_ptr(), st.data_ptr())
+            assert ei.value.code == B.FRW_EINVAL
+    inf_eps = np.array(cubes.eps, np.float64)
+    inf_eps[0] = np.inf
+    d1 = torch.from_numpy(np.ascontiguousarray(good[1:2])).cuda()
+    assert B.frw_microwalk_cubes_noalloc(N, 1, d1.data_ptr(), inf_eps, 0, spc, 3, ex_ok.data_ptr(), 0,
+                                         stream) == B.FRW_EINVAL
