@@ -205,6 +205,17 @@ int frw_extract(frw_ctx *ctx, int32_t structure_id, int32_t master,
 int frw_extract_sums(frw_ctx *ctx, int32_t structure_id, int32_t master, const frw_extract_params *params,
                      uint64_t *sums, uint64_t *n_walks, frw_stats *stats);
 
+/* The exact sums of frw_extract_sums batch by batch (for a sigma-target extraction
+ * shared by several processes, Sec. IV's stop rule evaluated on the combined
+ * batches): walks params->walk_begin .. walk_begin + walk_budget - 1 in batches of
+ * params->batch walks (0: 16384); walk_begin must be a multiple of the batch size
+ * (FRW_EINVAL otherwise) so that batches line up across processes; sigma_target
+ * must be 0.  n_b = ceil(walk_budget / batch) batches.  Host outputs: sums[b * 4
+ * (n_cond + 1) + i] = word i of batch b in frw_extract_sums' layout; n_in_batch[b]
+ * = walks counted in batch b (the batch size, less for a final partial batch). */
+int frw_extract_batch_sums(frw_ctx *ctx, int32_t structure_id, int32_t master, const frw_extract_params *params,
+                           uint64_t *sums, uint64_t *n_in_batch, frw_stats *stats);
+
 /* Several extractions (possibly different structures, masters, budgets and
  * targets) interleaved in one engine run.  C_rows / stderr_rows are host arrays
  * holding each job's n_cond + 1 entries back to back in job order; stats (may be

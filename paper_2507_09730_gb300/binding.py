@@ -27,7 +27,8 @@ EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream",
            "frw_microwalk_cubes", "frw_microwalk_cubes_noalloc", "frw_table", "frw_strerror", "frw_last_error",
            "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
            "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums", "frw_extract_matrix",
-           "frw_cancel", "frw_get_serve_info", "frw_fdm_cubes", "frw_load_structure_boxes")
+           "frw_cancel", "frw_get_serve_info", "frw_fdm_cubes", "frw_load_structure_boxes",
+           "frw_extract_batch_sums")
 
 
 class frw_box(ctypes.Structure):
@@ -143,6 +144,8 @@ def lib():
     L.frw_autotune.argtypes = [c_void_p, POINTER(frw_job), c_int32, c_uint64, POINTER(frw_tuning)]
     L.frw_extract_sums.argtypes = [c_void_p, c_int32, c_int32, POINTER(frw_extract_params), P(c_uint64),
                                    POINTER(c_uint64), POINTER(frw_stats)]
+    L.frw_extract_batch_sums.argtypes = [c_void_p, c_int32, c_int32, POINTER(frw_extract_params), P(c_uint64),
+                                         P(c_uint64), POINTER(frw_stats)]
     L.frw_extract_matrix.argtypes = [c_void_p, c_int32, POINTER(frw_extract_params), P(c_double), P(c_double),
                                      P(c_double), POINTER(frw_stats)]
     L.frw_strerror.argtypes = [c_int]
@@ -253,6 +256,21 @@ def frw_extract_sums(ctx, sid: int, master: int, n_cond: int, walk_budget: int, 
     _check(ctx, lib().frw_extract_sums(ctx, int(sid), int(master), ctypes.byref(p), _ptr(words, c_uint64),
                                        ctypes.byref(n), ctypes.byref(st)))
     return words, int(n.value), st.as_dict()
+
+
+def frw_extract_batch_sums(ctx, sid: int, master: int, n_cond: int, walk_budget: int, request_id: int = 0,
+                           batch: int = 0, walk_begin: int = 0):
+    """-> (per-batch exact sums, shape (n_batches, 4 (n_cond + 1)) uint64, walks per
+    batch, stats); budget mode, walk_begin a multiple of the batch size."""
+    b = int(batch) if batch else 16384
+    nb = (int(walk_budget) + b - 1) // b
+    p = frw_extract_params(int(walk_budget), 0.0, int(request_id), int(batch), int(walk_begin))
+    words = np.zeros((max(nb, 1), 4 * (n_cond + 1)), np.uint64)
+    cnt = np.zeros(max(nb, 1), np.uint64)
+    st = frw_stats()
+    _check(ctx, lib().frw_extract_batch_sums(ctx, int(sid), int(master), ctypes.byref(p), _ptr(words, c_uint64),
+                                             _ptr(cnt, c_uint64), ctypes.byref(st)))
+    return words[:nb], cnt[:nb], st.as_dict()
 
 
 def frw_extract_matrix(ctx, sid: int, n_cond: int, walk_budget: int, sigma_target: float = 0.0,

@@ -1092,7 +1092,10 @@ static uint32_t run_pool_for(frw_ctx *ctx, uint64_t walks)
 // every job published before it starts.  The kernel applies each job's stop rule
 // and folds its batches; the host reads the decided sums back.  The caller holds
 // the engine lock.
-static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_out)
+// acc_out (optional): the run's batch accumulator arena, copied back after the run
+// (per batch: S1 and S2 as int128 pairs, then the ACC_EXTRA counters)
+static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_out,
+                    std::vector<unsigned long long> *acc_out = nullptr)
 {
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<JobRun *> live;
@@ -1160,6 +1163,10 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     for (uint32_t i = 0; i < nj; i++) {
         if (hjs[i].decided == 0u) return fail(ctx, FRW_EDEVICE, "a job was not decided when the kernel ended");
         take_result(*live[i], hjs[i], hsum.data() + live[i]->sum_off, hnext[i]);
+    }
+    if (acc_out) {
+        acc_out->assign(A.acc, 0ull);
+        CK(cudaMemcpy(acc_out->data(), ctx->rb.acc, sizeof(unsigned long long) * A.acc, cudaMemcpyDeviceToHost));
     }
     float kms = 0.f;
     cudaEventElapsedTime(&kms, ctx->ev[0], ctx->ev[1]);
@@ -1332,6 +1339,42 @@ extern "C" int frw_extract_sums(frw_ctx *ctx, int32_t sid, int32_t master, const
         sums[2 * nc1 + 2 * k + 1] = (uint64_t)(b >> 64);
     }
     *n_walks = runs[0].walks;
+    if (stats) *stats = st;
+    return FRW_OK;
+}
+
+extern "C" int frw_extract_batch_sums(frw_ctx *ctx, int32_t sid, int32_t master, const frw_extract_params *p,
+                                      uint64_t *sums, uint64_t *n_in_batch, frw_stats *stats)
+{
+    if (!ctx || !p || !sums || !n_in_batch) return FRW_EINVAL;
+    if (p->sigma_target != 0.0) return fail(ctx, FRW_EINVAL, "batch sums are taken in budget mode (sigma_target = 0)");
+    frw_job j;
+    j.structure_id = sid;
+    j.master = master;
+    j.walk_budget = p->walk_budget;
+    j.sigma_target = 0.0;
+    j.request_id = p->request_id;
+    j.batch = p->batch;
+    int rc = check_job(ctx, j);
+    if (rc) return rc;
+    const uint64_t B = p->batch ? p->batch : 16384;
+    if (p->walk_begin % B) return fail(ctx, FRW_EINVAL, "walk_begin must be a multiple of the batch size");
+    std::lock_guard<std::mutex> engine(ctx->engine_mu);
+    CK(cudaSetDevice(ctx->device));
+    std::vector<JobRun> runs(1);
+    runs[0].desc = j;
+    runs[0].walk_begin = p->walk_begin;
+    frw_stats st;
+    std::vector<unsigned long long> acc;
+    rc = run_jobs(ctx, runs, &st, &acc);
+    if (rc) return rc;
+    const JobRun &r = runs[0];
+    const int nc1 = r.d.n_c + 1;
+    for (uint64_t b = 0; b < r.n_batches; b++) {
+        const unsigned long long *blk = acc.data() + r.d.acc_base + b * r.d.acc_stride;
+        for (int w = 0; w < 4 * nc1; w++) sums[b * 4 * nc1 + w] = blk[w];
+        n_in_batch[b] = blk[4 * nc1];
+    }
     if (stats) *stats = st;
     return FRW_OK;
 }

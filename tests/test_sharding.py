@@ -159,3 +159,149 @@ def test_lost_rank_ends_the_exchange_with_an_error():
         p.join(timeout=60)
     assert rank == 0 and what != "no error"
     assert time.time() - t0 < 100
+
+
+# ---------------------------------------------------------------------------
+# sigma-target extraction across ranks: the stop rule on the combined batches
+
+def _standin_batch_sums(k, batch, master=0, seed=3):
+    """Stand-in engine: walk w ends at electrode e with weight omega (fixed point
+    of the library's scales), so that the relative errors fall like 1/sqrt(n)."""
+    def walk(w):
+        rng = np.random.default_rng([w, seed])
+        e = master if rng.random() < 0.6 else int(rng.integers(0, k))
+        om = (1.0 if e == master else -0.4) * (0.5 + rng.random())
+        return e, int(round(om * 2 ** 64)), int(round(om * om * 2 ** 40))
+
+    def sums(begin, n):
+        nb = (n + batch - 1) // batch
+        words = np.zeros((nb, 4 * k), np.uint64)
+        cnt = np.zeros(nb, np.uint64)
+        for b in range(nb):
+            s1, s2 = [0] * k, [0] * k
+            lo, hi = begin + b * batch, min(begin + (b + 1) * batch, begin + n)
+            for w in range(lo, hi):
+                e, a, q = walk(w)
+                s1[e] += a
+                s2[e] += q
+            words[b] = np.concatenate([S.ints_to_words(s1), S.ints_to_words(s2)])
+            cnt[b] = hi - lo
+        return words, cnt
+    return sums
+
+
+def _sigma_rank_main(rank, world, port, k, batch, sigma, budget, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        C, se, used, conv = S.extract_sharded_sigma(_standin_batch_sums(k, batch), k - 1, 0, sigma, budget, batch,
+                                                    rank, world, S.allgather_words, batches_per_round=2)
+        q.put((rank, C.tolist(), se.tolist(), used, conv))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sigma_fold_matches_a_plain_recomputation():
+    """The fold stops at the first full batch where the self term and the largest
+    coupling both reach the target; recomputed here in plain floating point from
+    the same per-batch sums (exact sums converted once per check)."""
+    k, batch, sigma, budget = 4, 64, 0.03, 64 * 200
+    sums = _standin_batch_sums(k, batch)
+    w, cnt = sums(0, budget)
+    F = S.SigmaFold(k - 1, 0, sigma, budget, batch)
+    for g in range(w.shape[0]):
+        if F.add(g, w[g], int(cnt[g])):
+            break
+    assert F.decided == 1 and F.used < budget
+    tot1 = np.zeros(k, dtype=object)
+    tot2 = np.zeros(k, dtype=object)
+    stop = None
+    for g in range(w.shape[0]):
+        v = S.words_to_ints(w[g])
+        tot1 += np.array(v[:k], dtype=object)
+        tot2 += np.array(v[k:], dtype=object)
+        n = (g + 1) * batch
+        c = np.array([float(x) / 2 ** 64 for x in tot1]) / n
+        var = (np.array([float(x) / 2 ** 40 for x in tot2]) - c * c * n) / (n * (n - 1.0))
+        se = np.sqrt(np.maximum(var, 0))
+        jb = 1 + int(np.argmax(np.abs(c[1:k - 1])))          # largest coupling, ground (last) excluded
+        if se[0] / abs(c[0]) <= sigma and se[jb] / abs(c[jb]) <= sigma:
+            stop = n
+            break
+    assert stop == F.used
+    C, se, used, conv = F.row()
+    assert conv and used == stop
+    C2, se2 = S.row_from_sums([int(x) for x in tot1], [int(x) for x in tot2], stop)
+    np.testing.assert_array_equal(C, C2)
+    np.testing.assert_array_equal(se, se2)
+    # a budget too small to converge: decided by the budget, partial last batch included
+    F2 = S.SigmaFold(k - 1, 0, 1e-6, 1000, batch)
+    w2, cnt2 = sums(0, 1000)
+    done = [F2.add(g, w2[g], int(cnt2[g])) for g in range(w2.shape[0])]
+    assert done[-1] and not any(done[:-1]) and F2.decided == 2 and F2.used == 1000
+
+
+def test_two_gloo_ranks_stop_at_the_single_run_batch():
+    import multiprocessing as mp
+    k, batch, sigma, budget = 4, 64, 0.03, 64 * 200
+    C1, se1, used1, conv1 = S.extract_sharded_sigma(_standin_batch_sums(k, batch), k - 1, 0, sigma, budget, batch)
+    assert conv1 and used1 < budget
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sigma_rank_main, args=(r, 2, port, k, batch, sigma, budget, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=180) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, C, se, used, conv in got:
+        assert used == used1 and conv == conv1
+        np.testing.assert_array_equal(np.array(C), C1)
+        np.testing.assert_array_equal(np.array(se), se1)
+
+
+@pytest.mark.gpu
+def test_gpu_sigma_shards_equal_one_run():
+    """Three shards of a sigma-target extraction on one GPU (the ranks' rounds run
+    one after the other) give the row, the walk count and the decision of one
+    frw_extract with the same target, bit for bit; the per-batch sums add up to
+    frw_extract_sums over the same walks."""
+    import itertools
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_09730_gb300 import binding as B
+    from paper_2507_09730_gb300 import workloads as W
+    s = W.interconnect(1)
+    master, batch, sigma, budget, request = 11, 4096, 0.02, 2_000_000, 6
+    with B.Context(0, N=16, precision=B.FRW_FP32_GEOM, seed=21, slots=1 << 16) as c:
+        sid = c.load(s)
+
+        def sums(begin, n):
+            w, cnt, _ = B.frw_extract_batch_sums(c.ctx, sid, master, s.n_cond, n, request, batch, begin)
+            return w, cnt
+
+        w, cnt = sums(3 * batch, 5 * batch + 17)
+        assert list(cnt) == [batch] * 5 + [17]
+        tot, n, _ = B.frw_extract_sums(c.ctx, sid, master, s.n_cond, 5 * batch + 17, request, batch, 3 * batch)
+        S1, S2, nn = S.combine([(w[b], cnt[b]) for b in range(w.shape[0])])
+        assert nn == n and S.ints_to_words(S1 + S2).tolist() == tot.tolist()
+        with pytest.raises(B.FRWError):
+            B.frw_extract_batch_sums(c.ctx, sid, master, s.n_cond, batch, request, batch, 5)
+
+        world, m = 3, 2
+        rounds = itertools.count()
+
+        def gather(p0):
+            r = next(rounds)
+            return [p0] + [S.round_payload(sums, s.n_cond, budget, batch, r, q, world, m) for q in range(1, world)]
+
+        C, se, used, conv = S.extract_sharded_sigma(sums, s.n_cond, master, sigma, budget, batch, 0, world, gather, m)
+        Cf, sef, st, convf = c.extract(sid, master, budget, sigma, request, batch)
+    assert conv and convf and used == st["walks"] < budget
+    np.testing.assert_array_equal(C, Cf)
+    np.testing.assert_array_equal(se, sef)
