@@ -185,6 +185,44 @@ int frw_load_structure_boxes(frw_ctx *ctx, const frw_box *domain, const frw_box 
                              const frw_block *blocks, int32_t n_blocks, int32_t *structure_id);
 int frw_unload_structure(frw_ctx *ctx, int32_t structure_id);
 
+/* A structure in full (one descriptor for every input of Algorithm 1 this library
+ * takes): the domain box; grounded_walls (must be 1: the domain walls are the
+ * ground electrode, index n_cond of every row -- Algorithm 1 ends a walk on an
+ * electrode and the FD lattice of Eq. 4-6 has Dirichlet panels only, so no other
+ * wall condition is offered); conductor boxes with their conductor ids
+ * (box_conductor may be NULL: box i is conductor i, n_boxes = n_cond) as for
+ * frw_load_structure_boxes; the permittivity table and background material; an
+ * optional permittivity voxel map; dielectric blocks.
+ * Voxel map (Sec. III-A: permittivity constant in each voxel): voxel_mat (host,
+ * may be NULL) holds vox_dims[0] * vox_dims[1] * vox_dims[2] material ids, x
+ * slowest and z fastest (cell (i, j, k) at (i * ny + j) * nz + k), of the cells of
+ * a uniform grid over the domain: cell i on axis a spans [e_a(i), e_a(i + 1)) with
+ * e_a(i) = lo_a + ((hi_a - lo_a) * i) / n_a and e_a(n_a) = hi_a.  An id below n_mat
+ * gives the cell that material; FRW_VOXEL_NONE leaves it to the background.
+ * Priority: a dielectric block (later blocks first) wins over the voxel map,
+ * which wins over the background.  The map is loaded as boxes: maximal runs of
+ * one material along z, runs with equal extent and material merged across
+ * consecutive y, then rectangles merged across consecutive x, the boxes ordered
+ * by their first cell (x, then y, then z) and placed below the blocks.  At most
+ * 2^24 cells and 65535 boxes and blocks together (FRW_ECAPACITY beyond).
+ * Otherwise as frw_load_structure. */
+#define FRW_VOXEL_NONE 255
+typedef struct {
+    frw_box domain;
+    int32_t grounded_walls;
+    int32_t n_boxes, n_cond;
+    int32_t n_mat, background_mat;
+    int32_t n_blocks;
+    int32_t vox_dims[3];
+    int32_t reserved;
+    const frw_box *boxes;
+    const int32_t *box_conductor;
+    const double *eps_r;
+    const frw_block *blocks;
+    const uint8_t *voxel_mat;
+} frw_structure;
+int frw_load_structure_ex(frw_ctx *ctx, const frw_structure *desc, int32_t *structure_id);
+
 /* Capacitance row of `master` (Algorithm 1 output).  C_row and stderr_row are host
  * arrays of n_cond + 1 doubles (last entry = grounded walls).  stats may be NULL.
  * Returns FRW_ENOTCONV (results still filled) when the budget ran out before the

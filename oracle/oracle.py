@@ -205,6 +205,71 @@ def panel_node(N, kind, axis, naxis, n):
 
 
 # ---------------------------------------------------------------------------
+# Permittivity voxel map of a structure -> dielectric boxes.  The map's cells
+# partition the domain uniformly (cell i of axis a spans [e(i), e(i + 1)) with
+# e(i) = lo + ((hi - lo) * i) / n and e(n) = hi); every cell with a material is
+# covered by exactly one box: maximal runs of one material along z, runs of equal
+# extent and material merged over consecutive y, rectangles merged over
+# consecutive x, boxes ordered by their first cell.  They lie below the blocks.
+VOXEL_NONE = 255
+
+
+def voxel_blocks(domain_lo, domain_hi, vm):
+    vm = np.asarray(vm, np.uint8)
+    nx, ny, nz = vm.shape
+    boxes = []                       # [i0, i1, j0, j1, k0, k1, m]
+    last_x = {}                      # (j0, j1, k0, k1, m) -> box extended at the previous x
+    for i in range(nx):
+        rects = []                   # [j0, j1, k0, k1, m]
+        last_y = {}                  # (k0, k1, m) -> rect
+        for j in range(ny):
+            col = [int(v) for v in vm[i, j]]
+            k = 0
+            while k < nz:
+                m = col[k]
+                k1 = k + 1
+                while k1 < nz and col[k1] == m:
+                    k1 += 1
+                if m != VOXEL_NONE:
+                    r = last_y.get((k, k1, m))
+                    if r is not None and r[1] == j:
+                        r[1] = j + 1
+                    else:
+                        r = [j, j + 1, k, k1, m]
+                        last_y[(k, k1, m)] = r
+                        rects.append(r)
+                k = k1
+        for r in rects:
+            b = last_x.get(tuple(r))
+            if b is not None and b[1] == i:
+                b[1] = i + 1
+            else:
+                b = [i, i + 1] + r
+                last_x[tuple(r)] = b
+                boxes.append(b)
+    boxes.sort(key=lambda b: (b[0], b[2], b[4]))
+    lo, hi = np.asarray(domain_lo, np.float64), np.asarray(domain_hi, np.float64)
+
+    def e(a, i, n):
+        return float(hi[a]) if i == n else float(lo[a]) + ((float(hi[a]) - float(lo[a])) * float(i)) / float(n)
+
+    blo = np.array([[e(0, b[0], nx), e(1, b[2], ny), e(2, b[4], nz)] for b in boxes]).reshape(-1, 3)
+    bhi = np.array([[e(0, b[1], nx), e(1, b[3], ny), e(2, b[5], nz)] for b in boxes]).reshape(-1, 3)
+    return blo, bhi, np.array([b[6] for b in boxes], np.int32)
+
+
+def structure_blocks(s):
+    """The structure's dielectric boxes in priority order: its voxel map's boxes
+    (if any), then its blocks."""
+    if getattr(s, "voxel_mat", None) is None:
+        return s.block_lo, s.block_hi, s.block_mat
+    vlo, vhi, vm = voxel_blocks(s.domain_lo, s.domain_hi, s.voxel_mat)
+    return (np.ascontiguousarray(np.concatenate([vlo, s.block_lo.reshape(-1, 3)])),
+            np.ascontiguousarray(np.concatenate([vhi, s.block_hi.reshape(-1, 3)])),
+            np.ascontiguousarray(np.concatenate([vm, s.block_mat.astype(np.int32)])))
+
+
+# ---------------------------------------------------------------------------
 @dataclass
 class RunResult:
     S1: np.ndarray
@@ -253,12 +318,15 @@ def frw_run(s, master, n_walks, N=8, seed=0, request=0, hybrid=1, first_mode=0, 
     else:
         om = kk = hp = st = br = None
         rp = (None,) * 5
+    blo, bhi, bmat = structure_blocks(s)
+    blo = np.ascontiguousarray(blo, np.float64)
+    bhi = np.ascontiguousarray(bhi, np.float64)
+    bmat = np.ascontiguousarray(bmat, np.int32)
     ntab = L.orc_frw_run(
         _p(s.domain_lo, ctypes.c_double), _p(s.domain_hi, ctypes.c_double), s.n_boxes,
         _p(s.cond_lo, ctypes.c_double), _p(s.cond_hi, ctypes.c_double), None if cid is None else _p(cid, ctypes.c_int32), nc,
-        s.n_blocks,
-        _p(s.block_lo, ctypes.c_double), _p(s.block_hi, ctypes.c_double),
-        _p(s.block_mat, ctypes.c_int32), s.n_mat, _p(s.eps, ctypes.c_double), int(s.background),
+        int(bmat.shape[0]),
+        _p(blo, ctypes.c_double), _p(bhi, ctypes.c_double), _p(bmat, ctypes.c_int32), s.n_mat, _p(s.eps, ctypes.c_double), int(s.background),
         int(N), int(seed), int(request), int(hybrid), int(first_mode), float(gauss_frac),
         int(max_hops), int(mwe), int(bool(fdm)), int(master), int(walk_begin), n, float(sigma_target), int(batch),
         _p(S1, ctypes.c_double), _p(S2, ctypes.c_double), _p(used, ctypes.c_uint64), *rp,

@@ -28,7 +28,7 @@ EXPORTS = ("frw_default_options", "frw_create", "frw_destroy", "frw_set_stream",
            "frw_submit", "frw_poll", "frw_wait", "frw_plan_create", "frw_plan_run", "frw_plan_destroy",
            "frw_get_tuning", "frw_set_tuning", "frw_autotune", "frw_extract_sums", "frw_extract_matrix",
            "frw_cancel", "frw_get_serve_info", "frw_fdm_cubes", "frw_load_structure_boxes",
-           "frw_extract_batch_sums")
+           "frw_extract_batch_sums", "frw_load_structure_ex")
 
 
 class frw_box(ctypes.Structure):
@@ -37,6 +37,17 @@ class frw_box(ctypes.Structure):
 
 class frw_block(ctypes.Structure):
     _fields_ = [("lo", c_double * 3), ("hi", c_double * 3), ("mat", c_int32), ("reserved", c_int32)]
+
+
+FRW_VOXEL_NONE = 255
+
+
+class frw_structure(ctypes.Structure):
+    _fields_ = [("domain", frw_box), ("grounded_walls", c_int32), ("n_boxes", c_int32), ("n_cond", c_int32),
+                ("n_mat", c_int32), ("background_mat", c_int32), ("n_blocks", c_int32),
+                ("vox_dims", c_int32 * 3), ("reserved", c_int32),
+                ("boxes", c_void_p), ("box_conductor", c_void_p), ("eps_r", c_void_p), ("blocks", c_void_p),
+                ("voxel_mat", c_void_p)]
 
 
 class frw_options(ctypes.Structure):
@@ -114,6 +125,7 @@ def lib():
     L.frw_set_stream.argtypes = [c_void_p, c_void_p]
     L.frw_load_structure.argtypes = [c_void_p, P(frw_box), P(frw_box), c_int32, P(c_double), c_int32, c_int32,
                                      P(frw_block), c_int32, P(c_int32)]
+    L.frw_load_structure_ex.argtypes = [c_void_p, POINTER(frw_structure), POINTER(c_int32)]
     L.frw_load_structure_boxes.argtypes = [c_void_p, P(frw_box), P(frw_box), P(c_int32), c_int32, c_int32,
                                            P(c_double), c_int32, c_int32, P(frw_block), c_int32, P(c_int32)]
     L.frw_unload_structure.argtypes = [c_void_p, c_int32]
@@ -217,6 +229,24 @@ def frw_load_structure(ctx, s) -> int:
         blk[b].mat = int(s.block_mat[b])
     eps = np.ascontiguousarray(s.eps, np.float64)
     sid = c_int32(-1)
+    vm = getattr(s, "voxel_mat", None)
+    if vm is not None:
+        vm = np.ascontiguousarray(vm, np.uint8)
+        cid = None if s.cond_id is None else np.ascontiguousarray(s.cond_id, np.int32)
+        d = frw_structure()
+        d.domain = dom
+        d.grounded_walls = 1
+        d.n_boxes, d.n_cond = s.n_boxes, s.n_cond
+        d.n_mat, d.background_mat = len(eps), int(s.background)
+        d.n_blocks = s.n_blocks
+        d.vox_dims = (c_int32 * 3)(*vm.shape)
+        d.boxes = ctypes.cast(cond, c_void_p)
+        d.box_conductor = None if cid is None else cid.ctypes.data
+        d.eps_r = eps.ctypes.data
+        d.blocks = ctypes.cast(blk, c_void_p)
+        d.voxel_mat = vm.ctypes.data
+        _check(ctx, lib().frw_load_structure_ex(ctx, ctypes.byref(d), ctypes.byref(sid)))
+        return sid.value
     if s.cond_id is None:
         rc = lib().frw_load_structure(ctx, ctypes.byref(dom), cond, s.n_cond, _ptr(eps, c_double), len(eps),
                                       int(s.background), blk, s.n_blocks, ctypes.byref(sid))

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -759,6 +760,92 @@ extern "C" int frw_load_structure_boxes(frw_ctx *ctx, const frw_box *domain, con
     if (!box_conductor) return FRW_EINVAL;
     return load_structure(ctx, domain, boxes, box_conductor, n_boxes, n_cond, eps_r, n_mat, background_mat, blocks,
                           n_blocks, structure_id);
+}
+
+// Boxes of a permittivity voxel map over the domain (the frw_structure rule): runs
+// of one material along z, merged across y where extent and material agree, then
+// across x; ordered by first cell.  Cells of FRW_VOXEL_NONE produce no box.
+static int voxel_boxes(frw_ctx *ctx, const frw_box &dom, const uint8_t *vm, const int32_t dims[3], int32_t n_mat,
+                       std::vector<frw_block> &out)
+{
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    if (nx < 1 || ny < 1 || nz < 1) return fail(ctx, FRW_EINVAL, "voxel map dimensions must be positive");
+    if (nx * ny * nz > (int64_t)1 << 24) return fail(ctx, FRW_ECAPACITY, "voxel map larger than 2^24 cells");
+    for (int64_t c = 0; c < nx * ny * nz; c++)
+        if (vm[c] != FRW_VOXEL_NONE && (int)vm[c] >= n_mat) return fail(ctx, FRW_EINVAL, "voxel material out of range");
+    struct Rect { int64_t j0, j1, k0, k1; int m; };
+    struct Box { int64_t i0, i1, j0, j1, k0, k1; int m; };
+    std::vector<Box> boxes;
+    std::map<std::tuple<int64_t, int64_t, int64_t, int64_t, int>, size_t> open_x;   // -> index in boxes
+    for (int64_t i = 0; i < nx; i++) {
+        std::vector<Rect> rects;
+        std::map<std::tuple<int64_t, int64_t, int>, size_t> open_y;                    // -> index in rects
+        for (int64_t j = 0; j < ny; j++) {
+            const uint8_t *col = vm + (i * ny + j) * nz;
+            for (int64_t k = 0; k < nz;) {
+                const int m = col[k];
+                int64_t k1 = k + 1;
+                while (k1 < nz && col[k1] == m) k1++;
+                if (m != FRW_VOXEL_NONE) {
+                    auto key = std::make_tuple(k, k1, m);
+                    auto it = open_y.find(key);
+                    if (it != open_y.end() && rects[it->second].j1 == j) rects[it->second].j1 = j + 1;
+                    else {
+                        open_y[key] = rects.size();
+                        rects.push_back({j, j + 1, k, k1, m});
+                    }
+                }
+                k = k1;
+            }
+        }
+        for (const Rect &r : rects) {
+            auto key = std::make_tuple(r.j0, r.j1, r.k0, r.k1, r.m);
+            auto it = open_x.find(key);
+            if (it != open_x.end() && boxes[it->second].i1 == i) boxes[it->second].i1 = i + 1;
+            else {
+                open_x[key] = boxes.size();
+                boxes.push_back({i, i + 1, r.j0, r.j1, r.k0, r.k1, r.m});
+            }
+        }
+    }
+    std::sort(boxes.begin(), boxes.end(), [](const Box &a, const Box &b) {
+        return std::make_tuple(a.i0, a.j0, a.k0) < std::make_tuple(b.i0, b.j0, b.k0);
+    });
+    auto edge = [&](int a, int64_t i, int64_t n) {
+        return i == n ? dom.hi[a] : dom.lo[a] + ((dom.hi[a] - dom.lo[a]) * (double)i) / (double)n;
+    };
+    out.clear();
+    out.reserve(boxes.size());
+    for (const Box &b : boxes) {
+        frw_block q;
+        q.lo[0] = edge(0, b.i0, nx); q.hi[0] = edge(0, b.i1, nx);
+        q.lo[1] = edge(1, b.j0, ny); q.hi[1] = edge(1, b.j1, ny);
+        q.lo[2] = edge(2, b.k0, nz); q.hi[2] = edge(2, b.k1, nz);
+        q.mat = b.m;
+        out.push_back(q);
+    }
+    return FRW_OK;
+}
+
+extern "C" int frw_load_structure_ex(frw_ctx *ctx, const frw_structure *d, int32_t *structure_id)
+{
+    if (!ctx || !d || !structure_id) return FRW_EINVAL;
+    if (d->grounded_walls != 1)
+        return fail(ctx, FRW_EINVAL, "the domain walls must be grounded (grounded_walls = 1)");
+    if (d->n_blocks < 0 || (d->n_blocks > 0 && !d->blocks)) return fail(ctx, FRW_EINVAL, "bad block list");
+    if (!d->box_conductor && d->n_boxes != d->n_cond)
+        return fail(ctx, FRW_EINVAL, "without box_conductor every conductor is one box (n_boxes = n_cond)");
+    std::vector<frw_block> all;
+    if (d->voxel_mat) {
+        if (!box_ok(d->domain)) return fail(ctx, FRW_EINVAL, "degenerate domain");
+        int rc = voxel_boxes(ctx, d->domain, d->voxel_mat, d->vox_dims, d->n_mat, all);
+        if (rc) return rc;
+    }
+    if ((int64_t)all.size() + d->n_blocks > 65535)
+        return fail(ctx, FRW_ECAPACITY, "more than 65535 dielectric boxes (voxel map and blocks)");
+    for (int b = 0; b < d->n_blocks; b++) all.push_back(d->blocks[b]);
+    return load_structure(ctx, &d->domain, d->boxes, d->box_conductor, d->n_boxes, d->n_cond, d->eps_r, d->n_mat,
+                          d->background_mat, all.empty() ? nullptr : all.data(), (int32_t)all.size(), structure_id);
 }
 
 extern "C" int frw_unload_structure(frw_ctx *ctx, int32_t sid)

@@ -32,6 +32,8 @@ __all__ = [
     "l_shape_pair",
     "split_conductor",
     "split_blocks",
+    "voxel_two_plate",
+    "voxel_interconnect",
     "interconnect",
     "batched_family",
     "serving_pool",
@@ -58,6 +60,10 @@ class Structure:
     block_mat: np.ndarray = field(default_factory=lambda: np.zeros((0,), np.int32))
     masters: tuple = (0,)            # conductors the workload extracts rows for
     cond_id: np.ndarray | None = None   # (n_boxes,) int32 conductor of each box; None: box k = conductor k
+    # permittivity voxel map over the domain, shape (nx, ny, nz) uint8 (x slowest):
+    # cell (i, j, k) has material voxel_mat[i, j, k], 255 = none (background); the
+    # blocks lie on top of it
+    voxel_mat: np.ndarray | None = None
 
     def __post_init__(self):
         self.domain_lo = np.ascontiguousarray(self.domain_lo, np.float64).reshape(3)
@@ -70,6 +76,9 @@ class Structure:
         self.block_mat = np.ascontiguousarray(self.block_mat, np.int32).reshape(-1)
         if self.cond_id is not None:
             self.cond_id = np.ascontiguousarray(self.cond_id, np.int32).reshape(-1)
+        if self.voxel_mat is not None:
+            self.voxel_mat = np.ascontiguousarray(self.voxel_mat, np.uint8)
+            assert self.voxel_mat.ndim == 3
 
     @property
     def n_boxes(self) -> int:
@@ -95,7 +104,7 @@ class Structure:
         """Same geometry with every permittivity multiplied by ``factor``."""
         return Structure(self.name + f"*eps{factor:g}", self.domain_lo, self.domain_hi,
                          self.cond_lo, self.cond_hi, self.eps * factor, self.background,
-                         self.block_lo, self.block_hi, self.block_mat, self.masters, self.cond_id)
+                         self.block_lo, self.block_hi, self.block_mat, self.masters, self.cond_id, self.voxel_mat)
 
 
 # ---------------------------------------------------------------------------
@@ -170,6 +179,35 @@ def split_blocks(s: Structure, pieces=(4, 4, 2)) -> Structure:
     return Structure(s.name + "+split_blocks" + "x".join(map(str, pieces)), s.domain_lo, s.domain_hi,
                      s.cond_lo, s.cond_hi, s.eps, s.background, np.array(blo), np.array(bhi),
                      np.array(bm, np.int32), s.masters, s.cond_id)
+
+
+VOXEL_NONE = 255
+
+
+def voxel_two_plate() -> Structure:
+    """The two-plate structure with its high-k cube given as a permittivity voxel
+    map instead of a block: 20^3 cells of 0.2 um over the 4 um domain, cells 9-10
+    on every axis ([1.8, 2.2] um) of the high-k material, the rest none
+    (background).  The same permittivity everywhere as tiny_two_plate()."""
+    s = tiny_two_plate()
+    vm = np.full((20, 20, 20), VOXEL_NONE, np.uint8)
+    vm[9:11, 9:11, 9:11] = 1
+    return Structure("voxel_two_plate", s.domain_lo, s.domain_hi, s.cond_lo, s.cond_hi, s.eps, s.background,
+                     masters=s.masters, voxel_mat=vm)
+
+
+def voxel_interconnect(seed: int = 0, dims=(10, 10, 4), fill: float = 0.3) -> Structure:
+    """The interconnect structure with a random permittivity voxel map under its
+    shells and LDE blocks: each cell of a dims grid over the domain is, with
+    probability `fill`, one of two extra dielectrics (eps 3.2 or 4.1), else none.
+    The blocks stay on top of the map."""
+    s = interconnect(seed)
+    rng = np.random.default_rng(np.random.SeedSequence([7, seed, *dims]))
+    n0 = s.n_mat
+    eps = np.concatenate([s.eps, [3.2, 4.1]])
+    vm = np.where(rng.random(dims) < fill, rng.integers(n0, n0 + 2, dims), VOXEL_NONE).astype(np.uint8)
+    return Structure(f"voxel_interconnect{seed}", s.domain_lo, s.domain_hi, s.cond_lo, s.cond_hi, eps, s.background,
+                     s.block_lo, s.block_hi, s.block_mat, s.masters, s.cond_id, vm)
 
 
 # ---------------------------------------------------------------------------

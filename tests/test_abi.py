@@ -76,7 +76,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         import pytest
         pytest.skip("no C compiler")
     structs = [n for n in ("frw_box", "frw_block", "frw_options", "frw_extract_params", "frw_stats", "frw_job",
-                           "frw_tuning", "frw_serve_info")]
+                           "frw_tuning", "frw_serve_info", "frw_structure")]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "frw.h"', "int main(void) {"]
     for n in structs:
         lines.append(f'    printf("{n} %zu\\n", sizeof({n}));')
