@@ -487,60 +487,44 @@ def batched_measurement(N, precision, tuning, steps=1):
             "converged_before_budget": conv / (steps * len(jobs))}
 
 
-SERVE_BUDGET = 4_000_000     # walk budget (cap) of one served request
 
 
 def serving_measurement(N, precision, rate, duration, seed=0):
-    """Serving form: Poisson arrivals of extraction requests over a pool of 32
-    structures with 4-200 conductors, 1-sigma targets U[0.5 %, 2 %].  Served
-    through frw_submit (admitted into the running walk kernel as room frees up)
-    and, on the same arrival times, one request per launch in arrival order
-    (frw_extract).  Latency = completion - arrival."""
+    """Serving form (paper_2507_09730_gb300.studies.serving_point): Poisson
+    arrivals of extraction requests over a pool of 32 structures with 4-200
+    conductors, 1-sigma targets U[0.5 %, 2 %], served through frw_submit and, on
+    the same arrival times, one request per launch; latency = completion -
+    arrival."""
+    from paper_2507_09730_gb300 import studies
+    return studies.serving_point(N, precision, rate, duration, seed)
+
+
+def interconnect_seeds(N, precision, sigma, budget, tuning, seeds=(0, 1, 2, 3), steps=2):
+    """The interconnect configuration at seeds 0-3 (each seed its own wire widths,
+    spacings and LDE blocks; masters the fourth wire of each layer): walks/s of
+    the same extraction as the main line (tuned settings of seed 0) and each
+    master's self capacitance with its standard error."""
     from paper_2507_09730_gb300 import binding as B
-    pool = W.serving_pool(32)
-    reqs = W.serving_requests(pool, rate=rate, duration=duration, seed=seed)
-    ctx = B.Context(0, N=N, precision=precision, seed=0, serve_arena_mb=16384, serve_jobs=4096)
-    sids = [ctx.load(st) for st in pool]
-    ctx.extract_batch([dict(structure_id=sid, master=m, walk_budget=20000, request_id=1 + m)
-                       for sid, st in zip(sids, pool) for m in range(0, st.n_cond, max(1, st.n_cond // 4))])
-
-    def job(i, r):
-        return dict(structure_id=sids[r.structure], master=r.master, walk_budget=SERVE_BUDGET, sigma_target=r.sigma,
-                    request_id=10_000 + i)
-
-    t0 = time.perf_counter()
-    tickets = []
-    for i, r in enumerate(reqs):
-        dt = r.t - (time.perf_counter() - t0)
-        if dt > 0:
-            time.sleep(dt)
-        tickets.append(ctx.submit(job(i, r)))
-    lat, walks, rows = [], 0, []
-    for t in tickets:
-        C, se, st, conv = ctx.wait(t)
-        lat.append(st["seconds"])
-        walks += st["walks"]
-        rows.append(C)
-    span = time.perf_counter() - t0
-    served = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-              "walks_per_s": walks / span, "makespan_s": span}
-    t0 = time.perf_counter()
-    lat_b, walks_b, same = [], 0, 0
-    for i, r in enumerate(reqs):
-        dt = r.t - (time.perf_counter() - t0)
-        if dt > 0:
-            time.sleep(dt)
-        C, se, st, conv = ctx.extract(sids[r.structure], r.master, SERVE_BUDGET, r.sigma, 10_000 + i)
-        lat_b.append(time.perf_counter() - t0 - r.t)
-        walks_b += st["walks"]
-        same += int(np.array_equal(C, rows[i]))
-    span_b = time.perf_counter() - t0
-    ctx.close()
-    return {"rate_per_s": rate, "arrival_window_s": duration, "requests": len(reqs),
-            "walks_per_request": walks / max(1, len(reqs)), "served": served,
-            "one_job_per_launch": {"p50_s": float(np.percentile(lat_b, 50)), "p99_s": float(np.percentile(lat_b, 99)),
-                                   "walks_per_s": walks_b / span_b, "makespan_s": span_b},
-            "identical_results": same}
+    out = []
+    for sd in seeds:
+        s = W.interconnect(sd)
+        c = B.Context(0, N=N, precision=precision, seed=0)
+        c.set_tuning(**{k: tuning[k] for k in ("pool_per_cta", "hops_per_epoch", "suspend_lanes",
+                                               "suspend_min_steps")})
+        sid = c.load(s)
+        jobs = lambda r: [dict(structure_id=sid, master=m, walk_budget=budget, sigma_target=sigma,
+                               request_id=r * 4 + i) for i, m in enumerate(s.masters)]
+        c.extract_batch(jobs(7))
+        walks, kms, rows = 0, 0.0, None
+        for k in range(steps):
+            rows, _ = c.extract_batch(jobs(100 + k))
+            walks += sum(r[2]["walks"] for r in rows)
+            kms += rows[0][2]["kernel_ms"]
+        c.close()
+        out.append({"seed": sd, "walks_per_s": walks / (kms / 1e3),
+                    "rows": [{"master": m, "C_ii_fF": float(C[m]), "stderr_fF": float(se[m]), "walks": int(st["walks"])}
+                             for m, (C, se, st) in zip(s.masters, rows)]})
+    return out
 
 
 def structure_bytes(s):
@@ -708,11 +692,13 @@ def main():
         line["batched"] = batched_measurement(a.N, prec, tuning)
         line["microwalk_kernel"] = microwalk_kernel(alu_peak)
         line["fp32_vs_fp64"] = fp32_deviation(s, masters, a.N, a.sigma, a.budget)
+        line["interconnect_seeds"] = interconnect_seeds(a.N, prec, a.sigma, a.budget, tuning)
     if rank == 0 and world == 1 and a.serve_seconds > 0:
+        from paper_2507_09730_gb300 import studies
         line["serving"] = {
             "workload": "Poisson arrivals over 32 structures of 4-200 conductors, N=%d, sigma U[0.5%%, 2%%], "
                         "budget %d per request; served = frw_submit into the running kernel, "
-                        "one_job_per_launch = frw_extract in arrival order, same GPU" % (a.N, SERVE_BUDGET),
+                        "one_job_per_launch = frw_extract in arrival order, same GPU" % (a.N, studies.SERVE_BUDGET),
             "at_200_per_s": serving_measurement(a.N, prec, 200.0, a.serve_seconds),
             "at_25_per_s": serving_measurement(a.N, prec, 25.0, 2.0 * a.serve_seconds)}
     if rank == 0 and world == 1 and not a.no_cpu:

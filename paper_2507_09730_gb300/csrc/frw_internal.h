@@ -261,7 +261,8 @@ struct EngineView {
     uint64_t rec_cap, acc_cap, jsum_cap;   // record, accumulator and running-sum capacities (bounds checks)
     MWJob *mwq;                      // one MicroWalk job record per slot
     TableCache tc;
-    const uint32_t *W;     // [16][16]
+    const uint32_t *W;     // [16][16] quantised alpha of Eq. 6 by global material (row: centre)
+    int wtab_lanes;        // 1: every material id of the context is below 7 (the per-lane table copies)
     const double *eps;     // [16]
     FillConsts fc;
     double *fill_scratch;  // per walk-kernel CTA: fill_stride doubles of table-fill scratch
@@ -308,7 +309,8 @@ cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t p
 size_t fill_smem_bytes(int N);
 size_t mw_smem_bytes(int N, int warps);
 cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uint64_t spc,
-                            uint32_t key0, uint32_t key1, int n_mat, const uint8_t *matmap_local_to_global,
+                            uint32_t key0, uint32_t key1, int n_mat, int n_global_mat,
+                            const uint8_t *matmap_local_to_global,
                             const uint32_t *W, uint32_t *d_exit, uint32_t *d_steps,
                             unsigned long long *d_head, uint32_t *d_err, const LaunchShape &L,
                             cudaStream_t st);

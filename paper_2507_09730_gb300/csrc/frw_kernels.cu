@@ -948,104 +948,288 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
 }
 
 // ---------------------------------------------------------------------------
-// MicroWalk kernel (Algorithm 3).  Per warp, shared memory holds one column of
-// per-axis block masks per lane: mask(a, c) has bit 0 (background) and bit t+1
-// for every listed block whose range on axis a contains c; rows c = -1 and c = N
-// are 0 (boundary).  The material of node (x, y, z) is given by the highest set
-// bit of mask(0,x) & mask(1,y) & mask(2,z) through a 16-entry nibble map.
+// MicroWalk (Algorithm 3).
+//
+// Lattice masks.  Per warp, shared memory holds one column of 16-bit rows per
+// lane, laid out [row][lane] (the 32 lanes of a warp read one row as 64
+// contiguous bytes).  Row R = a (N + 4) + c + 2 for axis a and coordinate
+// c = -2 .. N + 1.  Bit 0 is set in every row, bit 1 in the rows of the interior
+// coordinates 0 .. N - 1, bit 2 + q in the rows whose coordinate lies in listed
+// block q's voxel range on that axis (q < KMAX).  The highest set bit of
+// mask(0, x) & mask(1, y) & mask(2, z) is the slot of node (x, y, z): 0 for a
+// boundary node, 1 for the background, 2 + q for block q (later blocks win).
+// Rows -2 and N + 1 exist so that a walker resting on a boundary node (c = -1 or
+// N) reads its neighbours' rows in bounds.
+//
+// Columns.  A slot's material m is a column of the jump-weight table: column
+// (m + 1) mod 16, so that column 0 is the boundary (material BOUNDARY, also the
+// conductor objects of MicroWalk-E).  A lane keeps its cube's slot -> column
+// bytes in four registers A (slots 0-3), B (4-7), C (8-11), D (12-15) and turns a
+// mask into a column with bfind and prmt (the permute's sign-replicate mode gives
+// 0 for the half of the map a position does not address).
+//
+// Weight table W'[cv][ck]: the quantised alpha of Eq. 6 of a walker on a node of
+// column cv towards a neighbour of column ck (2^24 towards the boundary); row 0,
+// a walker on a boundary or conductor node, is all zeros, so that such a walker
+// stays where it is.  The lattice step therefore needs no branch: blocks of
+// steps run unconditionally and the end of a walk (or of a MicroWalk-E walk on a
+// conductor node) is found once per block, from the steps that started on a
+// node of non-zero column.
 
-__device__ __forceinline__ int mat_of(uint64_t mm, uint32_t mask)
+__device__ __forceinline__ int mask_axis_rows(int N) { return N + 4; }
+__device__ __forceinline__ int mask_rows(int N) { return 3 * (N + 4); }
+
+__device__ __forceinline__ uint32_t bfind_u32(uint32_t m)
 {
-    const int slot = 32 - __clz((int)mask);
-    return (int)((mm >> (4 * slot)) & 15ull);
+    uint32_t p;
+    asm("bfind.u32 %0, %1;" : "=r"(p) : "r"(m));
+    return p;
+}
+__device__ __forceinline__ uint32_t prmt_b32(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// A lane's slot -> column map.  Columns decoded by the wide form (slots 0-15) come
+// out as column + G, G = byte 0 of C replicated into bytes 1-3; the table address
+// of the lane absorbs G (MWTab::bind), so decoding needs no mask.
+struct MWMap {
+    uint32_t A, B, C, D, G;
+};
+// from a nibble map of slot -> material (slot 0 BOUNDARY, 1 background, 2 + q block q)
+__device__ __forceinline__ MWMap mw_map(uint64_t mm)
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const uint32_t m = (uint32_t)(mm >> (4 * (4 * i + b))) & 15u;
+            v |= ((m + 1u) & 15u) << (8 * b);
+        }
+        w[i] = v;
+    }
+    MWMap M;
+    M.A = w[0]; M.B = w[1]; M.C = w[2]; M.D = w[3];
+    M.G = (w[2] & 255u) * 0x01010100u;
+    return M;
 }
 
-// Lattice masks: 16-bit rows, laid out [row][lane] (row R = a * (N + 2) + c + 1 for
-// axis a, coordinate c = -1..N), so the 32 lanes of a warp read one row as 64
-// contiguous bytes, with no bank conflict.  Bit 0: inside the cube; bit q + 1:
-// inside listed block q (q < 14).
-__device__ __forceinline__ int mask_rows(int N) { return 3 * (N + 2); }
-
-// Build lane r's mask column (all 32 lanes cooperate): blocks given as voxel
-// ranges [lo, hi) per axis through rng(q, a, lo, hi).
-template <class RangeFn>
-__device__ __forceinline__ void build_masks(uint16_t *Mw, int r, int N, int lane, int K, RangeFn rng)
+template <bool WIDE>
+__device__ __forceinline__ uint32_t mw_col(uint32_t m, const MWMap &M)
 {
-    const int NP2 = N + 2;
-    for (int row = lane; row < 3 * NP2; row += 32) {
-        const int a = row / NP2;
-        const int c = row - a * NP2 - 1;
-        uint32_t m = 0;
-        if (c >= 0 && c < N) {
-            m = 1u;
-            for (int q = 0; q < K; q++) {
-                int lo, hi;
-                rng(q, a, lo, hi);
-                if (lo <= c && c < hi) m |= 2u << q;
+    const uint32_t pos = bfind_u32(m);   // m always has bit 0
+    if (!WIDE) return prmt_b32(M.A, M.B, pos);               // slots 0-7: exact column
+    return prmt_b32(M.A, M.B, pos) | prmt_b32(M.C, M.D, pos ^ 8u);   // column + G
+}
+
+// Weight table as one lane reads it: byte address of W'[0][0] for this lane and
+// the byte strides of a row and of a column.  Two layouts: a copy per lane of a
+// table of 8 columns ([entry][lane], conflict-free; materials 0-6), or one shared
+// table of 16 columns.
+struct MWTab {
+    uint32_t base, row, col;
+    // the base for the wide decode of a lane whose map has offset G
+    __device__ __forceinline__ uint32_t wide_base(uint32_t G) const { return base - G * row - G * col; }
+    __device__ __forceinline__ MWTab with_base(uint32_t b) const { return MWTab{b, row, col}; }
+};
+constexpr int WTAB_LANES_WORDS = 64 * 32;   // 8 x 8 entries x 32 lanes
+constexpr int WTAB_FULL_WORDS = 256;
+
+__device__ __forceinline__ uint32_t wprime(const uint32_t *__restrict__ Wg, int cv, int ck)
+{
+    return cv == 0 ? 0u : __ldg(&Wg[((cv - 1) & 15) * 16 + ((ck - 1) & 15)]);
+}
+// fill the table (all threads of the block); lanes_layout: the per-lane copies
+__device__ __forceinline__ void wtab_fill(uint32_t *Wt, const uint32_t *__restrict__ Wg, bool lanes_layout, int tid,
+                                          int nthreads)
+{
+    if (lanes_layout) {
+        for (int i = tid; i < WTAB_LANES_WORDS; i += nthreads) {
+            const int e = i >> 5;
+            Wt[i] = wprime(Wg, e >> 3, e & 7);
+        }
+    } else {
+        for (int i = tid; i < WTAB_FULL_WORDS; i += nthreads) Wt[i] = wprime(Wg, i >> 4, i & 15);
+    }
+}
+__device__ __forceinline__ MWTab wtab_lane(const uint32_t *Wt, bool lanes_layout, int lane)
+{
+    MWTab t;
+    if (lanes_layout) {
+        t.base = smem_addr(Wt) + 4u * (uint32_t)lane;
+        t.row = 8u * 128u;
+        t.col = 128u;
+    } else {
+        t.base = smem_addr(Wt);
+        t.row = 64u;
+        t.col = 4u;
+    }
+    return t;
+}
+
+// Every row of the warp's 32 columns set to a boundary row (all nodes boundary
+// nodes, so that a lane without a cube rests).
+__device__ __forceinline__ void masks_clear(uint16_t *Mw, int N, int lane)
+{
+    for (int i = lane; i < mask_rows(N) * 32; i += 32) Mw[i] = 1;
+}
+
+// Build lane r's mask column (all 32 lanes cooperate).  Lane q < K supplies block
+// q's voxel ranges [lo, hi) per axis through rng(lo[3], hi[3]).  Each block's bit
+// is toggled at its lo and hi coordinates in the warp's scratch T (32 words), and
+// a prefix XOR over the coordinates (one lane per coordinate) gives every row:
+// the x and y axes in the low and high halves of one scan, z in a second.
+template <class RangeFn>
+__device__ __forceinline__ void build_masks(uint16_t *Mw, uint32_t *T, int r, int N, int lane, int K, RangeFn rng)
+{
+    const int RA = N + 4;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    if (lane < K) rng(lo, hi);
+    const uint32_t bit = 4u << (lane & 15);
+#pragma unroll
+    for (int pass = 0; pass < 2; pass++) {
+        T[lane] = 0u;
+        __syncwarp();
+        if (lane < K) {
+            if (pass == 0) {
+                atomicXor(&T[lo[0]], bit);
+                if (hi[0] < 32) atomicXor(&T[hi[0]], bit);
+                atomicXor(&T[lo[1]], bit << 16);
+                if (hi[1] < 32) atomicXor(&T[hi[1]], bit << 16);
+            } else {
+                atomicXor(&T[lo[2]], bit);
+                if (hi[2] < 32) atomicXor(&T[hi[2]], bit);
             }
         }
-        Mw[row * 32 + r] = (uint16_t)m;
+        __syncwarp();
+        uint32_t v = T[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t w = __shfl_up_sync(FULL_MASK, v, d);
+            if (lane >= d) v ^= w;
+        }
+        if (lane < N) {
+            if (pass == 0) {
+                Mw[(lane + 2) * 32 + r] = (uint16_t)((v & 0xffffu) | 3u);
+                Mw[(RA + lane + 2) * 32 + r] = (uint16_t)((v >> 16) | 3u);
+            } else {
+                Mw[(2 * RA + lane + 2) * 32 + r] = (uint16_t)((v & 0xffffu) | 3u);
+            }
+        }
+        __syncwarp();
     }
 }
 
-// One step of the lattice walk: weights W[mv][m_k] of Eq. 6 (quantised), integer
-// prefix sums, neighbour chosen by (u * S) >> 32.  Returns 1 on reaching a
-// boundary node, 2 (MWE only) on stepping onto a node of material BOUNDARY inside
-// the lattice (a conductor of a MicroWalk-E cube; slot = its mask slot), else 0.
-// M points at the lane's column (Mw + lane).  The weight table is either one copy
-// per lane (WS = 32: Wl = Wrep + lane, lookups never conflict) or a single shared
-// copy (WS = 1: Wl = W).
-template <int WS, bool MWE>
-__device__ __forceinline__ int mw_step(const uint16_t *__restrict__ M, const uint32_t *__restrict__ Wl, int N,
-                                       int &x, int &y, int &z, uint64_t mm, uint32_t u, int &slot)
+// Row addresses of a lane's column: the byte address of row c = -1 of each axis.
+struct MWRows {
+    uint32_t x, y, z;
+};
+__device__ __forceinline__ MWRows mw_rows(const uint16_t *Mw, int N, int lane)
 {
-    const int AR = (N + 2) * 32;
-    const uint16_t *Mx = M + x * 32, *My = M + AR + y * 32, *Mz = M + 2 * AR + z * 32;
-    const uint32_t xm = Mx[0], x0 = Mx[32], xp = Mx[64];
-    const uint32_t ym = My[0], y0 = My[32], yp = My[64];
-    const uint32_t zm = Mz[0], z0 = Mz[32], zp = Mz[64];
+    const uint32_t m = smem_addr(Mw + lane);
+    const uint32_t RA = (uint32_t)mask_axis_rows(N);
+    return MWRows{m + 64u, m + RA * 64u + 64u, m + 2u * RA * 64u + 64u};
+}
+
+// One step of the lattice walk from node (x, y, z): weights W'[cv][ck] of Eq. 6
+// (quantised) towards the six neighbours (order -x, +x, -y, +y, -z, +z), integer
+// prefix sums p0..p5, r = (u p5) >> 32, the first k with r < p_k taken.  With b_k
+// = [r >= p_k] the move is dx = 2 b0 - 1 - b1, dy = 2 b2 - b1 - b3, dz = 2 b4 -
+// b3 - b5 (b5 = 0 whenever p5 > 0; all six are 1 on a node of column 0, whose
+// weights are all 0, so that the walker does not move).  Returns the column of
+// the node the step started on (+ G in the wide form): equal to G for a walker
+// that rests.
+template <bool WIDE>
+__device__ __forceinline__ uint32_t mw_step(const MWRows &R, const MWTab &T, const MWMap &M, int &x, int &y, int &z,
+                                            uint32_t u)
+{
+    const uint32_t ax = R.x + (uint32_t)x * 64u, ay = R.y + (uint32_t)y * 64u, az = R.z + (uint32_t)z * 64u;
+    const uint32_t xm = lds_u16(ax), x0 = lds_u16(ax + 64u), xp = lds_u16(ax + 128u);
+    const uint32_t ym = lds_u16(ay), y0 = lds_u16(ay + 64u), yp = lds_u16(ay + 128u);
+    const uint32_t zm = lds_u16(az), z0 = lds_u16(az + 64u), zp = lds_u16(az + 128u);
     const uint32_t yz = y0 & z0, xz = x0 & z0, xy = x0 & y0;
-    const int mv = mat_of(mm, xy & z0);
-    const uint32_t *Wr = Wl + mv * 16 * WS;
-    const uint32_t n0 = xm & yz, n1 = xp & yz, n2 = ym & xz, n3 = yp & xz, n4 = zm & xy, n5 = zp & xy;
-    const int m0 = mat_of(mm, n0), m1 = mat_of(mm, n1), m2 = mat_of(mm, n2);
-    const int m3 = mat_of(mm, n3), m4 = mat_of(mm, n4), m5 = mat_of(mm, n5);
-    const uint32_t w0 = Wr[m0 * WS];
-    const uint32_t w1 = Wr[m1 * WS];
-    const uint32_t w2 = Wr[m2 * WS];
-    const uint32_t w3 = Wr[m3 * WS];
-    const uint32_t w4 = Wr[m4 * WS];
-    const uint32_t w5 = Wr[m5 * WS];
+    const uint32_t ev = mw_col<WIDE>(xy & z0, M);
+    const uint32_t wr = T.base + ev * T.row;
+    const uint32_t w0 = lds_u32(wr + mw_col<WIDE>(xm & yz, M) * T.col);
+    const uint32_t w1 = lds_u32(wr + mw_col<WIDE>(xp & yz, M) * T.col);
+    const uint32_t w2 = lds_u32(wr + mw_col<WIDE>(ym & xz, M) * T.col);
+    const uint32_t w3 = lds_u32(wr + mw_col<WIDE>(yp & xz, M) * T.col);
+    const uint32_t w4 = lds_u32(wr + mw_col<WIDE>(zm & xy, M) * T.col);
+    const uint32_t w5 = lds_u32(wr + mw_col<WIDE>(zp & xy, M) * T.col);
     const uint32_t p0 = w0, p1 = p0 + w1, p2 = p1 + w2, p3 = p2 + w3, p4 = p3 + w4, p5 = p4 + w5;
     const uint32_t r = __umulhi(u, p5);
-    const int k = (int)(r >= p0) + (int)(r >= p1) + (int)(r >= p2) + (int)(r >= p3) + (int)(r >= p4);
-    const int d = (k & 1) ? 1 : -1;
-    const int ax = k >> 1;
-    x += (ax == 0) ? d : 0;
-    y += (ax == 1) ? d : 0;
-    z += (ax == 2) ? d : 0;
-    if (((unsigned)x >= (unsigned)N) | ((unsigned)y >= (unsigned)N) | ((unsigned)z >= (unsigned)N)) return 1;
-    if (MWE) {
-        const int mk = k == 0 ? m0 : k == 1 ? m1 : k == 2 ? m2 : k == 3 ? m3 : k == 4 ? m4 : m5;
-        if (mk == BOUNDARY) {
-            const uint32_t nk = k == 0 ? n0 : k == 1 ? n1 : k == 2 ? n2 : k == 3 ? n3 : k == 4 ? n4 : n5;
-            slot = 32 - __clz((int)nk);
-            return 2;
-        }
-    }
-    return 0;
+    const int b0 = r >= p0, b1 = r >= p1, b2 = r >= p2, b3 = r >= p3, b4 = r >= p4, b5 = r >= p5;
+    x += 2 * b0 - 1 - b1;
+    y += 2 * b2 - b1 - b3;
+    z += 2 * b4 - b3 - b5;
+    return ev;
 }
 
-// replicate the 16 x 16 weight table once per lane: Wrep[entry * 32 + lane]
-__device__ __forceinline__ void replicate_w(uint32_t *Wrep, const uint32_t *__restrict__ Wg)
+// slot of node (x, y, z) (MicroWalk-E: which object a walker rests on)
+__device__ __forceinline__ int mw_slot_at(const MWRows &R, int x, int y, int z)
 {
-    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) Wrep[i] = Wg[i >> 5];
+    const uint32_t m = lds_u16(R.x + (uint32_t)x * 64u + 64u) & lds_u16(R.y + (uint32_t)y * 64u + 64u) &
+                       lds_u16(R.z + (uint32_t)z * 64u + 64u);
+    return (int)bfind_u32(m);
 }
 
+// Four steps with the words of one Philox block; returns the steps that started
+// on a node of non-zero column (the walk's own steps).  T: the lane's table with
+// the base for this decode form (MWLane::base_n or base_w).
+template <bool WIDE>
+__device__ __forceinline__ uint32_t mw_block4(const MWRows &R, const MWTab &T, const MWMap &M, int &x, int &y, int &z,
+                                              uint4 w)
+{
+    const uint32_t rest = WIDE ? M.G : 0u;
+    uint32_t moved = 0;
+    moved += mw_step<WIDE>(R, T, M, x, y, z, w.x) != rest;
+    moved += mw_step<WIDE>(R, T, M, x, y, z, w.y) != rest;
+    moved += mw_step<WIDE>(R, T, M, x, y, z, w.z) != rest;
+    moved += mw_step<WIDE>(R, T, M, x, y, z, w.w) != rest;
+    return moved;
+}
+
+// A lane's walk: identity, cube (block count, column map) and the table bases for
+// the narrow and the wide decode.  A warp runs the wide decode while any of its
+// walking lanes holds more than 6 blocks; every lane, walking or resting, then
+// reads its table through the base of the form in use.
 struct MWLane {
     uint32_t walk_lo, walk_hi, hop, key0, key1, tag;
-    uint64_t mm;
+    int K;
+    MWMap map;
+    uint32_t base_n, base_w;
 };
+__device__ __forceinline__ void mw_lane_cube(MWLane &L, const MWTab &T0, int K, uint64_t mm)
+{
+    L.K = K;
+    L.map = mw_map(mm);
+    L.base_n = T0.base;
+    L.base_w = T0.wide_base(L.map.G);
+}
+__device__ __forceinline__ void mw_lane_reset(MWLane &L, const MWTab &T0)
+{
+    L.walk_lo = L.walk_hi = L.hop = L.key0 = L.key1 = L.tag = 0;
+    L.K = 0;
+    L.map = MWMap{0u, 0u, 0u, 0u, 0u};
+    L.base_n = L.base_w = T0.base;
+}
 
 // Job source: stand-alone cubes given as integer voxel ranges (64 int32 per cube).
 struct CubeSource {
@@ -1058,10 +1242,12 @@ struct CubeSource {
     uint32_t *err;
     int N;
     int n_mat;               // material ids of the records index 0 .. n_mat - 1
+    int lanes_table;         // 1: per-lane weight-table copies (global materials 0-6)
     __device__ uint64_t grab(uint32_t n) const { return atomicAdd(head, (unsigned long long)n); }
     __device__ void overrun() const { atomicOr(err, ERR_MW_STEPS); }
     __device__ bool valid(uint64_t j) const { return j < total; }
     __device__ int gmat(int local) const { return (int)((mmap_lo >> (4 * (local & 15))) & 15ull); }
+    __device__ uint64_t cube_of(uint64_t j) const { return j / spc; }
     // A record is usable when 0 <= K <= 8 (what 64 words hold), every material id
     // is below n_mat and every block range satisfies 0 <= lo < hi <= N.
     __device__ bool record_ok(const int32_t *c) const
@@ -1078,18 +1264,21 @@ struct CubeSource {
         }
         return true;
     }
-    __device__ void build(uint64_t j, uint16_t *Mw, int r, int N_, int lane) const
+    // (all lanes) build lane r's masks for cube `cube`; malformed records build none
+    __device__ void build(uint64_t cube, uint16_t *Mw, uint32_t *T, int r, int N_, int lane) const
     {
-        const int32_t *c = cubes + (j / spc) * 64;
-        const int K = min(max(c[1], 0), 8);   // a 64-word record holds at most 8 blocks
-        build_masks(Mw, r, N_, lane, K, [&](int q, int a, int &lo, int &hi) {
-            lo = c[2 + 7 * q + 2 * a];
-            hi = c[3 + 7 * q + 2 * a];
+        const int32_t *c = cubes + cube * 64;
+        const int K = record_ok(c) ? c[1] : 0;   // a 64-word record holds at most 8 blocks
+        build_masks(Mw, T, r, N_, lane, K, [&](int lo[3], int hi[3]) {
+            for (int a = 0; a < 3; a++) {
+                lo[a] = c[2 + 7 * lane + 2 * a];
+                hi[a] = c[3 + 7 * lane + 2 * a];
+            }
         });
     }
     // false (and the error flag set) for a malformed record: the sample is then
     // written as exit 0, 0 steps and not walked
-    __device__ bool load(uint64_t j, MWLane &L, int &x, int &y, int &z) const
+    __device__ bool load(uint64_t j, MWLane &L, const MWTab &T0, int &x, int &y, int &z) const
     {
         const int32_t *c = cubes + (j / spc) * 64;
         if (!record_ok(c)) {
@@ -1101,7 +1290,7 @@ struct CubeSource {
         const int K = c[1];
         uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)gmat(c[0]) << 4);
         for (int t = 0; t < K; t++) mm |= (uint64_t)gmat(c[2 + 7 * t + 6]) << (4 * (t + 2));
-        L.mm = mm;
+        mw_lane_cube(L, T0, K, mm);
         L.walk_lo = (uint32_t)j;
         L.walk_hi = (uint32_t)(j >> 32);
         L.hop = 0;
@@ -1126,23 +1315,32 @@ struct CubeSource {
 
 constexpr uint32_t MW_STEP_CAP = 1u << 26;
 
+// Stand-alone MicroWalk over a job source.  Per lane: one walk at a time, in
+// blocks of 8 steps (two Philox blocks); a lane whose walk ended rests on a
+// boundary node until it is refilled at the next block boundary.  A lane that
+// takes its next sample on the cube it already holds keeps its masks.  Warps use
+// the narrow column decode while every cube they hold has at most 6 blocks.
 template <class Src>
 __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict__ Wg, int N)
 {
     extern __shared__ uint32_t smem[];
-    uint32_t *Wrep = smem;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint16_t *Mw = reinterpret_cast<uint16_t *>(smem + 256 * 32) + (size_t)warp * mask_rows(N) * 32;
-    replicate_w(Wrep, Wg);
+    const bool lanes_table = src.lanes_table != 0;
+    uint32_t *Wt = smem;
+    const int wt_words = lanes_table ? WTAB_LANES_WORDS : WTAB_FULL_WORDS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t *Tw = smem + wt_words + warp * 32;
+    uint16_t *Mw = reinterpret_cast<uint16_t *>(smem + wt_words + nwarps * 32) + (size_t)warp * mask_rows(N) * 32;
+    wtab_fill(Wt, Wg, lanes_table, threadIdx.x, blockDim.x);
+    masks_clear(Mw, N, lane);
     __syncthreads();
-    const uint16_t *M = Mw + lane;
-    const uint32_t *Wl = Wrep + lane;
+    const MWRows R = mw_rows(Mw, N, lane);
+    const MWTab T0 = wtab_lane(Wt, lanes_table, lane);
     bool active = false, exhausted = false;
-    int x = 0, y = 0, z = 0;
+    int x = -1, y = 0, z = 0;
     uint32_t t = 0;
+    uint64_t held = ~0ull;   // cube whose masks this lane's column holds
     MWLane L;
-    L.walk_lo = L.walk_hi = L.hop = L.key0 = L.key1 = L.tag = 0;
-    L.mm = 0;
+    mw_lane_reset(L, T0);
     for (;;) {
         const bool need = !active && !exhausted;
         const uint32_t bal = __ballot_sync(FULL_MASK, need);
@@ -1154,39 +1352,48 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
             const uint64_t myj = base + (uint64_t)__popc(bal & ((1u << lane) - 1u));
             const bool got = need && src.valid(myj);
             if (need && !got) exhausted = true;
-            uint32_t todo = __ballot_sync(FULL_MASK, got);
+            const uint64_t cube = got ? src.cube_of(myj) : held;
+            uint32_t todo = __ballot_sync(FULL_MASK, got && cube != held);
             while (todo) {
                 const int r = __ffs(todo) - 1;
                 todo &= todo - 1u;
-                const uint64_t jr = __shfl_sync(FULL_MASK, myj, r);
-                src.build(jr, Mw, r, N, lane);
+                const uint64_t cr = __shfl_sync(FULL_MASK, cube, r);
+                src.build(cr, Mw, Tw, r, N, lane);
             }
             __syncwarp();
             if (got) {
+                held = cube;
                 t = 0;
-                active = src.load(myj, L, x, y, z);
+                active = src.load(myj, L, T0, x, y, z);
+                if (!active) { x = -1; y = 0; z = 0; }
             }
         }
         if (__ballot_sync(FULL_MASK, active) == 0u) break;
-        if (active) {
-            const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
-            const uint32_t words[4] = {blk.x, blk.y, blk.z, blk.w};
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (active) {
-                    int slot_unused = 0;
-                    if (mw_step<32, false>(M, Wl, N, x, y, z, L.mm, words[k], slot_unused)) {
-                        src.finish(L, x, y, z, t + (uint32_t)k + 1u);
-                        active = false;
-                    }
-                }
-            }
-            t += 4;
-            if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
-                src.overrun();
-                src.finish(L, x, y, z, t);
-                active = false;
-            }
+        const bool wide = __any_sync(FULL_MASK, active && L.K > 6);
+        uint32_t moved;
+        const uint4 b0 = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
+        const uint4 b1 = philox10(L.walk_lo, L.walk_hi, L.hop, 2u + (t >> 2), L.key0, L.key1);
+        if (wide) {
+            const MWTab T = T0.with_base(L.base_w);
+            moved = mw_block4<true>(R, T, L.map, x, y, z, b0);
+            moved += mw_block4<true>(R, T, L.map, x, y, z, b1);
+        } else {
+            const MWTab T = T0.with_base(L.base_n);
+            moved = mw_block4<false>(R, T, L.map, x, y, z, b0);
+            moved += mw_block4<false>(R, T, L.map, x, y, z, b1);
+        }
+        const bool inside = ((unsigned)x < (unsigned)N) & ((unsigned)y < (unsigned)N) & ((unsigned)z < (unsigned)N);
+        if (active && (moved < 8u || !inside)) {   // on a boundary node: the walk has ended
+            src.finish(L, x, y, z, t + moved);
+            active = false;
+            x = -1; y = 0; z = 0;
+        }
+        t += 8;
+        if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
+            src.overrun();
+            src.finish(L, x, y, z, t);
+            active = false;
+            x = -1; y = 0; z = 0;
         }
         __syncwarp();
     }
@@ -1690,14 +1897,6 @@ __device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 #define FRW_FILL_GLOBAL 0
 #endif
 constexpr int WALK_THREADS = FRW_WALK_THREADS;
-// 1: the walk kernel's MicroWalk loop keeps one copy of the lattice step (the four
-// steps of a Philox block in a loop that is not unrolled): less code competes with
-// the geometry phase's for the instruction cache (+19 % walks/s in budget mode on
-// the interconnect workload; the stand-alone MicroWalk kernel, alone on its SMs,
-// keeps the unrolled form)
-#ifndef FRW_MW_COMPACT
-#define FRW_MW_COMPACT 1
-#endif
 // 1: the walk kernel's table fill works in global scratch (per CTA) instead of
 // shared memory, so that the shared region holds only the MicroWalk masks
 constexpr bool FILL_GLOBAL = FRW_FILL_GLOBAL != 0;
@@ -1725,7 +1924,9 @@ __device__ __forceinline__ long long clock_after(const uint32_t *anchor)
 constexpr uint32_t FDM_CLAIM_CAP = 8;    // FRW-FDM: walk ids a CTA claims per epoch
 
 struct WalkShared {
-    uint32_t W[256];                 // quantised weights of Eq. 6, [centre][neighbour material]
+    uint32_t W[WTAB_FULL_WORDS];     // jump-weight table W'[centre column][neighbour column] (one copy)
+    uint32_t Wl[WTAB_LANES_WORDS];   // the same table of 8 columns, one copy per lane (materials 0-6)
+    uint32_t scan[32 * (FRW_WALK_THREADS / 32)];   // per-warp scratch of the mask build
     uint32_t g_head, g_back, pad3[2];
     uint32_t q_count, q_head, s_count, g_count;
     uint32_t f_count, active, issuable, stop;
@@ -1746,16 +1947,19 @@ size_t fill_smem_bytes(int N)
     return sizeof(double) * (size_t)(MAXN + H * H * N + MAXN * MAXN + FILL_CHUNKS + 1);
 }
 
+// stand-alone MicroWalk CTA: weight table (the larger, per-lane layout), one
+// 32-word scan scratch per warp, the warps' mask columns
 size_t mw_smem_bytes(int N, int warps)
 {
-    return sizeof(uint32_t) * 256 * 32 + sizeof(uint16_t) * (size_t)warps * 3 * (N + 2) * 32;
+    return sizeof(uint32_t) * (WTAB_LANES_WORDS + 32 * (size_t)warps) +
+           sizeof(uint16_t) * (size_t)warps * 3 * (N + 4) * 32;
 }
 
 // dynamic shared memory of the walk kernel: one region shared in turn by the
 // MicroWalk masks, the table fill and the reduction
 size_t walk_scratch_bytes(int N, int max_nc)
 {
-    const size_t masks = sizeof(uint16_t) * (size_t)MW_WARPS * 3 * (N + 2) * 32;
+    const size_t masks = sizeof(uint16_t) * (size_t)MW_WARPS * 3 * (N + 4) * 32;
     const size_t fill = FILL_GLOBAL ? 0 : fill_smem_bytes(N);
     const size_t red = sizeof(unsigned long long) * acc_stride_for(max_nc);
     return std::max(masks, std::max(fill, red));
@@ -1790,7 +1994,8 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
     const uint32_t base = blockIdx.x * P;
     unsigned char *dsm = dsm_all;
     double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.fill_stride;
-    for (int i = tid; i < 256; i += WALK_THREADS) sh.W[i] = E.W[i];
+    wtab_fill(sh.W, E.W, false, tid, WALK_THREADS);
+    if (E.wtab_lanes) wtab_fill(sh.Wl, E.W, true, tid, WALK_THREADS);
     for (uint32_t o = tid; o < P; o += WALK_THREADS) {
         const uint32_t s = base + o;
         E.s.state[s] = ST_FRESH;
@@ -1924,17 +2129,20 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
             }
         } else {
             // ---------------- MicroWalk ----------------
-            const int mwarp = warp;
-            uint16_t *Mw = reinterpret_cast<uint16_t *>(dsm) + (size_t)mwarp * mask_rows(N) * 32;
-            const uint16_t *M = Mw + lane;
-            const uint32_t *Wl = sh.W;
+            // (masks re-cleared: the fill and reduction phases use the same region)
+            uint16_t *Mw = reinterpret_cast<uint16_t *>(dsm) + (size_t)warp * mask_rows(N) * 32;
+            uint32_t *Tw = sh.scan + warp * 32;
+            masks_clear(Mw, N, lane);
+            __syncwarp();
+            const MWRows R = mw_rows(Mw, N, lane);
+            const bool lanes_table = E.wtab_lanes != 0;
+            const MWTab T0 = wtab_lane(lanes_table ? sh.Wl : sh.W, lanes_table, lane);
             const uint32_t qn = sh.q_count;
             bool active = false, exhausted = false;
-            int x = 0, y = 0, z = 0;
+            int x = -1, y = 0, z = 0;
             uint32_t t = 0, t_in = 0, my_o = 0;
             MWLane L;
-            L.walk_lo = L.walk_hi = L.hop = L.key0 = L.key1 = L.tag = 0;
-            L.mm = 0;
+            mw_lane_reset(L, T0);
             for (;;) {
                 const bool need = !active && !exhausted;
                 const uint32_t bal = __ballot_sync(FULL_MASK, need);
@@ -1954,10 +2162,11 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                         const uint32_t orr = __shfl_sync(FULL_MASK, oj, r);
                         const MWJob &b = E.mwq[base + orr];
                         const int K = min((int)b.K, KMAX);
-                        build_masks(Mw, r, N, lane, K, [&](int q, int a, int &lo, int &hi) {
-                            const uint2 rr = b.rng[q];
-                            lo = rng_lo(rr, a);
-                            hi = rng_hi(rr, a);
+                        build_masks(Mw, Tw, r, N, lane, K, [&](int lo[3], int hi[3]) {
+                            const uint2 rr = b.rng[lane];
+                            lo[0] = (int)(rr.x & 255u); hi[0] = (int)((rr.x >> 8) & 255u);
+                            lo[1] = (int)((rr.x >> 16) & 255u); hi[1] = (int)(rr.x >> 24);
+                            lo[2] = (int)(rr.y & 255u); hi[2] = (int)((rr.y >> 8) & 255u);
                         });
                     }
                     __syncwarp();
@@ -1965,12 +2174,17 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                         const MWJob &b = E.mwq[base + oj];
                         L.walk_lo = b.walk_lo; L.walk_hi = b.walk_hi; L.hop = b.hop;
                         L.key0 = b.key0; L.key1 = b.key1; L.tag = b.slot;
-                        L.mm = (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32);
+                        mw_lane_cube(L, T0, min((int)b.K, KMAX), (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32));
                         x = (int)(b.start & 255u); y = (int)((b.start >> 8) & 255u); z = (int)((b.start >> 16) & 255u);
                         t = b.pad0;
                         t_in = t;
                         my_o = oj;
                         active = true;
+                        if (!FRW_CHECKED(E, (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N &&
+                                                (unsigned)z < (unsigned)N)) {
+                            active = false;
+                            x = -1; y = 0; z = 0;
+                        }
                     }
                 }
                 const uint32_t ab = __ballot_sync(FULL_MASK, active);
@@ -1983,7 +2197,9 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                 const bool other_work = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.finished >=
                                                                            SUSPEND_MIN_FINISHED || sh.issuable), 0) != 0u;
                 if (qexh && progressed && other_work && __popc(ab) <= E.suspend_lanes) {
-                    if (active) {
+                    if (active && FRW_CHECKED(E, (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N &&
+                                                     (unsigned)z < (unsigned)N)) {
+                        // a walking lane is always on a node inside the lattice here
                         MWJob &b = E.mwq[base + my_o];
                         b.start = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16);
                         b.pad0 = t;
@@ -1994,68 +2210,42 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     }
                     break;
                 }
-                if (active && !FRW_CHECKED(E, (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N &&
-                                                   (unsigned)z < (unsigned)N))
+                // four steps without a branch; a lane without a walk rests on a boundary node
+                const bool wide = __any_sync(FULL_MASK, active && L.K > 6);
+                const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
+                const uint32_t moved = wide ? mw_block4<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk)
+                                            : mw_block4<false>(R, T0.with_base(L.base_n), L.map, x, y, z, blk);
+                const bool inside = ((unsigned)x < (unsigned)N) & ((unsigned)y < (unsigned)N) & ((unsigned)z < (unsigned)N);
+                if (active && (moved < 4u || !inside)) {
+                    // the walk has ended: on a boundary node (the exit node; reached at any of
+                    // the four steps), or (MicroWalk-E) it rests on a conductor node inside the
+                    // expanded cube (conductor flagged by bit 31)
+                    const uint32_t sl2 = L.tag;
+                    uint32_t en = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+                    if (MWE && inside) {
+                        const int slot = mw_slot_at(R, x, y, z);
+                        en = FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
+                                 ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                                 : 0x80000000u;
+                    }
+                    E.s.exitnode[sl2] = en;
+                    E.s.steps[sl2] += t + moved;
+                    __threadfence_block();      // exit data before the state (read by geometry warps)
+                    E.s.state[sl2] = ST_MWDONE;
                     active = false;
-                if (active) {
-                    const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
-#if FRW_MW_COMPACT
-                    // one copy of the step in the loop body (smaller code next to the geometry phase's)
-                    int k = 0, code = 0, slot = 0;
-#pragma unroll 1
-                    for (; k < 4; k++) {
-                        const uint32_t u = k == 0 ? blk.x : k == 1 ? blk.y : k == 2 ? blk.z : blk.w;
-                        code = mw_step<1, MWE>(M, Wl, N, x, y, z, L.mm, u, slot);
-                        if (code) break;
-                    }
-                    if (code) {
-                        const uint32_t sl2 = L.tag;
-                        // exit node, or (MicroWalk-E) the conductor reached, flagged by bit 31
-                        E.s.exitnode[sl2] =
-                            code == 2 ? (FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
-                                             ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
-                                             : 0x80000000u)
-                                      : ((uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16));
-                        E.s.steps[sl2] += t + (uint32_t)k + 1u;
-                        __threadfence_block();      // exit data before the state (read by geometry warps)
-                        E.s.state[sl2] = ST_MWDONE;
-                        active = false;
-                        atomicAdd(&sh.finished, 1u);
-                    }
-#else
-                    const uint32_t words[4] = {blk.x, blk.y, blk.z, blk.w};
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        if (active) {
-                            int slot = 0;
-                            const int code = mw_step<1, MWE>(M, Wl, N, x, y, z, L.mm, words[k], slot);
-                            if (code) {
-                                const uint32_t sl2 = L.tag;
-                                // exit node, or (MicroWalk-E) the conductor reached, flagged by bit 31
-                                E.s.exitnode[sl2] =
-                                    code == 2 ? (FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
-                                                     ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
-                                                     : 0x80000000u)
-                                              : ((uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16));
-                                E.s.steps[sl2] += t + (uint32_t)k + 1u;
-                                __threadfence_block();      // exit data before the state (read by geometry warps)
-                                E.s.state[sl2] = ST_MWDONE;
-                                active = false;
-                                atomicAdd(&sh.finished, 1u);
-                            }
-                        }
-                    }
-#endif
-                    t += 4;
-                    if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
-                        atomicOr(&E.status[STAT_ERR], ERR_MW_STEPS);
-                        const uint32_t sl2 = L.tag;
-                        E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
-                        E.s.steps[sl2] += t;
-                        __threadfence_block();
-                        E.s.state[sl2] = ST_MWDONE;
-                        active = false;
-                    }
+                    x = -1; y = 0; z = 0;
+                    atomicAdd(&sh.finished, 1u);
+                }
+                t += 4;
+                if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
+                    atomicOr(&E.status[STAT_ERR], ERR_MW_STEPS);
+                    const uint32_t sl2 = L.tag;
+                    E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+                    E.s.steps[sl2] += t;
+                    __threadfence_block();
+                    E.s.state[sl2] = ST_MWDONE;
+                    active = false;
+                    x = -1; y = 0; z = 0;
                 }
                 __syncwarp();
             }
@@ -2273,7 +2463,7 @@ cudaError_t launch_fill_one(const EngineView &E, uint32_t kind, const uint32_t p
 }
 
 cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uint64_t spc, uint32_t key0,
-                            uint32_t key1, int n_mat, const uint8_t *map, const uint32_t *W, uint32_t *d_exit,
+                            uint32_t key1, int n_mat, int n_global_mat, const uint8_t *map, const uint32_t *W, uint32_t *d_exit,
                             uint32_t *d_steps, unsigned long long *d_head, uint32_t *d_err,
                             const LaunchShape &L, cudaStream_t st)
 {
@@ -2293,6 +2483,7 @@ cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uin
     src.d_steps = d_steps;
     src.N = N;
     src.n_mat = n_mat;
+    src.lanes_table = n_global_mat <= 7 ? 1 : 0;   // columns 0-7 only: the per-lane table copies
     const int threads = 32 * L.mw_warps;
     k_mw<CubeSource><<<L.sms * L.mw_ctas_per_sm, threads, mw_smem_bytes(N, L.mw_warps), st>>>(src, W, N);
     return cudaGetLastError();
@@ -2383,7 +2574,7 @@ extern "C" int frw_microwalk_cubes_noalloc(int32_t N, int32_t n_cubes, const int
     if (cudaMemcpyAsync(scr + NOALLOC_W_OFFSET, W, sizeof(W), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FRW_EDEVICE;
     const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32) ^ (uint32_t)request_id;
-    if (launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, n_mat, map, scr + NOALLOC_W_OFFSET,
+    if (launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, n_mat, n_mat, map, scr + NOALLOC_W_OFFSET,
                         d_exit, d_steps, reinterpret_cast<unsigned long long *>(scr), scr + 2, L,
                         st) != cudaSuccess)
         return FRW_EDEVICE;

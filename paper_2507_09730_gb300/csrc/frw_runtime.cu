@@ -202,6 +202,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.mwq = ctx->mwq;
     E.tc = ctx->tc;
     E.W = ctx->d_W;
+    E.wtab_lanes = ctx->eps.size() <= 7 ? 1 : 0;
     E.eps = ctx->d_eps;
     E.fc = ctx->fc;
     E.status = ctx->status;
@@ -1529,7 +1530,8 @@ extern "C" int frw_microwalk_cubes(frw_ctx *ctx, int32_t N, int32_t n_cubes, con
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st);
     const uint32_t key0 = (uint32_t)ctx->opt.seed, key1 = (uint32_t)(ctx->opt.seed >> 32) ^ (uint32_t)request_id;
     if (e == cudaSuccess)
-        e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, n_mat, map.data(), ctx->d_W, d_exit,
+        e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, samples_per_cube, key0, key1, n_mat, (int)ctx->eps.size(),
+                            map.data(), ctx->d_W, d_exit,
                             d_steps, d_head, ctx->status + STAT_ERR, ctx->shape, st);
     if (e != cudaSuccess) {
         for (void *p : tmp) cudaFree(p);
@@ -2260,7 +2262,8 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
                 if ((e = cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), st)) != cudaSuccess) break;
                 if ((e = cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st)) != cudaSuccess) break;
                 if ((e = cudaEventRecord(ctx->ev[2], st)) != cudaSuccess) break;
-                e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, spc, 1u, 2u, 4, map.data(), ctx->d_W, d_exit, d_steps,
+                e = launch_mw_cubes(N, d_cubes, (uint64_t)n_cubes, spc, 1u, 2u, 4, (int)ctx->eps.size(), map.data(),
+                                    ctx->d_W, d_exit, d_steps,
                                     d_head, ctx->status + STAT_ERR, L, st);
                 if (e != cudaSuccess) break;
                 if ((e = cudaEventRecord(ctx->ev[3], st)) != cudaSuccess) break;

@@ -12,7 +12,17 @@ nsweep   the interconnect extraction (3 masters, 0.5 % sigma, FP32 geometry)
          at several lattice edges N (Fig. 5a: how the work splits with N):
          walks/s, hops and MicroWalk steps per walk, phase shares of the walk
          kernel.
-Prints one JSON line per N.
+serving  the serving configuration: Poisson arrivals over a pool of 32
+         interconnect-style structures of 4-200 conductors, N = 24, FP32
+         geometry, 1-sigma targets U[0.5 %, 2 %], budget 4e6 walks per request;
+         served through frw_submit (admitted into the running walk kernel) and,
+         on the same arrival times, one request per launch (frw_extract): p50 /
+         p99 latency from arrival to completion, walks/s, identical results.
+         First the configuration as stated (200 requests/s for 60 s), then a
+         rate sweep over shorter windows to find the highest rate the GPU
+         sustains (the served p99 stays near the service time instead of
+         growing with the window).
+Prints one JSON line per case (per N, per rate).
 """
 from __future__ import annotations
 
@@ -101,8 +111,73 @@ def n_sweep(Ns=(8, 12, 16, 20, 24, 32), sigma=0.005, steps=2):
     return out
 
 
+SERVE_BUDGET = 4_000_000     # walk budget (cap) of one served request
+
+
+def serving_point(N, precision, rate, duration, seed=0, baseline=True):
+    """One serving measurement (see the module doc): requests drawn for `rate`
+    per second over `duration` seconds, served, then (baseline) replayed one
+    per launch; latency = completion - arrival."""
+    import time
+    pool = W.serving_pool(32)
+    reqs = W.serving_requests(pool, rate=rate, duration=duration, seed=seed)
+    ctx = B.Context(0, N=N, precision=precision, seed=0, serve_arena_mb=16384, serve_jobs=4096)
+    sids = [ctx.load(st) for st in pool]
+    ctx.extract_batch([dict(structure_id=sid, master=m, walk_budget=20000, request_id=1 + m)
+                       for sid, st in zip(sids, pool) for m in range(0, st.n_cond, max(1, st.n_cond // 4))])
+
+    def job(i, r):
+        return dict(structure_id=sids[r.structure], master=r.master, walk_budget=SERVE_BUDGET, sigma_target=r.sigma,
+                    request_id=10_000 + i)
+
+    t0 = time.perf_counter()
+    tickets = []
+    for i, r in enumerate(reqs):
+        dt = r.t - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(ctx.submit(job(i, r)))
+    lat, walks, rows = [], 0, []
+    for t in tickets:
+        C, se, st, conv = ctx.wait(t)
+        lat.append(st["seconds"])
+        walks += st["walks"]
+        rows.append(C)
+    span = time.perf_counter() - t0
+    out = {"rate_per_s": rate, "arrival_window_s": duration, "requests": len(reqs),
+           "walks_per_request": walks / max(1, len(reqs)),
+           "served": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                      "walks_per_s": walks / span, "makespan_s": span}}
+    if baseline:
+        t0 = time.perf_counter()
+        lat_b, walks_b, same = [], 0, 0
+        for i, r in enumerate(reqs):
+            dt = r.t - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            C, se, st, conv = ctx.extract(sids[r.structure], r.master, SERVE_BUDGET, r.sigma, 10_000 + i)
+            lat_b.append(time.perf_counter() - t0 - r.t)
+            walks_b += st["walks"]
+            same += int(np.array_equal(C, rows[i]))
+        span_b = time.perf_counter() - t0
+        out["one_job_per_launch"] = {"p50_s": float(np.percentile(lat_b, 50)),
+                                     "p99_s": float(np.percentile(lat_b, 99)),
+                                     "walks_per_s": walks_b / span_b, "makespan_s": span_b}
+        out["identical_results"] = same
+    ctx.close()
+    return out
+
+
+def serving(N=24, rates=(25, 50, 75, 100, 125, 150), window=15.0):
+    """The serving configuration as stated, then the rate sweep (module doc)."""
+    out = [dict(case="configuration 4 as stated", **serving_point(N, B.FRW_FP32_GEOM, 200.0, 60.0))]
+    for r in rates:
+        out.append(dict(case="rate sweep", **serving_point(N, B.FRW_FP32_GEOM, float(r), window)))
+    return out
+
+
 if __name__ == "__main__":
     case = sys.argv[1]
-    rows = {"tau": expected_steps, "nsweep": n_sweep}[case]()
+    rows = {"tau": expected_steps, "nsweep": n_sweep, "serving": serving}[case]()
     for r in rows:
         print(json.dumps(r), flush=True)
