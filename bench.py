@@ -78,9 +78,12 @@ def case_microwalk():
     st = torch.empty(n_cubes * spc, dtype=torch.int32, device="cuda")
     c = B.Context(0, N=N, slots=1 << 12)
     for r in range(2):
+        t0 = time.perf_counter()
         B.frw_microwalk_cubes(c.ctx, N, n_cubes, rec.data_ptr(), cubes.eps, spc, r, ex.data_ptr(), st.data_ptr())
-    torch.cuda.synchronize()
-    print(f"MicroWalk kernel: {n_cubes * spc} samples, {int(st.to(torch.int64).sum().item())} steps")
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    steps = int(st.to(torch.int64).sum().item())
+    print(f"MicroWalk kernel: {n_cubes * spc} samples, {steps} steps, {1e3 * dt:.2f} ms ({steps / dt:.3e} steps/s)")
     c.close()
 
 

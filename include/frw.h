@@ -307,6 +307,10 @@ typedef struct {
     int32_t mw_warps_per_cta;  /* stand-alone MicroWalk kernel: warps per CTA (1 .. 16) */
     int32_t mw_ctas_per_sm;    /* ... CTAs per SM (1 .. 32) */
     int32_t suspend_min_steps; /* ... once each of them has made this many steps in the epoch (4 .. 4096) */
+    int32_t geo_warps;         /* 0: the walk kernel alternates geometry and MicroWalk phases with all its
+                                  warps; 1 .. 13: it runs this many warps per CTA on geometry and the
+                                  others on MicroWalk at the same time (the pool then at most 2048) */
+    int32_t reserved;
     double walks_per_s;        /* frw_autotune: measured with the chosen walk-kernel settings */
     double mw_steps_per_s;     /* frw_autotune: measured with the chosen MicroWalk shape */
 } frw_tuning;

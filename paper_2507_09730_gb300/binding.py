@@ -72,6 +72,7 @@ class frw_job(ctypes.Structure):
 class frw_tuning(ctypes.Structure):
     _fields_ = [("pool_per_cta", c_int32), ("hops_per_epoch", c_int32), ("suspend_lanes", c_int32),
                 ("mw_warps_per_cta", c_int32), ("mw_ctas_per_sm", c_int32), ("suspend_min_steps", c_int32),
+                ("geo_warps", c_int32), ("reserved", c_int32),
                 ("walks_per_s", c_double), ("mw_steps_per_s", c_double)]
 
     def as_dict(self):

@@ -275,6 +275,7 @@ struct EngineView {
     int mwe;               // MicroWalk-E expansion factor (0 or 1: plain MicroWalk)
     int transition;        // non-stratified transitions: 0 MicroWalk, 1 FD solve (FRW-FDM)
     unsigned char *fdm_scratch;   // FRW-FDM: per walk-kernel CTA, fdm_cube_scratch_bytes(N)
+    int geo_warps;         // 0: phased walk kernel; else warps per CTA on geometry (warp-specialised kernel)
     int suspend_lanes;     // a MicroWalk warp with at most this many lanes left may suspend them
     uint32_t suspend_min_steps;   // ... once each has made this many steps in the epoch
 };
@@ -296,6 +297,7 @@ cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t 
 size_t walk_smem_bytes(int N, int max_nc, int transition);
 size_t walk_fill_scratch_doubles(int N);
 int walk_pool_slots();
+int walk_geo_warps_max();
 int walk_ctas_per_sm(int N, int fp32, int mwe, int transition);
 // FD transitions (Algorithm 2) of stand-alone cubes, one CTA per cube at a time;
 // scratch = grid x fdm_cube_scratch_bytes(N)

@@ -794,10 +794,13 @@ __device__ FRW_OUTLINE bool issue_walk(const EngineView &E, IssueRanges &ir, Wal
 // Geometry-phase work of one slot: a new walk and its first transition if the
 // slot is free, then one step of the walk (Algorithm 1 inner loop): absorption
 // test, cube sizing, classification, then the analytical route in place or a
-// MicroWalk job queued for this CTA.
-template <typename T, bool MWE>
-__device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const FillList &fl, uint16_t *qlist,
-                         uint32_t *q_count, IssueRanges &ir)
+// MicroWalk job queued for this CTA through push_mw(o).  Returns the state the
+// slot is left in: ST_IDLE (no walk id left), ST_FRESH (the walk ended), ST_FIRST
+// or ST_HOP (waiting for a table, or its analytical hops of this round done),
+// ST_MW (MicroWalk job queued).
+template <typename T, bool MWE, class PushMW>
+__device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const FillList &fl, IssueRanges &ir,
+                             PushMW push_mw)
 {
     typedef Ar<T> A;
     const int N = E.N;
@@ -811,7 +814,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         if (!issue_walk(E, ir, w)) {
             E.s.state[s] = ST_IDLE;
             E.s.job[s] = w.job;
-            return;
+            return ST_IDLE;
         }
         w.hop = 0; w.steps = 0; w.cnt_sh = 0; w.cnt_mw = 0; w.branch = -1; w.omega = 0.0;
         st = ST_FIRST;
@@ -823,7 +826,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         if (!first_transition<T>(E, J, S, w, pos, fl)) {   // table not ready: retry next epoch
             E.s.state[s] = ST_FIRST;
             store_walk(E, s, w);
-            return;
+            return ST_FIRST;
         }
         w.hop = 1;
     } else if (st == ST_MWDONE) {
@@ -833,7 +836,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
             finish_walk(E, J, w, (int)(en & 0xffu));
             E.s.state[s] = ST_FRESH;
             E.s.job[s] = w.job;
-            return;
+            return ST_FRESH;
         }
         const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
         const T c[3] = {(T)E.s.cube[s], (T)E.s.cube[NS + s], (T)E.s.cube[2 * NS + s]};
@@ -855,7 +858,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         finish_walk(E, J, w, d <= S.tau ? who : -1);
         E.s.state[s] = ST_FRESH;
         E.s.job[s] = w.job;
-        return;
+        return ST_FRESH;
     }
     R = E.fp32 ? A::sub(d, S.margin) : d;
     classify_cube(S, pos, R, N, q);
@@ -869,7 +872,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         finish_walk(E, J, w, -1);
         E.s.state[s] = ST_FRESH;
         E.s.job[s] = w.job;
-        return;
+        return ST_FRESH;
     }
     hb = philox10((uint32_t)w.walk, (uint32_t)(w.walk >> 32), w.hop, 0u, J.key0, J.key1);
     int m = -1, fr[3] = {0, 1, 2};
@@ -901,7 +904,7 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
         E.s.pos[2 * NS + s] = (double)pos[2];
         E.s.state[s] = ST_HOP;
         store_walk(E, s, w);
-        return;
+        return ST_HOP;
     }
     break;
   }
@@ -938,13 +941,8 @@ __device__ void geo_slot(const EngineView &E, uint32_t s, uint32_t o, const Fill
     w.cnt_mw++;
     E.s.state[s] = ST_MW;
     store_walk(E, s, w);
-    {
-        cg::coalesced_group g = cg::coalesced_threads();
-        uint32_t base = 0;
-        if (g.thread_rank() == 0) base = atomicAdd(q_count, (uint32_t)g.size());
-        const uint32_t qi = g.shfl(base, 0) + g.thread_rank();
-        if (FRW_CHECKED(E, qi < E.pool)) qlist[qi] = (uint16_t)o;
-    }
+    push_mw(o);
+    return ST_MW;
 }
 
 // ---------------------------------------------------------------------------
@@ -1206,6 +1204,22 @@ __device__ __forceinline__ uint32_t mw_block4(const MWRows &R, const MWTab &T, c
     return moved;
 }
 
+// The same four steps in a loop that is not unrolled (one copy of the step: less
+// code next to a large kernel's other phases in the instruction cache).
+template <bool WIDE>
+__device__ __forceinline__ uint32_t mw_block4_compact(const MWRows &R, const MWTab &T, const MWMap &M, int &x, int &y,
+                                                      int &z, uint4 w)
+{
+    const uint32_t rest = WIDE ? M.G : 0u;
+    uint32_t moved = 0;
+#pragma unroll 1
+    for (int k = 0; k < 4; k++) {
+        moved += mw_step<WIDE>(R, T, M, x, y, z, w.x) != rest;
+        w = make_uint4(w.y, w.z, w.w, w.x);
+    }
+    return moved;
+}
+
 // A lane's walk: identity, cube (block count, column map) and the table bases for
 // the narrow and the wide decode.  A warp runs the wide decode while any of its
 // walking lanes holds more than 6 blocks; every lane, walking or resting, then
@@ -1248,49 +1262,56 @@ struct CubeSource {
     __device__ bool valid(uint64_t j) const { return j < total; }
     __device__ int gmat(int local) const { return (int)((mmap_lo >> (4 * (local & 15))) & 15ull); }
     __device__ uint64_t cube_of(uint64_t j) const { return j / spc; }
-    // A record is usable when 0 <= K <= 8 (what 64 words hold), every material id
-    // is below n_mat and every block range satisfies 0 <= lo < hi <= N.
-    __device__ bool record_ok(const int32_t *c) const
-    {
-        const int K = c[1];
-        if (K < 0 || K > 8 || c[0] < 0 || c[0] >= n_mat) return false;
-        for (int t = 0; t < K; t++) {
-            const int m = c[8 + 7 * t];
-            if (m < 0 || m >= n_mat) return false;
-            for (int a = 0; a < 3; a++) {
-                const int lo = c[2 + 7 * t + 2 * a], hi = c[3 + 7 * t + 2 * a];
-                if (!(0 <= lo && lo < hi && hi <= N)) return false;
-            }
-        }
-        return true;
-    }
-    // (all lanes) build lane r's masks for cube `cube`; malformed records build none
-    __device__ void build(uint64_t cube, uint16_t *Mw, uint32_t *T, int r, int N_, int lane) const
+    // (all lanes) check cube `cube`'s record and build lane r's masks from it.  A
+    // record is usable when 0 <= K <= 8 (what 64 words hold), every material id is
+    // below n_mat and every block range satisfies 0 <= lo < hi <= N; lane q checks
+    // block q.  Returns the verdict (the same on every lane); a malformed record
+    // builds a cube without blocks.
+    __device__ bool build(uint64_t cube, uint16_t *Mw, uint32_t *T, int r, int N_, int lane) const
     {
         const int32_t *c = cubes + cube * 64;
-        const int K = record_ok(c) ? c[1] : 0;   // a 64-word record holds at most 8 blocks
-        build_masks(Mw, T, r, N_, lane, K, [&](int lo[3], int hi[3]) {
+        const int K0 = c[1];
+        bool ok = K0 >= 0 && K0 <= 8 && c[0] >= 0 && c[0] < n_mat;
+        const int Kc = ok ? K0 : 0;
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        bool mine = true;
+        if (lane < Kc) {
+            const int m = c[8 + 7 * lane];
+            mine = m >= 0 && m < n_mat;
             for (int a = 0; a < 3; a++) {
                 lo[a] = c[2 + 7 * lane + 2 * a];
                 hi[a] = c[3 + 7 * lane + 2 * a];
+                mine = mine && 0 <= lo[a] && lo[a] < hi[a] && hi[a] <= N;
+            }
+        }
+        ok = __all_sync(FULL_MASK, mine) && ok;
+        build_masks(Mw, T, r, N_, lane, ok ? Kc : 0, [&](int l[3], int h[3]) {
+            for (int a = 0; a < 3; a++) {
+                l[a] = lo[a];
+                h[a] = hi[a];
             }
         });
+        return ok;
     }
-    // false (and the error flag set) for a malformed record: the sample is then
-    // written as exit 0, 0 steps and not walked
-    __device__ bool load(uint64_t j, MWLane &L, const MWTab &T0, int &x, int &y, int &z) const
+    // Start sample j on the lane's cube (fresh: its column map is computed, else
+    // kept from the previous sample of the same cube).  False (and the error flag
+    // set) for a malformed record: the sample is then written as exit 0, 0 steps
+    // and not walked.
+    __device__ bool load(uint64_t j, MWLane &L, const MWTab &T0, bool ok, bool fresh, int &x, int &y, int &z) const
     {
-        const int32_t *c = cubes + (j / spc) * 64;
-        if (!record_ok(c)) {
+        if (!ok) {
             atomicOr(err, ERR_INPUT);
             if (d_exit) d_exit[j] = 0u;
             if (d_steps) d_steps[j] = 0u;
             return false;
         }
-        const int K = c[1];
-        uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)gmat(c[0]) << 4);
-        for (int t = 0; t < K; t++) mm |= (uint64_t)gmat(c[2 + 7 * t + 6]) << (4 * (t + 2));
-        mw_lane_cube(L, T0, K, mm);
+        if (fresh) {
+            const int32_t *c = cubes + (j / spc) * 64;
+            const int K = c[1];
+            uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)gmat(c[0]) << 4);
+            for (int t = 0; t < K; t++) mm |= (uint64_t)gmat(c[2 + 7 * t + 6]) << (4 * (t + 2));
+            mw_lane_cube(L, T0, K, mm);
+        }
         L.walk_lo = (uint32_t)j;
         L.walk_hi = (uint32_t)(j >> 32);
         L.hop = 0;
@@ -1338,7 +1359,8 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
     bool active = false, exhausted = false;
     int x = -1, y = 0, z = 0;
     uint32_t t = 0;
-    uint64_t held = ~0ull;   // cube whose masks this lane's column holds
+    uint64_t held = ~0ull;   // cube whose masks (and column map) this lane holds
+    bool held_ok = false;    // ... and whether its record is well formed
     MWLane L;
     mw_lane_reset(L, T0);
     for (;;) {
@@ -1353,18 +1375,20 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
             const bool got = need && src.valid(myj);
             if (need && !got) exhausted = true;
             const uint64_t cube = got ? src.cube_of(myj) : held;
-            uint32_t todo = __ballot_sync(FULL_MASK, got && cube != held);
+            const bool fresh = got && cube != held;
+            uint32_t todo = __ballot_sync(FULL_MASK, fresh);
             while (todo) {
                 const int r = __ffs(todo) - 1;
                 todo &= todo - 1u;
                 const uint64_t cr = __shfl_sync(FULL_MASK, cube, r);
-                src.build(cr, Mw, Tw, r, N, lane);
+                const bool ok = src.build(cr, Mw, Tw, r, N, lane);
+                if (lane == r) held_ok = ok;
             }
             __syncwarp();
             if (got) {
                 held = cube;
                 t = 0;
-                active = src.load(myj, L, T0, x, y, z);
+                active = src.load(myj, L, T0, held_ok, fresh, x, y, z);
                 if (!active) { x = -1; y = 0; z = 0; }
             }
         }
@@ -1413,6 +1437,19 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
 // assembled face by face with two small contractions each.  Only the modes that
 // the right-hand side excites are kept: odd p and q for the SGF and the
 // layer-normal flux kernel, even p with odd q for the flux kernel across layers.
+// A group of whole warps that cooperates on a table fill or a batch reduction:
+// thread index within the group, group size, and the barrier that synchronises
+// it (0: the whole CTA, __syncthreads; else a named barrier of `nt` threads).
+struct Grp {
+    int tid, nt, bar;
+    __device__ __forceinline__ void sync() const
+    {
+        if (bar == 0) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+    }
+};
+__device__ __forceinline__ Grp cta_grp() { return Grp{(int)threadIdx.x, (int)blockDim.x, 0}; }
+
 struct FillJob {
     uint32_t kind;
     uint32_t prof[4];
@@ -1428,10 +1465,10 @@ struct FillJob {
 constexpr int FILL_CHUNKS = 256;   // chunks of the table fill's final sums (any block size)
 
 __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__restrict__ eps, const FillConsts &C,
-                           double *sm)
+                           double *sm, const Grp &G)
 {
     const int H = N / 2, M = H * H, P = 6 * N * N;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = G.tid, nt = G.nt;
     double *ek = sm;                 // N
     double *yh = ek + MAXN;          // M * N
     double *Z = yh + M * N;          // N * N
@@ -1442,7 +1479,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
     const bool perp = (kind == TAB_FLUX_PERP);
     const bool flux = (kind == TAB_FLUX_PAR || kind == TAB_FLUX_PERP || kind == TAB_FLUX_HOM);
     for (int k = tid; k < N; k += nt) ek[k] = hom ? 1.0 : eps[nib(F.prof[k >> 3], k & 7)];
-    __syncthreads();
+    G.sync();
     const int c0 = H - 1, c1 = H;
     // tridiagonal solve per mode
     for (int m = tid; m < M; m += nt) {
@@ -1485,7 +1522,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
             yh[m * N + k] = yk;
         }
     }
-    __syncthreads();
+    G.sync();
     const double *U = C.u;   // U[(p-1)*N + i]
     // faces: f = 2*ta + side; panel (u, w) on the other two table axes in increasing order
     for (int f = 0; f < 6; f++) {
@@ -1520,7 +1557,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
                 Z[o] = acc;
             }
         }
-        __syncthreads();
+        G.sync();
         // stage 2
         for (int o = tid; o < N * N; o += nt) {
             const int u = o / N, w = o - u * N;
@@ -1543,7 +1580,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
             }
             V[f * N * N + o] = e * acc;
         }
-        __syncthreads();
+        G.sync();
     }
     // totals and thresholds in canonical order: a sequential scan over FILL_CHUNKS
     // fixed chunks, so that the sums round the same way whatever the block size
@@ -1555,7 +1592,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
         for (int n = b0; n < b1; n++) part += flux ? fabs(V[n]) : V[n];
         red[c] = part;
     }
-    __syncthreads();
+    G.sync();
     if (tid == 0) {
         double run = 0.0;
         for (int i = 0; i < FILL_CHUNKS; i++) {
@@ -1565,7 +1602,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
         }
         red[FILL_CHUNKS] = run;
     }
-    __syncthreads();
+    G.sync();
     const double total = red[FILL_CHUNKS];
     for (int c = tid; c < FILL_CHUNKS; c += nt) {
         const int b0 = min(P, c * chunk), b1 = min(P, b0 + chunk);
@@ -1593,7 +1630,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
         if (!flux && fabs(total - 1.0) > 1e-9) atomicOr(F.err, ERR_FILL);
         if (!(total > 0.0)) atomicOr(F.err, ERR_FILL);
     }
-    __syncthreads();
+    G.sync();
     // guide table: first panel with threshold > bucket start (binary search)
     for (int k = tid; k < GUIDE; k += nt) {
         const uint32_t start = (uint32_t)k << 21;
@@ -1605,7 +1642,7 @@ __device__ FRW_OUTLINE void fill_table(const FillJob &F, int N, const double *__
         }
         F.guide[k] = (uint16_t)lo;
     }
-    __syncthreads();
+    G.sync();
 }
 
 __global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t entry, double *values)
@@ -1621,7 +1658,7 @@ __global__ void k_fill_one(EngineView E, uint32_t kind, uint4 prof, uint32_t ent
     F.values = values;
     F.err = &E.status[STAT_ERR];
     F.V = E.fill_scratch;
-    fill_table(F, E.N, E.eps, E.fc, fsm);
+    fill_table(F, E.N, E.eps, E.fc, fsm, cta_grp());
 }
 
 // ---------------------------------------------------------------------------
@@ -1651,20 +1688,20 @@ __device__ __forceinline__ void to_fixed128(double v, double scale, unsigned lon
 
 // CTA-cooperative reduction of one complete batch g into its accumulator block;
 // sets batch_ready[g] (release) once the block is written.
-__device__ FRW_OUTLINE void reduce_batch(const EngineView &E, uint32_t g, unsigned long long *acc_sm)
+__device__ FRW_OUTLINE void reduce_batch(const EngineView &E, uint32_t g, unsigned long long *acc_sm, const Grp &G)
 {
     const DevJob &J = E.jobs[__ldcg(E.batch_job + g)];
     const int nc1 = J.n_c + 1;
     const uint32_t words = J.acc_stride;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) acc_sm[i] = 0ull;
-    __syncthreads();
+    for (uint32_t i = G.tid; i < words; i += G.nt) acc_sm[i] = 0ull;
+    G.sync();
     const uint64_t b = g - J.batch_base;
     const uint64_t w0 = b * J.batch;
     const uint64_t w1 = min(w0 + J.batch, J.walk_count);
     unsigned long long *ex = acc_sm + 4 * nc1;
     unsigned long long loc[ACC_EXTRA];
     for (int x = 0; x < ACC_EXTRA; x++) loc[x] = 0ull;
-    for (uint64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+    for (uint64_t w = w0 + G.tid; w < w1; w += G.nt) {
         const uint64_t r = J.rec_base + w;
         const int k = cuda::atomic_ref<int32_t, cuda::thread_scope_device>(E.rec.k[r]).load(cuda::memory_order_acquire);
         if (k == REC_PENDING) continue;
@@ -1691,18 +1728,18 @@ __device__ FRW_OUTLINE void reduce_batch(const EngineView &E, uint32_t g, unsign
     for (int x = 0; x < ACC_EXTRA; x++) {
         unsigned long long v = loc[x];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL_MASK, v, o);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&ex[x], v);
+        if ((G.tid & 31) == 0 && v) atomicAdd(&ex[x], v);
     }
-    __syncthreads();
+    G.sync();
     unsigned long long *out = E.acc + J.acc_base + b * words;
     const bool in_range = FRW_CHECKED(E, J.acc_base + (b + 1) * words <= E.acc_cap);
-    for (uint32_t i = threadIdx.x; i < words && in_range; i += blockDim.x) out[i] = acc_sm[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    for (uint32_t i = G.tid; i < words && in_range; i += G.nt) out[i] = acc_sm[i];
+    G.sync();
+    if (G.tid == 0) {
         __threadfence();
         cuda::atomic_ref<uint32_t, cuda::thread_scope_device>(E.batch_ready[g]).store(1u, cuda::memory_order_release);
     }
-    __syncthreads();
+    G.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -1897,6 +1934,23 @@ __device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 #define FRW_FILL_GLOBAL 0
 #endif
 constexpr int WALK_THREADS = FRW_WALK_THREADS;
+// MicroWalk block of the walk kernel: FRW_MW_WIDE_ONLY 1 keeps only the wide
+// column decode (one code path); FRW_MW_COMPACT 1 runs the four steps as a loop.
+// Both on by default: the walk kernel's phases share the SM's instruction cache,
+// and the smallest MicroWalk loop measured fastest on the interconnect workload
+// (budget mode, 3 x 2^20 walks, N = 24: 44.7 ms against 49.7 ms with both decode
+// forms unrolled, 45.6 ms with both compact, 50.0 ms wide and unrolled)
+#ifndef FRW_MW_WIDE_ONLY
+#define FRW_MW_WIDE_ONLY 1
+#endif
+#ifndef FRW_MW_COMPACT
+#define FRW_MW_COMPACT 1
+#endif
+#if FRW_MW_COMPACT
+#define FRW_MW_BLOCK mw_block4_compact
+#else
+#define FRW_MW_BLOCK mw_block4
+#endif
 // 1: the walk kernel's table fill works in global scratch (per CTA) instead of
 // shared memory, so that the shared region holds only the MicroWalk masks
 constexpr bool FILL_GLOBAL = FRW_FILL_GLOBAL != 0;
@@ -1969,8 +2023,18 @@ size_t walk_scratch_bytes(int N, int max_nc)
 // values, plus the fill's work arrays when they do not live in shared memory)
 size_t walk_fill_scratch_doubles(int N)
 {
-    return 6 * (size_t)N * N + (FILL_GLOBAL ? (fill_smem_bytes(N) + sizeof(double) - 1) / sizeof(double) : 0);
+    // the work arrays too: the warp-specialised kernel fills tables in global memory
+    return 6 * (size_t)N * N + (fill_smem_bytes(N) + sizeof(double) - 1) / sizeof(double);
 }
+
+// dynamic shared memory of the warp-specialised walk kernel: the reduction's
+// accumulator block, then the masks of up to WALK_WARPS - 1 MicroWalk warps
+size_t walk_ws_smem_bytes(int N, int max_nc)
+{
+    const size_t acc = ((size_t)acc_stride_for(max_nc) * 8 + 127) / 128 * 128;
+    return acc + sizeof(uint16_t) * (size_t)(WALK_WARPS - 1) * 3 * (N + 4) * 32;
+}
+int walk_geo_warps_max() { return WALK_WARPS - 1; }
 
 size_t walk_smem_bytes(int N, int max_nc, int transition)
 {
@@ -2084,7 +2148,13 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                 const uint32_t i = atomicAdd(&sh.g_head, 1u);
                 if (i >= ng) break;
                 const uint32_t o = i < n1 ? sh.glist[i] : sh.glist[P - 1u - (i - n1)];
-                geo_slot<T, MWE>(E, base + o, o, fl, q_now, &sh.q_count, sh.ir);
+                geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, [&](uint32_t oo) {
+                    cg::coalesced_group g = cg::coalesced_threads();
+                    uint32_t b0 = 0;
+                    if (g.thread_rank() == 0) b0 = atomicAdd(&sh.q_count, (uint32_t)g.size());
+                    const uint32_t qi = g.shfl(b0, 0) + g.thread_rank();
+                    if (FRW_CHECKED(E, qi < E.pool)) q_now[qi] = (uint16_t)oo;
+                });
             }
         }
         __syncthreads();
@@ -2211,10 +2281,14 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     break;
                 }
                 // four steps without a branch; a lane without a walk rests on a boundary node
-                const bool wide = __any_sync(FULL_MASK, active && L.K > 6);
                 const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
-                const uint32_t moved = wide ? mw_block4<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk)
-                                            : mw_block4<false>(R, T0.with_base(L.base_n), L.map, x, y, z, blk);
+#if FRW_MW_WIDE_ONLY
+                const uint32_t moved = FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk);
+#else
+                const bool wide = __any_sync(FULL_MASK, active && L.K > 6);
+                const uint32_t moved = wide ? FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk)
+                                            : FRW_MW_BLOCK<false>(R, T0.with_base(L.base_n), L.map, x, y, z, blk);
+#endif
                 const bool inside = ((unsigned)x < (unsigned)N) & ((unsigned)y < (unsigned)N) & ((unsigned)z < (unsigned)N);
                 if (active && (moved < 4u || !inside)) {
                     // the walk has ended: on a boundary node (the exit node; reached at any of
@@ -2272,7 +2346,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
             F.values = nullptr;
             F.err = &E.status[STAT_ERR];
             F.V = fill_v;
-            fill_table(F, N, E.eps, E.fc, FILL_GLOBAL ? fill_v + 6 * N * N : reinterpret_cast<double *>(dsm));
+            fill_table(F, N, E.eps, E.fc, FILL_GLOBAL ? fill_v + 6 * N * N : reinterpret_cast<double *>(dsm), cta_grp());
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
@@ -2290,7 +2364,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
             const uint32_t g = sh.red;
             __syncthreads();
             if (g == 0xffffffffu) break;
-            reduce_batch(E, g, reinterpret_cast<unsigned long long *>(dsm));
+            reduce_batch(E, g, reinterpret_cast<unsigned long long *>(dsm), cta_grp());
             if (tid == 0) advance_job(E, __ldcg(E.batch_job + g));
         }
         const long long c3 = clock_after(&sh.red);
@@ -2344,10 +2418,393 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised walk kernel.  The CTA's warps split into a geometry group
+// (warps 0 .. G - 1) and a MicroWalk group (the others), which run at the same
+// time and meet only through two bitmaps over the CTA's slots in shared memory:
+// gbits (the slot's walk waits for geometry work: a new walk, analytical hops,
+// or the follow-up of a finished MicroWalk job) and mbits (the slot holds a
+// queued MicroWalk job).  At any time a slot is in at most one of them, or held
+// by the one thread working on it, or idle (no walk id).
+//  - The geometry group works in rounds, kept together by a named barrier of its
+//    own: claim walk ids for idle slots, take every bit of gbits, run geo_slot on
+//    each slot (a walk that ends takes the next id in the same slot), fill the
+//    analytical tables claimed in the round (work space in global memory), reduce
+//    completed batches, and decide whether the run ends.
+//  - A MicroWalk warp takes jobs from mbits whenever lanes are free, builds each
+//    new lane's masks, walks in blocks of four steps, and hands a finished walk
+//    back by setting its bit in gbits.  It never waits for the geometry group.
+// Walks are keyed by their ids and accumulated exactly, so the results equal the
+// phased kernel's bit for bit; only the schedule differs.
+
+constexpr int WS_WORDS = POOL_MAX / 32;      // bitmap words of a pool of at most POOL_MAX slots
+constexpr int WS_BAR = 1;                    // named barrier of the geometry group
+
+struct WalkSharedWS {
+    uint32_t W[WTAB_FULL_WORDS];
+    uint32_t Wl[WTAB_LANES_WORDS];
+    uint32_t scan[32 * WALK_WARPS];
+    uint32_t gbits[WS_WORDS], mbits[WS_WORDS], work[WS_WORDS], wpre[WS_WORDS + 1];
+    uint16_t idle[POOL_MAX];
+    uint32_t n_idle, g_pos, g_total, f_count;
+    int32_t m_count;                         // queued MicroWalk jobs (a hint: may lag a push or a claim)
+    uint32_t stop, red, issuable, j_lo, j_pub, progress_seen, pad0;
+    unsigned long long idle_t0;
+    unsigned long long mw_busy;              // cycles MicroWalk warps spent with a lane walking
+    IssueRanges ir;
+    uint32_t fill[FILL_MAX];
+};
+
+__device__ __forceinline__ void ws_set(uint32_t *bm, uint32_t o) { atomicOr(&bm[o >> 5], 1u << (o & 31)); }
+
+// claim one set bit of bm[0 .. nw), scanning from word `start`: the slot, or -1
+__device__ __forceinline__ int ws_claim(uint32_t *bm, int nw, int start)
+{
+    int w = start;
+    for (int i = 0; i < nw; i++) {
+        uint32_t v = *(volatile uint32_t *)&bm[w];
+        while (v) {
+            const uint32_t b = v & (0u - v);
+            const uint32_t old = atomicAnd(&bm[w], ~b);
+            if (old & b) return 32 * w + __ffs((int)b) - 1;
+            v = old & ~b;
+        }
+        if (++w == nw) w = 0;
+    }
+    return -1;
+}
+
+template <typename T, bool MWE>
+__global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk_ws(EngineView E)
+{
+    extern __shared__ __align__(16) unsigned char dsm_all[];
+    __shared__ WalkSharedWS sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N = E.N;
+    const uint32_t P = E.pool;
+    const int nw = (int)((P + 31) / 32);
+    const uint32_t base = blockIdx.x * P;
+    const int G = E.geo_warps, NG = 32 * G;
+    const bool geo = warp < G;
+    double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.fill_stride;
+    unsigned long long *acc_sm = reinterpret_cast<unsigned long long *>(dsm_all);
+    const size_t acc_bytes = ((size_t)acc_stride_for(E.max_nc) * 8 + 127) / 128 * 128;
+    wtab_fill(sh.W, E.W, false, tid, WALK_THREADS);
+    if (E.wtab_lanes) wtab_fill(sh.Wl, E.W, true, tid, WALK_THREADS);
+    for (uint32_t o = tid; o < P; o += WALK_THREADS) {
+        E.s.state[base + o] = ST_IDLE;
+        E.s.job[base + o] = 0u;
+        sh.idle[o] = (uint16_t)o;
+    }
+    for (int w = tid; w < WS_WORDS; w += WALK_THREADS) {
+        sh.gbits[w] = 0u;
+        sh.mbits[w] = 0u;
+    }
+    if (tid == 0) {
+        sh.n_idle = P; sh.g_pos = 0; sh.g_total = 0; sh.f_count = 0; sh.m_count = 0;
+        sh.stop = 0; sh.red = 0; sh.issuable = 0; sh.j_lo = 0; sh.j_pub = 0; sh.progress_seen = 0;
+        sh.idle_t0 = 0; sh.mw_busy = 0;
+    }
+    __syncthreads();
+    if (geo) {
+        // ======================== geometry group ========================
+        const Grp grp{tid, NG, WS_BAR};
+        const FillList fl{sh.fill, &sh.f_count, (uint32_t)FILL_MAX};
+        unsigned long long cyc[3] = {0, 0, 0};
+        const long long t_start = clock64();
+        uint32_t rounds = 0;
+        auto push_mw = [&](uint32_t o) {
+            __threadfence_block();           // job record and slot state before the bit
+            ws_set(sh.mbits, o);
+            atomicAdd(&sh.m_count, 1);
+        };
+        for (;;) {
+            const long long c0 = clock64();
+            // (a) walk ids for the idle slots
+            if (warp == 0) {
+                uint32_t lo, pub, open;
+                scan_jobs(E, lo, pub, open);
+                if (lane == 0) {
+                    sh.issuable = open;
+                    sh.j_lo = lo;
+                    sh.j_pub = pub;
+                    sh.f_count = 0;
+                }
+                __syncwarp();
+                claim_ids(E, sh.ir, open ? sh.n_idle : 0u, lo, pub);
+            }
+            grp.sync();
+            // (b) idle slots that got an id join the round; (c) take the round's slots
+            const uint32_t take = min(sh.n_idle, sh.ir.total);
+            for (uint32_t i = tid; i < take; i += NG) {
+                const uint32_t o = sh.idle[sh.n_idle - 1u - i];
+                E.s.state[base + o] = ST_FRESH;
+                ws_set(sh.gbits, o);
+            }
+            grp.sync();
+            for (int w = tid; w < WS_WORDS; w += NG) sh.work[w] = w < nw ? atomicExch(&sh.gbits[w], 0u) : 0u;
+            grp.sync();
+            if (tid == 0) {
+                sh.n_idle -= take;
+                uint32_t acc = 0;
+                for (int w = 0; w < nw; w++) {
+                    sh.wpre[w] = acc;
+                    acc += (uint32_t)__popc(sh.work[w]);
+                }
+                sh.wpre[nw] = acc;
+                sh.g_total = acc;
+                sh.g_pos = 0;
+            }
+            grp.sync();
+            // (d) geometry work on every taken slot, handed out one at a time
+            const uint32_t total = sh.g_total;
+            for (;;) {
+                const uint32_t k = atomicAdd(&sh.g_pos, 1u);
+                if (k >= total) break;
+                int lo = 0, hi = nw;                 // word w with wpre[w] <= k < wpre[w + 1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sh.wpre[mid] <= k) lo = mid;
+                    else hi = mid;
+                }
+                uint32_t m = sh.work[lo];
+                for (uint32_t q = k - sh.wpre[lo]; q > 0u; q--) m &= m - 1u;   // drop the lower set bits
+                if (m == 0u) {                   // cannot happen: the prefix counts say bit k is here
+                    atomicOr(&E.status[STAT_ERR], ERR_CHECK);
+                    continue;
+                }
+                const uint32_t o = 32u * (uint32_t)lo + (uint32_t)(__ffs((int)m) - 1);
+                if (!FRW_CHECKED(E, o < P)) continue;
+                uint32_t st = ST_FRESH;
+#pragma unroll 1
+                for (int rep = 0; rep < 2; rep++) {   // a walk that ends takes the next id in the same slot
+                    st = geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, push_mw);
+                    if (st != ST_FRESH) break;
+                }
+                if (st == ST_IDLE) {
+                    const uint32_t i = atomicAdd(&sh.n_idle, 1u);
+                    if (FRW_CHECKED(E, i < P)) sh.idle[i] = (uint16_t)o;
+                } else if (st != ST_MW) {
+                    ws_set(sh.gbits, o);          // waits for a table, or more hops: next round
+                }
+            }
+            grp.sync();
+            const long long c1 = clock_after(&sh.g_pos);
+            // (e) tables claimed in this round
+            const uint32_t nf = min(sh.f_count, (uint32_t)FILL_MAX);
+            for (uint32_t f = 0; f < nf; f++) {
+                const uint32_t e = sh.fill[f];
+                if (e == 0xffffffffu) continue;
+                FillJob F;
+                const uint32_t *kk = E.tc.keys + 5 * e;
+                F.kind = kk[0];
+                F.prof[0] = kk[1]; F.prof[1] = kk[2]; F.prof[2] = kk[3]; F.prof[3] = kk[4];
+                F.thr = E.tc.thr + (size_t)e * E.tc.P;
+                F.sgn = E.tc.sgn + (size_t)e * E.tc.P32;
+                F.guide = E.tc.guide + (size_t)e * GUIDE;
+                F.ktot = E.tc.ktot + e;
+                F.values = nullptr;
+                F.err = &E.status[STAT_ERR];
+                F.V = fill_v;
+                fill_table(F, N, E.eps, E.fc, fill_v + 6 * N * N, grp);
+                grp.sync();
+                if (tid == 0) {
+                    __threadfence();
+                    atomicExch(&E.tc.state[e], TE_READY);
+                    atomicAdd(&E.status[STAT_BUILT], 1u);
+                }
+                grp.sync();
+            }
+            const long long c2 = clock_after(&sh.f_count);
+            // (f) completed batches
+            for (;;) {
+                if (tid == 0) sh.red = take_batch(E);
+                grp.sync();
+                const uint32_t g = sh.red;
+                grp.sync();
+                if (g == 0xffffffffu) break;
+                reduce_batch(E, g, acc_sm, grp);
+                if (tid == 0) advance_job(E, __ldcg(E.batch_job + g));
+            }
+            const long long c3 = clock_after(&sh.red);
+            rounds++;
+            if (tid == 0) {
+                cyc[0] += (unsigned long long)(c1 - c0);
+                cyc[1] += (unsigned long long)(c2 - c1);
+                cyc[2] += (unsigned long long)(c3 - c2);
+                // (g) end of the run, or an idle wait limited while no CTA makes progress
+                const bool idle = sh.n_idle == P && sh.issuable == 0u;
+                uint32_t stop = 0;
+                if (*(volatile uint32_t *)&E.ctrl[CTRL_ABORT]) stop = 1;
+                if (*(volatile uint32_t *)&E.status[STAT_ERR]) stop = 1;
+                const bool undecided =
+                    *(volatile uint32_t *)&E.jctl[JC_DECIDED] < *(volatile uint32_t *)&E.jctl[JC_PUBLISHED];
+                if (idle) {
+                    if (!undecided && *(volatile uint32_t *)&E.ctrl[CTRL_OPEN] == 0u) {
+                        stop = 1;
+                    } else {
+                        unsigned long long now;
+                        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                        const uint32_t prog = *(volatile uint32_t *)&E.status[STAT_PROGRESS];
+                        if (sh.idle_t0 == 0 || prog != sh.progress_seen) {
+                            sh.idle_t0 = now;
+                            sh.progress_seen = prog;
+                        } else if ((double)(now - sh.idle_t0) * 1e-9 > E.idle_timeout_s) {
+                            atomicOr(&E.status[STAT_ERR], ERR_IDLE_TIMEOUT);
+                            stop = 1;
+                        }
+                        __nanosleep(20000);
+                    }
+                } else {
+                    sh.idle_t0 = 0;
+                    if ((rounds & 7u) == 0u) atomicAdd(&E.status[STAT_PROGRESS], 1u);
+                    if (total == 0u) __nanosleep(2000);   // walks held by MicroWalk: let it run
+                }
+                if (stop) *(volatile uint32_t *)&sh.stop = 1u;
+            }
+            grp.sync();
+            if (*(volatile uint32_t *)&sh.stop) break;
+        }
+        if (tid == 0) {
+            const long long t_all = clock64() - t_start;
+            atomicAdd(&E.cycles[0], cyc[0]);
+            atomicAdd(&E.cycles[1], cyc[1]);
+            atomicAdd(&E.cycles[2], cyc[2]);
+            atomicAdd(&E.cycles[4], (unsigned long long)t_all);
+            atomicMax(&E.status[STAT_EPOCHS], rounds);
+        }
+    } else {
+        // ======================== MicroWalk group ========================
+        const int mwarp = warp - G;
+        uint16_t *Mw = reinterpret_cast<uint16_t *>(dsm_all + acc_bytes) + (size_t)mwarp * mask_rows(N) * 32;
+        uint32_t *Tw = sh.scan + warp * 32;
+        masks_clear(Mw, N, lane);
+        __syncwarp();
+        const MWRows R = mw_rows(Mw, N, lane);
+        const bool lanes_table = E.wtab_lanes != 0;
+        const MWTab T0 = wtab_lane(lanes_table ? sh.Wl : sh.W, lanes_table, lane);
+        bool active = false;
+        int x = -1, y = 0, z = 0;
+        uint32_t t = 0, my_o = 0;
+        MWLane L;
+        mw_lane_reset(L, T0);
+        int rot = (mwarp * 7 + lane * 3) % nw;
+        unsigned long long busy = 0;
+        for (;;) {
+            const bool need = !active;
+            // warp-uniform: stop, and whether to look for jobs
+            const uint32_t flags = __shfl_sync(FULL_MASK, (*(volatile uint32_t *)&sh.stop ? 1u : 0u) |
+                                                              (*(volatile int32_t *)&sh.m_count > 0 ? 2u : 0u), 0);
+            if ((flags & 1u) && !__any_sync(FULL_MASK, active && *(volatile uint32_t *)&E.status[STAT_ERR] == 0u))
+                break;                           // the run is over (or failed: walks in flight are dropped)
+            if (__any_sync(FULL_MASK, need) && (flags & 2u)) {
+                int o = -1;
+                if (need) {
+                    o = ws_claim(sh.mbits, nw, rot);
+                    if (o >= 0) atomicSub(&sh.m_count, 1);
+                    if (++rot == nw) rot = 0;
+                }
+                const bool got = o >= 0;
+                uint32_t todo = __ballot_sync(FULL_MASK, got);
+                if (todo) __threadfence_block();     // pairs with the pusher's fence
+                while (todo) {
+                    const int r = __ffs(todo) - 1;
+                    todo &= todo - 1u;
+                    const uint32_t orr = (uint32_t)__shfl_sync(FULL_MASK, o, r);
+                    const MWJob &b = E.mwq[base + orr];
+                    const int K = min((int)b.K, KMAX);
+                    build_masks(Mw, Tw, r, N, lane, K, [&](int lo[3], int hi[3]) {
+                        const uint2 rr = b.rng[lane];
+                        lo[0] = (int)(rr.x & 255u); hi[0] = (int)((rr.x >> 8) & 255u);
+                        lo[1] = (int)((rr.x >> 16) & 255u); hi[1] = (int)(rr.x >> 24);
+                        lo[2] = (int)(rr.y & 255u); hi[2] = (int)((rr.y >> 8) & 255u);
+                    });
+                }
+                __syncwarp();
+                if (got) {
+                    const MWJob &b = E.mwq[base + (uint32_t)o];
+                    L.walk_lo = b.walk_lo; L.walk_hi = b.walk_hi; L.hop = b.hop;
+                    L.key0 = b.key0; L.key1 = b.key1; L.tag = b.slot;
+                    mw_lane_cube(L, T0, min((int)b.K, KMAX), (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32));
+                    x = (int)(b.start & 255u); y = (int)((b.start >> 8) & 255u); z = (int)((b.start >> 16) & 255u);
+                    t = b.pad0;
+                    my_o = (uint32_t)o;
+                    active = true;
+                    if (!FRW_CHECKED(E, (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N &&
+                                            (unsigned)z < (unsigned)N)) {
+                        active = false;
+                        x = -1; y = 0; z = 0;
+                    }
+                }
+            }
+            if (__ballot_sync(FULL_MASK, active) == 0u) {
+                __nanosleep(1000);
+                continue;
+            }
+            const long long cb = clock64();
+            const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
+#if FRW_MW_WIDE_ONLY
+            const uint32_t moved = FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk);
+#else
+            const bool wide = __any_sync(FULL_MASK, active && L.K > 6);
+            const uint32_t moved = wide ? FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk)
+                                        : FRW_MW_BLOCK<false>(R, T0.with_base(L.base_n), L.map, x, y, z, blk);
+#endif
+            const bool inside = ((unsigned)x < (unsigned)N) & ((unsigned)y < (unsigned)N) & ((unsigned)z < (unsigned)N);
+            if (active && (moved < 4u || !inside)) {
+                // the walk has ended (see the phased kernel): exit node or conductor
+                const uint32_t sl2 = L.tag;
+                uint32_t en = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+                if (MWE && inside) {
+                    const int slot = mw_slot_at(R, x, y, z);
+                    en = FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
+                             ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                             : 0x80000000u;
+                }
+                E.s.exitnode[sl2] = en;
+                E.s.steps[sl2] += t + moved;
+                __threadfence_block();          // exit data before the state and the bit
+                E.s.state[sl2] = ST_MWDONE;
+                ws_set(sh.gbits, my_o);
+                active = false;
+                x = -1; y = 0; z = 0;
+            }
+            t += 4;
+            if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
+                atomicOr(&E.status[STAT_ERR], ERR_MW_STEPS);
+                const uint32_t sl2 = L.tag;
+                E.s.exitnode[sl2] = (uint32_t)(x + 1) | ((uint32_t)(y + 1) << 8) | ((uint32_t)(z + 1) << 16);
+                E.s.steps[sl2] += t;
+                __threadfence_block();
+                E.s.state[sl2] = ST_MWDONE;
+                ws_set(sh.gbits, my_o);
+                active = false;
+                x = -1; y = 0; z = 0;
+            }
+            busy += (unsigned long long)(clock64() - cb);
+            __syncwarp();
+        }
+        if (lane == 0) atomicAdd(&sh.mw_busy, busy);
+    }
+    __syncthreads();
+    if (tid == 0) atomicAdd(&E.cycles[3], sh.mw_busy / (unsigned long long)max(1, WALK_WARPS - G));
+}
+
 // Shared-memory carve-out for the resident CTAs of the walk kernel (WALK_CTAS;
 // one for the FDM comparator): no more than they need, so that the rest of the
 // SM's on-chip memory serves as L1 (the geometry phase's structure data and stack
 // live there).
+template <typename T, bool MWE> static cudaError_t set_walk_ws_attributes(int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_walk_ws<T, MWE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k_walk_ws<T, MWE>)) != cudaSuccess) return e;
+    const size_t need = (size_t)WALK_CTAS * ((size_t)smem + fa.sharedSizeBytes + 1024);
+    const int pct = (int)std::min<size_t>(100, (need * 100 + 228 * 1024 - 1) / (228 * 1024));
+    return cudaFuncSetAttribute(k_walk_ws<T, MWE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 template <typename T, bool MWE, bool FDM> static cudaError_t set_walk_attributes(int smem)
 {
     cudaError_t e = cudaFuncSetAttribute(k_walk<T, MWE, FDM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -2369,13 +2826,33 @@ static cudaError_t walk_attributes(int N, int max_nc, int fp32, int mwe, int tra
     return fp32 ? set_walk_attributes<float, false, false>(smem) : set_walk_attributes<double, false, false>(smem);
 }
 
-cudaError_t prepare_walk(const EngineView &E) { return walk_attributes(E.N, E.max_nc, E.fp32, E.mwe, E.transition); }
+cudaError_t prepare_walk(const EngineView &E)
+{
+    if (E.geo_warps > 0 && E.transition != 1) {
+        const int smem = (int)walk_ws_smem_bytes(E.N, E.max_nc);
+        if (E.mwe > 1) return E.fp32 ? set_walk_ws_attributes<float, true>(smem) : set_walk_ws_attributes<double, true>(smem);
+        return E.fp32 ? set_walk_ws_attributes<float, false>(smem) : set_walk_ws_attributes<double, false>(smem);
+    }
+    return walk_attributes(E.N, E.max_nc, E.fp32, E.mwe, E.transition);
+}
 
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st)
 {
     (void)L;
-    const size_t smem = walk_smem_bytes(E.N, E.max_nc, E.transition);
     const unsigned grid = E.NS / E.pool;
+    if (E.geo_warps > 0 && E.transition != 1) {
+        if (E.geo_warps >= WALK_WARPS || E.pool > (uint32_t)POOL_MAX) return cudaErrorInvalidValue;
+        const size_t smem = walk_ws_smem_bytes(E.N, E.max_nc);
+        if (E.mwe > 1) {
+            if (E.fp32) k_walk_ws<float, true><<<grid, WALK_THREADS, smem, st>>>(E);
+            else k_walk_ws<double, true><<<grid, WALK_THREADS, smem, st>>>(E);
+        } else {
+            if (E.fp32) k_walk_ws<float, false><<<grid, WALK_THREADS, smem, st>>>(E);
+            else k_walk_ws<double, false><<<grid, WALK_THREADS, smem, st>>>(E);
+        }
+        return cudaGetLastError();
+    }
+    const size_t smem = walk_smem_bytes(E.N, E.max_nc, E.transition);
     if (E.transition == 1) {
         if (E.fp32) k_walk<float, false, true><<<grid, WALK_THREADS, smem, st>>>(E);
         else k_walk<double, false, true><<<grid, WALK_THREADS, smem, st>>>(E);

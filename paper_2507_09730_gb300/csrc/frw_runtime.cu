@@ -217,6 +217,7 @@ static EngineView make_view(frw_ctx *ctx)
     E.fdm_scratch = ctx->fdm_scratch;
     E.suspend_lanes = ctx->tune.suspend_lanes;
     E.suspend_min_steps = (uint32_t)ctx->tune.suspend_min_steps;
+    E.geo_warps = ctx->opt.transition == FRW_TRANSITION_FDM ? 0 : ctx->tune.geo_warps;
     return E;
 }
 
@@ -346,6 +347,8 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->tune.hops_per_epoch = 4;
     ctx->tune.suspend_lanes = 8;
     ctx->tune.suspend_min_steps = 64;
+    ctx->tune.geo_warps = 0;
+    ctx->tune.reserved = 0;
     ctx->tune.mw_warps_per_cta = ctx->shape.mw_warps;
     ctx->tune.mw_ctas_per_sm = ctx->shape.mw_ctas_per_sm;
     ctx->tune.walks_per_s = 0.0;
@@ -2100,7 +2103,8 @@ static int tuning_ok(frw_ctx *ctx, const frw_tuning &t)
     return t.pool_per_cta >= 256 && t.pool_per_cta <= pool0 && t.pool_per_cta % 256 == 0 && t.hops_per_epoch >= 1 &&
            t.hops_per_epoch <= 64 && t.suspend_lanes >= 0 && t.suspend_lanes <= 32 && t.suspend_min_steps >= 4 &&
            t.suspend_min_steps <= 4096 && t.mw_warps_per_cta >= 1 &&
-           t.mw_warps_per_cta <= 16 && t.mw_ctas_per_sm >= 1 && t.mw_ctas_per_sm <= 32;
+           t.mw_warps_per_cta <= 16 && t.mw_ctas_per_sm >= 1 && t.mw_ctas_per_sm <= 32 && t.geo_warps >= 0 &&
+           t.geo_warps <= walk_geo_warps_max();
 }
 
 static int apply_tuning(frw_ctx *ctx, const frw_tuning &t)

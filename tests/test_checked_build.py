@@ -18,7 +18,8 @@ def test_gpu_suites_pass_on_the_checked_build():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    files = ["tests/test_gpu_parity.py", "tests/test_gpu_mwe.py", "tests/test_serving.py", "tests/test_batched.py"]
+    files = ["tests/test_gpu_parity.py", "tests/test_gpu_mwe.py", "tests/test_serving.py", "tests/test_batched.py",
+             "tests/test_gpu_ws.py"]
     env = dict(os.environ, FRW_CHECKED="1")
     r = subprocess.run([sys.executable, "-m", "pytest", *files, "-m", "gpu", "-q", "-x", "-p", "no:cacheprovider"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
