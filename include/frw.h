@@ -143,6 +143,8 @@ typedef struct {
     uint64_t walks_issued;     /* walk ids started (>= walks: a sigma-target run stops mid-flight) */
     double kernel_ms;          /* device time of the walk kernel (CUDA events on the launch stream) */
     double reduce_ms;          /* walk-kernel time in its batch-reduction phase (as geom_ms) */
+    uint64_t stage_bytes;      /* bytes of the structure's geometry that each walk-kernel CTA copied into
+                                  shared memory and read from there (0: read from global memory) */
 } frw_stats;
 
 /* Fill *opt with defaults (N = 24, FP64 geometry, hybrid on, offset 0.5,
@@ -310,7 +312,11 @@ typedef struct {
     int32_t geo_warps;         /* 0: the walk kernel alternates geometry and MicroWalk phases with all its
                                   warps; 1 .. 13: it runs this many warps per CTA on geometry and the
                                   others on MicroWalk at the same time (the pool then at most 2048) */
-    int32_t reserved;
+    int32_t unstaged;          /* 0: when every job of a closed run or plan uses one structure, each CTA of
+                                  the phased walk kernel copies that structure's conductor boxes, dielectric
+                                  blocks and slab masks into shared memory (the groups that fit without
+                                  lowering the kernel's CTAs per SM) and sizes cubes from the copy;
+                                  1: the geometry is read from global memory only */
     double walks_per_s;        /* frw_autotune: measured with the chosen walk-kernel settings */
     double mw_steps_per_s;     /* frw_autotune: measured with the chosen MicroWalk shape */
 } frw_tuning;

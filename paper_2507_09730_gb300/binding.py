@@ -72,7 +72,7 @@ class frw_job(ctypes.Structure):
 class frw_tuning(ctypes.Structure):
     _fields_ = [("pool_per_cta", c_int32), ("hops_per_epoch", c_int32), ("suspend_lanes", c_int32),
                 ("mw_warps_per_cta", c_int32), ("mw_ctas_per_sm", c_int32), ("suspend_min_steps", c_int32),
-                ("geo_warps", c_int32), ("reserved", c_int32),
+                ("geo_warps", c_int32), ("unstaged", c_int32),
                 ("walks_per_s", c_double), ("mw_steps_per_s", c_double)]
 
     def as_dict(self):
@@ -93,7 +93,7 @@ class frw_stats(ctypes.Structure):
                 ("mw_hops", c_uint64), ("tables_built", c_uint64), ("rounds", c_uint64), ("seconds", c_double),
                 ("geom_ms", c_double), ("fill_ms", c_double), ("mw_ms", c_double), ("launches", c_uint64),
                 ("mw_jobs", c_uint64), ("walks_issued", c_uint64), ("kernel_ms", c_double),
-                ("reduce_ms", c_double)]
+                ("reduce_ms", c_double), ("stage_bytes", c_uint64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "branch"}

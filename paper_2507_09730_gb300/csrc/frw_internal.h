@@ -31,6 +31,7 @@ enum : uint32_t {
 // status words
 enum { STAT_ACTIVE = 0, STAT_ERR = 1, STAT_BUILT = 2, STAT_MWJOBS = 3, STAT_EPOCHS = 4, STAT_SUSPENDED = 5,
        STAT_PROGRESS = 6,   // epochs in which some walk-kernel CTA had work (its idle CTAs wait while it moves)
+       STAT_STAGED = 7,     // walk-kernel CTAs that read the structure geometry from their shared-memory copy
        STAT_WORDS = 8 };
 // host control words read by the running walk kernel
 enum { CTRL_OPEN = 0, CTRL_ABORT = 1, CTRL_WORDS = 4 };
@@ -276,9 +277,29 @@ struct EngineView {
     int transition;        // non-stratified transitions: 0 MicroWalk, 1 FD solve (FRW-FDM)
     unsigned char *fdm_scratch;   // FRW-FDM: per walk-kernel CTA, fdm_cube_scratch_bytes(N)
     int geo_warps;         // 0: phased walk kernel; else warps per CTA on geometry (warp-specialised kernel)
+    int stage_sid;         // structure whose geometry every CTA copies into shared memory (-1: none)
+    uint32_t stage_flags;  // STAGE_* groups copied
+    uint32_t stage_off;    // byte offset of the copy in the walk kernel's dynamic shared memory
+    uint32_t stage_bytes;  // its size (dynamic shared memory = stage_off + stage_bytes)
     int suspend_lanes;     // a MicroWalk warp with at most this many lanes left may suspend them
     uint32_t suspend_min_steps;   // ... once each has made this many steps in the epoch
 };
+
+// Shared-memory copy of one structure's geometry in the walk kernel (the max-cube
+// query of Sec. II-A and the cube classification read it): groups of arrays in
+// this order, each group 16-byte aligned; T = float or double (tsize bytes).
+constexpr uint32_t STAGE_BOXES = 1u;    // conductor boxes: clo[3 n_c], chi[3 n_c]
+constexpr uint32_t STAGE_BLOCKS = 2u;   // dielectric blocks: blo[3 n_b], bhi[3 n_b], then bmat[n_b]
+constexpr uint32_t STAGE_SLABS = 4u;    // slab masks: sl_L[3 S w], sl_H[3 S w]
+__host__ __device__ inline uint32_t stage_round16(uint32_t b) { return (b + 15u) & ~15u; }
+__host__ __device__ inline uint32_t stage_group_bytes(uint32_t grp, int n_c, int n_b, int sl_S, int sl_words,
+                                                      int tsize)
+{
+    if (grp == STAGE_BOXES) return stage_round16(6u * (uint32_t)n_c * (uint32_t)tsize);
+    if (grp == STAGE_BLOCKS)
+        return n_b > 0 ? stage_round16(6u * (uint32_t)n_b * (uint32_t)tsize) + stage_round16((uint32_t)n_b) : 0u;
+    return stage_round16(2u * 3u * (uint32_t)sl_S * (uint32_t)sl_words * 4u);
+}
 
 // ---- launchers (frw_kernels.cu) ----
 struct LaunchShape {
@@ -299,6 +320,9 @@ size_t walk_fill_scratch_doubles(int N);
 int walk_pool_slots();
 int walk_geo_warps_max();
 int walk_ctas_per_sm(int N, int fp32, int mwe, int transition);
+// dynamic shared memory a walk-kernel CTA may add for the geometry copy without
+// lowering the kernel's CTAs per SM below ctas_per_sm (0: no copy for this view)
+uint32_t walk_stage_cap(const EngineView &E, int ctas_per_sm);
 // FD transitions (Algorithm 2) of stand-alone cubes, one CTA per cube at a time;
 // scratch = grid x fdm_cube_scratch_bytes(N)
 size_t fdm_cube_scratch_bytes(int N);

@@ -38,6 +38,13 @@ namespace cg = cooperative_groups;
 #define FRW_CHECKED(E, cond) true
 #endif
 
+// Per-slot walk state, MicroWalk job records and result records are each touched
+// once per hop and never reused from L1: they go through L2 only (ld/st .cg), so
+// that L1 keeps the structure data and sampling tables the geometry work reads
+// again and again.
+template <class V> __device__ __forceinline__ V ldcg(const V *p) { return __ldcg(p); }
+template <class V> __device__ __forceinline__ void stcg(V *p, V v) { __stcg(p, v); }
+
 __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                           uint32_t k0, uint32_t k1)
 {
@@ -103,6 +110,23 @@ template <typename T> __device__ __forceinline__ int cell_of(T x, T org, T inv, 
     return i < n ? i : n - 1;
 }
 
+// Loads of the structure arrays that the walk kernel may copy into shared memory
+// (conductor boxes, dielectric blocks, slab masks): generic loads, which serve a
+// pointer into shared memory and one into global memory alike.  With
+// FRW_STAGE_GEOM=0 nothing is copied and the arrays are read through the
+// read-only data path.
+#ifndef FRW_STAGE_GEOM
+#define FRW_STAGE_GEOM 1
+#endif
+template <class V> __device__ __forceinline__ V gload(const V *p)
+{
+#if FRW_STAGE_GEOM
+    return *p;
+#else
+    return __ldg(p);
+#endif
+}
+
 // L-infinity distance to the nearest electrode (conductor box or grounded wall);
 // who = conductor of the nearest box (lowest index on ties: boxes are sorted by
 // conductor) or n_cond for the walls.  The grid cell of p lists, in ascending
@@ -121,12 +145,12 @@ __device__ FRW_OUTLINE T nearest_electrode(const SView<T> &S, const T p[3], int 
     const int cell = (cx * S.gdim[1] + cy) * S.gdim[2] + cz;
     const uint32_t i0 = __ldg(&S.g_off[cell]), i1 = __ldg(&S.g_off[cell + 1]);
     for (uint32_t i = i0; i < i1; i++) {
-        const int k = __ldg(&S.g_ids[i]);
+        const int k = (int)__ldg(&S.g_ids[i]);
         T d = T(0);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const T t1 = A::sub(__ldg(&S.clo[a * n + k]), p[a]);
-            const T t2 = A::sub(p[a], __ldg(&S.chi[a * n + k]));
+            const T t1 = A::sub(gload(&S.clo[a * n + k]), p[a]);
+            const T t2 = A::sub(p[a], gload(&S.chi[a * n + k]));
             if (t1 > d) d = t1;
             if (t2 > d) d = t2;
         }
@@ -193,8 +217,8 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
     int bg = S.bg;
     const int nb = S.n_b;
     const int SS = S.sl_S, nw = S.sl_words;
-    const T *__restrict__ blo = S.blo, *__restrict__ bhi = S.bhi;
-    const uint8_t *__restrict__ bmat = S.bmat;
+    const T *blo = S.blo, *bhi = S.bhi;   // generic: shared or global memory
+    const uint8_t *bmat = S.bmat;
     const uint32_t *Lx = S.sl_L + (size_t)(0 * SS + cell_of(A::add(c[0], R), S.sl_org[0], S.sl_inv[0], SS)) * nw;
     const uint32_t *Hx = S.sl_H + (size_t)(0 * SS + cell_of(A::sub(c[0], R), S.sl_org[0], S.sl_inv[0], SS)) * nw;
     const uint32_t *Ly = S.sl_L + (size_t)(1 * SS + cell_of(A::add(c[1], R), S.sl_org[1], S.sl_inv[1], SS)) * nw;
@@ -202,8 +226,8 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
     const uint32_t *Lz = S.sl_L + (size_t)(2 * SS + cell_of(A::add(c[2], R), S.sl_org[2], S.sl_inv[2], SS)) * nw;
     const uint32_t *Hz = S.sl_H + (size_t)(2 * SS + cell_of(A::sub(c[2], R), S.sl_org[2], S.sl_inv[2], SS)) * nw;
     for (int wd = 0; wd < nw; wd++) {
-      uint32_t cand = __ldg(&Lx[wd]) & __ldg(&Hx[wd]) & __ldg(&Ly[wd]) & __ldg(&Hy[wd]) & __ldg(&Lz[wd]) &
-                      __ldg(&Hz[wd]);
+      uint32_t cand = gload(&Lx[wd]) & gload(&Hx[wd]) & gload(&Ly[wd]) & gload(&Hy[wd]) & gload(&Lz[wd]) &
+                      gload(&Hz[wd]);
       while (cand) {
         const int b = 32 * wd + __ffs(cand) - 1;
         cand &= cand - 1u;
@@ -211,8 +235,8 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
         bool rej = false;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            lo[a] = __ldg(&blo[a * nb + b]);
-            hi[a] = __ldg(&bhi[a * nb + b]);
+            lo[a] = gload(&blo[a * nb + b]);
+            hi[a] = gload(&bhi[a * nb + b]);
             rej |= !(hi[a] > base[a]) || (lo[a] > xmax[a]);
         }
         if (rej) continue;
@@ -226,7 +250,7 @@ __device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, 
             full &= (r0[a] == 0) && (r1[a] == N);
         }
         if (empty) continue;
-        const int m = __ldg(&bmat[b]);
+        const int m = gload(&bmat[b]);
         if (full) { count = 0; bg = m; continue; }
         if (count < KMAX)
             q.rng[count] = make_uint2((uint32_t)r0[0] | ((uint32_t)r1[0] << 8) | ((uint32_t)r0[1] << 16) |
@@ -308,8 +332,8 @@ __device__ FRW_OUTLINE bool classify_cube_e(const SView<T> &S, const T c[3], T R
         bool rej = false;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            lo[a] = __ldg(&S.clo[a * n + k]);
-            hi[a] = __ldg(&S.chi[a * n + k]);
+            lo[a] = gload(&S.clo[a * n + k]);
+            hi[a] = gload(&S.chi[a * n + k]);
             rej |= !(hi[a] > base[a]) || (lo[a] > xmax[a]);
         }
         if (rej) continue;
@@ -526,12 +550,12 @@ __device__ FRW_OUTLINE void finish_walk(const EngineView &E, const DevJob &J, co
     const uint64_t rel = w.walk - J.walk_begin;
     const uint64_t r = J.rec_base + rel;
     if (!FRW_CHECKED(E, rel < J.walk_count && r < E.rec_cap && J.batch_base + rel / J.batch < E.rq_cap)) return;
-    E.rec.omega[r] = w.omega;
-    E.rec.hops[r] = w.hop;
-    E.rec.steps[r] = (uint32_t)w.steps;
-    E.rec.cnt_sh[r] = w.cnt_sh;
-    E.rec.cnt_mw[r] = w.cnt_mw;
-    E.rec.branch[r] = w.branch;
+    stcg(&E.rec.omega[r], w.omega);
+    stcg(&E.rec.hops[r], w.hop);
+    stcg(&E.rec.steps[r], (uint32_t)w.steps);
+    stcg(&E.rec.cnt_sh[r], w.cnt_sh);
+    stcg(&E.rec.cnt_mw[r], w.cnt_mw);
+    stcg(&E.rec.branch[r], w.branch);
     cuda::atomic_ref<int32_t, cuda::thread_scope_device>(E.rec.k[r]).store(k, cuda::memory_order_release);
     const uint64_t bi = rel / J.batch;
     const uint64_t g = J.batch_base + bi;
@@ -652,26 +676,26 @@ __device__ __forceinline__ uint32_t nib(uint32_t v, int i) { return (v >> (4 * i
 
 __device__ __forceinline__ void store_walk(const EngineView &E, uint32_t s, const WalkState &w)
 {
-    E.s.job[s] = w.job;
-    E.s.hop[s] = w.hop;
-    E.s.walk[s] = w.walk;
-    E.s.steps[s] = w.steps;
-    E.s.cnt_sh[s] = w.cnt_sh;
-    E.s.cnt_mw[s] = w.cnt_mw;
-    E.s.branch[s] = w.branch;
-    E.s.omega[s] = w.omega;
+    stcg(&E.s.job[s], w.job);
+    stcg(&E.s.hop[s], w.hop);
+    stcg(&E.s.walk[s], w.walk);
+    stcg(&E.s.steps[s], w.steps);
+    stcg(&E.s.cnt_sh[s], w.cnt_sh);
+    stcg(&E.s.cnt_mw[s], w.cnt_mw);
+    stcg(&E.s.branch[s], w.branch);
+    stcg(&E.s.omega[s], w.omega);
 }
 
 __device__ __forceinline__ void load_walk(const EngineView &E, uint32_t s, WalkState &w)
 {
-    w.job = E.s.job[s];
-    w.hop = E.s.hop[s];
-    w.walk = E.s.walk[s];
-    w.steps = E.s.steps[s];
-    w.cnt_sh = E.s.cnt_sh[s];
-    w.cnt_mw = E.s.cnt_mw[s];
-    w.branch = E.s.branch[s];
-    w.omega = E.s.omega[s];
+    w.job = ldcg(&E.s.job[s]);
+    w.hop = ldcg(&E.s.hop[s]);
+    w.walk = ldcg(&E.s.walk[s]);
+    w.steps = ldcg(&E.s.steps[s]);
+    w.cnt_sh = ldcg(&E.s.cnt_sh[s]);
+    w.cnt_mw = ldcg(&E.s.cnt_mw[s]);
+    w.branch = ldcg(&E.s.branch[s]);
+    w.omega = ldcg(&E.s.omega[s]);
 }
 
 __device__ __forceinline__ bool job_open(const EngineView &E, int j)
@@ -800,7 +824,7 @@ __device__ FRW_OUTLINE bool issue_walk(const EngineView &E, IssueRanges &ir, Wal
 // ST_MW (MicroWalk job queued).
 template <typename T, bool MWE, class PushMW>
 __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const FillList &fl, IssueRanges &ir,
-                             PushMW push_mw)
+                             const SView<T> *staged, PushMW push_mw)
 {
     typedef Ar<T> A;
     const int N = E.N;
@@ -820,7 +844,8 @@ __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const 
         st = ST_FIRST;
     }
     const DevJob &J = E.jobs[w.job];
-    const SView<T> &S = structure_view<T>(E, J.sid);
+    // the CTA's shared-memory copy of the geometry when the walk's structure is the staged one
+    const SView<T> &S = (staged != nullptr && J.sid == E.stage_sid) ? *staged : structure_view<T>(E, J.sid);
     T pos[3];
     if (st == ST_FIRST) {
         if (!first_transition<T>(E, J, S, w, pos, fl)) {   // table not ready: retry next epoch
@@ -830,7 +855,7 @@ __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const 
         }
         w.hop = 1;
     } else if (st == ST_MWDONE) {
-        const uint32_t en = E.s.exitnode[s];
+        const uint32_t en = ldcg(&E.s.exitnode[s]);
         if (MWE && (en & 0x80000000u)) {   // MicroWalk-E: absorbed by a conductor inside its expanded cube
             w.hop++;
             finish_walk(E, J, w, (int)(en & 0xffu));
@@ -839,14 +864,14 @@ __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const 
             return ST_FRESH;
         }
         const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
-        const T c[3] = {(T)E.s.cube[s], (T)E.s.cube[NS + s], (T)E.s.cube[2 * NS + s]};
-        const T R = (T)E.s.cube[3 * NS + s];
+        const T c[3] = {(T)ldcg(&E.s.cube[s]), (T)ldcg(&E.s.cube[NS + s]), (T)ldcg(&E.s.cube[2 * NS + s])};
+        const T R = (T)ldcg(&E.s.cube[3 * NS + s]);
         node_point(c, R, N, node, pos);
         w.hop++;
     } else {   // ST_HOP
-        pos[0] = (T)E.s.pos[s];
-        pos[1] = (T)E.s.pos[NS + s];
-        pos[2] = (T)E.s.pos[2 * NS + s];
+        pos[0] = (T)ldcg(&E.s.pos[s]);
+        pos[1] = (T)ldcg(&E.s.pos[NS + s]);
+        pos[2] = (T)ldcg(&E.s.pos[2 * NS + s]);
     }
   T R;
   CubeInfo q;
@@ -899,9 +924,9 @@ __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const 
         if (hops_here + 1 < E.hops_per_epoch) continue;   // next hop of the same walk in this epoch
     }
     if (wait || m >= 0) {
-        E.s.pos[s] = (double)pos[0];
-        E.s.pos[NS + s] = (double)pos[1];
-        E.s.pos[2 * NS + s] = (double)pos[2];
+        stcg(&E.s.pos[s], (double)pos[0]);
+        stcg(&E.s.pos[NS + s], (double)pos[1]);
+        stcg(&E.s.pos[2 * NS + s], (double)pos[2]);
         E.s.state[s] = ST_HOP;
         store_walk(E, s, w);
         return ST_HOP;
@@ -930,19 +955,30 @@ __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const 
     uint64_t mm = (uint64_t)BOUNDARY | ((uint64_t)q.bg << 4);
     for (int t = 0; t < q.K; t++) mm |= (uint64_t)rng_mat(q.rng[t]) << (4 * (t + 2));
     uint4 *dst = reinterpret_cast<uint4 *>(jb);
-    dst[0] = make_uint4(s, w.hop, (uint32_t)w.walk, (uint32_t)(w.walk >> 32));
-    dst[1] = make_uint4(start, (uint32_t)q.K, (uint32_t)mm, (uint32_t)(mm >> 32));
-    dst[2] = make_uint4(J.key0, J.key1, 0u, 0u);      // pad0 = steps already taken (resume)
-    for (int t = 0; t < q.K; t++) jb->rng[t] = q.rng[t];
-    E.s.cube[s] = (double)pos[0];
-    E.s.cube[NS + s] = (double)pos[1];
-    E.s.cube[2 * NS + s] = (double)pos[2];
-    E.s.cube[3 * NS + s] = (double)R;
+    stcg(&dst[0], make_uint4(s, w.hop, (uint32_t)w.walk, (uint32_t)(w.walk >> 32)));
+    stcg(&dst[1], make_uint4(start, (uint32_t)q.K, (uint32_t)mm, (uint32_t)(mm >> 32)));
+    stcg(&dst[2], make_uint4(J.key0, J.key1, 0u, 0u));      // pad0 = steps already taken (resume)
+    for (int t = 0; t < q.K; t++) stcg(&jb->rng[t], q.rng[t]);
+    stcg(&E.s.cube[s], (double)pos[0]);
+    stcg(&E.s.cube[NS + s], (double)pos[1]);
+    stcg(&E.s.cube[2 * NS + s], (double)pos[2]);
+    stcg(&E.s.cube[3 * NS + s], (double)R);
     w.cnt_mw++;
     E.s.state[s] = ST_MW;
     store_walk(E, s, w);
     push_mw(o);
     return ST_MW;
+}
+
+// The fixed fields of a MicroWalk job record, read through L2 in three 16-byte loads.
+struct MWHead {
+    uint32_t slot, hop, walk_lo, walk_hi, start, K, mm_lo, mm_hi, key0, key1, steps;
+};
+__device__ __forceinline__ MWHead mw_head(const MWJob &b)
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(&b);
+    const uint4 a = ldcg(p), c = ldcg(p + 1), d = ldcg(p + 2);
+    return MWHead{a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z};
 }
 
 // ---------------------------------------------------------------------------
@@ -2047,6 +2083,74 @@ int walk_pool_slots() { return POOL_MAX; }
 // FDM = true: the FRW-FDM comparator, whose non-stratified transitions solve the
 // cube's FD system (Algorithm 2) one cube at a time with the whole CTA, in place
 // of the MicroWalk phase (one CTA per SM: the solve's vectors fill shared memory).
+// Copy the geometry of structure E.stage_sid (the groups of E.stage_flags) into
+// `region` and return a view of it whose arrays point there (the groups not
+// copied keep their global arrays); nullptr when the groups do not fit the
+// E.stage_bytes the host allotted (error bit ERR_CHECK, the walks then read global
+// memory).  Every thread of the CTA calls it; the caller synchronises before use.
+template <typename T>
+__device__ const SView<T> *stage_structure(const EngineView &E, SView<T> &sv, unsigned char *region)
+{
+    if (!FRW_STAGE_GEOM || E.stage_sid < 0 || E.stage_flags == 0u) return nullptr;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const SView<T> &G = structure_view<T>(E, E.stage_sid);
+    const int ts = (int)sizeof(T);
+    const uint32_t fl = E.stage_flags;
+    uint32_t need = 0;
+    for (uint32_t g = STAGE_BOXES; g <= STAGE_SLABS; g <<= 1)
+        if (fl & g) need += stage_group_bytes(g, G.n_c, G.n_b, G.sl_S, G.sl_words, ts);
+    if (need > E.stage_bytes) {
+        if (tid == 0) atomicOr(&E.status[STAT_ERR], ERR_CHECK);
+        return nullptr;
+    }
+    const T *clo = G.clo, *chi = G.chi, *blo = G.blo, *bhi = G.bhi;
+    const uint8_t *bmat = G.bmat;
+    const uint32_t *sL = G.sl_L, *sH = G.sl_H;
+    uint32_t off = 0;
+    if (fl & STAGE_BOXES) {
+        T *d = reinterpret_cast<T *>(region + off);
+        const int n = 3 * G.n_c;
+        for (int i = tid; i < n; i += nt) {
+            d[i] = G.clo[i];
+            d[n + i] = G.chi[i];
+        }
+        clo = d;
+        chi = d + n;
+        off += stage_group_bytes(STAGE_BOXES, G.n_c, G.n_b, G.sl_S, G.sl_words, ts);
+    }
+    if ((fl & STAGE_BLOCKS) && G.n_b > 0) {
+        T *d = reinterpret_cast<T *>(region + off);
+        const int n = 3 * G.n_b;
+        for (int i = tid; i < n; i += nt) {
+            d[i] = G.blo[i];
+            d[n + i] = G.bhi[i];
+        }
+        uint8_t *m = region + off + stage_round16(6u * (uint32_t)G.n_b * (uint32_t)ts);
+        for (int i = tid; i < G.n_b; i += nt) m[i] = G.bmat[i];
+        blo = d;
+        bhi = d + n;
+        bmat = m;
+        off += stage_group_bytes(STAGE_BLOCKS, G.n_c, G.n_b, G.sl_S, G.sl_words, ts);
+    }
+    if (fl & STAGE_SLABS) {
+        uint32_t *d = reinterpret_cast<uint32_t *>(region + off);
+        const int n = 3 * G.sl_S * G.sl_words;
+        for (int i = tid; i < n; i += nt) {
+            d[i] = G.sl_L[i];
+            d[n + i] = G.sl_H[i];
+        }
+        sL = d;
+        sH = d + n;
+    }
+    if (tid == 0) {
+        sv = G;
+        sv.clo = clo; sv.chi = chi; sv.blo = blo; sv.bhi = bhi; sv.bmat = bmat;
+        sv.sl_L = sL; sv.sl_H = sH;
+        atomicAdd(&E.status[STAT_STAGED], 1u);
+    }
+    return &sv;
+}
+
 template <typename T, bool MWE, bool FDM>
 __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(EngineView E)
 {
@@ -2060,6 +2164,9 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
     double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.fill_stride;
     wtab_fill(sh.W, E.W, false, tid, WALK_THREADS);
     if (E.wtab_lanes) wtab_fill(sh.Wl, E.W, true, tid, WALK_THREADS);
+    // the geometry copy lives above the region the phases share (E.stage_off, set by the host)
+    __shared__ SView<T> sview_staged;
+    const SView<T> *staged = FDM ? nullptr : stage_structure<T>(E, sview_staged, dsm_all + E.stage_off);
     for (uint32_t o = tid; o < P; o += WALK_THREADS) {
         const uint32_t s = base + o;
         E.s.state[s] = ST_FRESH;
@@ -2148,7 +2255,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                 const uint32_t i = atomicAdd(&sh.g_head, 1u);
                 if (i >= ng) break;
                 const uint32_t o = i < n1 ? sh.glist[i] : sh.glist[P - 1u - (i - n1)];
-                geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, [&](uint32_t oo) {
+                geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, staged, [&](uint32_t oo) {
                     cg::coalesced_group g = cg::coalesced_threads();
                     uint32_t b0 = 0;
                     if (g.thread_rank() == 0) b0 = atomicAdd(&sh.q_count, (uint32_t)g.size());
@@ -2231,9 +2338,9 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                         todo &= todo - 1u;
                         const uint32_t orr = __shfl_sync(FULL_MASK, oj, r);
                         const MWJob &b = E.mwq[base + orr];
-                        const int K = min((int)b.K, KMAX);
+                        const int K = min((int)ldcg(&b.K), KMAX);
                         build_masks(Mw, Tw, r, N, lane, K, [&](int lo[3], int hi[3]) {
-                            const uint2 rr = b.rng[lane];
+                            const uint2 rr = ldcg(&b.rng[lane]);
                             lo[0] = (int)(rr.x & 255u); hi[0] = (int)((rr.x >> 8) & 255u);
                             lo[1] = (int)((rr.x >> 16) & 255u); hi[1] = (int)(rr.x >> 24);
                             lo[2] = (int)(rr.y & 255u); hi[2] = (int)((rr.y >> 8) & 255u);
@@ -2241,12 +2348,12 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     }
                     __syncwarp();
                     if (got) {
-                        const MWJob &b = E.mwq[base + oj];
+                        const MWHead b = mw_head(E.mwq[base + oj]);
                         L.walk_lo = b.walk_lo; L.walk_hi = b.walk_hi; L.hop = b.hop;
                         L.key0 = b.key0; L.key1 = b.key1; L.tag = b.slot;
                         mw_lane_cube(L, T0, min((int)b.K, KMAX), (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32));
                         x = (int)(b.start & 255u); y = (int)((b.start >> 8) & 255u); z = (int)((b.start >> 16) & 255u);
-                        t = b.pad0;
+                        t = b.steps;
                         t_in = t;
                         my_o = oj;
                         active = true;
@@ -2271,8 +2378,8 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                                                      (unsigned)z < (unsigned)N)) {
                         // a walking lane is always on a node inside the lattice here
                         MWJob &b = E.mwq[base + my_o];
-                        b.start = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16);
-                        b.pad0 = t;
+                        stcg(&b.start, (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16));
+                        stcg(&b.pad0, t);
                         const uint32_t qi = atomicAdd(&sh.q_next, 1u);
                         if (FRW_CHECKED(E, qi < P)) q_next[qi] = (uint16_t)my_o;
                         atomicAdd(&sh.s_count, 1u);
@@ -2299,11 +2406,11 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     if (MWE && inside) {
                         const int slot = mw_slot_at(R, x, y, z);
                         en = FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
-                                 ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                                 ? (0x80000000u | (ldcg(&E.mwq[base + my_o].rng[slot - 2].y) >> 24))
                                  : 0x80000000u;
                     }
-                    E.s.exitnode[sl2] = en;
-                    E.s.steps[sl2] += t + moved;
+                    stcg(&E.s.exitnode[sl2], en);
+                    stcg(&E.s.steps[sl2], ldcg(&E.s.steps[sl2]) + t + moved);
                     __threadfence_block();      // exit data before the state (read by geometry warps)
                     E.s.state[sl2] = ST_MWDONE;
                     active = false;
@@ -2578,7 +2685,7 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk_ws(EngineView 
                 uint32_t st = ST_FRESH;
 #pragma unroll 1
                 for (int rep = 0; rep < 2; rep++) {   // a walk that ends takes the next id in the same slot
-                    st = geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, push_mw);
+                    st = geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, nullptr, push_mw);
                     if (st != ST_FRESH) break;
                 }
                 if (st == ST_IDLE) {
@@ -2712,9 +2819,9 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk_ws(EngineView 
                     todo &= todo - 1u;
                     const uint32_t orr = (uint32_t)__shfl_sync(FULL_MASK, o, r);
                     const MWJob &b = E.mwq[base + orr];
-                    const int K = min((int)b.K, KMAX);
+                    const int K = min((int)ldcg(&b.K), KMAX);
                     build_masks(Mw, Tw, r, N, lane, K, [&](int lo[3], int hi[3]) {
-                        const uint2 rr = b.rng[lane];
+                        const uint2 rr = ldcg(&b.rng[lane]);
                         lo[0] = (int)(rr.x & 255u); hi[0] = (int)((rr.x >> 8) & 255u);
                         lo[1] = (int)((rr.x >> 16) & 255u); hi[1] = (int)(rr.x >> 24);
                         lo[2] = (int)(rr.y & 255u); hi[2] = (int)((rr.y >> 8) & 255u);
@@ -2722,12 +2829,12 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk_ws(EngineView 
                 }
                 __syncwarp();
                 if (got) {
-                    const MWJob &b = E.mwq[base + (uint32_t)o];
+                    const MWHead b = mw_head(E.mwq[base + (uint32_t)o]);
                     L.walk_lo = b.walk_lo; L.walk_hi = b.walk_hi; L.hop = b.hop;
                     L.key0 = b.key0; L.key1 = b.key1; L.tag = b.slot;
                     mw_lane_cube(L, T0, min((int)b.K, KMAX), (uint64_t)b.mm_lo | ((uint64_t)b.mm_hi << 32));
                     x = (int)(b.start & 255u); y = (int)((b.start >> 8) & 255u); z = (int)((b.start >> 16) & 255u);
-                    t = b.pad0;
+                    t = b.steps;
                     my_o = (uint32_t)o;
                     active = true;
                     if (!FRW_CHECKED(E, (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N &&
@@ -2758,11 +2865,11 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk_ws(EngineView 
                 if (MWE && inside) {
                     const int slot = mw_slot_at(R, x, y, z);
                     en = FRW_CHECKED(E, slot >= 2 && slot < 2 + KMAX)
-                             ? (0x80000000u | (E.mwq[base + my_o].rng[slot - 2].y >> 24))
+                             ? (0x80000000u | (ldcg(&E.mwq[base + my_o].rng[slot - 2].y) >> 24))
                              : 0x80000000u;
                 }
-                E.s.exitnode[sl2] = en;
-                E.s.steps[sl2] += t + moved;
+                stcg(&E.s.exitnode[sl2], en);
+                stcg(&E.s.steps[sl2], ldcg(&E.s.steps[sl2]) + t + moved);
                 __threadfence_block();          // exit data before the state and the bit
                 E.s.state[sl2] = ST_MWDONE;
                 ws_set(sh.gbits, my_o);
@@ -2816,9 +2923,18 @@ template <typename T, bool MWE, bool FDM> static cudaError_t set_walk_attributes
     return cudaFuncSetAttribute(k_walk<T, MWE, FDM>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
 }
 
-static cudaError_t walk_attributes(int N, int max_nc, int fp32, int mwe, int transition)
+// dynamic shared memory of one launch of the phased walk kernel: the phases'
+// region, then the geometry copy when the view has one
+static size_t walk_view_smem(const EngineView &E)
 {
-    const int smem = (int)walk_smem_bytes(N, max_nc, transition);
+    const size_t base = walk_smem_bytes(E.N, E.max_nc, E.transition);
+    if (E.stage_sid < 0 || E.stage_flags == 0u || E.transition == 1) return base;
+    return std::max(base, (size_t)E.stage_off + E.stage_bytes);
+}
+
+static cudaError_t walk_attributes(int N, int max_nc, int fp32, int mwe, int transition, size_t smem_bytes)
+{
+    const int smem = (int)smem_bytes;
     if (transition == 1)
         return fp32 ? set_walk_attributes<float, false, true>(smem) : set_walk_attributes<double, false, true>(smem);
     if (mwe > 1)
@@ -2833,7 +2949,7 @@ cudaError_t prepare_walk(const EngineView &E)
         if (E.mwe > 1) return E.fp32 ? set_walk_ws_attributes<float, true>(smem) : set_walk_ws_attributes<double, true>(smem);
         return E.fp32 ? set_walk_ws_attributes<float, false>(smem) : set_walk_ws_attributes<double, false>(smem);
     }
-    return walk_attributes(E.N, E.max_nc, E.fp32, E.mwe, E.transition);
+    return walk_attributes(E.N, E.max_nc, E.fp32, E.mwe, E.transition, walk_view_smem(E));
 }
 
 cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t st)
@@ -2852,7 +2968,7 @@ cudaError_t launch_walk(const EngineView &E, const LaunchShape &L, cudaStream_t 
         }
         return cudaGetLastError();
     }
-    const size_t smem = walk_smem_bytes(E.N, E.max_nc, E.transition);
+    const size_t smem = walk_view_smem(E);
     if (E.transition == 1) {
         if (E.fp32) k_walk<float, false, true><<<grid, WALK_THREADS, smem, st>>>(E);
         else k_walk<double, false, true><<<grid, WALK_THREADS, smem, st>>>(E);
@@ -3072,6 +3188,35 @@ template <typename T, bool MWE, bool FDM> static int walk_occupancy(int smem)
     set_walk_attributes<T, MWE, FDM>(smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_walk<T, MWE, FDM>, WALK_THREADS, smem);
     return n;
+}
+
+uint32_t walk_stage_cap(const EngineView &E, int ctas_per_sm)
+{
+    if (!FRW_STAGE_GEOM || E.transition == 1 || E.geo_warps > 0 || ctas_per_sm < 1) return 0;
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if (E.mwe > 1) e = E.fp32 ? cudaFuncGetAttributes(&fa, k_walk<float, true, false>) : cudaFuncGetAttributes(&fa, k_walk<double, true, false>);
+    else e = E.fp32 ? cudaFuncGetAttributes(&fa, k_walk<float, false, false>) : cudaFuncGetAttributes(&fa, k_walk<double, false, false>);
+    int dev = 0, per_sm = 0, per_block = 0, reserved = 0;
+    if (e != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const long long base = (long long)stage_round16((uint32_t)walk_smem_bytes(E.N, E.max_nc, 0));
+    const long long fit = std::min<long long>((long long)per_sm / ctas_per_sm - reserved, per_block) -
+                          (long long)fa.sharedSizeBytes - base;
+    const long long cap = std::min<long long>(fit, 32 * 1024) / 128 * 128;
+    if (cap <= 0) return 0u;
+    // confirm with the occupancy calculator at the enlarged size
+    const int smem = (int)(base + cap);
+    int n = 0;
+    if (E.mwe > 1) n = E.fp32 ? walk_occupancy<float, true, false>(smem) : walk_occupancy<double, true, false>(smem);
+    else n = E.fp32 ? walk_occupancy<float, false, false>(smem) : walk_occupancy<double, false, false>(smem);
+    cudaGetLastError();
+    return n >= ctas_per_sm ? (uint32_t)cap : 0u;
 }
 
 int walk_ctas_per_sm(int N, int fp32, int mwe, int transition)

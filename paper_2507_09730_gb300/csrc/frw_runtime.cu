@@ -218,8 +218,10 @@ static EngineView make_view(frw_ctx *ctx)
     E.suspend_lanes = ctx->tune.suspend_lanes;
     E.suspend_min_steps = (uint32_t)ctx->tune.suspend_min_steps;
     E.geo_warps = ctx->opt.transition == FRW_TRANSITION_FDM ? 0 : ctx->tune.geo_warps;
+    E.stage_sid = -1;   // no geometry copy unless choose_stage picks one
     return E;
 }
+
 
 // ---------------------------------------------------------------------------
 extern "C" void frw_default_options(frw_options *o)
@@ -348,7 +350,7 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
     ctx->tune.suspend_lanes = 8;
     ctx->tune.suspend_min_steps = 64;
     ctx->tune.geo_warps = 0;
-    ctx->tune.reserved = 0;
+    ctx->tune.unstaged = 0;
     ctx->tune.mw_warps_per_cta = ctx->shape.mw_warps;
     ctx->tune.mw_ctas_per_sm = ctx->shape.mw_ctas_per_sm;
     ctx->tune.walks_per_s = 0.0;
@@ -1139,6 +1141,37 @@ static double run_timeout_s()
     return t > 0.0 ? t : 3600.0;
 }
 
+// The geometry copy of a closed run or plan: when every job uses one structure,
+// the groups of its geometry (boxes, blocks, slab masks, in that order) that fit
+// the dynamic shared memory a CTA can add at the launched CTAs per SM.
+static void choose_stage(frw_ctx *ctx, EngineView &E, const std::vector<JobRun *> &live)
+{
+    E.stage_sid = -1;
+    E.stage_flags = 0;
+    E.stage_bytes = 0;
+    E.stage_off = 0;
+    if (ctx->tune.unstaged || live.empty()) return;
+    const int sid = live[0]->desc.structure_id;
+    for (const JobRun *j : live)
+        if (j->desc.structure_id != sid) return;
+    const uint32_t cap = walk_stage_cap(E, ctx->grid / std::max(1, ctx->shape.sms));
+    const DevStructure &d = ctx->structs[sid].d;
+    const int ts = E.fp32 ? 4 : 8;
+    uint32_t used = 0, fl = 0;
+    for (uint32_t g = STAGE_BOXES; g <= STAGE_SLABS; g <<= 1) {
+        const uint32_t b = stage_group_bytes(g, d.n_c, d.n_b, d.sl_S, d.sl_words, ts);
+        if (b > 0 && used + b <= cap) {
+            used += b;
+            fl |= g;
+        }
+    }
+    if (!fl) return;
+    E.stage_sid = sid;
+    E.stage_flags = fl;
+    E.stage_bytes = used;
+    E.stage_off = stage_round16((uint32_t)walk_smem_bytes(E.N, E.max_nc, E.transition));
+}
+
 static EngineView run_view(frw_ctx *ctx, RunBufs &B, const RecArrays &rec, uint64_t rec_cap, uint32_t jcap,
                            int max_nc, uint32_t pool, uint64_t batches)
 {
@@ -1224,7 +1257,8 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
     CK(publish_jobs(ctx->rb, live.data(), 0, nj, P, st));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(uint32_t) * STAT_WORDS, st));
     CK(cudaMemsetAsync(ctx->cycles, 0, sizeof(unsigned long long) * 8, st));
-    const EngineView E = run_view(ctx, ctx->rb, ctx->rec, ctx->rec_cap, nj, max_nc, run_pool, A.batches);
+    EngineView E = run_view(ctx, ctx->rb, ctx->rec, ctx->rec_cap, nj, max_nc, run_pool, A.batches);
+    choose_stage(ctx, E, live);
     CK(prepare_walk(E));
     CK(cudaEventRecord(ctx->ev[0], st));
     CK(launch_walk(E, ctx->shape, st));
@@ -1278,6 +1312,7 @@ static int run_jobs(frw_ctx *ctx, std::vector<JobRun> &jobs, frw_stats *stats_ou
             s.mw_ms = ctot > 0 ? kms * (double)cyc[3] / ctot : 0.0;
             s.launches = 1;
             s.kernel_ms = kms;
+            s.stage_bytes = ctx->h_status[STAT_STAGED] ? E.stage_bytes : 0;
         }
     }
     return FRW_OK;
@@ -2104,7 +2139,7 @@ static int tuning_ok(frw_ctx *ctx, const frw_tuning &t)
            t.hops_per_epoch <= 64 && t.suspend_lanes >= 0 && t.suspend_lanes <= 32 && t.suspend_min_steps >= 4 &&
            t.suspend_min_steps <= 4096 && t.mw_warps_per_cta >= 1 &&
            t.mw_warps_per_cta <= 16 && t.mw_ctas_per_sm >= 1 && t.mw_ctas_per_sm <= 32 && t.geo_warps >= 0 &&
-           t.geo_warps <= walk_geo_warps_max();
+           t.geo_warps <= walk_geo_warps_max() && (t.unstaged == 0 || t.unstaged == 1);
 }
 
 static int apply_tuning(frw_ctx *ctx, const frw_tuning &t)
@@ -2310,6 +2345,7 @@ struct frw_plan {
     Arena A;
     int max_nc = 1;
     uint32_t pool = 0;
+    uint32_t stage_bytes = 0;   // the walk kernel's geometry copy per CTA (0: none)
     RunBufs rb;
     RecArrays rec;
     std::vector<void *> allocs;
@@ -2409,7 +2445,9 @@ extern "C" int frw_plan_create(frw_ctx *ctx, const frw_job *jobs, int32_t n_jobs
     CK(cudaEventCreate(&P->ev1));
     // capture: reset, publication, the walk kernel
     std::lock_guard<std::mutex> engine(ctx->engine_mu);
-    const EngineView E = run_view(ctx, P->rb, P->rec, P->A.walks, nj, P->max_nc, P->pool, P->A.batches);
+    EngineView E = run_view(ctx, P->rb, P->rec, P->A.walks, nj, P->max_nc, P->pool, P->A.batches);
+    choose_stage(ctx, E, P->live);
+    P->stage_bytes = E.stage_sid >= 0 ? E.stage_bytes : 0;
     CK(prepare_walk(E));
     cudaStream_t st = ctx->stream;
     CK(cudaStreamSynchronize(st));
@@ -2498,6 +2536,7 @@ extern "C" int frw_plan_run(frw_plan *P, uint64_t request_offset, double *C_rows
             stats[i].launches = nj ? 1 : 0;
             stats[i].rounds = ctx->h_status[STAT_EPOCHS];
             stats[i].tables_built = ctx->h_status[STAT_BUILT];
+            stats[i].stage_bytes = ctx->h_status[STAT_STAGED] ? P->stage_bytes : 0;
         }
         if (j.desc.sigma_target > 0.0 && !j.converged) notconv = true;
     }
