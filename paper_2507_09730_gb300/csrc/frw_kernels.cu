@@ -822,18 +822,40 @@ __device__ FRW_OUTLINE bool issue_walk(const EngineView &E, IssueRanges &ir, Wal
 // slot is left in: ST_IDLE (no walk id left), ST_FRESH (the walk ended), ST_FIRST
 // or ST_HOP (waiting for a table, or its analytical hops of this round done),
 // ST_MW (MicroWalk job queued).
+// st_known: the slot's state as the caller read it after a CTA barrier that
+// follows every write to the slot, with a cancelled job's walk already turned into
+// ST_FRESH; ST_UNKNOWN: read it here (the slot may be handed over concurrently).
+constexpr uint32_t ST_UNKNOWN = 7u;
 template <typename T, bool MWE, class PushMW>
 __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const FillList &fl, IssueRanges &ir,
-                             const SView<T> *staged, PushMW push_mw)
+                             const SView<T> *staged, uint32_t st_known, PushMW push_mw)
 {
     typedef Ar<T> A;
     const int N = E.N;
     const uint32_t NS = E.NS;
-    uint32_t st = *(volatile uint32_t *)&E.s.state[s];
-    __threadfence_block();   // pairs with the MicroWalk warps' fence before they publish ST_MWDONE
+    uint32_t st = st_known;
+    if (st_known == ST_UNKNOWN) {
+        st = *(volatile uint32_t *)&E.s.state[s];
+        __threadfence_block();   // pairs with the MicroWalk warps' fence before they publish ST_MWDONE
+    }
+    // the position data of the step, loaded together with the walk state (one
+    // round trip): the last node's position, or the finished MicroWalk's cube and exit
+    double pq[4] = {0.0, 0.0, 0.0, 0.0};
+    uint32_t en = 0u;
+    if (st == ST_HOP || st == ST_MWDONE) {
+        const bool mwd = st == ST_MWDONE;
+        const double *src = mwd ? E.s.cube : E.s.pos;
+        pq[0] = ldcg(src + s);
+        pq[1] = ldcg(src + NS + s);
+        pq[2] = ldcg(src + 2 * NS + s);
+        if (mwd) {
+            pq[3] = ldcg(src + 3 * NS + s);
+            en = ldcg(&E.s.exitnode[s]);
+        }
+    }
     WalkState w;
     load_walk(E, s, w);
-    if (st != ST_FRESH && ((volatile int *)E.job_cancel)[w.job]) st = ST_FRESH;   // drop the walk
+    if (st_known == ST_UNKNOWN && st != ST_FRESH && ((volatile int *)E.job_cancel)[w.job]) st = ST_FRESH;   // drop the walk
     if (st == ST_FRESH) {
         if (!issue_walk(E, ir, w)) {
             E.s.state[s] = ST_IDLE;
@@ -855,7 +877,6 @@ __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const 
         }
         w.hop = 1;
     } else if (st == ST_MWDONE) {
-        const uint32_t en = ldcg(&E.s.exitnode[s]);
         if (MWE && (en & 0x80000000u)) {   // MicroWalk-E: absorbed by a conductor inside its expanded cube
             w.hop++;
             finish_walk(E, J, w, (int)(en & 0xffu));
@@ -864,14 +885,13 @@ __device__ uint32_t geo_slot(const EngineView &E, uint32_t s, uint32_t o, const 
             return ST_FRESH;
         }
         const int node[3] = {(int)(en & 255u) - 1, (int)((en >> 8) & 255u) - 1, (int)((en >> 16) & 255u) - 1};
-        const T c[3] = {(T)ldcg(&E.s.cube[s]), (T)ldcg(&E.s.cube[NS + s]), (T)ldcg(&E.s.cube[2 * NS + s])};
-        const T R = (T)ldcg(&E.s.cube[3 * NS + s]);
-        node_point(c, R, N, node, pos);
+        const T c[3] = {(T)pq[0], (T)pq[1], (T)pq[2]};
+        node_point(c, (T)pq[3], N, node, pos);
         w.hop++;
     } else {   // ST_HOP
-        pos[0] = (T)ldcg(&E.s.pos[s]);
-        pos[1] = (T)ldcg(&E.s.pos[NS + s]);
-        pos[2] = (T)ldcg(&E.s.pos[2 * NS + s]);
+        pos[0] = (T)pq[0];
+        pos[1] = (T)pq[1];
+        pos[2] = (T)pq[2];
     }
   T R;
   CubeInfo q;
@@ -1997,6 +2017,7 @@ constexpr int WALK_CTAS = FRW_WALK_CTAS;   // CTAs per SM the walk kernel is com
 constexpr int WALK_WARPS = WALK_THREADS / 32;
 constexpr int MW_WARPS = WALK_WARPS;
 constexpr int POOL_MAX = FRW_POOL_MAX;
+static_assert(POOL_MAX <= 2048, "slot list entries hold the slot index in 11 bits");
 constexpr int FILL_MAX = 128;
 constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // suspension only if this much geometry work is waiting
 
@@ -2215,8 +2236,10 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                 const bool need = act && st != ST_MW;
                 uint32_t wj = 0;
                 if (st != ST_FRESH && st != ST_IDLE && st != ST_MW) wj = E.s.job[s];
-                const bool free_slot =
-                    st == ST_FRESH || (need && st != ST_FRESH && ((volatile int *)E.job_cancel)[wj]);
+                const bool cancelled = need && st != ST_FRESH && ((volatile int *)E.job_cancel)[wj];
+                const bool free_slot = st == ST_FRESH || cancelled;
+                // list entry: slot | effective state << 11 (a cancelled job's walk is dropped)
+                const uint32_t entry = o | ((cancelled ? ST_FRESH : st) << 11);
                 // slots that start a walk (first transition) are listed from the front,
                 // the others from the back: warps then take work of one kind, the
                 // costliest first
@@ -2236,10 +2259,10 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                 const uint32_t below = (1u << lane) - 1u;
                 if (first) {
                     const uint32_t gi = g1 + __popc(b1 & below);
-                    if (FRW_CHECKED(E, gi < P)) sh.glist[gi] = (uint16_t)o;
+                    if (FRW_CHECKED(E, gi < P)) sh.glist[gi] = (uint16_t)entry;
                 } else if (need) {
                     const uint32_t gi = g2 + __popc(b2 & below);
-                    if (FRW_CHECKED(E, gi < P)) sh.glist[P - 1u - gi] = (uint16_t)o;
+                    if (FRW_CHECKED(E, gi < P)) sh.glist[P - 1u - gi] = (uint16_t)entry;
                 }
             }
             __syncthreads();
@@ -2254,8 +2277,9 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
             for (;;) {
                 const uint32_t i = atomicAdd(&sh.g_head, 1u);
                 if (i >= ng) break;
-                const uint32_t o = i < n1 ? sh.glist[i] : sh.glist[P - 1u - (i - n1)];
-                geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, staged, [&](uint32_t oo) {
+                const uint32_t ent = i < n1 ? sh.glist[i] : sh.glist[P - 1u - (i - n1)];
+                const uint32_t o = ent & 2047u;
+                geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, staged, ent >> 11, [&](uint32_t oo) {
                     cg::coalesced_group g = cg::coalesced_threads();
                     uint32_t b0 = 0;
                     if (g.thread_rank() == 0) b0 = atomicAdd(&sh.q_count, (uint32_t)g.size());
@@ -2316,6 +2340,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
             const MWTab T0 = wtab_lane(lanes_table ? sh.Wl : sh.W, lanes_table, lane);
             const uint32_t qn = sh.q_count;
             bool active = false, exhausted = false;
+            bool wexh = false;   // warp-uniform: some lane found the queue empty
             int x = -1, y = 0, z = 0;
             uint32_t t = 0, t_in = 0, my_o = 0;
             MWLane L;
@@ -2331,6 +2356,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     const uint32_t myj = b0 + (uint32_t)__popc(bal & ((1u << lane) - 1u));
                     const bool got = need && myj < qn;
                     if (need && !got) exhausted = true;
+                    wexh = __any_sync(FULL_MASK, exhausted);
                     const uint32_t oj = got ? (uint32_t)q_now[myj] : 0u;
                     uint32_t todo = __ballot_sync(FULL_MASK, got);
                     while (todo) {
@@ -2366,14 +2392,17 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                 }
                 const uint32_t ab = __ballot_sync(FULL_MASK, active);
                 if (ab == 0u) break;
-                // Suspend the few lanes left once the queue is empty, if every one of
-                // them has made progress this epoch and the CTA has other work
-                // waiting (so every job advances every epoch: no livelock).
-                const bool qexh = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.q_head >= qn), 0) != 0u;
-                const bool progressed = __all_sync(FULL_MASK, !active || t - t_in >= E.suspend_min_steps);
-                const bool other_work = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.finished >=
-                                                                           SUSPEND_MIN_FINISHED || sh.issuable), 0) != 0u;
-                if (qexh && progressed && other_work && __popc(ab) <= E.suspend_lanes) {
+                // Suspend the few lanes left once the queue is empty (as this warp has
+                // seen), if every one of them has made progress this epoch and the CTA
+                // has other work waiting (so every job advances every epoch: no livelock).
+                bool park = false;
+                if (wexh && __popc(ab) <= E.suspend_lanes) {
+                    const bool progressed = __all_sync(FULL_MASK, !active || t - t_in >= E.suspend_min_steps);
+                    const bool other_work = __shfl_sync(FULL_MASK, (uint32_t)(*(volatile uint32_t *)&sh.finished >=
+                                                                               SUSPEND_MIN_FINISHED || sh.issuable), 0) != 0u;
+                    park = progressed && other_work;
+                }
+                if (park) {
                     if (active && FRW_CHECKED(E, (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N &&
                                                      (unsigned)z < (unsigned)N)) {
                         // a walking lane is always on a node inside the lattice here
@@ -2387,17 +2416,22 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     }
                     break;
                 }
-                // four steps without a branch; a lane without a walk rests on a boundary node
-                const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2), L.key0, L.key1);
+                // eight steps (two Philox blocks) without a branch; a lane without a
+                // walk, or whose walk ended in the first block, rests on a boundary node
+                uint32_t moved = 0;
+#pragma unroll 1
+                for (uint32_t hb = 0; hb < 2u; hb++) {
+                    const uint4 blk = philox10(L.walk_lo, L.walk_hi, L.hop, 1u + (t >> 2) + hb, L.key0, L.key1);
 #if FRW_MW_WIDE_ONLY
-                const uint32_t moved = FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk);
+                    moved += FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk);
 #else
-                const bool wide = __any_sync(FULL_MASK, active && L.K > 6);
-                const uint32_t moved = wide ? FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk)
-                                            : FRW_MW_BLOCK<false>(R, T0.with_base(L.base_n), L.map, x, y, z, blk);
+                    const bool wide = __any_sync(FULL_MASK, active && L.K > 6);
+                    moved += wide ? FRW_MW_BLOCK<true>(R, T0.with_base(L.base_w), L.map, x, y, z, blk)
+                                  : FRW_MW_BLOCK<false>(R, T0.with_base(L.base_n), L.map, x, y, z, blk);
 #endif
+                }
                 const bool inside = ((unsigned)x < (unsigned)N) & ((unsigned)y < (unsigned)N) & ((unsigned)z < (unsigned)N);
-                if (active && (moved < 4u || !inside)) {
+                if (active && (moved < 8u || !inside)) {
                     // the walk has ended: on a boundary node (the exit node; reached at any of
                     // the four steps), or (MicroWalk-E) it rests on a conductor node inside the
                     // expanded cube (conductor flagged by bit 31)
@@ -2417,7 +2451,7 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
                     x = -1; y = 0; z = 0;
                     atomicAdd(&sh.finished, 1u);
                 }
-                t += 4;
+                t += 8;
                 if (active && t >= MW_STEP_CAP) {   // safety net: never loop without bound
                     atomicOr(&E.status[STAT_ERR], ERR_MW_STEPS);
                     const uint32_t sl2 = L.tag;
@@ -2685,7 +2719,7 @@ __global__ void __launch_bounds__(WALK_THREADS, WALK_CTAS) k_walk_ws(EngineView 
                 uint32_t st = ST_FRESH;
 #pragma unroll 1
                 for (int rep = 0; rep < 2; rep++) {   // a walk that ends takes the next id in the same slot
-                    st = geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, nullptr, push_mw);
+                    st = geo_slot<T, MWE>(E, base + o, o, fl, sh.ir, nullptr, ST_UNKNOWN, push_mw);
                     if (st != ST_FRESH) break;
                 }
                 if (st == ST_IDLE) {
