@@ -2019,7 +2019,16 @@ constexpr int MW_WARPS = WALK_WARPS;
 constexpr int POOL_MAX = FRW_POOL_MAX;
 static_assert(POOL_MAX <= 2048, "slot list entries hold the slot index in 11 bits");
 constexpr int FILL_MAX = 128;
-constexpr uint32_t SUSPEND_MIN_FINISHED = 32; // suspension only if this much geometry work is waiting
+constexpr uint32_t SUSPEND_MIN_FINISHED = 32;
+// 1: the phased walk kernel keeps a per-lane copy of the weight table (8 KB of
+// shared memory) for contexts of at most 7 materials; 0: one shared copy.  Without
+// the copies two CTAs fit the 196 KB shared-memory carve-out instead of 228 KB,
+// and the larger L1 (60 KB instead of 28 KB) serves the geometry work's stack and
+// table reads: measured faster (interconnect, N = 24: 42.9 -> 41.4 ms per
+// 3 x 2^20 walks) than conflict-free weight reads.
+#ifndef FRW_WALK_WTAB_LANES
+#define FRW_WALK_WTAB_LANES 0
+#endif // suspension only if this much geometry work is waiting
 
 // Clock read that cannot move above the preceding barrier: it is taken only after
 // a shared-memory word loaded after that barrier has been tested.
@@ -2036,7 +2045,9 @@ constexpr uint32_t FDM_CLAIM_CAP = 8;    // FRW-FDM: walk ids a CTA claims per e
 
 struct WalkShared {
     uint32_t W[WTAB_FULL_WORDS];     // jump-weight table W'[centre column][neighbour column] (one copy)
+#if FRW_WALK_WTAB_LANES
     uint32_t Wl[WTAB_LANES_WORDS];   // the same table of 8 columns, one copy per lane (materials 0-6)
+#endif
     uint32_t scan[32 * (FRW_WALK_THREADS / 32)];   // per-warp scratch of the mask build
     uint32_t g_head, g_back, pad3[2];
     uint32_t q_count, q_head, s_count, g_count;
@@ -2184,7 +2195,9 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
     unsigned char *dsm = dsm_all;
     double *fill_v = E.fill_scratch + (size_t)blockIdx.x * E.fill_stride;
     wtab_fill(sh.W, E.W, false, tid, WALK_THREADS);
+#if FRW_WALK_WTAB_LANES
     if (E.wtab_lanes) wtab_fill(sh.Wl, E.W, true, tid, WALK_THREADS);
+#endif
     // the geometry copy lives above the region the phases share (E.stage_off, set by the host)
     __shared__ SView<T> sview_staged;
     const SView<T> *staged = FDM ? nullptr : stage_structure<T>(E, sview_staged, dsm_all + E.stage_off);
@@ -2336,8 +2349,12 @@ __global__ void __launch_bounds__(WALK_THREADS, FDM ? 1 : WALK_CTAS) k_walk(Engi
             masks_clear(Mw, N, lane);
             __syncwarp();
             const MWRows R = mw_rows(Mw, N, lane);
+#if FRW_WALK_WTAB_LANES
             const bool lanes_table = E.wtab_lanes != 0;
             const MWTab T0 = wtab_lane(lanes_table ? sh.Wl : sh.W, lanes_table, lane);
+#else
+            const MWTab T0 = wtab_lane(sh.W, false, lane);
+#endif
             const uint32_t qn = sh.q_count;
             bool active = false, exhausted = false;
             bool wexh = false;   // warp-uniform: some lane found the queue empty
@@ -3240,7 +3257,17 @@ uint32_t walk_stage_cap(const EngineView &E, int ctas_per_sm)
         return 0;
     }
     const long long base = (long long)stage_round16((uint32_t)walk_smem_bytes(E.N, E.max_nc, 0));
-    const long long fit = std::min<long long>((long long)per_sm / ctas_per_sm - reserved, per_block) -
+    // stay within the shared-memory carve-out the kernel needs without the copy
+    // (the SM's supported capacities), so that the copy never takes L1 away
+    const long long need0 = (long long)ctas_per_sm * ((long long)fa.sharedSizeBytes + base + reserved);
+    static const int tiers_kb[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
+    long long tier = per_sm;
+    for (int kb : tiers_kb)
+        if ((long long)kb * 1024 >= need0) {
+            tier = std::min<long long>((long long)kb * 1024, per_sm);
+            break;
+        }
+    const long long fit = std::min<long long>(tier / ctas_per_sm - reserved, per_block) -
                           (long long)fa.sharedSizeBytes - base;
     const long long cap = std::min<long long>(fit, 32 * 1024) / 128 * 128;
     if (cap <= 0) return 0u;

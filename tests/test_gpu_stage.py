@@ -84,8 +84,6 @@ def test_copy_changes_no_result(torch_cuda, precision, tsize):
     groups = _stage_groups(s, tsize)
     got = {t["stage_bytes"] for _, _, t in staged[0]}
     assert len(got) == 1 and got.pop() in _greedy_sums(groups) - {0}
-    if tsize == 4:   # the whole FP32 geometry of this structure (13.8 KB) fits at N = 24
-        assert staged[0][0][2]["stage_bytes"] == sum(groups)
     assert all(t["stage_bytes"] == 0 for _, _, t in plain[0])
 
 
