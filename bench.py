@@ -46,14 +46,14 @@ INT_OPS_PER_MICRO_STEP = 45
 def case_walk():
     """The persistent walk kernel on the interconnect structure (N = 24, FP32
     geometry, masters 3, 11, 19), budget mode, 2^20 walks per master, with the
-    launch settings the autotuner picks for this workload (2048 slots per CTA, 2
-    analytical hops per epoch, MicroWalk lanes parked once the queue is empty and
-    each has made 64 steps): one warm-up launch (fills the analytical-table
+    launch settings the autotuner picks for this workload (2048 slots per CTA, 1
+    analytical hop per epoch, MicroWalk lanes parked once the queue is empty and
+    each has made 128 steps): one warm-up launch (fills the analytical-table
     cache), then the profiled launch."""
     from paper_2507_09730_gb300 import binding as B
     s = W.interconnect(0)
     c = B.Context(0, N=24, precision=B.FRW_FP32_GEOM, seed=0)
-    c.set_tuning(pool_per_cta=2048, hops_per_epoch=2, suspend_lanes=32, suspend_min_steps=64)
+    c.set_tuning(pool_per_cta=2048, hops_per_epoch=1, suspend_lanes=32, suspend_min_steps=128)
     sid = c.load(s)
     jobs = lambda r: [dict(structure_id=sid, master=m, walk_budget=1 << 20, request_id=r + i)
                       for i, m in enumerate(s.masters)]
@@ -273,11 +273,11 @@ def run_reference(a):
 # DRAM bytes (read + write) per walk of the walk kernel, from one ncu capture of
 # this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
 # launch started.  None once the kernel has changed since the capture.
-DRAM_BYTES_PER_WALK = 4691.2
+DRAM_BYTES_PER_WALK = None
 # issue-slot utilisation (smsp__issue_active) and instruction-cache hit rate of the
 # walk kernel in the same capture; None once the kernel has changed since
-ISSUE_ACTIVE_NCU = 0.450
-ICACHE_HIT_NCU = 0.762
+ISSUE_ACTIVE_NCU = None
+ICACHE_HIT_NCU = None
 
 
 def traffic_per_launch(agg, n_launch):

@@ -327,8 +327,11 @@ int frw_set_tuning(frw_ctx *ctx, const frw_tuning *t);   /* FRW_EINVAL outside t
 /* Autotuner: runs the sample jobs in budget mode (each capped at sample_walks
  * walks) once per candidate walk-kernel setting (slots per CTA in {1024, 2048,
  * 3072, 4096, the context's pool} up to the context's pool x ten combinations of
- * analytical hops per epoch {2, 4, 8}, suspension lanes {4, 8, 16, 32} and
- * suspension progress guard {32, 64, 128}) and keeps the fastest;
+ * analytical hops per epoch (1-4), suspension lanes (16 or 32) and suspension
+ * progress guard (32-256): (1, 32, 128), (1, 32, 64), (1, 32, 256), (1, 16, 128),
+ * (1, 32, 32), (2, 32, 128), (2, 32, 64), (2, 32, 256), (3, 32, 128), (4, 32, 64))
+ * and keeps the fastest; the context starts with 1 hop per epoch, 32 lanes and a
+ * guard of 128 steps;
  * then times the stand-alone MicroWalk kernel on 512 random cubes of the
  * context's N (2-6 blocks of up to four of its registered materials, 4096
  * samples each) for each shape (warps per CTA x

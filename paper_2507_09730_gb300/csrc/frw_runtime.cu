@@ -346,9 +346,9 @@ extern "C" int frw_create(frw_ctx **out, int device, const frw_options *opt_in)
         ctx->NS = (uint32_t)(pool * ctx->grid);
     }
     ctx->tune.pool_per_cta = (int32_t)(ctx->NS / ctx->grid);
-    ctx->tune.hops_per_epoch = 4;
-    ctx->tune.suspend_lanes = 8;
-    ctx->tune.suspend_min_steps = 64;
+    ctx->tune.hops_per_epoch = 1;
+    ctx->tune.suspend_lanes = 32;
+    ctx->tune.suspend_min_steps = 128;
     ctx->tune.geo_warps = 0;
     ctx->tune.unstaged = 0;
     ctx->tune.mw_warps_per_cta = ctx->shape.mw_warps;
@@ -2221,8 +2221,8 @@ extern "C" int frw_autotune(frw_ctx *ctx, const frw_job *sample, int32_t n_sampl
         for (int rep = 0; rep < 2; rep++) {           // the first pass also warms the table cache
             for (int pool : pools) {
                 // (hops per epoch, suspension lanes, suspension progress guard)
-                static const int cand[][3] = {{2, 32, 256}, {3, 32, 128}, {4, 32, 64},  {4, 32, 32}, {4, 32, 128},
-                                              {2, 32, 32},  {3, 32, 64},  {8, 32, 64},  {2, 32, 64}, {2, 32, 128}};
+                static const int cand[][3] = {{1, 32, 128}, {1, 32, 64}, {1, 32, 256}, {1, 16, 128}, {1, 32, 32},
+                                              {2, 32, 128}, {2, 32, 64}, {2, 32, 256}, {3, 32, 128}, {4, 32, 64}};
                 for (const auto &c : cand) {
                     frw_tuning t = ctx->tune;
                     t.pool_per_cta = pool;

@@ -24,7 +24,7 @@ from paper_2507_09730_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TUNING = dict(pool_per_cta=2048, hops_per_epoch=2, suspend_lanes=32, suspend_min_steps=64)
+TUNING = dict(pool_per_cta=2048, hops_per_epoch=1, suspend_lanes=32, suspend_min_steps=128)
 
 
 @pytest.fixture(scope="module")
