@@ -168,7 +168,7 @@ def serving_point(N, precision, rate, duration, seed=0, baseline=True):
     return out
 
 
-def serving(N=24, rates=(25, 50, 75, 100, 125, 150), window=15.0):
+def serving(N=24, rates=(25, 50, 75, 100, 125, 150, 175), window=15.0):
     """The serving configuration as stated, then the rate sweep (module doc)."""
     out = [dict(case="configuration 4 as stated", **serving_point(N, B.FRW_FP32_GEOM, 200.0, 60.0))]
     for r in rates:
