@@ -341,5 +341,17 @@ cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uin
                             unsigned long long *d_head, uint32_t *d_err, const LaunchShape &L,
                             cudaStream_t st);
 cudaError_t set_kernel_attributes(int N, int mw_warps, int max_nc);
+// uniform-grid candidate lists of one structure (frw_kernels.cu, k_grid_lists):
+// pass 0 writes the counts and turns them into offsets off[0 .. cells] (off has
+// cells + 1 entries; off[cells] = the list total), pass 1 writes ids[off[c] ..)
+struct GridBuild {
+    int gdim[3];
+    int n_box;
+    double dlo[3], dhi[3];   // domain
+    double w[3];             // cell edge per axis (extent / gdim)
+    double tol;              // list tolerance (covers FP32 rounding of device distances)
+    const double *clo, *chi; // device boxes, SoA [a * n_box + k]
+};
+cudaError_t launch_grid_lists(const GridBuild &G, uint32_t *off, uint16_t *ids, int pass, cudaStream_t st);
 
 }  // namespace frw

@@ -3133,6 +3133,98 @@ cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uin
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Candidate lists of the uniform grid of the max-cube query (Sec. II-A), built
+// on the device when a structure is loaded.  Cell c lists, in ascending order,
+// every conductor box whose L-infinity distance to the cell (grown by 2 % of a
+// cell on each side) is at most U + tol, U the smallest upper bound of the
+// nearest-electrode distance over the grown cell (walls and boxes), so that the
+// box nearest to any point of the cell, and every box tied with it, is listed.
+// Pass 0 writes each cell's count into off[cell]; an exclusive scan turns the
+// counts into offsets; pass 1 writes the lists.  The arithmetic is written out
+// operation by operation (no contraction) in double precision.
+__device__ __forceinline__ double dmin_rn(double a, double b) { return b < a ? b : a; }
+__device__ __forceinline__ double dmax_rn(double a, double b) { return a < b ? b : a; }
+
+__global__ void k_grid_lists(GridBuild G, uint32_t *off, uint16_t *ids, int pass)
+{
+    const uint32_t plane = (uint32_t)G.gdim[1] * (uint32_t)G.gdim[2];
+    const uint32_t cells = (uint32_t)G.gdim[0] * plane;
+    const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= cells) return;
+    const int ii[3] = {(int)(cell / plane), (int)((cell / (uint32_t)G.gdim[2]) % (uint32_t)G.gdim[1]),
+                       (int)(cell % (uint32_t)G.gdim[2])};
+    double lo[3], hi[3];
+    double U = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double w = G.w[a], m = __dmul_rn(0.02, w);
+        lo[a] = __dsub_rn(__dadd_rn(G.dlo[a], __dmul_rn((double)ii[a], w)), m);
+        hi[a] = __dadd_rn(__dadd_rn(G.dlo[a], __dmul_rn((double)(ii[a] + 1), w)), m);
+        U = dmin_rn(U, dmin_rn(__dsub_rn(hi[a], G.dlo[a]), __dsub_rn(G.dhi[a], lo[a])));
+    }
+    const int n = G.n_box;
+    for (int k = 0; k < n; k++) {
+        double dmax = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            dmax = dmax_rn(dmax, dmax_rn(__dsub_rn(G.clo[a * n + k], lo[a]), __dsub_rn(hi[a], G.chi[a * n + k])));
+        U = dmin_rn(U, dmax);
+    }
+    const double lim = __dadd_rn(U, G.tol);
+    const uint32_t base = pass ? off[cell] : 0u;
+    uint32_t c = 0;
+    for (int k = 0; k < n; k++) {
+        double dm = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            dm = dmax_rn(dm, dmax_rn(__dsub_rn(G.clo[a * n + k], hi[a]), __dsub_rn(lo[a], G.chi[a * n + k])));
+        if (dm <= lim) {
+            if (pass) ids[base + c] = (uint16_t)k;
+            c++;
+        }
+    }
+    if (!pass) off[cell] = c;
+}
+
+// One CTA: a[0 .. n) (counts) -> exclusive prefix sums, a[n] = the total.
+__global__ void k_scan_exclusive(uint32_t *a, uint32_t n)
+{
+    __shared__ uint32_t part[1024];
+    const uint32_t t = threadIdx.x, nt = blockDim.x;
+    const uint32_t chunk = (n + nt - 1) / nt;
+    const uint32_t b = min(t * chunk, n), e = min(b + chunk, n);
+    uint32_t s = 0;
+    for (uint32_t i = b; i < e; i++) s += a[i];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        uint32_t acc = 0;
+        for (uint32_t i = 0; i < nt; i++) {
+            const uint32_t v = part[i];
+            part[i] = acc;
+            acc += v;
+        }
+        a[n] = acc;
+    }
+    __syncthreads();
+    uint32_t acc = part[t];
+    for (uint32_t i = b; i < e; i++) {
+        const uint32_t v = a[i];
+        a[i] = acc;
+        acc += v;
+    }
+}
+
+cudaError_t launch_grid_lists(const GridBuild &G, uint32_t *off, uint16_t *ids, int pass, cudaStream_t st)
+{
+    const uint64_t cells = (uint64_t)G.gdim[0] * G.gdim[1] * G.gdim[2];
+    if (cells == 0 || cells >= (1ull << 31)) return cudaErrorInvalidValue;
+    k_grid_lists<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(G, off, ids, pass);
+    if (pass == 0) k_scan_exclusive<<<1, 1024, 0, st>>>(off, (uint32_t)cells);
+    return cudaGetLastError();
+}
+
 }  // namespace frw
 
 // ---------------------------------------------------------------------------

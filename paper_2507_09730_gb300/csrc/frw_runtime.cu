@@ -478,7 +478,11 @@ struct IndexHost {
     std::vector<uint32_t> L, H;
 };
 
-static void build_index(const frw_box &dom, const frw_box *cond, int nc, const frw_block *blk, int nb, IndexHost &X)
+// Index of one structure: the uniform grid's dimensions (and, with host_lists,
+// its candidate lists, built on the host's cores; otherwise the device builds the
+// lists, k_grid_lists) and the slab masks of the dielectric blocks.
+static void build_index(const frw_box &dom, const frw_box *cond, int nc, const frw_block *blk, int nb, IndexHost &X,
+                        bool host_lists)
 {
     double ext[3], vol = 1.0, edge = 0.0;
     for (int a = 0; a < 3; a++) {
@@ -494,8 +498,10 @@ static void build_index(const frw_box &dom, const frw_box *cond, int nc, const f
         X.g_inv[a] = X.gdim[a] / ext[a];
     }
     const size_t cells = (size_t)X.gdim[0] * X.gdim[1] * X.gdim[2];
-    X.g_off.assign(cells + 1, 0);
+    X.g_off.clear();
     X.g_ids.clear();
+    if (host_lists) {
+    X.g_off.assign(cells + 1, 0);
     // candidate lists of the x-slabs [i0, i1) of cells (independent), in cell order
     auto slab = [&](int i0, int i1, std::vector<uint32_t> &count, std::vector<uint16_t> &ids) {
         std::vector<double> dmin(nc);
@@ -558,6 +564,7 @@ static void build_index(const frw_box &dom, const frw_box *cond, int nc, const f
             p += n;
             X.g_off[++cell] = (uint32_t)X.g_ids.size();
         }
+    }
     }
     // slabs
     X.S = 256;
@@ -714,7 +721,10 @@ static int load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *in
         return FRW_OK;
     };
     IndexHost X;
-    build_index(*domain, conductors, n_box, blocks, n_blocks, X);
+    // FRW_INDEX_HOST=1: the grid's candidate lists built on the host (the same lists)
+    const char *ih = std::getenv("FRW_INDEX_HOST");
+    const bool host_lists = ih && ih[0] == '1';
+    build_index(*domain, conductors, n_box, blocks, n_blocks, X, host_lists);
     for (int a = 0; a < 3; a++) {
         D.gdim[a] = X.gdim[a];
         D.g_org[a] = X.g_org[a];
@@ -728,7 +738,7 @@ static int load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *in
     }
     D.sl_S = X.S;
     D.sl_words = X.words;
-    if ((rc = up((uint32_t **)&D.g_off, X.g_off)) || (rc = up((uint16_t **)&D.g_ids, X.g_ids)) ||
+    if ((host_lists && ((rc = up((uint32_t **)&D.g_off, X.g_off)) || (rc = up((uint16_t **)&D.g_ids, X.g_ids)))) ||
         (rc = up((uint32_t **)&D.sl_L, X.L)) || (rc = up((uint32_t **)&D.sl_H, X.H)) ||
         (rc = up((double **)&D.c_lo, clo)) || (rc = up((double **)&D.c_hi, chi)) ||
         (rc = up((float **)&D.c_lo_f, clof)) || (rc = up((float **)&D.c_hi_f, chif)) ||
@@ -738,6 +748,40 @@ static int load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *in
         for (void *p : H.dev) cudaFree(p);
         H.dev.clear();
         return rc;
+    }
+    if (!host_lists) {
+        // the grid's candidate lists on the device: counts, offsets, then the lists
+        GridBuild G;
+        for (int a = 0; a < 3; a++) {
+            G.gdim[a] = X.gdim[a];
+            G.dlo[a] = domain->lo[a];
+            G.dhi[a] = domain->hi[a];
+            G.w[a] = (domain->hi[a] - domain->lo[a]) / X.gdim[a];
+        }
+        G.n_box = n_box;
+        G.tol = 1e-6 * edge;
+        G.clo = D.c_lo;
+        G.chi = D.c_hi;
+        const size_t cells = (size_t)X.gdim[0] * X.gdim[1] * X.gdim[2];
+        uint32_t *off = nullptr, total = 0;
+        uint16_t *ids = nullptr;
+        cudaError_t e = cudaSuccess;
+        if ((rc = dalloc(ctx, &off, cells + 1, H.dev)) == FRW_OK) {
+            e = launch_grid_lists(G, off, nullptr, 0, ctx->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&total, off + cells, sizeof(total), cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e == cudaSuccess && (rc = dalloc(ctx, &ids, total, H.dev)) == FRW_OK)
+                e = launch_grid_lists(G, off, ids, 1, ctx->stream);
+        }
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "grid index build");
+        if (rc) {
+            for (void *p : H.dev) cudaFree(p);
+            H.dev.clear();
+            return rc;
+        }
+        D.g_off = off;
+        D.g_ids = ids;
     }
     const SView<float> vf = sview<float>(D);
     const SView<double> vd = sview<double>(D);
