@@ -1391,6 +1391,7 @@ struct CubeSource {
 };
 
 constexpr uint32_t MW_STEP_CAP = 1u << 26;
+constexpr uint32_t MW_CHUNK = 512;   // job ids a warp of the stand-alone MicroWalk kernel claims at a time
 
 // Stand-alone MicroWalk over a job source.  Per lane: one walk at a time, in
 // blocks of 8 steps (two Philox blocks); a lane whose walk ended rests on a
@@ -1417,6 +1418,9 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
     uint32_t t = 0;
     uint64_t held = ~0ull;   // cube whose masks (and column map) this lane holds
     bool held_ok = false;    // ... and whether its record is well formed
+    // the warp's chunk of consecutive job ids [c_next, c_end) (warp-uniform): the
+    // lanes' successive jobs stay on one cube, so a lane rarely rebuilds its masks
+    uint64_t c_next = 0, c_end = 0;
     MWLane L;
     mw_lane_reset(L, T0);
     for (;;) {
@@ -1424,10 +1428,20 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
         const uint32_t bal = __ballot_sync(FULL_MASK, need);
         if (bal) {
             const int leader = __ffs(bal) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = src.grab((uint32_t)__popc(bal));
-            base = __shfl_sync(FULL_MASK, base, leader);
-            const uint64_t myj = base + (uint64_t)__popc(bal & ((1u << lane) - 1u));
+            const uint32_t n = (uint32_t)__popc(bal), rk = (uint32_t)__popc(bal & ((1u << lane) - 1u));
+            uint64_t myj;
+            if (c_end - c_next >= n) {
+                myj = c_next + rk;
+                c_next += n;
+            } else {
+                const uint64_t avail = c_end - c_next;
+                unsigned long long nb = 0;
+                if (lane == leader) nb = src.grab(MW_CHUNK);
+                nb = __shfl_sync(FULL_MASK, nb, leader);
+                myj = rk < avail ? c_next + rk : nb + (rk - avail);
+                c_next = nb + (n - avail);
+                c_end = nb + MW_CHUNK;
+            }
             const bool got = need && src.valid(myj);
             if (need && !got) exhausted = true;
             const uint64_t cube = got ? src.cube_of(myj) : held;
