@@ -1313,6 +1313,7 @@ struct CubeSource {
     int N;
     int n_mat;               // material ids of the records index 0 .. n_mat - 1
     int lanes_table;         // 1: per-lane weight-table copies (global materials 0-6)
+    uint32_t chunk;          // job ids a warp claims at a time (32 .. MW_CHUNK)
     __device__ uint64_t grab(uint32_t n) const { return atomicAdd(head, (unsigned long long)n); }
     __device__ void overrun() const { atomicOr(err, ERR_MW_STEPS); }
     __device__ bool valid(uint64_t j) const { return j < total; }
@@ -1391,7 +1392,10 @@ struct CubeSource {
 };
 
 constexpr uint32_t MW_STEP_CAP = 1u << 26;
-constexpr uint32_t MW_CHUNK = 512;   // job ids a warp of the stand-alone MicroWalk kernel claims at a time
+// job ids a warp of the stand-alone MicroWalk kernel claims at a time: at most
+// this many, fewer (down to 32) when the launch has too few jobs to give every
+// warp several chunks
+constexpr uint32_t MW_CHUNK = 512;
 
 // Stand-alone MicroWalk over a job source.  Per lane: one walk at a time, in
 // blocks of 8 steps (two Philox blocks); a lane whose walk ended rests on a
@@ -1436,11 +1440,11 @@ __global__ void __launch_bounds__(512) k_mw(Src src, const uint32_t *__restrict_
             } else {
                 const uint64_t avail = c_end - c_next;
                 unsigned long long nb = 0;
-                if (lane == leader) nb = src.grab(MW_CHUNK);
+                if (lane == leader) nb = src.grab(src.chunk);   // chunk >= 32 >= n: the ids fit
                 nb = __shfl_sync(FULL_MASK, nb, leader);
                 myj = rk < avail ? c_next + rk : nb + (rk - avail);
                 c_next = nb + (n - avail);
-                c_end = nb + MW_CHUNK;
+                c_end = nb + src.chunk;
             }
             const bool got = need && src.valid(myj);
             if (need && !got) exhausted = true;
@@ -3142,6 +3146,8 @@ cudaError_t launch_mw_cubes(int N, const int32_t *d_cubes, uint64_t n_cubes, uin
     src.N = N;
     src.n_mat = n_mat;
     src.lanes_table = n_global_mat <= 7 ? 1 : 0;   // columns 0-7 only: the per-lane table copies
+    const uint64_t warps = (uint64_t)L.sms * L.mw_ctas_per_sm * L.mw_warps;
+    src.chunk = (uint32_t)std::min<uint64_t>(MW_CHUNK, std::max<uint64_t>(32, src.total / (4 * std::max<uint64_t>(warps, 1))));
     const int threads = 32 * L.mw_warps;
     k_mw<CubeSource><<<L.sms * L.mw_ctas_per_sm, threads, mw_smem_bytes(N, L.mw_warps), st>>>(src, W, N);
     return cudaGetLastError();
