@@ -78,6 +78,38 @@ def test_microwalk_paths_bit_exact(torch_cuda, N):
         np.testing.assert_array_equal(st[ci * spc:(ci + 1) * spc].astype(np.uint64), steps_o)
 
 
+def test_microwalk_chunks_across_cubes_bit_exact(torch_cuda):
+    """Warps of the MicroWalk kernel claim chunks of consecutive sample ids (up to
+    512): at 997 cubes x 10007 samples (both prime) the chunks straddle cube
+    boundaries, lanes change cubes mid-chunk and the last chunk runs past the end.
+    Every sample must still be the oracle's walk for its id: checked on the ids
+    around every 97th cube boundary, around chunk boundaries, the last ids and
+    random ones; every sample must also have been written (steps > 0)."""
+    N, n_cubes, spc = 8, 997, 10007
+    c = ctx_for(N)
+    cubes = W.random_cubes(n_cubes, N=N, seed=5)
+    ex, st = _run_cubes(torch_cuda, c, cubes, spc, request=6)
+    assert (st > 0).all()
+    nodes_g = B.decode_exit(ex)
+    total = n_cubes * spc
+    rng = np.random.default_rng(1)
+    ids = set(rng.integers(0, total, 300).tolist())
+    for ci in range(0, n_cubes, 97):
+        ids.update(j for j in (ci * spc - 1, ci * spc, ci * spc + 1) if 0 <= j < total)
+    for k in range(1, total // 512, 977):
+        ids.update((k * 512 - 1, k * 512))
+    ids.update(range(total - 40, total))
+    lats = {}
+    for j in sorted(ids):
+        ci = j // spc
+        if ci not in lats:
+            lats[ci] = O.lattice_from_ranges(N, cubes.bg[ci], cubes.ranges[ci, :cubes.nblk[ci]],
+                                             cubes.mat[ci, :cubes.nblk[ci]])
+        nodes_o, steps_o = O.microwalk_many(N, lats[ci], cubes.eps, 0, 6, j, 1)
+        np.testing.assert_array_equal(nodes_g[j:j + 1], nodes_o)
+        assert int(st[j]) == int(steps_o[0]), j
+
+
 def test_microwalk_theorem1_on_gpu(torch_cuda):
     """Theorem 1: the GPU exit histogram follows e_c^T A_II^{-1} A_IB (exact chain solve)."""
     from scipy import stats
