@@ -2009,13 +2009,16 @@ __device__ FRW_OUTLINE uint32_t take_batch(const EngineView &E)
 #endif
 constexpr int WALK_THREADS = FRW_WALK_THREADS;
 // MicroWalk block of the walk kernel: FRW_MW_WIDE_ONLY 1 keeps only the wide
-// column decode (one code path); FRW_MW_COMPACT 1 runs the four steps as a loop.
-// Both on by default: the walk kernel's phases share the SM's instruction cache,
-// and the smallest MicroWalk loop measured fastest on the interconnect workload
-// (budget mode, 3 x 2^20 walks, N = 24: 44.7 ms against 49.7 ms with both decode
-// forms unrolled, 45.6 ms with both compact, 50.0 ms wide and unrolled)
+// column decode (one code path), 0 lets a warp whose lanes all hold cubes of at
+// most 6 blocks use the narrow decode (two compact loops); FRW_MW_COMPACT 1 runs
+// the four steps as a loop.  Measured on the interconnect workload (budget mode,
+// 3 x 2^20 walks, N = 24): with two analytical hops per geometry visit the single
+// wide loop was fastest (44.7 ms against 45.6 ms with both forms compact, 49.7 ms
+// both unrolled, 50.0 ms wide and unrolled); with one hop per visit, which
+// relieved the instruction cache, both compact forms are (33.7-33.9 against
+// 35.5-35.7 ms)
 #ifndef FRW_MW_WIDE_ONLY
-#define FRW_MW_WIDE_ONLY 1
+#define FRW_MW_WIDE_ONLY 0
 #endif
 #ifndef FRW_MW_COMPACT
 #define FRW_MW_COMPACT 1
