@@ -273,11 +273,11 @@ def run_reference(a):
 # DRAM bytes (read + write) per walk of the walk kernel, from one ncu capture of
 # this workload (k_walk, 3 x 2^20 walks in budget mode); scaled by the walks a
 # launch started.  None once the kernel has changed since the capture.
-DRAM_BYTES_PER_WALK = 4903.9
+DRAM_BYTES_PER_WALK = 4878.3
 # issue-slot utilisation (smsp__issue_active) and instruction-cache hit rate of the
 # walk kernel in the same capture; None once the kernel has changed since
-ISSUE_ACTIVE_NCU = 0.476
-ICACHE_HIT_NCU = 0.824
+ISSUE_ACTIVE_NCU = 0.494
+ICACHE_HIT_NCU = 0.830
 
 
 def traffic_per_launch(agg, n_launch):

@@ -29,6 +29,16 @@ namespace cg = cooperative_groups;
 // inlined in several places, stay out of line: the persistent walk kernel's hot
 // loops then fit the instruction cache.
 #define FRW_OUTLINE __noinline__
+// the max-cube query and the cube classification as calls (one copy each) or
+// inlined at their call sites: the query inlined measured 2 % faster on the
+// interconnect workload (budget mode, 3 x 2^20 walks: 33.2 against 34.0 ms), the
+// classification inlined 3 % slower
+#ifndef FRW_NEAREST_CALL
+#define FRW_NEAREST_CALL __forceinline__
+#endif
+#ifndef FRW_CLASSIFY_CALL
+#define FRW_CLASSIFY_CALL FRW_OUTLINE
+#endif
 
 // Bounds checks of the debug build (-DFRW_CHECKS): a failed check sets ERR_CHECK
 // (the run then ends with an error status) and the guarded access is skipped.
@@ -133,7 +143,7 @@ template <class V> __device__ __forceinline__ V gload(const V *p)
 // order, every box that can be nearest (or tie) anywhere in the cell, so the
 // result equals the scan over all boxes.
 template <typename T>
-__device__ FRW_OUTLINE T nearest_electrode(const SView<T> &S, const T p[3], int &who)
+__device__ FRW_NEAREST_CALL T nearest_electrode(const SView<T> &S, const T p[3], int &who)
 {
     typedef Ar<T> A;
     T best = A::inf();
@@ -202,7 +212,7 @@ __device__ __forceinline__ int rng_mat(const uint2 r) { return (int)((r.y >> 16)
 // centre inside), list reset by a block covering every voxel, and the class:
 // homogeneous, layered along one axis, non-stratified, or too many blocks.
 template <typename T>
-__device__ FRW_OUTLINE void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeInfo &q)
+__device__ FRW_CLASSIFY_CALL void classify_cube(const SView<T> &S, const T c[3], T R, int N, CubeInfo &q)
 {
     typedef Ar<T> A;
     const T h = A::div(A::mul(T(2), R), T(N));
