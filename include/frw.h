@@ -164,9 +164,13 @@ int frw_set_stream(frw_ctx *ctx, void *cuda_stream);
 /* Load a structure (Algorithm 1 input): grounded domain box, n_cond disjoint
  * conductor boxes inside it, permittivity table eps_r[n_mat] (> 0), background
  * material, dielectric blocks.  All inputs are host pointers, copied; the caller
- * keeps ownership.  Returns FRW_EINVAL for overlapping/outside conductors, bad
- * material ids or non-positive permittivities, FRW_ECAPACITY if the context would
- * exceed FRW_MAX_MATERIALS distinct permittivities. */
+ * keeps ownership.  The index of the max-cube query (Sec. II-A: a uniform grid
+ * whose cells list the conductor boxes that can be nearest) is built on the
+ * device; with the environment variable FRW_INDEX_HOST=1 the host's cores build
+ * the same lists.  The call returns when the structure is ready.  Returns
+ * FRW_EINVAL for overlapping/outside conductors, bad material ids or
+ * non-positive permittivities, FRW_ECAPACITY if the context would exceed
+ * FRW_MAX_MATERIALS distinct permittivities. */
 int frw_load_structure(frw_ctx *ctx, const frw_box *domain, const frw_box *conductors,
                        int32_t n_cond, const double *eps_r, int32_t n_mat, int32_t background_mat,
                        const frw_block *blocks, int32_t n_blocks, int32_t *structure_id);
